@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark: Newton load steps of Galerkin FFT homogenization under stress
+control on a 128^3 polycrystal (arXiv:1901.06531, Sec. 2.2-2.3 and 4).
+
+Workload (synthetic, seeded): 128^3 voxels, 200-grain periodic Voronoi
+tessellation, St Venant-Kirchhoff cubic stiffness C11=168, C12=121, C44=75 GPa
+rotated by uniform random orientations per grain; cyclic stress control
+P11 = 0 -> +0.2 -> -0.2 -> 0 GPa in 20 steps, other P-bar components 0, with
+F12 = F13 = F23 = 0 prescribed to fix the rigid rotation (the paper's load
+case (1) pattern).  Solver: FP32 inner CG / FP64 outer Newton, Newton tol
+1e-8, CG tol 1e-10 (FP64 floor) with a 1e-4 relative forcing term.
+
+A step is one load increment: predictor, Newton iterations (constitutive
+update, FP64 residual, CG on the projected operator, update) to convergence.
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N1 = 128
+NGRAINS = 200
+SEED = 1003
+TOL_NEWTON, TOL_CG, CG_REL = 1e-8, 1e-10, 1e-4
+WORKLOAD = ("polycrystal 128^3, 200-grain Voronoi, SVK cubic (168/121/75 GPa) rotated per grain, "
+            "cyclic stress P11 +-0.2 GPa in 20 steps (F12=F13=F23=0), FP32 inner / FP64 outer")
+METRIC = "Newton load steps/s at 128^3 (FP32-inner/FP64-outer), polycrystal cyclic stress control"
+# algorithmic bytes per voxel of each inner-operator kernel (FP32): x-y forward
+# reads x (9 x 4 B) and the packed tangent (45 x 4 B) and writes the half
+# spectrum (9 x 0.5 x 8 B); the z-pass reads and writes the spectrum; the x-y
+# inverse reads the spectrum and the dot operand p and writes y.
+KERNELS = ["xy_forward_tangent", "zpass_projection", "xy_inverse_dot"]
+ALGO_BYTES_F32 = [36 + 180 + 36, 36 + 36, 36 + 36 + 36]
+ALGO_BYTES_F64 = [72 + 360 + 72, 72 + 72, 72 + 72 + 72]
+
+
+def workload(n=N1, ngrains=NGRAINS, seed=SEED):
+    from paper_1901_06531_gb300 import inputs
+    g, _ = inputs.voronoi((n, n, n), ngrains, seed)
+    R = inputs.random_rotations(ngrains, seed + 1)
+    params = np.tile([168.0, 121.0, 75.0], (ngrains, 1))
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(20, 0.2))
+    return g, params, R, mask, target
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("transform.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1901_06531_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != src_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+import bench
+from oracle import materials as omat, solver as osolver
+g, params, R, mask, target = bench.workload()
+n = g.shape[0]
+m0, t0 = mask[0], target[0]
+pbar = np.where(m0 == 1, t0, 0.0)
+# iteration counts of the first load step, from the oracle on the same recipe at 16^3
+gs, ps, Rs, _, _ = bench.workload(16, 12, {seed})
+os_ = osolver.solve(omat.Material(gs, omat.SVK_CUBIC, ps, Rs), mask[:1], target[:1], {tn}, {tc})
+n_newton, n_cg = int(os_["newton"][0]), int(os_["cg"][0])
+# constitutive update on a 16-plane slab at the predictor state, scaled to the cell
+slab = 16
+F = np.zeros((9, slab) + g.shape[1:]); F[0] = F[4] = F[8] = 1.0
+F[0] += 2e-4
+t = time.perf_counter()
+P_s, K_s = omat.Material(g[:slab], omat.SVK_CUBIC, params, R).PK(F)
+t_pk = (time.perf_counter() - t) * (n / slab)
+P = np.tile(P_s, (1, n // slab, 1, 1))
+K = np.tile(K_s, (1, 1, n // slab, 1, 1))
+t = time.perf_counter(); b = osolver.residual(P, m0, pbar); t_res = time.perf_counter() - t
+t_mv = []
+for _ in range({nmv}):
+    t = time.perf_counter(); y = osolver.matvec(K, b, m0); t_mv.append(time.perf_counter() - t)
+est = [(n_newton + 1) * t_pk + n_newton * t_res + n_cg * tm for tm in t_mv]
+print(json.dumps(dict(t_pk=t_pk, t_res=t_res, t_mv=t_mv, n_newton=n_newton, n_cg=n_cg, est=est)))
+"""
+
+
+def oracle_sample(cores, nmv=1):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = ORACLE_SAMPLE.format(root=ROOT, seed=SEED, tn=TOL_NEWTON, tc=TOL_CG, nmv=nmv)
+    t = time.perf_counter()
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1800)
+    wall = time.perf_counter() - t
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    d["wall"] = wall
+    return d
+
+
+def cpu_baseline_entry(d, cores):
+    return {"value": 1.0 / float(np.mean(d["est"])), "unit": "load steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": (f"128^3 oracle (FP64, DFT by definition): constitutive on a 16-plane slab "
+                       f"x8 ({d['t_pk']:.1f} s), one residual ({d['t_res']:.1f} s), projected "
+                       f"operator ({np.mean(d['t_mv']):.1f} s each, {len(d['t_mv'])} runs); "
+                       f"load step = (n_newton+1) constitutive + "
+                       f"n_newton residuals + n_cg operators with n_newton={d['n_newton']}, "
+                       f"n_cg={d['n_cg']} from the oracle's first step of the same recipe at 16^3; "
+                       f"{d['wall']:.0f} s of CPU work")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    d = oracle_sample(cores, nmv=args.warmup + args.steps)
+    d["est"] = d["est"][args.warmup:]
+    d["t_mv"] = d["t_mv"][args.warmup:]
+    est = float(np.mean(d["est"]))
+    value = 1.0 / est
+    line = {"metric": METRIC, "value": value, "unit": "load steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD + " [CPU oracle, bounded sample per step]"},
+            "cpu_baseline": cpu_baseline_entry(d, cores),
+            "e2e": {"value": value, "unit": "load steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    line["cpu_baseline"]["value"] = value
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU path
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1901_06531_gb300 import build
+    build.build()
+    from paper_1901_06531_gb300 import mixfft as mf
+
+    g, params, R, mask, target = workload()
+    n = N1
+    N = n ** 3
+    nsteps_hist = mask.shape[0]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+
+    def steps(c, k0, k1):
+        idx = [k % nsteps_hist for k in range(k0, k1)]
+        return c.solve(mask[idx], target[idx], TOL_NEWTON, TOL_CG, CG_REL)
+
+    # warm-up steps, then restart the history from F = I
+    steps(ctx, 0, args.warmup)
+    ctx.set_F(None)
+    l0 = mf.kernel_launches()
+    per_step = []
+    its = []
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for k in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            o = steps(ctx, k, k + 1)
+            b.record(stream)
+            per_step.append((a, b))
+            its.append((int(o["newton"][0]), int(o["cg"][0])))
+        ev1.record(stream)
+        barrier()
+    launches = mf.kernel_launches() - l0
+    total_ms = ev0.elapsed_time(ev1)
+    step_ms = [a.elapsed_time(b) for a, b in per_step]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers: step inputs go in as
+    # arguments, <F>, <P> and the full F field come back to pinned host memory
+    ctx.set_F(None)
+    Fhost = torch.empty(9 * N, dtype=torch.float64, pin_memory=True).numpy()
+    import ctypes
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        steps(ctx, k, k + 1)
+        mf._check("mf_get_fields", mf._lib.mf_get_fields(ctx.h, Fhost.ctypes.data_as(ctypes.c_void_p),
+                                                         None))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * args.steps / e2e_s, "unit": "load steps/s",
+           "h2d_bytes_per_step": 9 + 9 * 8, "d2h_bytes_per_step": 2 * 9 * 8 + 9 * N * 8}
+
+    # inner-operator kernels: per-kernel time after an L2 flush, and the whole
+    # projected operator in FP32 and FP64 (Gvoxel/s)
+    ctx.set_F(None)
+    steps(ctx, 0, 1)
+    ctx.constitutive()
+    m0 = mask[0]
+    kms = ctx.time_kernels(m0, reps=20)
+    x = torch.randn(9 * N, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+
+    def time_matvec(c, xx, yy, reps):
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.matvec(xx, yy, m0)
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+    time_matvec(ctx, x, y, 3)
+    mv32_ms = time_matvec(ctx, x, y, 30)
+    del ctx, x, y
+    torch.cuda.empty_cache()
+
+    # plain FP64 GPU path on the same steps, for the load-step comparison
+    ctx64 = mf.Context(n, n, n, mf.MF_FP64)
+    ctx64.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    fp64_steps = max(1, min(args.fp64_steps, args.steps))
+    steps(ctx64, 0, 1)
+    ctx64.set_F(None)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    o64 = steps(ctx64, 0, fp64_steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = a.elapsed_time(b) / fp64_steps
+    ctx64.constitutive()
+    x64 = torch.randn(9 * N, dtype=torch.float64, device="cuda")
+    y64 = torch.empty_like(x64)
+    time_matvec(ctx64, x64, y64, 2)
+    mv64_ms = time_matvec(ctx64, x64, y64, 10)
+    kms64 = ctx64.time_kernels(m0, reps=5)
+    del ctx64, x64, y64
+
+    peak, peak_kind = measured_peaks()
+    dom = int(np.argmax(kms))
+    achieved = ALGO_BYTES_F32[dom] * N / (kms[dom] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "load steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": N, "grains": NGRAINS, "load_steps": nsteps_hist,
+                   "l2": "inputs larger than L2 (K alone is 377 MB); kernel timings flush L2",
+                   "parallelism": "replicas"},
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "kernel": KERNELS[dom], "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
+                     else peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(KERNELS[dom]),
+                     "algorithmic_bytes_per_voxel": ALGO_BYTES_F32[dom]},
+        "kernels_fp32": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9,
+                             "frac": b * N / (t * 1e-3) / 1e9 / peak}
+                         for k, t, b in zip(KERNELS, kms, ALGO_BYTES_F32)},
+        "kernels_fp64": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9}
+                         for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
+        "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9},
+        "load_step_ms": {"fp32_inner_median": float(np.median(step_ms)),
+                         "fp64_plain": fp64_ms, "fp64_steps_timed": fp64_steps},
+        "iterations": {"fp32_inner_newton_cg_per_step": its,
+                       "fp64_newton": o64["newton"].tolist(), "fp64_cg": o64["cg"].tolist()},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        line["cpu_baseline"] = cpu_baseline_entry(oracle_sample(cores), cores)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * mixfft.h -- C ABI of the GB300 library for Galerkin FFT homogenization
+ * with macroscopic stress and mixed stress/strain control
+ * (Lucarini & Segurado, "An algorithm for stress and mixed control in
+ * Galerkin based FFT homogenization", arXiv:1901.06531).
+ *
+ * Problem statement (Sec. 2): a periodic cell of nx*ny*nz unit voxels, a
+ * phase id per voxel with per-phase material parameters, and a load history
+ * in which each of the nine components of the macroscopic deformation
+ * gradient F-bar or of the macroscopic first Piola stress P-bar is
+ * prescribed per step (Sec. 2.3, Eq. eq:mixedeqil).  Each step is solved by
+ * Newton (Eq. eq:lineariz) with conjugate gradients on the linear system
+ *     G*(K : dF) = -G*(P(F) - P-bar)                      (Eq. linequil2ast)
+ * where G* is the projection operator whose null frequency carries the
+ * per-component control (Eq. eq:Gnewnew).
+ *
+ * Conventions for every entry point:
+ *  - tensor fields are component-major, c = 3*i + j for component ij, each
+ *    component a [z][y][x] block with x fastest: field[c*N + (z*ny + y)*nx + x],
+ *    N = nx*ny*nz;
+ *  - masks are 9 bytes, 1 = stress controlled (P-bar prescribed), 0 = strain
+ *    controlled (F-bar prescribed);
+ *  - "host" pointers are ordinary CPU memory owned by the caller and only read
+ *    or written during the call; "device" pointers are CUDA global memory on
+ *    the context's device, owned by the caller;
+ *  - every call returns an mf_status; no call throws or aborts.  After
+ *    MF_CUDA_ERROR the context should be destroyed.
+ *  - a context is not thread safe; calls on one context are serialised on its
+ *    CUDA stream.
+ */
+#ifndef MIXFFT_H
+#define MIXFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MF_OK = 0,
+  MF_INVALID_ARG = 1,     /* bad size, pointer, model or parameter; nothing launched */
+  MF_NOT_CONVERGED = 2,   /* Newton or CG iteration cap reached */
+  MF_CG_BREAKDOWN = 3,    /* p.Ap <= 0 or non-finite in CG (indefinite tangent) */
+  MF_NONPOSITIVE_J = 4,   /* det F <= 0 in a neo-Hookean voxel */
+  MF_CUDA_ERROR = 5,      /* a CUDA runtime call failed */
+  MF_DEVICE_TIMEOUT = 6,  /* a bounded device-side wait gave up */
+  MF_NO_WORKSPACE = 7     /* mf_bind_workspace was not called or is too small */
+} mf_status;
+
+typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
+typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
+
+typedef struct mf_ctx mf_ctx;
+
+/* Create a context for one cell of nx*ny*nz voxels on the current CUDA device.
+ * nx, ny: even, of the form 2^a 3^b, 4..256; nz: 2^a 3^b, 2..256.  The x-y
+ * plane of one component must fit in shared memory: nx*ny <= 16384 for
+ * MF_FP64 and for MF_FP32_INNER (the FP64 residual uses the same plane).
+ * precision MF_FP64: every step in FP64.  MF_FP32_INNER: the CG iterations
+ * (transforms, projection, tangent apply, vector updates) run in FP32 with
+ * FP64 dot products, while P, K, the residual, the null-frequency control and
+ * the Newton update stay FP64 (defect correction).
+ * stream: a cudaStream_t (NULL = legacy default stream) used for every launch
+ * and copy of this context.  *out is NULL on failure. */
+int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream);
+
+/* Bytes of device workspace the context needs (fields F, P, K, residual, CG
+ * vectors, spectrum, tables, reduction scratch), 256-byte aligned. */
+size_t mf_workspace_bytes(const mf_ctx* ctx);
+
+/* Hand the context a device buffer of at least mf_workspace_bytes() bytes,
+ * 256-byte aligned, owned by the caller and kept alive until mf_destroy or
+ * the next bind.  The library allocates no device memory of its own. */
+int mf_bind_workspace(mf_ctx* ctx, void* dev, size_t bytes);
+
+/* Microstructure and phase parameters (Sec. 2.1: the cell is a spatial
+ * arrangement of phases; Sec. 3 materials).
+ *   phase  host, N int32 in [0, nphase), x fastest;
+ *   model  MF_NEOHOOKE: params host (nphase, 2) = (mu, lambda) per phase;
+ *          MF_SVK_CUBIC: params host (nphase, 3) = (C11, C12, C44), rot host
+ *          (nphase, 3, 3) row-major rotation per phase or NULL (identity);
+ *          the stiffness of phase p is C'_ijkl = R_ia R_jb R_kc R_ld C_abcd;
+ *   scale  host, N doubles multiplying P and K per voxel, or NULL.
+ * Copies are enqueued on the stream; the host arrays may be reused on return.
+ * Resets F to the identity. */
+int mf_set_material(mf_ctx* ctx, int model, int nphase, const double* params,
+                    const double* rot, const int32_t* phase, const double* scale);
+
+/* Set the deformation-gradient field from host memory (9N doubles) or, with
+ * F_host NULL, to the identity everywhere. */
+int mf_set_F(mf_ctx* ctx, const double* F_host);
+
+/* Run a load history (Sec. 2.3; Sec. 4 stopping rules).
+ *   mask    host, nsteps*9 bytes, 1 = P-bar prescribed, 0 = F-bar prescribed;
+ *   target  host, nsteps*9 doubles: P-bar where mask is 1, F-bar where 0;
+ *   tol_newton: stop when max_v |dF_v| / |<F>| < tol_newton;
+ *   tol_cg: CG stops when sqrt(sum_v |r_v|^2 / N) <= tol_cg (MF_FP64), or
+ *           <= max(tol_cg, cg_rel * initial value) (MF_FP32_INNER);
+ *   cg_rel: relative CG forcing term for MF_FP32_INNER (ignored for MF_FP64);
+ *   Fbar_out, Pbar_out: host, nsteps*9 doubles or NULL: <F>, <P> per step;
+ *   iters_out: host, nsteps*2 int32 or NULL: Newton iterations and total CG
+ *              iterations per step.
+ * The run continues from the current F (identity after mf_set_material).
+ * On a failure the outputs of the completed steps are written and the
+ * status of the failing step is returned. */
+int mf_solve(mf_ctx* ctx, int nsteps, const uint8_t* mask, const double* target,
+             double tol_newton, double tol_cg, double cg_rel, int max_newton,
+             int max_cg, double* Fbar_out, double* Pbar_out, int32_t* iters_out);
+
+/* Copy the current F and P fields to host memory (9N doubles each; either
+ * pointer may be NULL).  P is the stress at the current F. */
+int mf_get_fields(mf_ctx* ctx, double* F_host, double* P_host);
+
+/* ---- operator-level entry points (tests, benchmarks, adjoints) ---------- */
+
+/* Evaluate P(F) and K = dP/dF (Eq. eq:lineariz) at the current F.  K is kept
+ * in the context (45 packed entries per voxel, FP64 or FP32 by precision). */
+int mf_constitutive(mf_ctx* ctx);
+
+/* Copy the tangent to host memory as 45 packed symmetric entries per voxel:
+ * K45_host[t*N + v], t = a*9 - a*(a-1)/2 + (b - a) for a <= b, a = 3i+j,
+ * b = 3k+l, value K_ijkl (converted to double). */
+int mf_get_tangent(mf_ctx* ctx, double* K45_host);
+
+/* Projected tangent product y = G*(K : x) (left side of Eq. linequil2ast,
+ * G* of Eq. eq:Gnewnew with the given mask), using the tangent of the last
+ * mf_constitutive.  x_dev, y_dev: device, 9N values of the context's inner
+ * type (double for MF_FP64, float for MF_FP32_INNER); may not alias. */
+int mf_matvec(mf_ctx* ctx, const void* x_dev, void* y_dev, const uint8_t* mask);
+
+/* Right-hand side b = -G*(P - P-bar) of Eq. (linequil2ast) in FP64 from the
+ * P of the last mf_constitutive.  b_dev: device, 9N doubles.  meanP_host:
+ * host, 9 doubles or NULL, receives <P> (Sec. 2.2: the null-frequency
+ * coefficient of P). */
+int mf_residual(mf_ctx* ctx, const uint8_t* mask, const double* pbar, double* b_dev,
+                double* meanP_host);
+
+/* Benchmark hook: time the three kernels of the inner projected operator
+ * (x-y forward with the tangent apply, z-pass with G-hat-star, x-y inverse)
+ * separately with CUDA events on the context's stream, each launch preceded
+ * by an L2 flush (a memset of the 9N-double residual buffer).  Uses the
+ * context's CG vectors as operands and the tangent of the last
+ * mf_constitutive.  ms_out: host, 3 floats, mean milliseconds per launch. */
+int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
+
+/* Number of kernel launches the library has issued in this process (all
+ * contexts); differences around a region count its launches. */
+long long mf_kernel_launches(void);
+
+/* Wait for the context's stream. */
+int mf_sync(mf_ctx* ctx);
+
+/* Static description of a status code. */
+const char* mf_status_string(int status);
+
+void mf_destroy(mf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MIXFFT_H */

@@ -1,0 +1,177 @@
+// Shared device machinery: complex helpers, per-axis FFT plans and the
+// in-place shared-memory FFT stages used by every transform kernel.
+//
+// Transforms are computed in place with mixed-radix (2, 3, 4) stages.  The
+// forward transform is decimation in frequency (natural order in, digit-
+// reversed order out), the inverse is its exact adjoint, decimation in time
+// (digit-reversed in, natural out).  The spectrum therefore never needs a
+// reordering pass: the projection is applied in digit-reversed order, with
+// each position's frequency read from a small table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MF_MAX_STAGES 10
+
+struct AxisPlan {
+  int n;                     // transform length
+  int nst;                   // number of stages
+  int rad[MF_MAX_STAGES];    // radix of each stage in DIF order
+};
+
+template <typename T> struct CT;
+template <> struct CT<double> { typedef double2 t; };
+template <> struct CT<float> { typedef float2 t; };
+
+__device__ __forceinline__ double2 cmake(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 cmake(float a, float b) { return make_float2(a, b); }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+// multiply by -i (FWD) or +i (INV)
+template <typename C, bool INV> __device__ __forceinline__ C rot90(C a) {
+  C r;
+  if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
+// Small DFT of length R on registers: y_k = sum_j x_j w^(jk), w = exp(-+2 pi i/R).
+template <int R, bool INV, typename C> struct Radix;
+
+template <bool INV, typename C> struct Radix<2, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C a = v[0], b = v[1]; v[0] = cadd(a, b); v[1] = csub(a, b);
+  }
+};
+
+template <bool INV, typename C> struct Radix<4, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    C t2 = cadd(v[1], v[3]), t3 = rot90<C, INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2); v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
+  }
+};
+
+template <bool INV, typename C> struct Radix<3, INV, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    typedef decltype(v[0].x) T;
+    const T h = (T)0.5;
+    const T s3 = (T)0.86602540378443864676372317075294;   // sin(2 pi / 3)
+    C a = v[0];
+    C t1 = cadd(v[1], v[2]);
+    C d = csub(v[1], v[2]);
+    C t2; t2.x = a.x - h * t1.x; t2.y = a.y - h * t1.y;
+    // forward: y1 = t2 - i s3 d, y2 = t2 + i s3 d; inverse: signs of i swap
+    C t3; t3.x = s3 * d.x; t3.y = s3 * d.y;
+    C it3 = rot90<C, INV>(t3);     // -i*t3 forward, +i*t3 inverse
+    v[0] = cadd(a, t1);
+    v[1] = cadd(t2, it3);
+    v[2] = csub(t2, it3);
+  }
+};
+
+// One in-place radix-R stage over `nseq` sequences of length n in shared
+// memory.  Element j of sequence s is at buf[(s / nlo) * hs + (s % nlo) * ls + j * es].
+// L is the current sub-transform length (n at the first DIF stage); the
+// twiddle table holds W_ntab^t = exp(-2 pi i t / ntab) with n | ntab.
+// SEQ_FAST chooses the thread order: consecutive threads walk sequences
+// (strided transforms) or butterflies (contiguous transforms).
+template <typename C, int R, bool INV, bool SEQ_FAST>
+__device__ __forceinline__ void fft_stage(C* buf, int n, int L, int nseq, int nlo, int hs,
+                                          int ls, int es, const C* tw, int ntab) {
+  const int m = L / R;
+  const int nb = n / R;
+  const int total = nb * nseq;
+  const int tstep = ntab / L;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int s, b;
+    if (SEQ_FAST) { s = t % nseq; b = t / nseq; } else { b = t % nb; s = t / nb; }
+    const int blk = b / m;
+    const int j0 = b - blk * m;
+    const int base = (s / nlo) * hs + (s % nlo) * ls + (blk * L + j0) * es;
+    const int step = m * es;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = buf[base + r * step];
+    if (!INV) {
+      Radix<R, false, C>::run(v);
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[j0 * k * tstep]);
+    } else {
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[j0 * k * tstep]);
+      Radix<R, true, C>::run(v);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[base + r * step] = v[r];
+  }
+}
+
+template <typename C, bool INV, bool SEQ_FAST>
+__device__ __forceinline__ void fft_stage_dispatch(int R, C* buf, int n, int L, int nseq, int nlo,
+                                                   int hs, int ls, int es, const C* tw, int ntab) {
+  if (R == 4) fft_stage<C, 4, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab);
+  else if (R == 2) fft_stage<C, 2, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab);
+  else fft_stage<C, 3, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab);
+}
+
+// Full transform of every sequence: DIF forward (INV = false) or its adjoint
+// DIT inverse (INV = true, unnormalised).  Ends with __syncthreads(); the
+// caller synchronises before the first stage.
+template <typename C, bool INV, bool SEQ_FAST>
+__device__ __forceinline__ void fft_run(C* buf, const AxisPlan& pl, int nseq, int nlo, int hs,
+                                        int ls, int es, const C* tw, int ntab) {
+  if (!INV) {
+    int L = pl.n;
+    for (int st = 0; st < pl.nst; ++st) {
+      const int R = pl.rad[st];
+      fft_stage_dispatch<C, false, SEQ_FAST>(R, buf, pl.n, L, nseq, nlo, hs, ls, es, tw, ntab);
+      L /= R;
+      __syncthreads();
+    }
+  } else {
+    int Ls[MF_MAX_STAGES];
+    int L = pl.n;
+    for (int st = 0; st < pl.nst; ++st) { Ls[st] = L; L /= pl.rad[st]; }
+    for (int st = pl.nst - 1; st >= 0; --st) {
+      fft_stage_dispatch<C, true, SEQ_FAST>(pl.rad[st], buf, pl.n, Ls[st], nseq, nlo, hs, ls, es,
+                                            tw, ntab);
+      __syncthreads();
+    }
+  }
+}
+
+// Index of the packed symmetric 9x9 tangent entry (a, b), a, b in [0, 9).
+__host__ __device__ __forceinline__ int sym45(int a, int b) {
+  if (a > b) { int t = a; a = b; b = t; }
+  return a * 9 - (a * (a - 1)) / 2 + (b - a);
+}
+
+// Device-side scalar block shared by the Newton/CG kernels (FP64).
+struct Scalars {
+  double rr;          // current r.r
+  double rr0;         // r.r at CG start
+  double pAp;
+  double alpha;
+  double beta;
+  double thr2N;       // CG stop: rr <= thr2N
+  double meanF[9];
+  double meanP[9];
+  double dF2max;      // max_v |dF_v|^2 of the last Newton update
+  double meanF_new[9];
+  int flags;          // bit 0: breakdown, bit 1: nonpositive J, bit 2: non-finite
+  int done;           // CG converged
+  int pad[2];
+};
+
+#define MF_FLAG_BREAKDOWN 1
+#define MF_FLAG_NONPOS_J 2
+#define MF_FLAG_NONFINITE 4

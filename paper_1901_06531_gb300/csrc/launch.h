@@ -1,0 +1,75 @@
+// Argument blocks and host-side launchers shared by the library's
+// translation units (host code only; no torch types).
+#pragma once
+
+#include "common.cuh"
+
+struct XYArgs {
+  int nx, ny, nz;
+  long long N;
+  AxisPlan px;     // length nx
+  AxisPlan pyh;    // length ny/2 (the y transform after its first radix-2 stage)
+  const void* twx; // W_nx^t, t < nx   (complex of the kernel's type)
+  const void* twy; // W_ny^t, t < ny
+  const int* xpos; // position of x-frequency k after the x DIF, k < nx
+};
+
+struct ZArgs {
+  int nx, ny, nz;
+  long long N;
+  AxisPlan pz;
+  const void* twz;   // W_nz^t
+  const int* xk;     // slot -> kx
+  const int* xe;     // slot -> parity e
+  const int* yk;     // row q' -> ky half index
+  const int* zk;     // position -> kz
+  int S;             // columns per block
+  unsigned mask;     // bit c set: component c stress controlled
+  double scale;      // multiplies every coefficient (1/N, or -1/N for the residual)
+  double add[9];     // added at the null frequency after scaling (residual: P-bar)
+  double* mean_out;  // residual: receives the null-frequency coefficient / N
+};
+
+// Process-wide count of kernel launches issued by the library.
+extern long long g_mf_launches;
+
+// transform.cu
+cudaError_t mf_launch_matvec_f64(const double* x, const double* K45, void* spec, double* y,
+                                 const double* w, double* partials, const XYArgs& xa,
+                                 const ZArgs& za, cudaStream_t st);
+cudaError_t mf_launch_matvec_f32(const float* x, const float* K45, void* spec, float* y,
+                                 const float* w, double* partials, const XYArgs& xa,
+                                 const ZArgs& za, cudaStream_t st);
+cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
+                               const XYArgs& xa, const ZArgs& za, cudaStream_t st);
+// which: 0 x-y forward with tangent apply, 1 z-pass, 2 x-y inverse with dot
+cudaError_t mf_launch_matvec_part(int which, bool f32, const void* x, const void* K45, void* spec,
+                                  void* y, const void* w, double* partials, const XYArgs& xa,
+                                  const ZArgs& za, cudaStream_t st);
+
+// pointwise.cu
+struct MatArgs {
+  int model;              // 0 neo-Hookean, 1 St Venant-Kirchhoff (cubic, rotated)
+  int nphase;
+  const double* table;    // neo-Hookean: (mu, lam) per phase; SVK: 36 Voigt entries per phase
+  const int32_t* phase;
+  const double* scale;    // per-voxel multiplier of P and K, or null
+};
+cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k_f32, bool want_K,
+                                   const MatArgs& m, long long N, double* partials, int nblk,
+                                   Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int nblk, Scalars* sc,
+                             cudaStream_t st);
+cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,
+                                const Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f32, long long n9,
+                              const double* b_partials, int nb_partials, double tol_cg,
+                              double cg_rel, long long N, Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_cg_alpha(const double* partials, int npart, Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_cg_update(void* x, void* r, const void* p, const void* Ap, bool f32,
+                                long long n9, double* partials, int nblk, Scalars* sc,
+                                cudaStream_t st);
+cudaError_t mf_launch_cg_direction(void* p, const void* r, bool f32, long long n9, const Scalars* sc,
+                                   cudaStream_t st);
+cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, long long N, double* partials,
+                                    int nblk, Scalars* sc, cudaStream_t st);

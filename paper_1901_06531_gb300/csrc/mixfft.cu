@@ -1,0 +1,588 @@
+// C ABI of the library (include/mixfft.h): context, workspace layout, plans
+// and tables, and the host side of the Newton-CG loop of Eq. (linequil2ast)
+// under the per-component stress/strain control of Eq. (eq:mixedeqil).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/mixfft.h"
+#include "launch.h"
+
+namespace {
+
+constexpr int kMaxPhases = 65536;
+constexpr int kPointwiseBlocks = 152 * 8;
+
+bool make_plan(int n, AxisPlan* p) {
+  p->n = n;
+  p->nst = 0;
+  int m = n;
+  while (m % 4 == 0) { p->rad[p->nst++] = 4; m /= 4; }
+  if (m % 2 == 0) { p->rad[p->nst++] = 2; m /= 2; }
+  while (m % 3 == 0) {
+    if (p->nst >= MF_MAX_STAGES) return false;
+    p->rad[p->nst++] = 3;
+    m /= 3;
+  }
+  return m == 1 && p->nst <= MF_MAX_STAGES;
+}
+
+// Position of frequency k after the DIF stages of plan p.
+int dif_pos(const AxisPlan& p, int k) {
+  int pos = 0, L = p.n;
+  for (int st = 0; st < p.nst; ++st) {
+    const int r = p.rad[st], m = L / r;
+    pos += m * (k % r);
+    k /= r;
+    L = m;
+  }
+  return pos;
+}
+
+bool smooth_size(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct mf_ctx {
+  int nx, ny, nz;
+  long long N;
+  int prec;
+  cudaStream_t st;
+  AxisPlan px, pyh, pz;
+  int zS;
+  // workspace
+  char* ws = nullptr;
+  size_t ws_need = 0;
+  // offsets into the workspace
+  size_t oF, oP, ob, oK, ox, or_, op, oAp, ospec, ophase, oscale, otable, opart, osc, ores,
+      oxpos, oxk, oxe, oyk, ozk, otw64, otw32;
+  size_t npart;
+  // material
+  int model = -1, nphase = 0;
+  bool has_scale = false;
+  bool have_K = false;
+
+  template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  bool f32() const { return prec == MF_FP32_INNER; }
+  size_t inner_size() const { return f32() ? sizeof(float) : sizeof(double); }
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_CUDA_ERROR; }
+
+XYArgs xy_args(const mf_ctx* c, bool f32) {
+  XYArgs a;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
+  a.px = c->px; a.pyh = c->pyh;
+  const size_t tw = f32 ? c->otw32 : c->otw64;
+  const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  a.twx = c->ws + tw;
+  a.twy = c->ws + tw + esz * c->nx;
+  a.xpos = c->at<int>(c->oxpos);
+  return a;
+}
+
+ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale) {
+  ZArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
+  a.pz = c->pz;
+  const size_t tw = f32 ? c->otw32 : c->otw64;
+  const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  a.twz = c->ws + tw + esz * (c->nx + c->ny);
+  a.xk = c->at<int>(c->oxk);
+  a.xe = c->at<int>(c->oxe);
+  a.yk = c->at<int>(c->oyk);
+  a.zk = c->at<int>(c->ozk);
+  a.S = c->zS;
+  a.mask = 0;
+  for (int k = 0; k < 9; ++k)
+    if (mask[k]) a.mask |= 1u << k;
+  a.scale = scale;
+  a.mean_out = nullptr;
+  return a;
+}
+
+MatArgs mat_args(const mf_ctx* c) {
+  MatArgs m;
+  m.model = c->model;
+  m.nphase = c->nphase;
+  m.table = c->at<double>(c->otable);
+  m.phase = c->at<int32_t>(c->ophase);
+  m.scale = c->has_scale ? c->at<double>(c->oscale) : nullptr;
+  return m;
+}
+
+int read_scalars(mf_ctx* c, Scalars* h) {
+  cudaError_t e = cudaMemcpyAsync(h, c->ws + c->osc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st);
+  if (e != cudaSuccess) return MF_CUDA_ERROR;
+  return cuda_status(cudaStreamSynchronize(c->st));
+}
+
+int flags_status(int flags) {
+  if (flags & MF_FLAG_NONPOS_J) return MF_NONPOSITIVE_J;
+  if (flags & (MF_FLAG_BREAKDOWN | MF_FLAG_NONFINITE)) return MF_CG_BREAKDOWN;
+  return MF_OK;
+}
+
+int run_constitutive(mf_ctx* c, bool want_K) {
+  cudaError_t e = mf_launch_constitutive(c->at<double>(c->oF), c->at<double>(c->oP), c->ws + c->oK,
+                                         c->f32(), want_K, mat_args(c), c->N, c->at<double>(c->opart),
+                                         kPointwiseBlocks, c->at<Scalars>(c->osc), c->st);
+  if (want_K && e == cudaSuccess) c->have_K = true;
+  return cuda_status(e);
+}
+
+int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out) {
+  ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N);
+  for (int k = 0; k < 9; ++k) za.add[k] = mask[k] ? pbar[k] : 0.0;
+  za.mean_out = mean_out;
+  return cuda_status(mf_launch_residual(c->at<double>(c->oP), c->ws + c->ospec, b,
+                                        c->at<double>(c->opart), xy_args(c, false), za, c->st));
+}
+
+int run_matvec(mf_ctx* c, const void* x, void* y, const void* w, const uint8_t* mask) {
+  const ZArgs za = z_args(c, c->f32(), mask, 1.0 / (double)c->N);
+  const XYArgs xa = xy_args(c, c->f32());
+  double* part = c->at<double>(c->opart);
+  cudaError_t e;
+  if (c->f32())
+    e = mf_launch_matvec_f32((const float*)x, (const float*)(c->ws + c->oK), c->ws + c->ospec,
+                             (float*)y, (const float*)w, part, xa, za, c->st);
+  else
+    e = mf_launch_matvec_f64((const double*)x, (const double*)(c->ws + c->oK), c->ws + c->ospec,
+                             (double*)y, (const double*)w, part, xa, za, c->st);
+  return cuda_status(e);
+}
+
+// One linear solve of Eq. (linequil2ast) by CG from dF = 0; the solution is
+// left in the x vector.  Returns a status and the iteration count.
+int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max_cg, int* its) {
+  const bool f32 = c->f32();
+  const long long n9 = 9 * c->N;
+  void* x = c->ws + c->ox;
+  void* r = c->ws + c->or_;
+  void* p = c->ws + c->op;
+  void* Ap = c->ws + c->oAp;
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, p, f32, n9, part, 9 * c->nz, tol_cg,
+                                    f32 ? cg_rel : 0.0, c->N, sc, c->st);
+  if (e != cudaSuccess) return MF_CUDA_ERROR;
+  *its = 0;
+  Scalars h;
+  for (;;) {
+    int s = read_scalars(c, &h);
+    if (s) return s;
+    s = flags_status(h.flags);
+    if (s) return s;
+    if (h.done) return MF_OK;
+    if (*its >= max_cg) return MF_NOT_CONVERGED;
+    s = run_matvec(c, p, Ap, p, mask);
+    if (s) return s;
+    if (mf_launch_cg_alpha(part, 9 * c->nz, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+    if (mf_launch_cg_update(x, r, p, Ap, f32, n9, part, kPointwiseBlocks, sc, c->st) != cudaSuccess)
+      return MF_CUDA_ERROR;
+    if (mf_launch_cg_direction(p, r, f32, n9, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+    ++*its;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mf_status_string(int s) {
+  switch (s) {
+    case MF_OK: return "ok";
+    case MF_INVALID_ARG: return "invalid argument";
+    case MF_NOT_CONVERGED: return "not converged";
+    case MF_CG_BREAKDOWN: return "CG breakdown (p.Ap <= 0 or non-finite)";
+    case MF_NONPOSITIVE_J: return "det F <= 0";
+    case MF_CUDA_ERROR: return "CUDA error";
+    case MF_DEVICE_TIMEOUT: return "device timeout";
+    case MF_NO_WORKSPACE: return "no workspace bound";
+    default: return "unknown status";
+  }
+}
+
+int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream) {
+  if (!out) return MF_INVALID_ARG;
+  *out = nullptr;
+  if (precision != MF_FP64 && precision != MF_FP32_INNER) return MF_INVALID_ARG;
+  if (nx < 4 || ny < 4 || nz < 2 || nx > 256 || ny > 256 || nz > 256) return MF_INVALID_ARG;
+  if ((nx & 1) || (ny & 1) || !smooth_size(nx) || !smooth_size(ny) || !smooth_size(nz))
+    return MF_INVALID_ARG;
+  // one component's x-y plane must fit in shared memory (FP64 residual)
+  if ((size_t)(ny / 2) * nx * sizeof(double2) + (size_t)(nx + ny) * 20 > 200 * 1024)
+    return MF_INVALID_ARG;
+  mf_ctx* c = new (std::nothrow) mf_ctx();
+  if (!c) return MF_INVALID_ARG;
+  c->nx = nx; c->ny = ny; c->nz = nz;
+  c->N = (long long)nx * ny * nz;
+  c->prec = precision;
+  c->st = (cudaStream_t)stream;
+  if (!make_plan(nx, &c->px) || !make_plan(ny / 2, &c->pyh) || !make_plan(nz, &c->pz)) {
+    delete c;
+    return MF_INVALID_ARG;
+  }
+  // z-pass tile: columns per block so that 9 * nz * S complex doubles fit
+  int S = 16;
+  while (S > 1 && (size_t)9 * nz * S * sizeof(double2) > 150 * 1024) S /= 2;
+  c->zS = S;
+
+  const long long N = c->N;
+  const size_t isz = c->inner_size();
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  c->oF = take(9 * N * sizeof(double));
+  c->oP = take(9 * N * sizeof(double));
+  c->ob = take(9 * N * sizeof(double));
+  c->oK = take(45 * N * isz);
+  c->ox = take(9 * N * isz);
+  c->or_ = take(9 * N * isz);
+  c->op = take(9 * N * isz);
+  c->oAp = take(9 * N * isz);
+  c->ospec = take(9 * (N / 2) * sizeof(double2));
+  c->ophase = take(N * sizeof(int32_t));
+  c->oscale = take(N * sizeof(double));
+  c->otable = take((size_t)kMaxPhases * 36 * sizeof(double));
+  c->npart = (size_t)(kPointwiseBlocks > 9 * nz ? kPointwiseBlocks : 9 * nz) * 18;
+  c->opart = take(c->npart * sizeof(double));
+  c->osc = take(sizeof(Scalars));
+  c->ores = take(9 * sizeof(double));
+  c->oxpos = take(nx * sizeof(int));
+  c->oxk = take(nx * sizeof(int));
+  c->oxe = take(nx * sizeof(int));
+  c->oyk = take((ny / 2) * sizeof(int));
+  c->ozk = take(nz * sizeof(int));
+  c->otw64 = take((nx + ny + nz) * sizeof(double2));
+  c->otw32 = take((nx + ny + nz) * sizeof(float2));
+  c->ws_need = off;
+  *out = c;
+  return MF_OK;
+}
+
+size_t mf_workspace_bytes(const mf_ctx* c) { return c ? c->ws_need : 0; }
+
+int mf_bind_workspace(mf_ctx* c, void* dev, size_t bytes) {
+  if (!c || !dev || bytes < c->ws_need || ((uintptr_t)dev & 255)) return MF_INVALID_ARG;
+  c->ws = (char*)dev;
+  c->model = -1;
+  c->have_K = false;
+  // host-built tables: digit-reversal maps and twiddles
+  const int nx = c->nx, ny = c->ny, nz = c->nz;
+  std::vector<int> xpos(nx), xk(nx), xe(nx), yk(ny / 2), zk(nz);
+  for (int k = 0; k < nx; ++k) xpos[k] = dif_pos(c->px, k);
+  for (int k = 0; k < nx; ++k) {
+    const int s = xpos[k];
+    if (k < nx / 2) { xk[s] = k; xe[s] = 0; }
+    else if (k == nx / 2) { xk[s] = 0; xe[s] = 1; }
+    else { xk[s] = nx - k; xe[s] = 1; }
+  }
+  for (int k = 0; k < ny / 2; ++k) yk[dif_pos(c->pyh, k)] = k;
+  for (int k = 0; k < nz; ++k) zk[dif_pos(c->pz, k)] = k;
+  std::vector<double2> tw64(nx + ny + nz);
+  std::vector<float2> tw32(nx + ny + nz);
+  int o = 0;
+  for (int n : {nx, ny, nz}) {
+    for (int t = 0; t < n; ++t) {
+      const double ang = -2.0 * M_PI * (double)t / (double)n;
+      tw64[o + t] = make_double2(cos(ang), sin(ang));
+      tw32[o + t] = make_float2((float)tw64[o + t].x, (float)tw64[o + t].y);
+    }
+    o += n;
+  }
+  cudaError_t e = cudaSuccess;
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, c->st);
+  };
+  put(c->oxpos, xpos.data(), nx * sizeof(int));
+  put(c->oxk, xk.data(), nx * sizeof(int));
+  put(c->oxe, xe.data(), nx * sizeof(int));
+  put(c->oyk, yk.data(), (ny / 2) * sizeof(int));
+  put(c->ozk, zk.data(), nz * sizeof(int));
+  put(c->otw64, tw64.data(), tw64.size() * sizeof(double2));
+  put(c->otw32, tw32.data(), tw32.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // host vectors go out of scope
+  return cuda_status(e);
+}
+
+int mf_set_material(mf_ctx* c, int model, int nphase, const double* params, const double* rot,
+                    const int32_t* phase, const double* scale) {
+  if (!c) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if ((model != MF_NEOHOOKE && model != MF_SVK_CUBIC) || nphase < 1 || nphase > kMaxPhases || !params ||
+      !phase)
+    return MF_INVALID_ARG;
+  for (long long v = 0; v < c->N; ++v)
+    if (phase[v] < 0 || phase[v] >= nphase) return MF_INVALID_ARG;
+  std::vector<double> table;
+  if (model == MF_NEOHOOKE) {
+    table.assign(params, params + 2 * nphase);
+    for (double x : table)
+      if (!isfinite(x)) return MF_INVALID_ARG;
+  } else {
+    table.assign((size_t)36 * nphase, 0.0);
+    for (int p = 0; p < nphase; ++p) {
+      const double c11 = params[3 * p], c12 = params[3 * p + 1], c44 = params[3 * p + 2];
+      if (!isfinite(c11) || !isfinite(c12) || !isfinite(c44)) return MF_INVALID_ARG;
+      // cubic tensor in the crystal frame
+      double C[3][3][3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          for (int cc = 0; cc < 3; ++cc)
+            for (int d = 0; d < 3; ++d) {
+              double v = 0.0;
+              if (a == b && cc == d) v += c12;
+              if (a == cc && b == d) v += c44;
+              if (a == d && b == cc) v += c44;
+              if (a == b && b == cc && cc == d) v += c11 - c12 - 2.0 * c44;
+              C[a][b][cc][d] = v;
+            }
+      double R[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+      if (rot)
+        for (int i = 0; i < 9; ++i) {
+          R[i / 3][i % 3] = rot[9 * p + i];
+          if (!isfinite(rot[9 * p + i])) return MF_INVALID_ARG;
+        }
+      // C'_ijkl = R_ia R_jb R_kc R_ld C_abcd, one index at a time
+      double T1[3][3][3][3], T2[3][3][3][3];
+      for (int i = 0; i < 3; ++i) for (int b = 0; b < 3; ++b) for (int cc = 0; cc < 3; ++cc)
+        for (int d = 0; d < 3; ++d) {
+          double s = 0; for (int a = 0; a < 3; ++a) s += R[i][a] * C[a][b][cc][d]; T1[i][b][cc][d] = s;
+        }
+      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) for (int cc = 0; cc < 3; ++cc)
+        for (int d = 0; d < 3; ++d) {
+          double s = 0; for (int b = 0; b < 3; ++b) s += R[j][b] * T1[i][b][cc][d]; T2[i][j][cc][d] = s;
+        }
+      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) {
+          double s = 0; for (int cc = 0; cc < 3; ++cc) s += R[k][cc] * T2[i][j][cc][d]; T1[i][j][k][d] = s;
+        }
+      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          double s = 0; for (int d = 0; d < 3; ++d) s += R[l][d] * T1[i][j][k][d]; T2[i][j][k][l] = s;
+        }
+      static const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
+      for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) table[36 * p + 6 * I + J] = T2[vi[I]][vj[I]][vi[J]][vj[J]];
+    }
+  }
+  if (scale)
+    for (long long v = 0; v < c->N; ++v)
+      if (!isfinite(scale[v])) return MF_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->otable, table.data(), table.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->ws + c->ophase, phase, c->N * sizeof(int32_t), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess && scale)
+    e = cudaMemcpyAsync(c->ws + c->oscale, scale, c->N * sizeof(double), cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return MF_CUDA_ERROR;
+  c->model = model;
+  c->nphase = nphase;
+  c->has_scale = scale != nullptr;
+  c->have_K = false;
+  return mf_set_F(c, nullptr);
+}
+
+int mf_set_F(mf_ctx* c, const double* F_host) {
+  if (!c) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  const long long N = c->N;
+  double* F = c->at<double>(c->oF);
+  cudaError_t e;
+  if (F_host) {
+    e = cudaMemcpyAsync(F, F_host, 9 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
+  } else {
+    std::vector<double> ident(9 * N, 0.0);
+    for (long long v = 0; v < N; ++v) ident[v] = ident[4 * N + v] = ident[8 * N + v] = 1.0;
+    e = cudaMemcpyAsync(F, ident.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  c->have_K = false;
+  return cuda_status(e);
+}
+
+int mf_constitutive(mf_ctx* c) {
+  if (!c) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (c->model < 0) return MF_INVALID_ARG;
+  int s = run_constitutive(c, true);
+  if (s) return s;
+  Scalars h;
+  s = read_scalars(c, &h);
+  if (s) return s;
+  return flags_status(h.flags);
+}
+
+int mf_get_tangent(mf_ctx* c, double* K45_host) {
+  if (!c || !K45_host) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (!c->have_K) return MF_INVALID_ARG;
+  const size_t n = 45 * (size_t)c->N;
+  if (!c->f32()) {
+    cudaError_t e = cudaMemcpyAsync(K45_host, c->ws + c->oK, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    return cuda_status(e);
+  }
+  std::vector<float> tmp(n);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), c->ws + c->oK, n * sizeof(float), cudaMemcpyDeviceToHost,
+                                  c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return MF_CUDA_ERROR;
+  for (size_t i = 0; i < n; ++i) K45_host[i] = tmp[i];
+  return MF_OK;
+}
+
+int mf_matvec(mf_ctx* c, const void* x_dev, void* y_dev, const uint8_t* mask) {
+  if (!c || !x_dev || !y_dev || !mask || x_dev == y_dev) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (!c->have_K) return MF_INVALID_ARG;
+  return run_matvec(c, x_dev, y_dev, nullptr, mask);
+}
+
+int mf_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b_dev, double* meanP_host) {
+  if (!c || !mask || !pbar || !b_dev) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (c->model < 0) return MF_INVALID_ARG;
+  double* mean = c->at<double>(c->ores);
+  int s = run_residual(c, mask, pbar, b_dev, mean);
+  if (s) return s;
+  if (meanP_host) {
+    cudaError_t e = cudaMemcpyAsync(meanP_host, mean, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    return cuda_status(e);
+  }
+  return MF_OK;
+}
+
+int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, double tol_newton,
+             double tol_cg, double cg_rel, int max_newton, int max_cg, double* Fbar_out,
+             double* Pbar_out, int32_t* iters_out) {
+  if (!c || nsteps < 0 || (nsteps > 0 && (!mask || !target)) || !(tol_newton > 0) || !(tol_cg > 0) ||
+      max_newton < 1 || max_cg < 1 || !(cg_rel >= 0))
+    return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (c->model < 0) return MF_INVALID_ARG;
+  for (int i = 0; i < 9 * nsteps; ++i)
+    if (mask[i] > 1 || !isfinite(target[i])) return MF_INVALID_ARG;
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  double* F = c->at<double>(c->oF);
+  const long long N = c->N;
+  if (mf_launch_mean_F(F, N, part, kPointwiseBlocks, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+  Scalars h;
+  for (int k = 0; k < nsteps; ++k) {
+    const uint8_t* m = mask + 9 * k;
+    const double* tgt = target + 9 * k;
+    double pbar[9];
+    for (int q = 0; q < 9; ++q) pbar[q] = m[q] ? tgt[q] : 0.0;
+    if (mf_launch_predictor(F, N, m, tgt, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+    int nn = 0, ncg = 0;
+    double ratio = INFINITY;
+    int s;
+    for (;;) {
+      const bool last = nn > 0 && ratio < tol_newton;
+      s = run_constitutive(c, !last);
+      if (s) return s;
+      if (last) break;
+      if (nn >= max_newton) return MF_NOT_CONVERGED;
+      s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores));
+      if (s) return s;
+      int its = 0;
+      s = run_cg(c, m, tol_cg, cg_rel, max_cg, &its);
+      ncg += its;
+      if (s) return s;
+      if (mf_launch_newton_update(F, c->ws + c->ox, c->f32(), N, part, kPointwiseBlocks, sc, c->st) !=
+          cudaSuccess)
+        return MF_CUDA_ERROR;
+      s = read_scalars(c, &h);
+      if (s) return s;
+      s = flags_status(h.flags);
+      if (s) return s;
+      double fn = 0.0;
+      for (int q = 0; q < 9; ++q) fn += h.meanF_new[q] * h.meanF_new[q];
+      ratio = sqrt(h.dF2max) / sqrt(fn);
+      ++nn;
+    }
+    s = read_scalars(c, &h);
+    if (s) return s;
+    s = flags_status(h.flags);
+    if (s) return s;
+    if (Fbar_out) memcpy(Fbar_out + 9 * k, h.meanF, 9 * sizeof(double));
+    if (Pbar_out) memcpy(Pbar_out + 9 * k, h.meanP, 9 * sizeof(double));
+    if (iters_out) { iters_out[2 * k] = nn; iters_out[2 * k + 1] = ncg; }
+  }
+  return MF_OK;
+}
+
+int mf_get_fields(mf_ctx* c, double* F_host, double* P_host) {
+  if (!c) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  cudaError_t e = cudaSuccess;
+  if (F_host)
+    e = cudaMemcpyAsync(F_host, c->ws + c->oF, 9 * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess && P_host)
+    e = cudaMemcpyAsync(P_host, c->ws + c->oP, 9 * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  return cuda_status(e);
+}
+
+int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
+  if (!c || !mask || !ms_out || reps < 1) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (!c->have_K) return MF_INVALID_ARG;
+  const ZArgs za = z_args(c, c->f32(), mask, 1.0 / (double)c->N);
+  const XYArgs xa = xy_args(c, c->f32());
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
+  cudaError_t e = cudaSuccess;
+  for (int which = 0; which < 3 && e == cudaSuccess; ++which) {
+    double tot = 0.0;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+      e = cudaMemsetAsync(c->ws + c->ob, r & 0xff, 9 * c->N * sizeof(double), c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+      if (e == cudaSuccess)
+        e = mf_launch_matvec_part(which, c->f32(), c->ws + c->op, c->ws + c->oK, c->ws + c->ospec,
+                                  c->ws + c->oAp, c->ws + c->op, c->at<double>(c->opart), xa, za, c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    ms_out[which] = (float)(tot / reps);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cuda_status(e);
+}
+
+long long mf_kernel_launches(void) { return g_mf_launches; }
+
+int mf_sync(mf_ctx* c) {
+  if (!c) return MF_INVALID_ARG;
+  return cuda_status(cudaStreamSynchronize(c->st));
+}
+
+void mf_destroy(mf_ctx* c) { delete c; }
+
+}  // extern "C"

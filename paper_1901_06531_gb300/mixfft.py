@@ -1,0 +1,186 @@
+"""Thin Python binding of the C ABI in include/mixfft.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library libmixfft.so.  PyTorch supplies the device workspace and the CUDA
+stream; numpy arrays are passed as host pointers.  If the library has not been
+built, importing this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmixfft.so")
+
+MF_OK, MF_INVALID_ARG, MF_NOT_CONVERGED, MF_CG_BREAKDOWN = 0, 1, 2, 3
+MF_NONPOSITIVE_J, MF_CUDA_ERROR, MF_DEVICE_TIMEOUT, MF_NO_WORKSPACE = 4, 5, 6, 7
+MF_FP64, MF_FP32_INNER = 0, 1
+MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_sz = ctypes.c_size_t
+
+_lib.mf_create.argtypes = [ctypes.POINTER(_vp), _i, _i, _i, _i, _vp]
+_lib.mf_workspace_bytes.argtypes = [_vp]
+_lib.mf_workspace_bytes.restype = _sz
+_lib.mf_bind_workspace.argtypes = [_vp, _vp, _sz]
+_lib.mf_set_material.argtypes = [_vp, _i, _i, _vp, _vp, _vp, _vp]
+_lib.mf_set_F.argtypes = [_vp, _vp]
+_lib.mf_solve.argtypes = [_vp, _i, _vp, _vp, _d, _d, _d, _i, _i, _vp, _vp, _vp]
+_lib.mf_get_fields.argtypes = [_vp, _vp, _vp]
+_lib.mf_constitutive.argtypes = [_vp]
+_lib.mf_get_tangent.argtypes = [_vp, _vp]
+_lib.mf_matvec.argtypes = [_vp, _vp, _vp, _vp]
+_lib.mf_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.mf_time_kernels.argtypes = [_vp, _vp, _i, _vp]
+_lib.mf_kernel_launches.argtypes = []
+_lib.mf_kernel_launches.restype = ctypes.c_longlong
+_lib.mf_sync.argtypes = [_vp]
+_lib.mf_status_string.argtypes = [_i]
+_lib.mf_status_string.restype = ctypes.c_char_p
+_lib.mf_destroy.argtypes = [_vp]
+_lib.mf_destroy.restype = None
+
+EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_material", "mf_set_F",
+            "mf_solve", "mf_get_fields", "mf_constitutive", "mf_get_tangent", "mf_matvec",
+            "mf_residual", "mf_time_kernels", "mf_kernel_launches", "mf_sync", "mf_status_string",
+            "mf_destroy"]
+
+
+def kernel_launches():
+    """mf_kernel_launches: kernels launched by the library in this process."""
+    return int(_lib.mf_kernel_launches())
+
+
+class MixFFTError(RuntimeError):
+    def __init__(self, call, status):
+        self.status = status
+        msg = _lib.mf_status_string(status).decode()
+        super().__init__(f"{call}: {msg} (status {status})")
+
+
+def _check(call, status):
+    if status != MF_OK:
+        raise MixFFTError(call, status)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    """One periodic cell on the current CUDA device (mf_create ... mf_destroy).
+
+    precision: MF_FP64 or MF_FP32_INNER.  stream: a torch.cuda.Stream or None
+    (the current stream).  The workspace is one torch uint8 tensor.
+    """
+
+    def __init__(self, nx, ny, nz, precision=MF_FP64, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = _vp()
+        _check("mf_create", _lib.mf_create(ctypes.byref(h), nx, ny, nz, precision,
+                                           _vp(self.stream.cuda_stream)))
+        self.h = h
+        nbytes = int(_lib.mf_workspace_bytes(h))
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        _check("mf_bind_workspace", _lib.mf_bind_workspace(h, _vp(aligned), nbytes))
+        self.inner_dtype = torch.float32 if precision == MF_FP32_INNER else torch.float64
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.mf_destroy(h)
+            self.h = None
+
+    # -- problem set-up --------------------------------------------------
+    def set_material(self, model, params, phase, rot=None, scale=None):
+        params = _c64(params)
+        phase = np.ascontiguousarray(phase, dtype=np.int32)
+        rot = None if rot is None else _c64(rot)
+        scale = None if scale is None else _c64(scale)
+        nphase = params.shape[0]
+        _check("mf_set_material", _lib.mf_set_material(self.h, model, nphase, _ptr(params), _ptr(rot),
+                                                       _ptr(phase), _ptr(scale)))
+
+    def set_F(self, F=None):
+        F = None if F is None else _c64(F)
+        _check("mf_set_F", _lib.mf_set_F(self.h, _ptr(F)))
+
+    # -- load history ----------------------------------------------------
+    def solve(self, mask, target, tol_newton=1e-8, tol_cg=1e-10, cg_rel=1e-4, max_newton=50,
+              max_cg=5000):
+        mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1, 9)
+        target = _c64(target).reshape(-1, 9)
+        n = mask.shape[0]
+        Fbar = np.zeros((n, 9))
+        Pbar = np.zeros((n, 9))
+        iters = np.zeros((n, 2), dtype=np.int32)
+        st = _lib.mf_solve(self.h, n, _ptr(mask), _ptr(target), tol_newton, tol_cg, cg_rel,
+                           max_newton, max_cg, _ptr(Fbar), _ptr(Pbar), _ptr(iters))
+        _check("mf_solve", st)
+        return {"Fbar": Fbar, "Pbar": Pbar, "newton": iters[:, 0].astype(np.int64),
+                "cg": iters[:, 1].astype(np.int64)}
+
+    def get_fields(self):
+        F = np.empty((9,) + self.shape)
+        P = np.empty((9,) + self.shape)
+        _check("mf_get_fields", _lib.mf_get_fields(self.h, _ptr(F), _ptr(P)))
+        return F, P
+
+    # -- operator level --------------------------------------------------
+    def constitutive(self):
+        _check("mf_constitutive", _lib.mf_constitutive(self.h))
+
+    def get_tangent(self):
+        K = np.empty((45,) + self.shape)
+        _check("mf_get_tangent", _lib.mf_get_tangent(self.h, _ptr(K)))
+        return K
+
+    def matvec(self, x, y, mask):
+        """y = G*(K : x); x, y: torch CUDA tensors of 9N values of the inner dtype."""
+        assert x.dtype == self.inner_dtype and y.dtype == self.inner_dtype
+        assert x.is_contiguous() and y.is_contiguous() and x.numel() == 9 * self.N == y.numel()
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        _check("mf_matvec", _lib.mf_matvec(self.h, _vp(x.data_ptr()), _vp(y.data_ptr()), _ptr(m)))
+
+    def residual(self, mask, pbar, b):
+        """b = -G*(P - P-bar) in FP64 into the torch tensor b; returns <P>."""
+        assert b.dtype == self.torch.float64 and b.is_contiguous() and b.numel() == 9 * self.N
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        pb = _c64(pbar)
+        meanP = np.zeros(9)
+        _check("mf_residual", _lib.mf_residual(self.h, _ptr(m), _ptr(pb), _vp(b.data_ptr()),
+                                               _ptr(meanP)))
+        return meanP
+
+    def time_kernels(self, mask, reps=20):
+        """Mean ms per launch of the three inner-operator kernels (x-y forward
+        with tangent apply, z-pass, x-y inverse), each after an L2 flush."""
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        ms = np.zeros(3, dtype=np.float32)
+        _check("mf_time_kernels", _lib.mf_time_kernels(self.h, _ptr(m), reps, _ptr(ms)))
+        return ms.astype(np.float64)
+
+    def sync(self):
+        _check("mf_sync", _lib.mf_sync(self.h))

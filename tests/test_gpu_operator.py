@@ -1,0 +1,138 @@
+"""GPU parity of the single-application steps against the oracle: the
+constitutive update (Eq. eq:lineariz), the projected operator G*(K:x)
+(Eq. linequil2ast with G* of Eq. eq:Gnewnew) and the FP64 residual.  One
+application involves no iteration, so FP64 must agree to 1e-12 relative."""
+import numpy as np
+import pytest
+
+from oracle import materials as omat, projector, solver as osolver
+from paper_1901_06531_gb300 import inputs
+
+from gpu_util import lib, neohooke_two_phase, polycrystal, rel
+
+pytestmark = pytest.mark.gpu
+
+MASKS = [np.zeros(9, np.uint8), np.ones(9, np.uint8),
+         np.array([0, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8)]
+# (nx, ny, nz): smallest grid, cubic, anisotropic with radix 3, odd nz, 3-stage
+# planes, a grid spanning many z-pass tiles
+SHAPES = [(4, 4, 2), (16, 16, 16), (12, 8, 6), (48, 36, 18), (24, 6, 9), (32, 64, 12)]
+
+
+def torch_field(a, dtype):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a).reshape(-1), dtype=dtype, device="cuda")
+
+
+def make(mf, shape_xyz, precision, model="nh", seed=0, scale=False):
+    nx, ny, nz = shape_xyz
+    shape = (nz, ny, nx)
+    ctx = mf.Context(nx, ny, nz, precision)
+    sc = inputs.lognormal_scale(shape, 0.3, seed + 7) if scale else None
+    if model == "nh":
+        ph, params = neohooke_two_phase(shape, seed)
+        ctx.set_material(mf.MF_NEOHOOKE, params, ph, scale=sc)
+        om = omat.Material(ph, omat.NEOHOOKE, params, scale=sc)
+    else:
+        g, params, R = polycrystal(shape, 5, seed)
+        ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R, scale=sc)
+        om = omat.Material(g, omat.SVK_CUBIC, params, R, scale=sc)
+    F = inputs.random_F(shape, seed + 1, 0.08)
+    ctx.set_F(F)
+    return ctx, om, F
+
+
+def K45_from_oracle(K):
+    out = np.empty((45,) + K.shape[2:])
+    t = 0
+    for a in range(9):
+        for b in range(a, 9):
+            out[t] = K[a, b]
+            t += 1
+    return out
+
+
+@pytest.mark.parametrize("model", ["nh", "svk"])
+@pytest.mark.parametrize("scale", [False, True])
+def test_constitutive_fp64(model, scale):
+    mf = lib()
+    ctx, om, F = make(mf, (12, 8, 6), mf.MF_FP64, model, seed=3, scale=scale)
+    ctx.constitutive()
+    Fg, Pg = ctx.get_fields()
+    P, K = om.PK(F)
+    assert rel(Pg, P) < 1e-13
+    assert rel(ctx.get_tangent(), K45_from_oracle(K)) < 1e-13
+
+
+def test_constitutive_fp32_tangent_is_rounded_fp64():
+    mf = lib()
+    ctx, om, F = make(mf, (8, 8, 4), mf.MF_FP32_INNER, "svk", seed=4)
+    ctx.constitutive()
+    _, Pg = ctx.get_fields()
+    P, K = om.PK(F)
+    assert rel(Pg, P) < 1e-13                      # P stays FP64
+    K45 = K45_from_oracle(K)
+    # FP64 tangent rounded once to FP32: within half an FP32 ulp (plus FP64 noise)
+    Kg = ctx.get_tangent()
+    assert np.all(np.abs(Kg - K45) <= 6.0e-8 * np.abs(K45) + 1e-12 * np.max(np.abs(K45)))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mi", range(len(MASKS)))
+def test_matvec_fp64(shape, mi):
+    import torch
+    mf = lib()
+    ctx, om, F = make(mf, shape, mf.MF_FP64, "nh" if mi != 1 else "svk", seed=5)
+    ctx.constitutive()
+    nx, ny, nz = shape
+    x = inputs.random_field((nz, ny, nx), 6)
+    xt = torch_field(x, torch.float64)
+    yt = torch.full_like(xt, float("nan"))
+    ctx.matvec(xt, yt, MASKS[mi])
+    ctx.sync()
+    _, K = om.PK(F)
+    ref = osolver.matvec(K, x, MASKS[mi])
+    got = yt.cpu().numpy().reshape(ref.shape)
+    assert np.all(np.isfinite(got))
+    assert rel(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES[:4])
+def test_matvec_fp32(shape):
+    import torch
+    mf = lib()
+    ctx, om, F = make(mf, shape, mf.MF_FP32_INNER, "svk", seed=8)
+    ctx.constitutive()
+    nx, ny, nz = shape
+    x = inputs.random_field((nz, ny, nx), 9)
+    xt = torch_field(x, torch.float32)
+    yt = torch.full_like(xt, float("nan"))
+    ctx.matvec(xt, yt, MASKS[2])
+    ctx.sync()
+    _, K = om.PK(F)
+    # same inputs as the FP32 path sees: x and K rounded to FP32
+    x32 = x.astype(np.float32).astype(np.float64)
+    K32 = K.astype(np.float32).astype(np.float64)
+    ref = osolver.matvec(K32, x32, MASKS[2])
+    got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
+    # FP32 transform error ~ eps32 * log2(N) relative to the field norm
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mi", range(len(MASKS)))
+def test_residual_fp64(shape, mi):
+    import torch
+    mf = lib()
+    ctx, om, F = make(mf, shape, mf.MF_FP64, "nh", seed=10)
+    ctx.constitutive()
+    pbar = np.array([0.05, 0.01, 0.0, -0.01, 0.02, 0.0, 0.0, 0.0, -0.03])
+    nx, ny, nz = shape
+    b = torch.full((9 * nx * ny * nz,), float("nan"), dtype=torch.float64, device="cuda")
+    meanP = ctx.residual(MASKS[mi], pbar, b)
+    P, _ = om.PK(F)
+    ref = osolver.residual(P, MASKS[mi], pbar)
+    got = b.cpu().numpy().reshape(ref.shape)
+    assert rel(got, ref) < 1e-12
+    np.testing.assert_allclose(meanP, P.reshape(9, -1).mean(1), rtol=0, atol=1e-14)

@@ -1,0 +1,177 @@
+"""GPU parity of converged load histories against the oracle (Sec. 2.3 mixed
+control, Eq. linequil2ast), the control exactness at every step, the FP32
+inner / FP64 outer mode, and the failure statuses."""
+import numpy as np
+import pytest
+
+from oracle import materials as omat, solver as osolver
+from paper_1901_06531_gb300 import inputs
+
+from gpu_util import lib, polycrystal, rel
+
+pytestmark = pytest.mark.gpu
+
+CASE1 = np.array([0, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8)
+
+
+def sphere_cell(mf, n, precision, r_frac=0.25):
+    ph = inputs.centred_sphere(n, r_frac)
+    params = np.array([[1.0, 2.0], [10.0, 20.0]])
+    ctx = mf.Context(n, n, n, precision)
+    ctx.set_material(mf.MF_NEOHOOKE, params, ph)
+    return ctx, omat.Material(ph, omat.NEOHOOKE, params)
+
+
+def check_control(out, mask, target, tol_p, tol_f):
+    for k in range(mask.shape[0]):
+        s = mask[k] == 1
+        if s.any():
+            assert np.max(np.abs(out["Pbar"][k][s] - target[k][s])) < tol_p
+        if (~s).any():
+            assert np.max(np.abs(out["Fbar"][k][~s] - target[k][~s])) < tol_f
+
+
+def test_uniaxial_stress_ramp_16_fp64():
+    """16^3 sphere, all nine components stress controlled, P11 -> 0.1 in 5
+    steps, Newton tol 1e-8, CG tol 1e-10."""
+    mf = lib()
+    ctx, om = sphere_cell(mf, 16, mf.MF_FP64)
+    mask, target = inputs.history_uniaxial_stress_ramp(5, 0.1)
+    out = ctx.solve(mask, target, 1e-8, 1e-10)
+    ref = osolver.solve(om, mask, target, 1e-8, 1e-10)
+    assert rel(out["Fbar"], ref["Fbar"]) < 1e-10
+    assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-10
+    F, P = ctx.get_fields()
+    assert rel(F, ref["F"]) < 1e-8
+    np.testing.assert_array_equal(out["newton"], ref["newton"])
+    assert np.all(np.abs(out["cg"] - ref["cg"]) <= 2 * out["newton"])
+    check_control(out, mask, target, 1e-12, 1e-14)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (12, 8, 6)])
+def test_mixed_control_tight_fp64(shape):
+    """Converged FP64 solve at Newton tol 1e-10 / CG tol 1e-12: fields agree
+    with the oracle to 1e-10 relative."""
+    mf = lib()
+    nx, ny, nz = shape
+    ph = inputs.periodic_sphere_phase((nz, ny, nx), [(nx / 2, ny / 2, nz / 2)], 0.3 * nz)
+    params = np.array([[1.0, 2.0], [10.0, 20.0]])
+    ctx = mf.Context(nx, ny, nz, mf.MF_FP64)
+    ctx.set_material(mf.MF_NEOHOOKE, params, ph)
+    om = omat.Material(ph, omat.NEOHOOKE, params)
+    mask, target = inputs.history_mixed_strain11(3, 1.05)
+    out = ctx.solve(mask, target, 1e-10, 1e-12)
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    F, P = ctx.get_fields()
+    assert rel(F, ref["F"]) < 1e-10
+    assert rel(P, ref["P"]) < 1e-10
+    assert rel(out["Pbar"], ref["Pbar"]) < 1e-10
+    check_control(out, mask, target, 1e-12, 1e-14)
+
+
+def test_polycrystal_cyclic_fp64():
+    """SVK cubic polycrystal, cyclic stress with the rigid rotation fixed by
+    F12 = F13 = F23 = 0 (the paper's case (1) pattern)."""
+    mf = lib()
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 31)
+    ctx = mf.Context(n, n, n, mf.MF_FP64)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    om = omat.Material(g, omat.SVK_CUBIC, params, R)
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(8, 0.2))
+    out = ctx.solve(mask, target, 1e-8, 1e-10)
+    ref = osolver.solve(om, mask, target, 1e-8, 1e-10)
+    assert rel(out["Fbar"], ref["Fbar"]) < 1e-10
+    assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-10
+    check_control(out, mask, target, 1e-11, 1e-14)
+
+
+def test_fp32_inner_matches_fp64_oracle():
+    """FP32 inner CG with FP64 residual and Newton update: converged averages
+    and fields against the FP64 oracle at the same Newton tolerance."""
+    mf = lib()
+    ctx, om = sphere_cell(mf, 16, mf.MF_FP32_INNER)
+    mask, target = inputs.history_uniaxial_stress_ramp(5, 0.1)
+    out = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    F, P = ctx.get_fields()
+    assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
+    assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-9
+    assert rel(F, ref["F"]) < 1e-8
+    check_control(out, mask, target, 1e-9, 1e-14)
+
+
+def test_fp32_inner_polycrystal():
+    mf = lib()
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 41)
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    om = omat.Material(g, omat.SVK_CUBIC, params, R)
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(4, 0.2))
+    out = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    F, _ = ctx.get_fields()
+    assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
+    assert rel(F, ref["F"]) < 1e-8
+
+
+def test_radix3_grid_solve():
+    mf = lib()
+    nx, ny, nz = 24, 12, 18
+    shape = (nz, ny, nx)
+    ph = inputs.periodic_sphere_phase(shape, [(12, 6, 9)], 4.0)
+    params = np.array([[1.0, 2.0], [5.0, 10.0]])
+    ctx = mf.Context(nx, ny, nz, mf.MF_FP64)
+    ctx.set_material(mf.MF_NEOHOOKE, params, ph)
+    om = omat.Material(ph, omat.NEOHOOKE, params)
+    mask = CASE1[None].copy()
+    target = np.array([[1.03, 0, 0, 0, 0, 0, 0, 0, 0]])
+    out = ctx.solve(mask, target, 1e-10, 1e-12)
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    F, _ = ctx.get_fields()
+    assert rel(F, ref["F"]) < 1e-10
+
+
+def test_status_nonpositive_J():
+    mf = lib()
+    ctx, _ = sphere_cell(mf, 8, mf.MF_FP64)
+    F = inputs.random_F((8, 8, 8), 1, 0.01)
+    F[8, 3, 3, 3] = -1.0        # one inverted voxel, planted on the host
+    ctx.set_F(F)
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.constitutive()
+    assert e.value.status == mf.MF_NONPOSITIVE_J
+
+
+def test_status_not_converged_and_invalid():
+    mf = lib()
+    ctx, _ = sphere_cell(mf, 8, mf.MF_FP64)
+    mask, target = inputs.history_uniaxial_stress_ramp(1, 0.1)
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.solve(mask, target, 1e-8, 1e-10, max_cg=1)
+    assert e.value.status == mf.MF_NOT_CONVERGED
+    ctx.set_F(None)
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.solve(mask, target, 1e-8, 1e-10, max_newton=1)
+    assert e.value.status == mf.MF_NOT_CONVERGED
+    bad = mask.copy(); bad[0, 0] = 2
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.solve(bad, target)
+    assert e.value.status == mf.MF_INVALID_ARG
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.set_material(mf.MF_NEOHOOKE, np.array([[1.0, 2.0]]), np.ones((8, 8, 8), np.int32))
+    assert e.value.status == mf.MF_INVALID_ARG
+
+
+def test_status_cg_breakdown_rotation_mode():
+    """Full stress control in compression leaves the rigid rotation with
+    negative curvature; the library reports it instead of diverging."""
+    mf = lib()
+    g, params, R = polycrystal((6, 6, 6), 5, 50)
+    ctx = mf.Context(6, 6, 6, mf.MF_FP64)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    mask, target = inputs.history_uniaxial_stress_ramp(2, -0.2)
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.solve(mask, target, 1e-8, 1e-10, max_cg=2000)
+    assert e.value.status in (mf.MF_CG_BREAKDOWN, mf.MF_NOT_CONVERGED)
