@@ -222,6 +222,28 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU path
+def run_matvec_only(args):
+    """Profiling driver: the 128^3 polycrystal tangent at the first load step,
+    then `--matvec-only` applications of the FP32 (or FP64) projected operator."""
+    import torch
+    from paper_1901_06531_gb300 import build
+    build.build()
+    from paper_1901_06531_gb300 import mixfft as mf
+    g, params, R, mask, target = workload()
+    n = N1
+    prec = mf.MF_FP64 if args.fp64 else mf.MF_FP32_INNER
+    ctx = mf.Context(n, n, n, prec)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    ctx.constitutive()
+    x = torch.randn(9 * n ** 3, dtype=ctx.inner_dtype, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.matvec_only):
+        ctx.matvec(x, y, mask[0])
+    torch.cuda.synchronize()
+    print(json.dumps({"matvec_only": args.matvec_only, "fp64": bool(args.fp64),
+                      "y_norm": float(y.double().norm())}))
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -397,8 +419,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matvec-only", type=int, default=0,
+                    help="profiling driver: run this many projected-operator applications only")
+    ap.add_argument("--fp64", action="store_true", help="with --matvec-only: the FP64 operator")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.matvec_only:
+        run_matvec_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -167,6 +167,9 @@ struct Scalars {
   double meanP[9];
   double dF2max;      // max_v |dF_v|^2 of the last Newton update
   double meanF_new[9];
+  double T[9];        // sum_v P_v F_v^T   (rotation moments, row-major)
+  double S[9];        // sum_v F_v F_v^T
+  double What[9];     // skew matrix of the last null-rotation projection
   int flags;          // bit 0: breakdown, bit 1: nonpositive J, bit 2: non-finite
   int done;           // CG converged
   int pad[2];

@@ -63,13 +63,26 @@ cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,
                                 const Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f32, long long n9,
-                              const double* b_partials, int nb_partials, double tol_cg,
-                              double cg_rel, long long N, Scalars* sc, cudaStream_t st);
+                              double* partials, int nblk, double tol_cg, double cg_rel, long long N,
+                              Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_alpha(const double* partials, int npart, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_update(void* x, void* r, const void* p, const void* Ap, bool f32,
                                 long long n9, double* partials, int nblk, Scalars* sc,
                                 cudaStream_t st);
 cudaError_t mf_launch_cg_direction(void* p, const void* r, bool f32, long long n9, const Scalars* sc,
                                    cudaStream_t st);
-cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, long long N, double* partials,
-                                    int nblk, Scalars* sc, cudaStream_t st);
+// Null rotations: up to three skew generators W_k (row-major 3x3) with the
+// fields n_k = W_k F orthonormal.
+struct Defl {
+  int m;
+  double W[3][9];
+};
+cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool defl, long long N,
+                                    double* partials, int nblk, Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_moments(const double* F, const double* P, long long N, double* partials, int nblk,
+                              Scalars* sc, cudaStream_t st);
+// Removes from y (9N, double or float) its components along the n_k:
+// y -= What F with What = sum_k (n_k . y) W_k; What is kept in sc for reuse.
+cudaError_t mf_launch_defl_project(void* y, bool f32, bool apply, const double* F, long long N,
+                                   const Defl& d, double* partials, int nblk, Scalars* sc,
+                                   cudaStream_t st);

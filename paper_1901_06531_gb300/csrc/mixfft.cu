@@ -51,6 +51,140 @@ bool smooth_size(int n) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Cyclic Jacobi eigen-decomposition of a symmetric m x m matrix (m <= 3):
+// on return A holds the eigenvalues on its diagonal, V the eigenvectors (columns).
+void jacobi_eig(int m, double A[3][3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += A[p][q] * A[p][q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        if (A[p][q] == 0.0) continue;
+        const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {   // A <- J^T A J
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+void skew_of(const double w[3], double W[9]) {
+  W[0] = 0; W[1] = -w[2]; W[2] = w[1];
+  W[3] = w[2]; W[4] = 0; W[5] = -w[0];
+  W[6] = -w[1]; W[7] = w[0]; W[8] = 0;
+}
+
+// Rigid rotations of the cell that the linearised problem cannot see.
+// A rotation increment W (skew) gives the compatible field n = W F; it is
+// admissible when (W <F>)_ij = 0 on every strain-controlled component.  By
+// objectivity (P(QF) = Q P(F)) the curvature n_a . A n_b equals
+// tr(W_a^T W_b T), T = sum_v P_v F_v^T, and n_a . n_b = tr(W_a^T W_b S),
+// S = sum_v F_v F_v^T.  Admissible rotations whose curvature is below
+// tau * kappa (kappa a stiffness scale) are returned with n_k orthonormal.
+Defl null_rotations(const double meanF[9], const uint8_t* mask, const double T[9], const double S[9],
+                    double kappa, double tau) {
+  Defl d;
+  memset(&d, 0, sizeof(d));
+  double Wg[3][9];
+  for (int a = 0; a < 3; ++a) {
+    double w[3] = {0, 0, 0};
+    w[a] = 1.0;
+    skew_of(w, Wg[a]);
+  }
+  // admissibility: C^T C over the strain-controlled components
+  double CtC[3][3] = {{0}};
+  for (int c = 0; c < 9; ++c) {
+    if (mask[c]) continue;
+    const int i = c / 3, j = c % 3;
+    double row[3];
+    for (int a = 0; a < 3; ++a)
+      row[a] = Wg[a][3 * i] * meanF[j] + Wg[a][3 * i + 1] * meanF[3 + j] + Wg[a][3 * i + 2] * meanF[6 + j];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) CtC[a][b] += row[a] * row[b];
+  }
+  double V[3][3];
+  jacobi_eig(3, CtC, V);
+  double Z[3][3];
+  int m = 0;
+  for (int k = 0; k < 3; ++k)
+    if (fabs(CtC[k][k]) <= 1e-20)
+      { for (int a = 0; a < 3; ++a) Z[a][m] = V[a][k]; ++m; }
+  if (m == 0) return d;
+  auto trWW = [&](const double* Wa, const double* Wb, const double* M) {
+    // tr(Wa^T Wb M) = sum_ij Wa_ij (Wb M)_ij
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double wm = 0.0;
+        for (int k = 0; k < 3; ++k) wm += Wb[3 * i + k] * M[3 * k + j];
+        s += Wa[3 * i + j] * wm;
+      }
+    return s;
+  };
+  double R[3][3], G[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      R[a][b] = 0.5 * (trWW(Wg[a], Wg[b], T) + trWW(Wg[b], Wg[a], T));
+      G[a][b] = trWW(Wg[a], Wg[b], S);
+    }
+  double Rz[3][3] = {{0}}, Gz[3][3] = {{0}};
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          Rz[p][q] += Z[a][p] * R[a][b] * Z[b][q];
+          Gz[p][q] += Z[a][p] * G[a][b] * Z[b][q];
+        }
+  // G-orthonormal eigenvectors of Rz v = lambda Gz v: Gz = Q g Q^T, then the
+  // standard problem for g^-1/2 Q^T Rz Q g^-1/2
+  double Qg[3][3];
+  jacobi_eig(m, Gz, Qg);
+  double H[3][3] = {{0}}, B[3][3];
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q) {
+      double s = 0.0;
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) s += Qg[a][p] * Rz[a][b] * Qg[b][q];
+      H[p][q] = s / sqrt(Gz[p][p] * Gz[q][q]);
+    }
+  double U[3][3];
+  jacobi_eig(m, H, U);
+  for (int k = 0; k < m; ++k) {
+    if (fabs(H[k][k]) > tau * kappa) continue;
+    for (int p = 0; p < m; ++p) B[p][0] = 0.0;
+    double v[3] = {0, 0, 0};        // coefficients in the Z basis
+    for (int p = 0; p < m; ++p) {
+      double s = 0.0;
+      for (int q = 0; q < m; ++q) s += Qg[p][q] * U[q][k] / sqrt(Gz[q][q]);
+      v[p] = s;
+    }
+    double w[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+      for (int p = 0; p < m; ++p) w[a] += Z[a][p] * v[p];
+    skew_of(w, d.W[d.m]);
+    ++d.m;
+  }
+  return d;
+}
+
 }  // namespace
 
 struct mf_ctx {
@@ -69,6 +203,7 @@ struct mf_ctx {
   size_t npart;
   // material
   int model = -1, nphase = 0;
+  double kappa = 1.0;      // stiffness scale of the material (null-rotation test)
   bool has_scale = false;
   bool have_K = false;
 
@@ -177,14 +312,24 @@ int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max
   void* Ap = c->ws + c->oAp;
   Scalars* sc = c->at<Scalars>(c->osc);
   double* part = c->at<double>(c->opart);
-  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, p, f32, n9, part, 9 * c->nz, tol_cg,
-                                    f32 ? cg_rel : 0.0, c->N, sc, c->st);
+  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, p, f32, n9, part, kPointwiseBlocks,
+                                    tol_cg, f32 ? cg_rel : 0.0, c->N, sc, c->st);
   if (e != cudaSuccess) return MF_CUDA_ERROR;
   *its = 0;
   Scalars h;
   for (;;) {
     int s = read_scalars(c, &h);
     if (s) return s;
+    if (f32 && (h.flags & MF_FLAG_BREAKDOWN) && !(h.flags & ~MF_FLAG_BREAKDOWN) && *its > 1) {
+      // FP32 inner solve: a direction of non-positive curvature after some
+      // progress ends the inner solve; the FP64 outer iteration continues
+      // from the current iterate (alpha was set to 0 for that direction).
+      int zero = 0;
+      if (cudaMemcpyAsync(&sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+          cudaStreamSynchronize(c->st) != cudaSuccess)
+        return MF_CUDA_ERROR;
+      return MF_OK;
+    }
     s = flags_status(h.flags);
     if (s) return s;
     if (h.done) return MF_OK;
@@ -392,6 +537,15 @@ int mf_set_material(mf_ctx* c, int model, int nphase, const double* params, cons
     e = cudaMemcpyAsync(c->ws + c->oscale, scale, c->N * sizeof(double), cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return MF_CUDA_ERROR;
+  double kap = 0.0;
+  for (int p = 0; p < nphase; ++p)
+    kap = fmax(kap, model == MF_NEOHOOKE ? fabs(params[2 * p]) : fabs(params[3 * p + 2]));
+  double smax = 1.0;
+  if (scale) {
+    smax = 0.0;
+    for (long long v = 0; v < c->N; ++v) smax = fmax(smax, fabs(scale[v]));
+  }
+  c->kappa = kap * smax > 0 ? kap * smax : 1.0;
   c->model = model;
   c->nphase = nphase;
   c->has_scale = scale != nullptr;
@@ -506,12 +660,31 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
       if (nn >= max_newton) return MF_NOT_CONVERGED;
       s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores));
       if (s) return s;
+      Defl defl;
+      defl.m = 0;
+      if (c->f32()) {
+        // FP32 inner solves: remove the null rigid rotations from the
+        // right-hand side and from the correction (their FP64 rounding noise
+        // would otherwise be amplified by a near-zero curvature)
+        if (mf_launch_moments(F, c->at<double>(c->oP), N, part, kPointwiseBlocks, sc, c->st) !=
+            cudaSuccess)
+          return MF_CUDA_ERROR;
+        s = read_scalars(c, &h);
+        if (s) return s;
+        defl = null_rotations(h.meanF, m, h.T, h.S, c->kappa, 1e-6);
+        if (defl.m > 0 && mf_launch_defl_project(c->at<double>(c->ob), false, true, F, N, defl, part,
+                                                 kPointwiseBlocks, sc, c->st) != cudaSuccess)
+          return MF_CUDA_ERROR;
+      }
       int its = 0;
       s = run_cg(c, m, tol_cg, cg_rel, max_cg, &its);
       ncg += its;
       if (s) return s;
-      if (mf_launch_newton_update(F, c->ws + c->ox, c->f32(), N, part, kPointwiseBlocks, sc, c->st) !=
-          cudaSuccess)
+      if (defl.m > 0 && mf_launch_defl_project(c->ws + c->ox, true, false, F, N, defl, part,
+                                               kPointwiseBlocks, sc, c->st) != cudaSuccess)
+        return MF_CUDA_ERROR;
+      if (mf_launch_newton_update(F, c->ws + c->ox, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc,
+                                  c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
       s = read_scalars(c, &h);
       if (s) return s;

@@ -256,15 +256,21 @@ __global__ void k_predictor(double* __restrict__ F, long long N, Load9 ld, const
 }
 
 template <typename T>
-__global__ void k_cg_init(const double* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                          T* __restrict__ p, long long n9) {
+__global__ void __launch_bounds__(kRedThreads) k_cg_init(const double* __restrict__ b, T* __restrict__ x,
+                                                         T* __restrict__ r, T* __restrict__ p, long long n9,
+                                                         double* __restrict__ partials) {
+  __shared__ double tot[1];
+  double acc[1] = {0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n9;
        i += (long long)gridDim.x * blockDim.x) {
     const T v = (T)b[i];
     r[i] = v;
     p[i] = v;
     x[i] = (T)0;
+    acc[0] += (double)v * (double)v;
   }
+  block_sum<1>(acc, tot);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_fin_cg_init(const double* __restrict__ partials, int npart,
@@ -338,10 +344,12 @@ __global__ void k_cg_direction(T* __restrict__ p, const T* __restrict__ r, long 
     p[i] = r[i] + beta * p[i];
 }
 
-template <typename T>
+// F += x, or with DEFL F += x - What F (What from the projection of x).
+template <typename T, bool DEFL>
 __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restrict__ F,
                                                                const T* __restrict__ x, long long N,
-                                                               double* __restrict__ partials) {
+                                                               double* __restrict__ partials,
+                                                               const Scalars* sc) {
   __shared__ double tot[10];
   double acc[10];
 #pragma unroll
@@ -350,13 +358,23 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
     double n2 = 0.0;
+    double f[9], d[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; d[c] = (double)x[c * N + v]; }
+    if (DEFL) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          d[3 * i + j] -= sc->What[3 * i] * f[j] + sc->What[3 * i + 1] * f[3 + j] +
+                          sc->What[3 * i + 2] * f[6 + j];
+    }
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      const double d = (double)x[c * N + v];
-      const double fn = F[c * N + v] + d;
+      const double fn = f[c] + d[c];
       F[c * N + v] = fn;
       acc[c] += fn;
-      n2 += d * d;
+      n2 += d[c] * d[c];
     }
     mx = fmax(mx, n2);
   }
@@ -385,6 +403,108 @@ __global__ void __launch_bounds__(kRedThreads) k_fin_newton(const double* __rest
   if (threadIdx.x == 0) {
     sc->dF2max = m;
     if (!isfinite(m)) sc->flags |= MF_FLAG_NONFINITE;
+  }
+}
+
+// Rotation moments T = sum_v P_v F_v^T and S = sum_v F_v F_v^T (row-major).
+__global__ void __launch_bounds__(kRedThreads) k_moments(const double* __restrict__ F,
+                                                         const double* __restrict__ P, long long N,
+                                                         double* __restrict__ partials) {
+  __shared__ double tot[18];
+  double acc[18];
+#pragma unroll
+  for (int c = 0; c < 18; ++c) acc[c] = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    double f[9], p[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; p[c] = P[c * N + v]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        acc[3 * i + j] += p[3 * i] * f[3 * j] + p[3 * i + 1] * f[3 * j + 1] + p[3 * i + 2] * f[3 * j + 2];
+        acc[9 + 3 * i + j] += f[3 * i] * f[3 * j] + f[3 * i + 1] * f[3 * j + 1] + f[3 * i + 2] * f[3 * j + 2];
+      }
+  }
+  block_sum<18>(acc, tot);
+  if (threadIdx.x < 18) partials[blockIdx.x * 18 + threadIdx.x] = tot[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_fin_moments(const double* __restrict__ partials,
+                                                             int nblk, Scalars* sc) {
+  __shared__ double shm[kRedThreads];
+  for (int col = 0; col < 18; ++col) {
+    const double s = column_sum(partials, nblk, 18, col, shm);
+    if (threadIdx.x == 0) {
+      if (col < 9) sc->T[col] = s;
+      else sc->S[col - 9] = s;
+    }
+  }
+}
+
+// B = sum_v y_v F_v^T, the moments that give n_k . y = W_k : B.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_defl_reduce(const T* __restrict__ y,
+                                                             const double* __restrict__ F, long long N,
+                                                             double* __restrict__ partials) {
+  __shared__ double tot[9];
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    double f[9], q[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; q[c] = (double)y[c * N + v]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        acc[3 * i + j] += q[3 * i] * f[3 * j] + q[3 * i + 1] * f[3 * j + 1] + q[3 * i + 2] * f[3 * j + 2];
+  }
+  block_sum<9>(acc, tot);
+  if (threadIdx.x < 9) partials[blockIdx.x * 9 + threadIdx.x] = tot[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_defl_fin(const double* __restrict__ partials, int nblk,
+                                                          Defl d, Scalars* sc) {
+  __shared__ double shm[kRedThreads];
+  __shared__ double B[9];
+  for (int col = 0; col < 9; ++col) {
+    const double s = column_sum(partials, nblk, 9, col, shm);
+    if (threadIdx.x == 0) B[col] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < d.m; ++k) {
+      double ck = 0.0;
+      for (int t = 0; t < 9; ++t) ck += d.W[k][t] * B[t];
+      for (int t = 0; t < 9; ++t) W[t] += ck * d.W[k][t];
+    }
+    for (int t = 0; t < 9; ++t) sc->What[t] = W[t];
+  }
+}
+
+template <typename T>
+__global__ void k_defl_apply(T* __restrict__ y, const double* __restrict__ F, long long N,
+                             const Scalars* sc) {
+  double W[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) W[t] = sc->What[t];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    double f[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[c * N + v];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double corr = W[3 * i] * f[j] + W[3 * i + 1] * f[3 + j] + W[3 * i + 2] * f[6 + j];
+        y[(3 * i + j) * N + v] = (T)((double)y[(3 * i + j) * N + v] - corr);
+      }
   }
 }
 
@@ -426,12 +546,11 @@ cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, co
 }
 
 cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f32, long long n9,
-                              const double* b_partials, int nb_partials, double tol_cg,
-                              double cg_rel, long long N, Scalars* sc, cudaStream_t st) {
-  const int g = grid_for(n9) > 4096 ? 4096 : grid_for(n9);
-  if (f32) k_cg_init<float><<<g, kRedThreads, 0, st>>>(b, (float*)x, (float*)r, (float*)p, n9);
-  else k_cg_init<double><<<g, kRedThreads, 0, st>>>(b, (double*)x, (double*)r, (double*)p, n9);
-  k_fin_cg_init<<<1, kRedThreads, 0, st>>>(b_partials, nb_partials, tol_cg, cg_rel, N, sc);
+                              double* partials, int nblk, double tol_cg, double cg_rel, long long N,
+                              Scalars* sc, cudaStream_t st) {
+  if (f32) k_cg_init<float><<<nblk, kRedThreads, 0, st>>>(b, (float*)x, (float*)r, (float*)p, n9, partials);
+  else k_cg_init<double><<<nblk, kRedThreads, 0, st>>>(b, (double*)x, (double*)r, (double*)p, n9, partials);
+  k_fin_cg_init<<<1, kRedThreads, 0, st>>>(partials, nblk, tol_cg, cg_rel, N, sc);
   g_mf_launches += 2;
   return cudaGetLastError();
 }
@@ -465,11 +584,37 @@ cudaError_t mf_launch_cg_direction(void* p, const void* r, bool f32, long long n
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, long long N, double* partials,
-                                    int nblk, Scalars* sc, cudaStream_t st) {
-  if (f32) k_newton_update<float><<<nblk, kRedThreads, 0, st>>>(F, (const float*)x, N, partials);
-  else k_newton_update<double><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials);
+cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool defl, long long N,
+                                    double* partials, int nblk, Scalars* sc, cudaStream_t st) {
+  if (f32 && defl) k_newton_update<float, true><<<nblk, kRedThreads, 0, st>>>(F, (const float*)x, N, partials, sc);
+  else if (f32) k_newton_update<float, false><<<nblk, kRedThreads, 0, st>>>(F, (const float*)x, N, partials, sc);
+  else if (defl) k_newton_update<double, true><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials, sc);
+  else k_newton_update<double, false><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials, sc);
   k_fin_newton<<<1, kRedThreads, 0, st>>>(partials, nblk, N, sc);
   g_mf_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_moments(const double* F, const double* P, long long N, double* partials, int nblk,
+                              Scalars* sc, cudaStream_t st) {
+  k_moments<<<nblk, kRedThreads, 0, st>>>(F, P, N, partials);
+  k_fin_moments<<<1, kRedThreads, 0, st>>>(partials, nblk, sc);
+  g_mf_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_defl_project(void* y, bool f32, bool apply, const double* F, long long N,
+                                   const Defl& d, double* partials, int nblk, Scalars* sc,
+                                   cudaStream_t st) {
+  if (f32) k_defl_reduce<float><<<nblk, kRedThreads, 0, st>>>((const float*)y, F, N, partials);
+  else k_defl_reduce<double><<<nblk, kRedThreads, 0, st>>>((const double*)y, F, N, partials);
+  k_defl_fin<<<1, kRedThreads, 0, st>>>(partials, nblk, d, sc);
+  g_mf_launches += 2;
+  if (apply) {
+    const int g = grid_for(N) > 4096 ? 4096 : grid_for(N);
+    if (f32) k_defl_apply<float><<<g, kRedThreads, 0, st>>>((float*)y, F, N, sc);
+    else k_defl_apply<double><<<g, kRedThreads, 0, st>>>((double*)y, F, N, sc);
+    g_mf_launches += 1;
+  }
   return cudaGetLastError();
 }
