@@ -37,13 +37,15 @@ TOL_NEWTON, TOL_CG, CG_REL = 1e-8, 1e-10, 1e-4
 WORKLOAD = ("polycrystal 128^3, 200-grain Voronoi, SVK cubic (168/121/75 GPa) rotated per grain, "
             "cyclic stress P11 +-0.2 GPa in 20 steps (F12=F13=F23=0), FP32 inner / FP64 outer")
 METRIC = "Newton load steps/s at 128^3 (FP32-inner/FP64-outer), polycrystal cyclic stress control"
-# algorithmic bytes per voxel of each inner-operator kernel (FP32): x-y forward
-# reads x (9 x 4 B) and the packed tangent (45 x 4 B) and writes the half
-# spectrum (9 x 0.5 x 8 B); the z-pass reads and writes the spectrum; the x-y
-# inverse reads the spectrum and the dot operand p and writes y.
-KERNELS = ["xy_forward_tangent", "zpass_projection", "xy_inverse_dot"]
-ALGO_BYTES_F32 = [36 + 180 + 36, 36 + 36, 36 + 36 + 36]
-ALGO_BYTES_F64 = [72 + 360 + 72, 72 + 72, 72 + 72 + 72]
+# algorithmic bytes per voxel of each kernel of one CG iteration.  FP32 (matrix-
+# free tangent): the tangent pass reads r, p', x, H = F - I (9 x 4 B each) and
+# the phase id (4 B) and writes p, x, t; the x-y forward reads t and writes the
+# half spectrum (9 x 0.5 x 8 B); the z-pass reads and writes the spectrum; the
+# x-y inverse reads the spectrum and r and writes r.  FP64 (packed tangent):
+# the tangent pass reads r, p', x (9 x 8 B each) and K (45 x 8 B), writes p, x, t.
+KERNELS = ["tangent_cg", "xy_forward", "zpass_projection", "xy_inverse_residual"]
+ALGO_BYTES_F32 = [4 * 36 + 4 + 3 * 36, 36 + 36, 36 + 36, 3 * 36]
+ALGO_BYTES_F64 = [3 * 72 + 360 + 3 * 72, 72 + 72, 72 + 72, 3 * 72]
 
 
 def workload(n=N1, ngrains=NGRAINS, seed=SEED):

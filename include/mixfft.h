@@ -125,8 +125,10 @@ int mf_constitutive(mf_ctx* ctx);
 int mf_get_tangent(mf_ctx* ctx, double* K45_host);
 
 /* Projected tangent product y = G*(K : x) (left side of Eq. linequil2ast,
- * G* of Eq. eq:Gnewnew with the given mask), using the tangent of the last
- * mf_constitutive.  x_dev, y_dev: device, 9N values of the context's inner
+ * G* of Eq. eq:Gnewnew with the given mask), using the tangent at the F of
+ * the last mf_constitutive: the packed FP64 tangent for MF_FP64, the
+ * matrix-free FP32 tangent (from F - I and the phase parameters) for
+ * MF_FP32_INNER.  x_dev, y_dev: device, 9N values of the context's inner
  * type (double for MF_FP64, float for MF_FP32_INNER); may not alias. */
 int mf_matvec(mf_ctx* ctx, const void* x_dev, void* y_dev, const uint8_t* mask);
 
@@ -137,12 +139,13 @@ int mf_matvec(mf_ctx* ctx, const void* x_dev, void* y_dev, const uint8_t* mask);
 int mf_residual(mf_ctx* ctx, const uint8_t* mask, const double* pbar, double* b_dev,
                 double* meanP_host);
 
-/* Benchmark hook: time the three kernels of the inner projected operator
- * (x-y forward with the tangent apply, z-pass with G-hat-star, x-y inverse)
- * separately with CUDA events on the context's stream, each launch preceded
- * by an L2 flush (a memset of the 9N-double residual buffer).  Uses the
- * context's CG vectors as operands and the tangent of the last
- * mf_constitutive.  ms_out: host, 3 floats, mean milliseconds per launch. */
+/* Benchmark hook: time the four kernels of one CG iteration separately with
+ * CUDA events on the context's stream, each launch preceded by an L2 flush (a
+ * memset of the 9N-double residual buffer): [0] the tangent pass (direction
+ * and solution updates, K:p, p.Kp), [1] the x-y forward transform, [2] the
+ * z-pass with G-hat-star, [3] the x-y inverse transform with the residual
+ * update.  Operands are the context's CG vectors; needs the operator of the
+ * last mf_constitutive.  ms_out: host, 4 floats, mean milliseconds per launch. */
 int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
 
 /* Number of kernel launches the library has issued in this process (all

@@ -34,18 +34,36 @@ struct ZArgs {
 extern long long g_mf_launches;
 
 // transform.cu
-cudaError_t mf_launch_matvec_f64(const double* x, const double* K45, void* spec, double* y,
-                                 const double* w, double* partials, const XYArgs& xa,
-                                 const ZArgs& za, cudaStream_t st);
-cudaError_t mf_launch_matvec_f32(const float* x, const float* K45, void* spec, float* y,
-                                 const float* w, double* partials, const XYArgs& xa,
-                                 const ZArgs& za, cudaStream_t st);
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
                                const XYArgs& xa, const ZArgs& za, cudaStream_t st);
-// which: 0 x-y forward with tangent apply, 1 z-pass, 2 x-y inverse with dot
-cudaError_t mf_launch_matvec_part(int which, bool f32, const void* x, const void* K45, void* spec,
-                                  void* y, const void* w, double* partials, const XYArgs& xa,
-                                  const ZArgs& za, cudaStream_t st);
+// which: 0 x-y forward of t, 1 z-pass, 2 x-y inverse with the CG residual update
+cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spec, void* r,
+                                   double* partials, const XYArgs& xa, const ZArgs& za,
+                                   const Scalars* sc, cudaStream_t st);
+// y = G*(t): x-y forward of t, z-pass, x-y inverse.  inv_mode 0 stores y in
+// out; 3 performs the CG update out -= alpha y (alpha in sc) and writes the
+// block partials of out.out.
+cudaError_t mf_launch_project(bool f32, const void* t, void* spec, void* out, int inv_mode,
+                              double* partials, const XYArgs& xa, const ZArgs& za,
+                              const Scalars* sc, cudaStream_t st);
+
+// cg.cu
+struct TangentArgs {
+  const void* K45;       // packed tangent (TAN 0)
+  const float* H;        // F - I in FP32 (matrix-free tangents)
+  const int32_t* phase;
+  const float* table;    // neo-Hookean (mu, lam) or SVK 6x6 Voigt per phase, FP32
+  const float* scale;    // per-voxel scale or null
+};
+// tan: 0 packed K (FP64 or FP32), 1 neo-Hookean from H, 2 SVK from H (FP32).
+cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* x, bool f32, int tan,
+                              bool cg, const TangentArgs& ta, void* t, long long N, double* partials,
+                              int nblk, const Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, const Scalars* sc,
+                                 cudaStream_t st);
+cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_t st);
 
 // pointwise.cu
 struct MatArgs {
@@ -65,12 +83,6 @@ cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, co
 cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f32, long long n9,
                               double* partials, int nblk, double tol_cg, double cg_rel, long long N,
                               Scalars* sc, cudaStream_t st);
-cudaError_t mf_launch_cg_alpha(const double* partials, int npart, Scalars* sc, cudaStream_t st);
-cudaError_t mf_launch_cg_update(void* x, void* r, const void* p, const void* Ap, bool f32,
-                                long long n9, double* partials, int nblk, Scalars* sc,
-                                cudaStream_t st);
-cudaError_t mf_launch_cg_direction(void* p, const void* r, bool f32, long long n9, const Scalars* sc,
-                                   cudaStream_t st);
 // Null rotations: up to three skew generators W_k (row-major 3x3) with the
 // fields n_k = W_k F orthonormal.
 struct Defl {

@@ -198,14 +198,15 @@ struct mf_ctx {
   char* ws = nullptr;
   size_t ws_need = 0;
   // offsets into the workspace
-  size_t oF, oP, ob, oK, ox, or_, op, oAp, ospec, ophase, oscale, otable, opart, osc, ores,
-      oxpos, oxk, oxe, oyk, ozk, otw64, otw32;
+  size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
+      otable32, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32;
   size_t npart;
   // material
   int model = -1, nphase = 0;
   double kappa = 1.0;      // stiffness scale of the material (null-rotation test)
   bool has_scale = false;
-  bool have_K = false;
+  bool have_K = false;     // packed tangent of the current F is in the workspace
+  bool have_H = false;     // FP32 H = F - I of the current F is in the workspace
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   bool f32() const { return prec == MF_FP32_INNER; }
@@ -271,13 +272,19 @@ int flags_status(int flags) {
   return MF_OK;
 }
 
-int run_constitutive(mf_ctx* c, bool want_K) {
+// P (and optionally the packed K) at the current F, voxel averages of F and
+// P; with want_H the FP32 H = F - I for the matrix-free tangent.
+int run_constitutive(mf_ctx* c, bool want_K, bool want_H) {
   cudaError_t e = mf_launch_constitutive(c->at<double>(c->oF), c->at<double>(c->oP), c->ws + c->oK,
                                          c->f32(), want_K, mat_args(c), c->N, c->at<double>(c->opart),
                                          kPointwiseBlocks, c->at<Scalars>(c->osc), c->st);
-  if (want_K && e == cudaSuccess) c->have_K = true;
+  c->have_K = want_K && e == cudaSuccess;
+  if (e == cudaSuccess && want_H) e = mf_launch_make_H(c->at<double>(c->oF), c->at<float>(c->oH), c->N, c->st);
+  c->have_H = want_H && e == cudaSuccess;
   return cuda_status(e);
 }
+
+bool operator_ready(const mf_ctx* c) { return c->f32() ? c->have_H : c->have_K; }
 
 int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out) {
   ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N);
@@ -287,32 +294,57 @@ int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, 
                                         c->at<double>(c->opart), xy_args(c, false), za, c->st));
 }
 
-int run_matvec(mf_ctx* c, const void* x, void* y, const void* w, const uint8_t* mask) {
+TangentArgs tangent_args(const mf_ctx* c) {
+  TangentArgs ta;
+  ta.K45 = c->ws + c->oK;
+  ta.H = c->at<float>(c->oH);
+  ta.phase = c->at<int32_t>(c->ophase);
+  ta.table = c->at<float>(c->otable32);
+  ta.scale = c->has_scale ? c->at<float>(c->oscale32) : nullptr;
+  return ta;
+}
+
+// Tangent flavour of the inner solve: the packed tangent in FP64, the
+// matrix-free law in FP32.
+int tangent_kind(const mf_ctx* c) {
+  if (!c->f32()) return 0;
+  return c->model == MF_NEOHOOKE ? 1 : 2;
+}
+
+// y = G*(K : x) for a device vector x of the inner type.
+int run_matvec(mf_ctx* c, const void* x, void* y, const uint8_t* mask) {
   const ZArgs za = z_args(c, c->f32(), mask, 1.0 / (double)c->N);
   const XYArgs xa = xy_args(c, c->f32());
-  double* part = c->at<double>(c->opart);
-  cudaError_t e;
-  if (c->f32())
-    e = mf_launch_matvec_f32((const float*)x, (const float*)(c->ws + c->oK), c->ws + c->ospec,
-                             (float*)y, (const float*)w, part, xa, za, c->st);
-  else
-    e = mf_launch_matvec_f64((const double*)x, (const double*)(c->ws + c->oK), c->ws + c->ospec,
-                             (double*)y, (const double*)w, part, xa, za, c->st);
+  cudaError_t e = mf_launch_tangent(x, nullptr, nullptr, nullptr, c->f32(), tangent_kind(c), false,
+                                    tangent_args(c), c->ws + c->oAp, c->N, nullptr, kPointwiseBlocks,
+                                    nullptr, c->st);
+  if (e == cudaSuccess)
+    e = mf_launch_project(c->f32(), c->ws + c->oAp, c->ws + c->ospec, y, 0, nullptr, xa, za, nullptr,
+                          c->st);
   return cuda_status(e);
 }
 
 // One linear solve of Eq. (linequil2ast) by CG from dF = 0; the solution is
-// left in the x vector.  Returns a status and the iteration count.
+// left in the x vector.  Per iteration: the tangent pass (direction update,
+// lagging solution update, K:p and p.Kp), the three transform passes whose
+// last one updates the residual, and two one-block reductions.  Returns a
+// status and the iteration count.
 int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max_cg, int* its) {
   const bool f32 = c->f32();
   const long long n9 = 9 * c->N;
   void* x = c->ws + c->ox;
   void* r = c->ws + c->or_;
-  void* p = c->ws + c->op;
-  void* Ap = c->ws + c->oAp;
+  void* pa = c->ws + c->op;    // previous direction
+  void* pb = c->ws + c->op2;   // current direction
+  void* t = c->ws + c->oAp;
   Scalars* sc = c->at<Scalars>(c->osc);
   double* part = c->at<double>(c->opart);
-  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, p, f32, n9, part, kPointwiseBlocks,
+  const ZArgs za = z_args(c, f32, mask, 1.0 / (double)c->N);
+  const XYArgs xa = xy_args(c, f32);
+  const TangentArgs ta = tangent_args(c);
+  const int tk = tangent_kind(c);
+  const int nplanes = 9 * c->nz;
+  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, pa, f32, n9, part, kPointwiseBlocks,
                                     tol_cg, f32 ? cg_rel : 0.0, c->N, sc, c->st);
   if (e != cudaSuccess) return MF_CUDA_ERROR;
   *its = 0;
@@ -328,20 +360,23 @@ int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max
       if (cudaMemcpyAsync(&sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
           cudaStreamSynchronize(c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
-      return MF_OK;
+      break;
     }
     s = flags_status(h.flags);
     if (s) return s;
-    if (h.done) return MF_OK;
+    if (h.done) break;
     if (*its >= max_cg) return MF_NOT_CONVERGED;
-    s = run_matvec(c, p, Ap, p, mask);
-    if (s) return s;
-    if (mf_launch_cg_alpha(part, 9 * c->nz, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
-    if (mf_launch_cg_update(x, r, p, Ap, f32, n9, part, kPointwiseBlocks, sc, c->st) != cudaSuccess)
-      return MF_CUDA_ERROR;
-    if (mf_launch_cg_direction(p, r, f32, n9, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+    e = mf_launch_tangent(pa, r, pb, x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc, c->st);
+    if (e == cudaSuccess) e = mf_launch_fin_alpha(part, kPointwiseBlocks, sc, c->st);
+    if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, c->st);
+    if (e == cudaSuccess) e = mf_launch_fin_beta(part, nplanes, sc, c->st);
+    if (e != cudaSuccess) return MF_CUDA_ERROR;
+    void* tmp = pa; pa = pb; pb = tmp;
     ++*its;
   }
+  // the solution lags one direction behind: x += alpha p of the last iteration
+  if (*its > 0 && mf_launch_axpy_alpha(x, pa, f32, n9, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+  return MF_OK;
 }
 
 }  // namespace
@@ -398,11 +433,15 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->ox = take(9 * N * isz);
   c->or_ = take(9 * N * isz);
   c->op = take(9 * N * isz);
+  c->op2 = take(9 * N * isz);
   c->oAp = take(9 * N * isz);
+  c->oH = take(precision == MF_FP32_INNER ? 9 * N * sizeof(float) : 256);
   c->ospec = take(9 * (N / 2) * sizeof(double2));
   c->ophase = take(N * sizeof(int32_t));
   c->oscale = take(N * sizeof(double));
+  c->oscale32 = take(N * sizeof(float));
   c->otable = take((size_t)kMaxPhases * 36 * sizeof(double));
+  c->otable32 = take((size_t)kMaxPhases * 36 * sizeof(float));
   c->npart = (size_t)(kPointwiseBlocks > 9 * nz ? kPointwiseBlocks : 9 * nz) * 18;
   c->opart = take(c->npart * sizeof(double));
   c->osc = take(sizeof(Scalars));
@@ -529,8 +568,17 @@ int mf_set_material(mf_ctx* c, int model, int nphase, const double* params, cons
   if (scale)
     for (long long v = 0; v < c->N; ++v)
       if (!isfinite(scale[v])) return MF_INVALID_ARG;
+  std::vector<float> table32(table.begin(), table.end());
   cudaError_t e = cudaMemcpyAsync(c->ws + c->otable, table.data(), table.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->ws + c->otable32, table32.data(), table32.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, c->st);
+  std::vector<float> scale32;
+  if (scale) scale32.assign(scale, scale + c->N);
+  if (e == cudaSuccess && scale)
+    e = cudaMemcpyAsync(c->ws + c->oscale32, scale32.data(), c->N * sizeof(float), cudaMemcpyHostToDevice,
+                        c->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->ws + c->ophase, phase, c->N * sizeof(int32_t), cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess && scale)
@@ -577,7 +625,7 @@ int mf_constitutive(mf_ctx* c) {
   if (!c) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   if (c->model < 0) return MF_INVALID_ARG;
-  int s = run_constitutive(c, true);
+  int s = run_constitutive(c, true, c->f32());
   if (s) return s;
   Scalars h;
   s = read_scalars(c, &h);
@@ -608,8 +656,8 @@ int mf_get_tangent(mf_ctx* c, double* K45_host) {
 int mf_matvec(mf_ctx* c, const void* x_dev, void* y_dev, const uint8_t* mask) {
   if (!c || !x_dev || !y_dev || !mask || x_dev == y_dev) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
-  if (!c->have_K) return MF_INVALID_ARG;
-  return run_matvec(c, x_dev, y_dev, nullptr, mask);
+  if (!operator_ready(c)) return MF_INVALID_ARG;
+  return run_matvec(c, x_dev, y_dev, mask);
 }
 
 int mf_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b_dev, double* meanP_host) {
@@ -654,7 +702,7 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
     int s;
     for (;;) {
       const bool last = nn > 0 && ratio < tol_newton;
-      s = run_constitutive(c, !last);
+      s = run_constitutive(c, !last && !c->f32(), !last && c->f32());
       if (s) return s;
       if (last) break;
       if (nn >= max_newton) return MF_NOT_CONVERGED;
@@ -721,21 +769,33 @@ int mf_get_fields(mf_ctx* c, double* F_host, double* P_host) {
 int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
   if (!c || !mask || !ms_out || reps < 1) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
-  if (!c->have_K) return MF_INVALID_ARG;
-  const ZArgs za = z_args(c, c->f32(), mask, 1.0 / (double)c->N);
-  const XYArgs xa = xy_args(c, c->f32());
+  if (!operator_ready(c)) return MF_INVALID_ARG;
+  const bool f32 = c->f32();
+  const ZArgs za = z_args(c, f32, mask, 1.0 / (double)c->N);
+  const XYArgs xa = xy_args(c, f32);
+  const TangentArgs ta = tangent_args(c);
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  // operands: a CG state made of the context's vectors (values are not used
+  // for anything but timing); alpha = beta = 0 keeps them bounded
+  cudaError_t e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
+  if (e != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
-  cudaError_t e = cudaSuccess;
-  for (int which = 0; which < 3 && e == cudaSuccess; ++which) {
+  for (int which = 0; which < 4 && e == cudaSuccess; ++which) {
     double tot = 0.0;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-      e = cudaMemsetAsync(c->ws + c->ob, r & 0xff, 9 * c->N * sizeof(double), c->st);
+      e = cudaMemsetAsync(c->ws + c->ob, r & 0xff, 9 * c->N * sizeof(double), c->st);   // L2 flush
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
-      if (e == cudaSuccess)
-        e = mf_launch_matvec_part(which, c->f32(), c->ws + c->op, c->ws + c->oK, c->ws + c->ospec,
-                                  c->ws + c->oAp, c->ws + c->op, c->at<double>(c->opart), xa, za, c->st);
+      if (e == cudaSuccess) {
+        if (which == 0)
+          e = mf_launch_tangent(c->ws + c->op, c->ws + c->or_, c->ws + c->op2, c->ws + c->ox, f32,
+                                tangent_kind(c), true, ta, c->ws + c->oAp, c->N, part, kPointwiseBlocks,
+                                sc, c->st);
+        else
+          e = mf_launch_project_part(which - 1, f32, c->ws + c->oAp, c->ws + c->ospec, c->ws + c->or_,
+                                     part, xa, za, sc, c->st);
+      }
       if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;

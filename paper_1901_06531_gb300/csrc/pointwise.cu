@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(const double* __restric
        i += (long long)gridDim.x * blockDim.x) {
     const T v = (T)b[i];
     r[i] = v;
-    p[i] = v;
+    p[i] = (T)0;    // previous direction of the first iteration
     x[i] = (T)0;
     acc[0] += (double)v * (double)v;
   }
@@ -281,67 +281,13 @@ __global__ void __launch_bounds__(kRedThreads) k_fin_cg_init(const double* __res
   if (threadIdx.x == 0) {
     sc->rr = rr;
     sc->rr0 = rr;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
     double thr = tol_cg;
     if (cg_rel > 0.0) thr = fmax(tol_cg, cg_rel * sqrt(rr / (double)N));
     sc->thr2N = thr * thr * (double)N;
     sc->done = (rr <= sc->thr2N) ? 1 : 0;
   }
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restrict__ partials, int npart,
-                                                          Scalars* sc) {
-  __shared__ double shm[kRedThreads];
-  const double pAp = column_sum(partials, npart, 1, 0, shm);
-  if (threadIdx.x == 0) {
-    sc->pAp = pAp;
-    if (!(pAp > 0.0) || !isfinite(pAp)) {
-      sc->flags |= MF_FLAG_BREAKDOWN;
-      sc->alpha = 0.0;
-    } else {
-      sc->alpha = sc->rr / pAp;
-    }
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_cg_update(T* __restrict__ x, T* __restrict__ r,
-                                                           const T* __restrict__ p,
-                                                           const T* __restrict__ Ap, long long n9,
-                                                           double* __restrict__ partials,
-                                                           const Scalars* sc) {
-  __shared__ double tot[1];
-  const T alpha = (T)sc->alpha;
-  double acc[1] = {0.0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n9;
-       i += (long long)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const T rn = r[i] - alpha * Ap[i];
-    r[i] = rn;
-    acc[0] += (double)rn * (double)rn;
-  }
-  block_sum<1>(acc, tot);
-  if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ partials, int npart,
-                                                         Scalars* sc) {
-  __shared__ double shm[kRedThreads];
-  const double rr_new = column_sum(partials, npart, 1, 0, shm);
-  if (threadIdx.x == 0) {
-    if (!isfinite(rr_new)) sc->flags |= MF_FLAG_NONFINITE;
-    sc->beta = rr_new / sc->rr;
-    sc->rr = rr_new;
-    sc->done = (rr_new <= sc->thr2N) ? 1 : 0;
-  }
-}
-
-template <typename T>
-__global__ void k_cg_direction(T* __restrict__ p, const T* __restrict__ r, long long n9,
-                               const Scalars* sc) {
-  const T beta = (T)sc->beta;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n9;
-       i += (long long)gridDim.x * blockDim.x)
-    p[i] = r[i] + beta * p[i];
 }
 
 // F += x, or with DEFL F += x - What F (What from the projection of x).
@@ -552,35 +498,6 @@ cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f
   else k_cg_init<double><<<nblk, kRedThreads, 0, st>>>(b, (double*)x, (double*)r, (double*)p, n9, partials);
   k_fin_cg_init<<<1, kRedThreads, 0, st>>>(partials, nblk, tol_cg, cg_rel, N, sc);
   g_mf_launches += 2;
-  return cudaGetLastError();
-}
-
-cudaError_t mf_launch_cg_alpha(const double* partials, int npart, Scalars* sc, cudaStream_t st) {
-  k_cg_alpha<<<1, kRedThreads, 0, st>>>(partials, npart, sc);
-  g_mf_launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t mf_launch_cg_update(void* x, void* r, const void* p, const void* Ap, bool f32,
-                                long long n9, double* partials, int nblk, Scalars* sc,
-                                cudaStream_t st) {
-  if (f32)
-    k_cg_update<float><<<nblk, kRedThreads, 0, st>>>((float*)x, (float*)r, (const float*)p,
-                                                     (const float*)Ap, n9, partials, sc);
-  else
-    k_cg_update<double><<<nblk, kRedThreads, 0, st>>>((double*)x, (double*)r, (const double*)p,
-                                                      (const double*)Ap, n9, partials, sc);
-  k_cg_beta<<<1, kRedThreads, 0, st>>>(partials, nblk, sc);
-  g_mf_launches += 2;
-  return cudaGetLastError();
-}
-
-cudaError_t mf_launch_cg_direction(void* p, const void* r, bool f32, long long n9, const Scalars* sc,
-                                   cudaStream_t st) {
-  const int g = grid_for(n9) > 4096 ? 4096 : grid_for(n9);
-  if (f32) k_cg_direction<float><<<g, kRedThreads, 0, st>>>((float*)p, (const float*)r, n9, sc);
-  else k_cg_direction<double><<<g, kRedThreads, 0, st>>>((double*)p, (const double*)r, n9, sc);
-  g_mf_launches += 1;
   return cudaGetLastError();
 }
 

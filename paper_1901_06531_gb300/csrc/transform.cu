@@ -24,8 +24,8 @@
 #include "launch.h"
 
 // ---------------------------------------------------------------- xy forward
-// MODE 0: input is (K : x) with K packed symmetric (45 x N) and x (9 x N).
-// MODE 1: input is the field itself, component c.
+// MODE 1: the input is the field itself, component c (the tangent has been
+// applied by the streaming pass).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_xy_forward(const T* __restrict__ in, const T* __restrict__ K45,
                                                     typename CT<T>::t* __restrict__ spec, XYArgs a) {
@@ -51,20 +51,7 @@ __global__ void __launch_bounds__(512) k_xy_forward(const T* __restrict__ in, co
     const int q = idx / nx, j = idx - (idx / nx) * nx;
     const long long v0 = plane + (long long)q * nx + j;
     const long long v1 = v0 + (long long)hy * nx;
-    T lo, hi;
-    if (MODE == 0) {
-      lo = (T)0; hi = (T)0;
-#pragma unroll
-      for (int d = 0; d < 9; ++d) {
-        const T* Kc = K45 + (long long)sym45(c, d) * N;
-        lo += Kc[v0] * in[d * N + v0];
-        hi += Kc[v1] * in[d * N + v1];
-      }
-    } else {
-      lo = in[c * N + v0];
-      hi = in[c * N + v1];
-    }
-    buf[idx] = cmake(lo, hi);
+    buf[idx] = cmake(in[c * N + v0], in[c * N + v1]);
   }
   __syncthreads();
 
@@ -100,14 +87,16 @@ __global__ void __launch_bounds__(512) k_xy_forward(const T* __restrict__ in, co
 }
 
 // ---------------------------------------------------------------- xy inverse
-// out[c] = oscale * (inverse transform of the plane).  DOT 1: the block's
-// partial of sum out[c] * w[c] (FP64) goes to partials[blockIdx.x]; DOT 2:
-// the partial of sum out[c]^2.
+// y = oscale * (inverse transform of the plane).  DOT 0: out[c] = y.
+// DOT 1: out[c] = y and the block's partial of sum y * w[c] (FP64) goes to
+// partials[blockIdx.x].  DOT 2: out[c] = y and the partial of sum y^2.
+// DOT 3 (CG residual update): out[c] -= alpha * y with alpha from sc, and the
+// partial of sum out[c]^2 after the update; y itself is not stored.
 template <typename T, int DOT>
 __global__ void __launch_bounds__(512) k_xy_inverse(const typename CT<T>::t* __restrict__ spec,
                                                     T* __restrict__ out, const T* __restrict__ w,
                                                     double* __restrict__ partials, T oscale,
-                                                    XYArgs a) {
+                                                    XYArgs a, const Scalars* sc) {
   typedef typename CT<T>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -153,14 +142,24 @@ __global__ void __launch_bounds__(512) k_xy_inverse(const typename CT<T>::t* __r
 
   const long long plane = (long long)z * ny * nx;
   double acc = 0.0;
+  T alpha = (T)0;
+  if (DOT == 3) alpha = (T)sc->alpha;
   for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
     const int q = idx / nx, j = idx - (idx / nx) * nx;
     const long long v0 = plane + (long long)q * nx + j;
     const long long v1 = v0 + (long long)hy * nx;
     const C v = buf[idx];
     const T o0 = v.x * oscale, o1 = v.y * oscale;
-    out[c * N + v0] = o0;
-    out[c * N + v1] = o1;
+    if (DOT == 3) {
+      const T r0 = out[c * N + v0] - alpha * o0;
+      const T r1 = out[c * N + v1] - alpha * o1;
+      out[c * N + v0] = r0;
+      out[c * N + v1] = r1;
+      acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+    } else {
+      out[c * N + v0] = o0;
+      out[c * N + v1] = o1;
+    }
     if (DOT == 1) acc += (double)o0 * (double)w[c * N + v0] + (double)o1 * (double)w[c * N + v1];
     if (DOT == 2) acc += (double)o0 * (double)o0 + (double)o1 * (double)o1;
   }
@@ -292,13 +291,14 @@ static cudaError_t launch_xy_forward(const T* in, const T* K45, void* spec, cons
 
 template <typename T, int DOT>
 static cudaError_t launch_xy_inverse(const void* spec, T* out, const T* w, double* partials,
-                                     T oscale, const XYArgs& a, cudaStream_t st) {
+                                     T oscale, const XYArgs& a, cudaStream_t st,
+                                     const Scalars* sc = nullptr) {
   const size_t sm = xy_smem<T>(a);
   cudaError_t e = cudaFuncSetAttribute(k_xy_inverse<T, DOT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_xy_inverse<T, DOT><<<9 * a.nz, 512, sm, st>>>((const typename CT<T>::t*)spec, out, w,
-                                                  partials, oscale, a);
+                                                  partials, oscale, a, sc);
   ++g_mf_launches;
   return cudaGetLastError();
 }
@@ -316,28 +316,6 @@ static cudaError_t launch_zpass(void* spec, const ZArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_matvec_f64(const double* x, const double* K45, void* spec, double* y,
-                                 const double* w, double* partials, const XYArgs& xa,
-                                 const ZArgs& za, cudaStream_t st) {
-  cudaError_t e = launch_xy_forward<double, 0>(x, K45, spec, xa, st);
-  if (e != cudaSuccess) return e;
-  e = launch_zpass<double, 0>(spec, za, st);
-  if (e != cudaSuccess) return e;
-  if (w) return launch_xy_inverse<double, 1>(spec, y, w, partials, 1.0, xa, st);
-  return launch_xy_inverse<double, 0>(spec, y, nullptr, nullptr, 1.0, xa, st);
-}
-
-cudaError_t mf_launch_matvec_f32(const float* x, const float* K45, void* spec, float* y,
-                                 const float* w, double* partials, const XYArgs& xa,
-                                 const ZArgs& za, cudaStream_t st) {
-  cudaError_t e = launch_xy_forward<float, 0>(x, K45, spec, xa, st);
-  if (e != cudaSuccess) return e;
-  e = launch_zpass<float, 0>(spec, za, st);
-  if (e != cudaSuccess) return e;
-  if (w) return launch_xy_inverse<float, 1>(spec, y, w, partials, 1.0f, xa, st);
-  return launch_xy_inverse<float, 0>(spec, y, nullptr, nullptr, 1.0f, xa, st);
-}
-
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
                                const XYArgs& xa, const ZArgs& za, cudaStream_t st) {
   cudaError_t e = launch_xy_forward<double, 1>(P, nullptr, spec, xa, st);
@@ -347,15 +325,33 @@ cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* p
   return launch_xy_inverse<double, 2>(spec, b, nullptr, partials, 1.0, xa, st);
 }
 
-cudaError_t mf_launch_matvec_part(int which, bool f32, const void* x, const void* K45, void* spec,
-                                  void* y, const void* w, double* partials, const XYArgs& xa,
-                                  const ZArgs& za, cudaStream_t st) {
+cudaError_t mf_launch_project(bool f32, const void* t, void* spec, void* out, int inv_mode,
+                              double* partials, const XYArgs& xa, const ZArgs& za,
+                              const Scalars* sc, cudaStream_t st) {
+  cudaError_t e;
   if (f32) {
-    if (which == 0) return launch_xy_forward<float, 0>((const float*)x, (const float*)K45, spec, xa, st);
-    if (which == 1) return launch_zpass<float, 0>(spec, za, st);
-    return launch_xy_inverse<float, 1>(spec, (float*)y, (const float*)w, partials, 1.0f, xa, st);
+    e = launch_xy_forward<float, 1>((const float*)t, nullptr, spec, xa, st);
+    if (e == cudaSuccess) e = launch_zpass<float, 0>(spec, za, st);
+    if (e != cudaSuccess) return e;
+    if (inv_mode == 3) return launch_xy_inverse<float, 3>(spec, (float*)out, nullptr, partials, 1.0f, xa, st, sc);
+    return launch_xy_inverse<float, 0>(spec, (float*)out, nullptr, nullptr, 1.0f, xa, st);
   }
-  if (which == 0) return launch_xy_forward<double, 0>((const double*)x, (const double*)K45, spec, xa, st);
+  e = launch_xy_forward<double, 1>((const double*)t, nullptr, spec, xa, st);
+  if (e == cudaSuccess) e = launch_zpass<double, 0>(spec, za, st);
+  if (e != cudaSuccess) return e;
+  if (inv_mode == 3) return launch_xy_inverse<double, 3>(spec, (double*)out, nullptr, partials, 1.0, xa, st, sc);
+  return launch_xy_inverse<double, 0>(spec, (double*)out, nullptr, nullptr, 1.0, xa, st);
+}
+
+cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spec, void* r,
+                                   double* partials, const XYArgs& xa, const ZArgs& za,
+                                   const Scalars* sc, cudaStream_t st) {
+  if (f32) {
+    if (which == 0) return launch_xy_forward<float, 1>((const float*)t, nullptr, spec, xa, st);
+    if (which == 1) return launch_zpass<float, 0>(spec, za, st);
+    return launch_xy_inverse<float, 3>(spec, (float*)r, nullptr, partials, 1.0f, xa, st, sc);
+  }
+  if (which == 0) return launch_xy_forward<double, 1>((const double*)t, nullptr, spec, xa, st);
   if (which == 1) return launch_zpass<double, 0>(spec, za, st);
-  return launch_xy_inverse<double, 1>(spec, (double*)y, (const double*)w, partials, 1.0, xa, st);
+  return launch_xy_inverse<double, 3>(spec, (double*)r, nullptr, partials, 1.0, xa, st, sc);
 }

@@ -175,10 +175,11 @@ class Context:
         return meanP
 
     def time_kernels(self, mask, reps=20):
-        """Mean ms per launch of the three inner-operator kernels (x-y forward
-        with tangent apply, z-pass, x-y inverse), each after an L2 flush."""
+        """Mean ms per launch of the four kernels of a CG iteration (tangent
+        pass, x-y forward, z-pass, x-y inverse with residual update), each
+        after an L2 flush."""
         m = np.ascontiguousarray(mask, dtype=np.uint8)
-        ms = np.zeros(3, dtype=np.float32)
+        ms = np.zeros(4, dtype=np.float32)
         _check("mf_time_kernels", _lib.mf_time_kernels(self.h, _ptr(m), reps, _ptr(ms)))
         return ms.astype(np.float64)
 

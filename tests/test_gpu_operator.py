@@ -98,10 +98,15 @@ def test_matvec_fp64(shape, mi):
 
 
 @pytest.mark.parametrize("shape", SHAPES[:4])
-def test_matvec_fp32(shape):
+@pytest.mark.parametrize("model,scale", [("svk", False), ("nh", False), ("nh", True), ("svk", True)])
+def test_matvec_fp32(shape, model, scale):
+    """FP32 operator with the matrix-free tangent (from F - I in FP32 and the
+    phase parameters) against the FP64 oracle: the error is the FP32
+    rounding of the tangent apply and of the transforms, relative to the
+    field norm."""
     import torch
     mf = lib()
-    ctx, om, F = make(mf, shape, mf.MF_FP32_INNER, "svk", seed=8)
+    ctx, om, F = make(mf, shape, mf.MF_FP32_INNER, model, seed=8, scale=scale)
     ctx.constitutive()
     nx, ny, nz = shape
     x = inputs.random_field((nz, ny, nx), 9)
@@ -110,14 +115,10 @@ def test_matvec_fp32(shape):
     ctx.matvec(xt, yt, MASKS[2])
     ctx.sync()
     _, K = om.PK(F)
-    # same inputs as the FP32 path sees: x and K rounded to FP32
-    x32 = x.astype(np.float32).astype(np.float64)
-    K32 = K.astype(np.float32).astype(np.float64)
-    ref = osolver.matvec(K32, x32, MASKS[2])
+    ref = osolver.matvec(K, x.astype(np.float32).astype(np.float64), MASKS[2])
     got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
-    # FP32 transform error ~ eps32 * log2(N) relative to the field norm
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err < 2e-6, err
+    assert err < 3e-6, err
 
 
 @pytest.mark.parametrize("shape", SHAPES)
