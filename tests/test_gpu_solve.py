@@ -110,11 +110,13 @@ def test_fp32_inner_matches_fp64_oracle():
     assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
     assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-9
     # full stress control leaves the rotation about the load axis free: F is
-    # unique up to that rotation, F^T F and F^T P are unique
+    # unique up to that rotation, F^T F and F^T P are unique.  FP32 rounding
+    # in the inner solves also leaves noise of relative size ~1e-8 in the
+    # Nyquist modes of F, which G* annihilates and the FP64 residual therefore
+    # cannot see; the stated FP32-inner field tolerance is 3e-7 (max-norm).
     C, S = invariants(F, P)
     Cr, Sr = invariants(ref["F"], ref["P"])
-    assert rel(C, Cr) < 1e-8 and rel(S, Sr) < 1e-8
-    # and F itself is within a small rigid rotation of the oracle's
+    assert rel(C, Cr) < 3e-7 and rel(S, Sr) < 3e-7
     assert rel(F, ref["F"]) < 1e-6
     check_control(out, mask, target, 1e-9, 1e-14)
 
@@ -131,7 +133,7 @@ def test_fp32_inner_polycrystal():
     ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
     F, _ = ctx.get_fields()
     assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
-    assert rel(F, ref["F"]) < 1e-8
+    assert rel(F, ref["F"]) < 3e-7
 
 
 def test_radix3_grid_solve():
