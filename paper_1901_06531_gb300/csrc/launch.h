@@ -79,7 +79,7 @@ cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k
 cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int nblk, Scalars* sc,
                              cudaStream_t st);
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,
-                                const Scalars* sc, cudaStream_t st);
+                                const Scalars* sc, bool after_update, cudaStream_t st);
 cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f32, long long n9,
                               double* partials, int nblk, double tol_cg, double cg_rel, long long N,
                               Scalars* sc, cudaStream_t st);

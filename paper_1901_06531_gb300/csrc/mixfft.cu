@@ -696,7 +696,7 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
     const double* tgt = target + 9 * k;
     double pbar[9];
     for (int q = 0; q < 9; ++q) pbar[q] = m[q] ? tgt[q] : 0.0;
-    if (mf_launch_predictor(F, N, m, tgt, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+    if (mf_launch_predictor(F, N, m, tgt, sc, false, c->st) != cudaSuccess) return MF_CUDA_ERROR;
     int nn = 0, ncg = 0;
     double ratio = INFINITY;
     int s;
@@ -733,6 +733,10 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
         return MF_CUDA_ERROR;
       if (mf_launch_newton_update(F, c->ws + c->ox, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc,
                                   c->st) != cudaSuccess)
+        return MF_CUDA_ERROR;
+      // FP32 corrections carry a rounding-level average on the strain-
+      // controlled components; the FP64 outer level re-imposes F-bar there
+      if (c->f32() && mf_launch_predictor(F, N, m, tgt, sc, true, c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
       s = read_scalars(c, &h);
       if (s) return s;

@@ -246,12 +246,16 @@ struct Load9 {
 };
 
 // Predictor of a load step: every strain-controlled component is shifted
-// uniformly so that its voxel average equals the prescribed F-bar.
-__global__ void k_predictor(double* __restrict__ F, long long N, Load9 ld, const Scalars* sc) {
+// uniformly so that its voxel average equals the prescribed F-bar.  With
+// after_update the averages measured by the last Newton update are used (the
+// FP32 inner solves re-impose the strain control in FP64 after each update).
+__global__ void k_predictor(double* __restrict__ F, long long N, Load9 ld, const Scalars* sc,
+                            bool after_update) {
+  const double* mean = after_update ? sc->meanF_new : sc->meanF;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 9 * N;
        i += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(i / N);
-    if (ld.mask[c] == 0) F[i] += ld.target[c] - sc->meanF[c];
+    if (ld.mask[c] == 0) F[i] += ld.target[c] - mean[c];
   }
 }
 
@@ -483,10 +487,10 @@ cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int
 }
 
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,
-                                const Scalars* sc, cudaStream_t st) {
+                                const Scalars* sc, bool after_update, cudaStream_t st) {
   Load9 ld;
   for (int c = 0; c < 9; ++c) { ld.mask[c] = mask9[c]; ld.target[c] = target9[c]; }
-  k_predictor<<<grid_for(9 * N) > 4096 ? 4096 : grid_for(9 * N), kRedThreads, 0, st>>>(F, N, ld, sc);
+  k_predictor<<<grid_for(9 * N) > 4096 ? 4096 : grid_for(9 * N), kRedThreads, 0, st>>>(F, N, ld, sc, after_update);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
