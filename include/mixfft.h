@@ -46,7 +46,8 @@ typedef enum {
   MF_NONPOSITIVE_J = 4,   /* det F <= 0 in a neo-Hookean voxel */
   MF_CUDA_ERROR = 5,      /* a CUDA runtime call failed */
   MF_DEVICE_TIMEOUT = 6,  /* a bounded device-side wait gave up */
-  MF_NO_WORKSPACE = 7     /* mf_bind_workspace was not called or is too small */
+  MF_NO_WORKSPACE = 7,    /* mf_bind_workspace was not called or is too small */
+  MF_TOO_LARGE = 8        /* the cell exceeds the static scratch of mf_residual_noalloc */
 } mf_status;
 
 typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
@@ -138,6 +139,30 @@ int mf_matvec(mf_ctx* ctx, const void* x_dev, void* y_dev, const uint8_t* mask);
  * coefficient of P). */
 int mf_residual(mf_ctx* ctx, const uint8_t* mask, const double* pbar, double* b_dev,
                 double* meanP_host);
+
+/* Residual without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc when they need the
+ * residual (a host callback, an allocator hook, a runtime that fixed its
+ * device memory budget at start-up).  It computes the same
+ * b = -G*(P - P-bar) as mf_residual, in FP64, without a context:
+ *   nx, ny, nz: as for mf_create, with nx*ny*nz <= 262144 (64^3); a larger
+ *               cell returns MF_TOO_LARGE and launches nothing;
+ *   P_dev:  device, 9N doubles (caller's), read only;
+ *   mask, pbar: host, 9 bytes / 9 doubles, as for mf_residual;
+ *   b_dev:  device, 9N doubles (caller's), written; must not alias P_dev;
+ *   meanP_host: host, 9 doubles or NULL, receives <P>;
+ *   stream: cudaStream_t for every copy and launch (NULL = default stream).
+ * All other memory -- the half spectrum, index and twiddle tables, reduction
+ * partials -- lives in one file-scope static device array of about 18.2 MiB
+ * that every GPU loading the library holds until the process exits.  No
+ * cudaMalloc or cudaFree is called.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call outside any stream capture.  All calls share the one array and
+ * each call overwrites it, so calls that may overlap on the GPU (different
+ * streams, or different host threads) race: serialise them.  The call
+ * synchronises its stream before returning. */
+int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, const uint8_t* mask,
+                        const double* pbar, double* b_dev, double* meanP_host, void* stream);
 
 /* Benchmark hook: time the four kernels of one CG iteration separately with
  * CUDA events on the context's stream, each launch preceded by an L2 flush (a

@@ -393,6 +393,7 @@ const char* mf_status_string(int s) {
     case MF_CUDA_ERROR: return "CUDA error";
     case MF_DEVICE_TIMEOUT: return "device timeout";
     case MF_NO_WORKSPACE: return "no workspace bound";
+    case MF_TOO_LARGE: return "cell larger than the static scratch of mf_residual_noalloc (64^3 voxels)";
     default: return "unknown status";
   }
 }

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libmixfft.so")
 
 MF_OK, MF_INVALID_ARG, MF_NOT_CONVERGED, MF_CG_BREAKDOWN = 0, 1, 2, 3
 MF_NONPOSITIVE_J, MF_CUDA_ERROR, MF_DEVICE_TIMEOUT, MF_NO_WORKSPACE = 4, 5, 6, 7
+MF_TOO_LARGE = 8
 MF_FP64, MF_FP32_INNER = 0, 1
 MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
 
@@ -41,6 +42,7 @@ _lib.mf_constitutive.argtypes = [_vp]
 _lib.mf_get_tangent.argtypes = [_vp, _vp]
 _lib.mf_matvec.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.mf_residual_noalloc.argtypes = [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mf_time_kernels.argtypes = [_vp, _vp, _i, _vp]
 _lib.mf_kernel_launches.argtypes = []
 _lib.mf_kernel_launches.restype = ctypes.c_longlong
@@ -52,13 +54,31 @@ _lib.mf_destroy.restype = None
 
 EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_material", "mf_set_F",
             "mf_solve", "mf_get_fields", "mf_constitutive", "mf_get_tangent", "mf_matvec",
-            "mf_residual", "mf_time_kernels", "mf_kernel_launches", "mf_sync", "mf_status_string",
+            "mf_residual", "mf_residual_noalloc", "mf_time_kernels", "mf_kernel_launches", "mf_sync", "mf_status_string",
             "mf_destroy"]
 
 
 def kernel_launches():
     """mf_kernel_launches: kernels launched by the library in this process."""
     return int(_lib.mf_kernel_launches())
+
+
+def residual_noalloc(nx, ny, nz, P, mask, pbar, b, stream=None):
+    """mf_residual_noalloc: b = -G*(P - P-bar) in FP64 with no device
+    allocation (for callers that cannot allocate at this point).  P, b: torch
+    CUDA float64 tensors of 9N values owned by the caller; returns <P>.
+    Calls sharing the library's static scratch must not overlap on the GPU."""
+    import torch
+    assert P.dtype == torch.float64 and b.dtype == torch.float64
+    assert P.is_contiguous() and b.is_contiguous() and P.numel() == b.numel() == 9 * nx * ny * nz
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    pb = _c64(pbar)
+    meanP = np.zeros(9)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check("mf_residual_noalloc", _lib.mf_residual_noalloc(nx, ny, nz, _vp(P.data_ptr()), _ptr(m), _ptr(pb),
+                                                           _vp(b.data_ptr()), _ptr(meanP),
+                                                           _vp(st.cuda_stream)))
+    return meanP
 
 
 class MixFFTError(RuntimeError):
