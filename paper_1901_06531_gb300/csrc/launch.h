@@ -5,6 +5,7 @@
 #include "common.cuh"
 
 struct XYArgs {
+  int v2;          // 1: fixed-size kernels (transform2*.cu), tables of that layout
   int nx, ny, nz;
   long long N;
   AxisPlan px;     // length nx
@@ -15,6 +16,7 @@ struct XYArgs {
 };
 
 struct ZArgs {
+  int v2;
   int nx, ny, nz;
   long long N;
   AxisPlan pz;
@@ -32,6 +34,20 @@ struct ZArgs {
 
 // Process-wide count of kernel launches issued by the library.
 extern long long g_mf_launches;
+
+// transform2_f32.cu / transform2_f64.cu: fixed-size kernels for square x-y
+// planes nx = ny and z lengths in {16, 32, 64, 128}.  Their spectrum layout:
+// per (c, z) ny rows (digit-reversed ky, yk table of ny entries) of nx/2 slots
+// (digit-reversed kx, xk table of nx/2 entries), xpos = slot of kx.
+bool mf_v2_supported(int nx, int ny, int nz);
+cudaError_t mf_v2_xyf_f32(const void* in, void* spec, const XYArgs& a, cudaStream_t st);
+cudaError_t mf_v2_xyi_f32(int mode, const void* spec, void* out, double* partials, const XYArgs& a,
+                          const Scalars* sc, cudaStream_t st);
+cudaError_t mf_v2_zp_f32(int mode, void* spec, const ZArgs& a, cudaStream_t st);
+cudaError_t mf_v2_xyf_f64(const void* in, void* spec, const XYArgs& a, cudaStream_t st);
+cudaError_t mf_v2_xyi_f64(int mode, const void* spec, void* out, double* partials, const XYArgs& a,
+                          const Scalars* sc, cudaStream_t st);
+cudaError_t mf_v2_zp_f64(int mode, void* spec, const ZArgs& a, cudaStream_t st);
 
 // transform.cu
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mixfft.h"
+#include "fft2.cuh"
 #include "launch.h"
 
 namespace {
@@ -157,7 +158,7 @@ Defl null_rotations(const double meanF[9], const uint8_t* mask, const double T[9
   // standard problem for g^-1/2 Q^T Rz Q g^-1/2
   double Qg[3][3];
   jacobi_eig(m, Gz, Qg);
-  double H[3][3] = {{0}}, B[3][3];
+  double H[3][3] = {{0}};
   for (int p = 0; p < m; ++p)
     for (int q = 0; q < m; ++q) {
       double s = 0.0;
@@ -169,7 +170,6 @@ Defl null_rotations(const double meanF[9], const uint8_t* mask, const double T[9
   jacobi_eig(m, H, U);
   for (int k = 0; k < m; ++k) {
     if (fabs(H[k][k]) > tau * kappa) continue;
-    for (int p = 0; p < m; ++p) B[p][0] = 0.0;
     double v[3] = {0, 0, 0};        // coefficients in the Z basis
     for (int p = 0; p < m; ++p) {
       double s = 0.0;
@@ -191,6 +191,7 @@ struct mf_ctx {
   int nx, ny, nz;
   long long N;
   int prec;
+  int v2 = 0;              // fixed-size transform kernels and their table layout
   cudaStream_t st;
   AxisPlan px, pyh, pz;
   int zS;
@@ -219,6 +220,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_CUDA_ERROR
 
 XYArgs xy_args(const mf_ctx* c, bool f32) {
   XYArgs a;
+  a.v2 = c->v2;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
   const size_t tw = f32 ? c->otw32 : c->otw64;
@@ -232,6 +234,7 @@ XYArgs xy_args(const mf_ctx* c, bool f32) {
 ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale) {
   ZArgs a;
   memset(&a, 0, sizeof(a));
+  a.v2 = c->v2;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.pz = c->pz;
   const size_t tw = f32 ? c->otw32 : c->otw64;
@@ -413,6 +416,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->nx = nx; c->ny = ny; c->nz = nz;
   c->N = (long long)nx * ny * nz;
   c->prec = precision;
+  c->v2 = mf_v2_supported(nx, ny, nz) ? 1 : 0;
   c->st = (cudaStream_t)stream;
   if (!make_plan(nx, &c->px) || !make_plan(ny / 2, &c->pyh) || !make_plan(nz, &c->pz)) {
     delete c;
@@ -450,7 +454,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->oxpos = take(nx * sizeof(int));
   c->oxk = take(nx * sizeof(int));
   c->oxe = take(nx * sizeof(int));
-  c->oyk = take((ny / 2) * sizeof(int));
+  c->oyk = take(ny * sizeof(int));
   c->ozk = take(nz * sizeof(int));
   c->otw64 = take((nx + ny + nz) * sizeof(double2));
   c->otw32 = take((nx + ny + nz) * sizeof(float2));
@@ -468,16 +472,25 @@ int mf_bind_workspace(mf_ctx* c, void* dev, size_t bytes) {
   c->have_K = false;
   // host-built tables: digit-reversal maps and twiddles
   const int nx = c->nx, ny = c->ny, nz = c->nz;
-  std::vector<int> xpos(nx), xk(nx), xe(nx), yk(ny / 2), zk(nz);
-  for (int k = 0; k < nx; ++k) xpos[k] = dif_pos(c->px, k);
-  for (int k = 0; k < nx; ++k) {
-    const int s = xpos[k];
-    if (k < nx / 2) { xk[s] = k; xe[s] = 0; }
-    else if (k == nx / 2) { xk[s] = 0; xe[s] = 1; }
-    else { xk[s] = nx - k; xe[s] = 1; }
+  std::vector<int> xpos(nx, 0), xk(nx, 0), xe(nx, 0), yk(ny, 0), zk(nz, 0);
+  if (c->v2) {
+    // half-length rows: slot of kx < nx/2; rows hold ky in digit-reversed order
+    const int h = nx / 2;
+    for (int k = 0; k < h; ++k) xpos[k] = fft2::dif_pos(h, k);
+    for (int k = 0; k < h; ++k) xk[xpos[k]] = k;
+    for (int k = 0; k < ny; ++k) yk[fft2::dif_pos(ny, k)] = k;
+    for (int k = 0; k < nz; ++k) zk[fft2::dif_pos(nz, k)] = k;
+  } else {
+    for (int k = 0; k < nx; ++k) xpos[k] = dif_pos(c->px, k);
+    for (int k = 0; k < nx; ++k) {
+      const int s = xpos[k];
+      if (k < nx / 2) { xk[s] = k; xe[s] = 0; }
+      else if (k == nx / 2) { xk[s] = 0; xe[s] = 1; }
+      else { xk[s] = nx - k; xe[s] = 1; }
+    }
+    for (int k = 0; k < ny / 2; ++k) yk[dif_pos(c->pyh, k)] = k;
+    for (int k = 0; k < nz; ++k) zk[dif_pos(c->pz, k)] = k;
   }
-  for (int k = 0; k < ny / 2; ++k) yk[dif_pos(c->pyh, k)] = k;
-  for (int k = 0; k < nz; ++k) zk[dif_pos(c->pz, k)] = k;
   std::vector<double2> tw64(nx + ny + nz);
   std::vector<float2> tw32(nx + ny + nz);
   int o = 0;
@@ -496,7 +509,7 @@ int mf_bind_workspace(mf_ctx* c, void* dev, size_t bytes) {
   put(c->oxpos, xpos.data(), nx * sizeof(int));
   put(c->oxk, xk.data(), nx * sizeof(int));
   put(c->oxe, xe.data(), nx * sizeof(int));
-  put(c->oyk, yk.data(), (ny / 2) * sizeof(int));
+  put(c->oyk, yk.data(), ny * sizeof(int));
   put(c->ozk, zk.data(), nz * sizeof(int));
   put(c->otw64, tw64.data(), tw64.size() * sizeof(double2));
   put(c->otw32, tw32.data(), tw32.size() * sizeof(float2));

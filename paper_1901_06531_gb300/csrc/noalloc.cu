@@ -140,6 +140,7 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
   if (e != cudaSuccess) return MF_CUDA_ERROR;
 
   XYArgs xa;
+  xa.v2 = 0;
   xa.nx = nx; xa.ny = ny; xa.nz = nz; xa.N = N;
   xa.px = px; xa.pyh = pyh;
   xa.twx = tab + o_tw;

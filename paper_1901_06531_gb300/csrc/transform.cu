@@ -318,6 +318,12 @@ static cudaError_t launch_zpass(void* spec, const ZArgs& a, cudaStream_t st) {
 
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
                                const XYArgs& xa, const ZArgs& za, cudaStream_t st) {
+  if (xa.v2) {
+    cudaError_t e = mf_v2_xyf_f64(P, spec, xa, st);
+    if (e == cudaSuccess) e = mf_v2_zp_f64(1, spec, za, st);
+    if (e == cudaSuccess) e = mf_v2_xyi_f64(2, spec, b, partials, xa, nullptr, st);
+    return e;
+  }
   cudaError_t e = launch_xy_forward<double, 1>(P, nullptr, spec, xa, st);
   if (e != cudaSuccess) return e;
   e = launch_zpass<double, 1>(spec, za, st);
@@ -329,6 +335,14 @@ cudaError_t mf_launch_project(bool f32, const void* t, void* spec, void* out, in
                               double* partials, const XYArgs& xa, const ZArgs& za,
                               const Scalars* sc, cudaStream_t st) {
   cudaError_t e;
+  if (xa.v2) {
+    e = f32 ? mf_v2_xyf_f32(t, spec, xa, st) : mf_v2_xyf_f64(t, spec, xa, st);
+    if (e == cudaSuccess) e = f32 ? mf_v2_zp_f32(0, spec, za, st) : mf_v2_zp_f64(0, spec, za, st);
+    if (e == cudaSuccess)
+      e = f32 ? mf_v2_xyi_f32(inv_mode, spec, out, partials, xa, sc, st)
+              : mf_v2_xyi_f64(inv_mode, spec, out, partials, xa, sc, st);
+    return e;
+  }
   if (f32) {
     e = launch_xy_forward<float, 1>((const float*)t, nullptr, spec, xa, st);
     if (e == cudaSuccess) e = launch_zpass<float, 0>(spec, za, st);
@@ -346,6 +360,11 @@ cudaError_t mf_launch_project(bool f32, const void* t, void* spec, void* out, in
 cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spec, void* r,
                                    double* partials, const XYArgs& xa, const ZArgs& za,
                                    const Scalars* sc, cudaStream_t st) {
+  if (xa.v2) {
+    if (which == 0) return f32 ? mf_v2_xyf_f32(t, spec, xa, st) : mf_v2_xyf_f64(t, spec, xa, st);
+    if (which == 1) return f32 ? mf_v2_zp_f32(0, spec, za, st) : mf_v2_zp_f64(0, spec, za, st);
+    return f32 ? mf_v2_xyi_f32(3, spec, r, partials, xa, sc, st) : mf_v2_xyi_f64(3, spec, r, partials, xa, sc, st);
+  }
   if (f32) {
     if (which == 0) return launch_xy_forward<float, 1>((const float*)t, nullptr, spec, xa, st);
     if (which == 1) return launch_zpass<float, 0>(spec, za, st);
@@ -354,4 +373,9 @@ cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spe
   if (which == 0) return launch_xy_forward<double, 1>((const double*)t, nullptr, spec, xa, st);
   if (which == 1) return launch_zpass<double, 0>(spec, za, st);
   return launch_xy_inverse<double, 3>(spec, (double*)r, nullptr, partials, 1.0, xa, st, sc);
+}
+
+bool mf_v2_supported(int nx, int ny, int nz) {
+  auto ok = [](int n) { return n == 16 || n == 32 || n == 64 || n == 128; };
+  return nx == ny && ok(nx) && ok(nz);
 }

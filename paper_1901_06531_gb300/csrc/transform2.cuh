@@ -1,0 +1,293 @@
+// Fixed-size transform kernels (square x-y planes NX = NY, z length NZ, both
+// compile-time) for the projected operator and the residual.
+//
+// Real-to-complex along x by the half-length method: a real row of NX values
+// is read as H = NX/2 complex samples z_j = t_2j + i t_2j+1, transformed at
+// length H, and split into the NX-point spectrum by
+//     X_k = E_k + W_NX^k O_k,  E_k = (Z_k + conj Z_(H-k)) / 2,
+//     O_k = (Z_k - conj Z_(H-k)) / 2i,            k = 0 .. H-1
+// (the x-Nyquist coefficient is not kept: G-hat-star is zero there).  Rows
+// therefore load and store contiguously.  The complex y transform follows on
+// the H columns; the z-pass transforms along z, applies G-hat-star and
+// transforms back.  Spectrum per (c, z): NY rows (digit-reversed ky) of H
+// slots (digit-reversed kx), dense.
+#pragma once
+
+#include "fft2.cuh"
+#include "launch.h"
+
+namespace tr2 {
+
+constexpr int kThreads = 256;
+
+// Asynchronous global -> shared copies of one complex element (8 or 16
+// bytes); many in flight per thread without holding registers.
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* smem, const C* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(C) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename T, int NX>
+struct XYShape {
+  typedef typename CT<T>::t C;
+  static constexpr int H = NX / 2;
+  static constexpr int PX = H + 1;            // odd pitch: rows fall in different banks
+  static constexpr int NY = NX;
+  static constexpr size_t smem() {
+    return (size_t)NY * PX * sizeof(C) + (size_t)(NX + NY) * sizeof(C) + (size_t)H * sizeof(int);
+  }
+};
+
+template <typename C>
+__device__ __forceinline__ void load_tables(C* twx, C* twy, int* posx, const C* gtw, const int* gpos,
+                                            int nx, int ny, int h) {
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) twx[i] = gtw[i];
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) twy[i] = gtw[nx + i];
+  for (int i = threadIdx.x; i < h; i += blockDim.x) posx[i] = gpos[i];
+}
+
+// ------------------------------------------------------------------ forward
+template <typename T, int NX>
+__global__ void __launch_bounds__(kThreads) k_xyf(const T* __restrict__ in, typename CT<T>::t* __restrict__ spec,
+                                                  int nz, long long N, const typename CT<T>::t* __restrict__ gtw,
+                                                  const int* __restrict__ gpos) {
+  typedef XYShape<T, NX> Sh;
+  typedef typename CT<T>::t C;
+  constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* twx = buf + NY * PX;
+  C* twy = twx + NX;
+  int* posx = reinterpret_cast<int*>(twy + NY);
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
+  const int c = blockIdx.x % 9, z = blockIdx.x / 9;
+  const C* src = reinterpret_cast<const C*>(in + c * N + (long long)z * NY * NX);
+  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+    const int y = idx / H, j = idx - (idx / H) * H;
+    cp_async_elem(buf + y * PX + j, src + idx);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // x: NY rows of H complex samples
+  fft2::forward<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
+  // split into the NX-point spectrum of each real row; pairs (k, H-k)
+  constexpr int NP = H / 2 + 1;
+  for (int idx = threadIdx.x; idx < NY * NP; idx += kThreads) {
+    const int y = idx % NY, k = idx / NY;
+    const int km = (H - k) % H;
+    C* row = buf + y * PX;
+    const int pa = posx[k], pb = posx[km];
+    const C za = row[pa], zb = row[pb];
+    // X_k from (Z_k, Z_(H-k)); X_(H-k) from (Z_(H-k), Z_k)
+    C ea, oa, eb, ob;
+    ea.x = (T)0.5 * (za.x + zb.x); ea.y = (T)0.5 * (za.y - zb.y);
+    oa.x = (T)0.5 * (za.y + zb.y); oa.y = (T)-0.5 * (za.x - zb.x);
+    eb.x = ea.x; eb.y = -ea.y;
+    ob.x = oa.x; ob.y = -oa.y;
+    const C xa = cadd(ea, cmul(oa, twx[k]));
+    if (km != k) {
+      const C xb = cadd(eb, cmul(ob, twx[km]));
+      row[pb] = xb;
+    }
+    row[pa] = xa;
+  }
+  __syncthreads();
+  // y: H columns of NY samples, stride PX
+  fft2::forward<C, NY, NY, H, 1, 1, 0, PX>(buf, twy);
+  C* dst = spec + ((long long)c * nz + z) * NY * H;
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+    const int y = idx / H, j = idx - (idx / H) * H;
+    dst[idx] = buf[y * PX + j];
+  }
+}
+
+// ------------------------------------------------------------------ inverse
+// MODE 0: out[c] = y.  MODE 2: out[c] = y, partial sum y^2.  MODE 3: out[c] -=
+// alpha y (alpha from sc), partial sum out^2.
+template <typename T, int NX, int MODE>
+__global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __restrict__ spec, T* __restrict__ out,
+                                                  double* __restrict__ partials, int nz, long long N,
+                                                  const typename CT<T>::t* __restrict__ gtw,
+                                                  const int* __restrict__ gpos, const Scalars* sc) {
+  typedef XYShape<T, NX> Sh;
+  typedef typename CT<T>::t C;
+  constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* twx = buf + NY * PX;
+  C* twy = twx + NX;
+  int* posx = reinterpret_cast<int*>(twy + NY);
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
+  const int c = blockIdx.x % 9, z = blockIdx.x / 9;
+  const C* src = spec + ((long long)c * nz + z) * NY * H;
+  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+    const int y = idx / H, j = idx - (idx / H) * H;
+    cp_async_elem(buf + y * PX + j, src + idx);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  fft2::inverse<C, NY, NY, H, 1, 1, 0, PX>(buf, twy);
+  // merge each row's spectrum into H complex samples (the adjoint of the
+  // split, times 2): Z_k = E_k + i O_k with E_k = X_k + conj X_(H-k),
+  // O_k = (X_k - conj X_(H-k)) conj(W_NX^k); X_H (Nyquist) is zero and the
+  // x-constant coefficient keeps only its real part (real output)
+  constexpr int NP = H / 2 + 1;
+  for (int idx = threadIdx.x; idx < NY * NP; idx += kThreads) {
+    const int y = idx % NY, k = idx / NY;
+    const int km = (H - k) % H;
+    C* row = buf + y * PX;
+    const int pa = posx[k], pb = posx[km];
+    C xa = row[pa], xb = row[pb];
+    C za, zb;
+    if (k == 0) {
+      // X_0 real, X_H = 0
+      const T x0 = xa.x;   // E = x0, O = x0: Z = x0 + i x0
+      za.x = x0; za.y = x0;
+      row[pa] = za;
+      continue;
+    }
+    // E_a = xa + conj(xb), D_a = xa - conj(xb)
+    C ea, da, eb, db;
+    ea.x = xa.x + xb.x; ea.y = xa.y - xb.y;
+    da.x = xa.x - xb.x; da.y = xa.y + xb.y;
+    const C oa = cmulc(da, twx[k]);
+    za.x = ea.x - oa.y; za.y = ea.y + oa.x;
+    if (km != k) {
+      eb.x = xb.x + xa.x; eb.y = xb.y - xa.y;
+      db.x = xb.x - xa.x; db.y = xb.y + xa.y;
+      const C ob = cmulc(db, twx[km]);
+      zb.x = eb.x - ob.y; zb.y = eb.y + ob.x;
+      row[pb] = zb;
+    }
+    row[pa] = za;
+  }
+  __syncthreads();
+  fft2::inverse<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
+  C* dst = reinterpret_cast<C*>(out + c * N + (long long)z * NY * NX);
+  double acc = 0.0;
+  T alpha = (T)0;
+  if (MODE == 3) alpha = (T)sc->alpha;
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+    const int y = idx / H, j = idx - (idx / H) * H;
+    const C v = buf[y * PX + j];
+    if (MODE == 3) {
+      C r = dst[idx];
+      r.x -= alpha * v.x;
+      r.y -= alpha * v.y;
+      dst[idx] = r;
+      acc += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
+    } else {
+      dst[idx] = v;
+      if (MODE == 2) acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+  }
+  if (MODE >= 2) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double s = (threadIdx.x < (kThreads >> 5)) ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ z-pass
+// Tile: S columns (consecutive (ky, kx) slots) x NZ x 9 components, component
+// pitch CP = NZ*S + 4 complex so that component planes fall in different banks.
+template <typename T, int NZ>
+struct ZShape {
+  typedef typename CT<T>::t C;
+  static constexpr int S = (sizeof(C) == 8) ? (NZ >= 256 ? 4 : 8) : (NZ >= 256 ? 2 : 4);
+  static constexpr int CP = NZ * S + 4;
+  static constexpr size_t smem() {
+    return (size_t)9 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int);
+  }
+};
+
+// MODE 0: operator (scale, mask).  MODE 1: residual (adds a.add at the null
+// frequency, records the null-frequency coefficient / N in a.mean_out).
+template <typename T, int NZ, int MODE>
+__global__ void __launch_bounds__(kThreads) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
+  typedef ZShape<T, NZ> Sh;
+  typedef typename CT<T>::t C;
+  constexpr int S = Sh::S, CP = Sh::CP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [9][CP]
+  C* twz = buf + 9 * CP;
+  int* zk = reinterpret_cast<int*>(twz + NZ);
+  const C* gtwz = reinterpret_cast<const C*>(a.twz);
+  for (int i = threadIdx.x; i < NZ; i += kThreads) { twz[i] = gtwz[i]; zk[i] = a.zk[i]; }
+  const int H = a.nx / 2;
+  const int ncol = a.ny * H;
+  const int col0 = blockIdx.x * S;
+  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kThreads) {
+    const int s = idx % S, cz = idx / S;
+    const int cc = cz / NZ, z = cz - (cz / NZ) * NZ;
+    cp_async_elem(buf + cc * CP + z * S + s, spec + (long long)cz * ncol + col0 + s);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  fft2::forward<C, NZ, NZ, 9 * S, S, CP, 1, S>(buf, twz);
+  const T scale = (T)a.scale;
+  for (int idx = threadIdx.x; idx < NZ * S; idx += kThreads) {
+    const int s = idx % S, p = idx / S;
+    const int col = col0 + s;
+    const int row = col / H, slot = col - (col / H) * H;
+    const int kx = a.xk[slot];
+    const int ky = a.yk[row];
+    const int kz = zk[p];
+    C* e = buf + p * S + s;
+    const bool nyq = (2 * ky == a.ny) || ((NZ % 2 == 0) && (2 * kz == NZ));
+    if (nyq) {
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) e[cc * CP] = cmake((T)0, (T)0);
+    } else if (kx == 0 && ky == 0 && kz == 0) {
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) {
+        const C X = e[cc * CP];
+        if (MODE == 1 && a.mean_out) a.mean_out[cc] = (double)X.x / (double)a.N;
+        if (a.mask & (1u << cc)) {
+          const T add = (MODE == 1) ? (T)a.add[cc] : (T)0;
+          e[cc * CP] = cmake(scale * X.x + add, scale * X.y);
+        } else {
+          e[cc * CP] = cmake((T)0, (T)0);
+        }
+      }
+    } else {
+      const int kys = (2 * ky < a.ny) ? ky : ky - a.ny;
+      const int kzs = (2 * kz < NZ) ? kz : kz - NZ;
+      const T xi0 = (T)kx / (T)a.nx, xi1 = (T)kys / (T)a.ny, xi2 = (T)kzs / (T)NZ;
+      const T inv = scale / (xi0 * xi0 + xi1 * xi1 + xi2 * xi2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const C A0 = e[(3 * i) * CP], A1 = e[(3 * i + 1) * CP], A2 = e[(3 * i + 2) * CP];
+        C q;
+        q.x = (A0.x * xi0 + A1.x * xi1 + A2.x * xi2) * inv;
+        q.y = (A0.y * xi0 + A1.y * xi1 + A2.y * xi2) * inv;
+        e[(3 * i) * CP] = cmake(q.x * xi0, q.y * xi0);
+        e[(3 * i + 1) * CP] = cmake(q.x * xi1, q.y * xi1);
+        e[(3 * i + 2) * CP] = cmake(q.x * xi2, q.y * xi2);
+      }
+    }
+  }
+  __syncthreads();
+  fft2::inverse<C, NZ, NZ, 9 * S, S, CP, 1, S>(buf, twz);
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kThreads) {
+    const int s = idx % S, cz = idx / S;
+    const int cc = cz / NZ, z = cz - (cz / NZ) * NZ;
+    spec[(long long)cz * ncol + col0 + s] = buf[cc * CP + z * S + s];
+  }
+}
+
+}  // namespace tr2

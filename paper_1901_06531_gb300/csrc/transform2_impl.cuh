@@ -1,0 +1,95 @@
+// Launchers of the fixed-size transform kernels for one precision T; included
+// by transform2_f32.cu and transform2_f64.cu (one translation unit each).
+#pragma once
+
+#include "transform2.cuh"
+
+namespace tr2 {
+
+template <typename T, int NX>
+cudaError_t launch_xyf(const T* in, void* spec, const XYArgs& a, cudaStream_t st) {
+  typedef typename CT<T>::t C;
+  const size_t sm = XYShape<T, NX>::smem();
+  cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_xyf<T, NX><<<9 * a.nz, kThreads, sm, st>>>(in, (C*)spec, a.nz, a.N, (const C*)a.twx, a.xpos);
+  ++g_mf_launches;
+  return cudaGetLastError();
+}
+
+template <typename T, int NX, int MODE>
+cudaError_t launch_xyi(const void* spec, T* out, double* partials, const XYArgs& a, const Scalars* sc,
+                       cudaStream_t st) {
+  typedef typename CT<T>::t C;
+  const size_t sm = XYShape<T, NX>::smem();
+  cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_xyi<T, NX, MODE><<<9 * a.nz, kThreads, sm, st>>>((const C*)spec, out, partials, a.nz, a.N,
+                                                     (const C*)a.twx, a.xpos, sc);
+  ++g_mf_launches;
+  return cudaGetLastError();
+}
+
+template <typename T, int NZ, int MODE>
+cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
+  typedef typename CT<T>::t C;
+  const size_t sm = ZShape<T, NZ>::smem();
+  cudaError_t e = cudaFuncSetAttribute(k_zp<T, NZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int ncol = a.ny * (a.nx / 2);
+  k_zp<T, NZ, MODE><<<ncol / ZShape<T, NZ>::S, kThreads, sm, st>>>((C*)spec, a);
+  ++g_mf_launches;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t xyf(const void* in, void* spec, const XYArgs& a, cudaStream_t st) {
+  const T* p = (const T*)in;
+  switch (a.nx) {
+    case 16: return launch_xyf<T, 16>(p, spec, a, st);
+    case 32: return launch_xyf<T, 32>(p, spec, a, st);
+    case 64: return launch_xyf<T, 64>(p, spec, a, st);
+    case 128: return launch_xyf<T, 128>(p, spec, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int MODE>
+cudaError_t xyi_m(const void* spec, void* out, double* partials, const XYArgs& a, const Scalars* sc,
+                  cudaStream_t st) {
+  T* o = (T*)out;
+  switch (a.nx) {
+    case 16: return launch_xyi<T, 16, MODE>(spec, o, partials, a, sc, st);
+    case 32: return launch_xyi<T, 32, MODE>(spec, o, partials, a, sc, st);
+    case 64: return launch_xyi<T, 64, MODE>(spec, o, partials, a, sc, st);
+    case 128: return launch_xyi<T, 128, MODE>(spec, o, partials, a, sc, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t xyi(int mode, const void* spec, void* out, double* partials, const XYArgs& a, const Scalars* sc,
+                cudaStream_t st) {
+  if (mode == 0) return xyi_m<T, 0>(spec, out, partials, a, sc, st);
+  if (mode == 2) return xyi_m<T, 2>(spec, out, partials, a, sc, st);
+  if (mode == 3) return xyi_m<T, 3>(spec, out, partials, a, sc, st);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int MODE>
+cudaError_t zp_m(void* spec, const ZArgs& a, cudaStream_t st) {
+  switch (a.nz) {
+    case 16: return launch_zp<T, 16, MODE>(spec, a, st);
+    case 32: return launch_zp<T, 32, MODE>(spec, a, st);
+    case 64: return launch_zp<T, 64, MODE>(spec, a, st);
+    case 128: return launch_zp<T, 128, MODE>(spec, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t zp(int mode, void* spec, const ZArgs& a, cudaStream_t st) {
+  return mode == 1 ? zp_m<T, 1>(spec, a, st) : zp_m<T, 0>(spec, a, st);
+}
+
+}  // namespace tr2

@@ -17,6 +17,8 @@ MASKS = [np.zeros(9, np.uint8), np.ones(9, np.uint8),
 # (nx, ny, nz): smallest grid, cubic, anisotropic with radix 3, odd nz, 3-stage
 # planes, a grid spanning many z-pass tiles
 SHAPES = [(4, 4, 2), (16, 16, 16), (12, 8, 6), (48, 36, 18), (24, 6, 9), (32, 64, 12)]
+# square x-y planes with z lengths the fixed-size transform kernels cover
+SHAPES_V2 = [(32, 32, 32), (64, 64, 16), (128, 128, 16), (16, 16, 128), (64, 64, 64)]
 
 
 def torch_field(a, dtype):
@@ -137,3 +139,83 @@ def test_residual_fp64(shape, mi):
     got = b.cpu().numpy().reshape(ref.shape)
     assert rel(got, ref) < 1e-12
     np.testing.assert_allclose(meanP, P.reshape(9, -1).mean(1), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("shape", SHAPES_V2)
+@pytest.mark.parametrize("mi", [0, 2])
+def test_fixed_size_kernels_fp64(shape, mi):
+    """The fixed-size kernels (half-length real rows, radix-8/16 stages) in
+    FP64: operator and residual to 1e-12 relative."""
+    import torch
+    mf = lib()
+    ctx, om, F = make(mf, shape, mf.MF_FP64, "nh", seed=12)
+    ctx.constitutive()
+    nx, ny, nz = shape
+    x = inputs.random_field((nz, ny, nx), 13)
+    xt = torch_field(x, torch.float64)
+    yt = torch.full_like(xt, float("nan"))
+    ctx.matvec(xt, yt, MASKS[mi])
+    P, K = om.PK(F)
+    ref = osolver.matvec(K, x, MASKS[mi])
+    assert rel(yt.cpu().numpy().reshape(ref.shape), ref) < 1e-12
+    pbar = np.array([0.05, 0.01, 0.0, -0.01, 0.02, 0.0, 0.0, 0.0, -0.03])
+    b = torch.full_like(xt, float("nan"))
+    meanP = ctx.residual(MASKS[mi], pbar, b)
+    refb = osolver.residual(P, MASKS[mi], pbar)
+    assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
+    np.testing.assert_allclose(meanP, P.reshape(9, -1).mean(1), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("shape", SHAPES_V2[:4])
+def test_fixed_size_kernels_fp32(shape):
+    import torch
+    mf = lib()
+    ctx, om, F = make(mf, shape, mf.MF_FP32_INNER, "svk", seed=14)
+    ctx.constitutive()
+    nx, ny, nz = shape
+    x = inputs.random_field((nz, ny, nx), 15)
+    xt = torch_field(x, torch.float32)
+    yt = torch.full_like(xt, float("nan"))
+    ctx.matvec(xt, yt, MASKS[2])
+    _, K = om.PK(F)
+    ref = osolver.matvec(K, x.astype(np.float32).astype(np.float64), MASKS[2])
+    got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-6
+
+
+def test_full_size_polycrystal_operator_and_residual():
+    """The bench's workload and launch configuration (128^3, 200-grain SVK
+    polycrystal, rotation-fixed mask): FP32 operator against the FP64
+    oracle element by element, and the FP64 residual to 1e-12."""
+    import torch
+    mf = lib()
+    n = 128
+    g, _ = inputs.voronoi((n, n, n), 200, 1003)
+    R = inputs.random_rotations(200, 1004)
+    params = np.tile([168.0, 121.0, 75.0], (200, 1))
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(20, 0.2))
+    m0 = mask[0]
+    F = inputs.random_F((n, n, n), 16, 0.002)
+    om = omat.Material(g, omat.SVK_CUBIC, params, R)
+    P, K = om.PK(F)
+    for prec in (mf.MF_FP32_INNER, mf.MF_FP64):
+        ctx = mf.Context(n, n, n, prec)
+        ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+        ctx.set_F(F)
+        ctx.constitutive()
+        if prec == mf.MF_FP32_INNER:
+            x = inputs.random_field((n, n, n), 17)
+            xt = torch_field(x, torch.float32)
+            yt = torch.empty_like(xt)
+            ctx.matvec(xt, yt, m0)
+            ref = osolver.matvec(K, x.astype(np.float32).astype(np.float64), m0)
+            got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-6
+            assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref))
+        else:
+            b = torch.empty(9 * n ** 3, dtype=torch.float64, device="cuda")
+            ctx.residual(m0, target[0] * m0, b)
+            refb = osolver.residual(P, m0, target[0] * m0)
+            assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
+        del ctx
+        torch.cuda.empty_cache()
