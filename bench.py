@@ -226,7 +226,8 @@ def run_reference(args):
 # ---------------------------------------------------------------- GPU path
 def run_matvec_only(args):
     """Profiling driver: the 128^3 polycrystal tangent at the first load step,
-    then `--matvec-only` applications of the FP32 (or FP64) projected operator."""
+    then `--matvec-only` applications of the FP32 (or FP64) projected operator,
+    or (`--kernels-only R`) R L2-flushed launches of each CG-iteration kernel."""
     import torch
     from paper_1901_06531_gb300 import build
     build.build()
@@ -237,6 +238,11 @@ def run_matvec_only(args):
     ctx = mf.Context(n, n, n, prec)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
     ctx.constitutive()
+    if args.kernels_only:
+        ms = ctx.time_kernels(mask[0], reps=args.kernels_only)
+        print(json.dumps({"kernels_only": args.kernels_only, "fp64": bool(args.fp64),
+                          "ms": dict(zip(KERNELS, [float(m) for m in ms]))}))
+        return
     x = torch.randn(9 * n ** 3, dtype=ctx.inner_dtype, device="cuda")
     y = torch.empty_like(x)
     for _ in range(args.matvec_only):
@@ -423,9 +429,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: run this many projected-operator applications only")
-    ap.add_argument("--fp64", action="store_true", help="with --matvec-only: the FP64 operator")
+    ap.add_argument("--kernels-only", type=int, default=0,
+                    help="profiling driver: time the four CG-iteration kernels this many times each")
+    ap.add_argument("--fp64", action="store_true", help="with --matvec-only / --kernels-only: FP64")
     args = ap.parse_args()
-    if args.matvec_only:
+    if args.matvec_only or args.kernels_only:
         run_matvec_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -41,6 +41,25 @@ __device__ __forceinline__ void block_sum_cg(double (&v)[NC], double* out) {
   __syncthreads();
 }
 
+// Per-thread dot-product accumulator: exact FP32 products (two-product by FMA)
+// summed with Neumaier compensation in FP32; the thread totals are then
+// combined in FP64.  FP64 arithmetic per element would cost as much as the
+// whole pass on a part whose FP64 rate is 1/57 of its FP32 rate.
+struct Dot32 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_term(float v) {
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    add_term(p);
+    add_term(fmaf(a, b, -p));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __device__ __forceinline__ constexpr int vgt(int i, int j) {
   return i == j ? i : (i + j == 3 ? 3 : (i + j == 2 ? 4 : 5));
 }
@@ -140,21 +159,39 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
                                                       double* __restrict__ partials, const Scalars* sc) {
   __shared__ double tot[1];
   T beta = (T)0, alpha = (T)0;
-  if (CG) { beta = (T)sc->beta; alpha = (T)sc->alpha; }
-  double acc[1] = {0.0};
+  if (CG) {
+    if (*(volatile const int*)&sc->stop) return;
+    beta = (T)sc->beta;
+    alpha = (T)sc->alpha;
+  }
+  double acc64 = 0.0;
+  Dot32 acc32;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
+    // every load of the voxel is issued before any arithmetic
+    T po[9], rv[9], xv[9];
+    float h[9];
+    int ph = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) po[c] = pin[c * N + v];
+    if (CG) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) { rv[c] = r[c * N + v]; xv[c] = x[c * N + v]; }
+    }
+    if (TAN != 0) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) h[c] = ta.H[c * N + v];
+      ph = ta.phase[v];
+    }
     T q[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      const T po = pin[c * N + v];
       if (CG) {
-        const T pn = r[c * N + v] + beta * po;
-        x[c * N + v] += alpha * po;
-        pout[c * N + v] = pn;
-        q[c] = pn;
+        q[c] = rv[c] + beta * po[c];
+        x[c * N + v] = xv[c] + alpha * po[c];
+        pout[c * N + v] = q[c];
       } else {
-        q[c] = po;
+        q[c] = po[c];
       }
     }
     T o[9];
@@ -168,10 +205,9 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
         o[a] = s;
       }
     } else {
-      float h[9], qf[9], tf[9];
+      float qf[9], tf[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) { h[c] = ta.H[c * N + v]; qf[c] = (float)q[c]; }
-      const int ph = ta.phase[v];
+      for (int c = 0; c < 9; ++c) qf[c] = (float)q[c];
       if (TAN == 1) neohooke_apply(h, ta.table[2 * ph], ta.table[2 * ph + 1], qf, tf);
       else svk_apply(h, ta.table + 36 * ph, qf, tf);
       const float s = ta.scale ? ta.scale[v] : 1.f;
@@ -181,10 +217,12 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       t[c * N + v] = o[c];
-      acc[0] += (double)q[c] * (double)o[c];
+      if (sizeof(T) == 4) acc32.add_prod((float)q[c], (float)o[c]);
+      else acc64 += (double)q[c] * (double)o[c];
     }
   }
   if (partials) {
+    double acc[1] = {sizeof(T) == 4 ? acc32.value() : acc64};
     block_sum_cg<1>(acc, tot);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
   }
@@ -207,12 +245,14 @@ __device__ __forceinline__ double col_sum(const double* partials, int n, double*
 __global__ void __launch_bounds__(kThreads) k_fin_alpha(const double* __restrict__ partials, int n,
                                                         Scalars* sc) {
   __shared__ double shm[kThreads];
+  if (*(volatile const int*)&sc->stop) return;
   const double pAp = col_sum(partials, n, shm);
   if (threadIdx.x == 0) {
     sc->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       sc->flags |= MF_FLAG_BREAKDOWN;
       sc->alpha = 0.0;
+      sc->stop = 1;
     } else {
       sc->alpha = sc->rr / pAp;
     }
@@ -222,12 +262,15 @@ __global__ void __launch_bounds__(kThreads) k_fin_alpha(const double* __restrict
 __global__ void __launch_bounds__(kThreads) k_fin_beta(const double* __restrict__ partials, int n,
                                                        Scalars* sc) {
   __shared__ double shm[kThreads];
+  if (*(volatile const int*)&sc->stop) return;
   const double rr = col_sum(partials, n, shm);
   if (threadIdx.x == 0) {
     if (!isfinite(rr)) sc->flags |= MF_FLAG_NONFINITE;
     sc->beta = rr / sc->rr;
     sc->rr = rr;
     sc->done = (rr <= sc->thr2N) ? 1 : 0;
+    sc->its += 1;
+    sc->stop = (sc->done || sc->flags || sc->its >= sc->max_its) ? 1 : 0;
   }
 }
 
@@ -241,11 +284,13 @@ __global__ void k_axpy_alpha(T* __restrict__ x, const T* __restrict__ p, long lo
 
 // H = F - I in FP32 (the state the matrix-free tangent needs).
 __global__ void k_make_H(const double* __restrict__ F, float* __restrict__ H, long long N) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 9 * N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / N);
-    const double d = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
-    H[i] = (float)(F[i] - d);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const double d = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
+      H[c * N + v] = (float)(F[c * N + v] - d);
+    }
   }
 }
 
@@ -271,6 +316,18 @@ cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* 
 
 cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st) {
   k_fin_alpha<<<1, kThreads, 0, st>>>(partials, n, sc);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_batch_init(Scalars* sc, int max_its) {
+  sc->its = 0;
+  sc->max_its = max_its;
+  sc->stop = (sc->done || sc->flags) ? 1 : 0;
+}
+
+cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st) {
+  k_cg_batch_init<<<1, 1, 0, st>>>(sc, max_its);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

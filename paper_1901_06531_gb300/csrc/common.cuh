@@ -172,7 +172,10 @@ struct Scalars {
   double What[9];     // skew matrix of the last null-rotation projection
   int flags;          // bit 0: breakdown, bit 1: nonpositive J, bit 2: non-finite
   int done;           // CG converged
-  int pad[2];
+  int its;            // CG iterations completed
+  int stop;           // CG finished (converged, failed or capped): iteration kernels return at once
+  int max_its;
+  int pad;
 };
 
 #define MF_FLAG_BREAKDOWN 1

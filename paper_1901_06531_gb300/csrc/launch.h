@@ -6,6 +6,7 @@
 
 struct XYArgs {
   int v2;          // 1: fixed-size kernels (transform2*.cu), tables of that layout
+  const int* skip; // if non-null and *skip != 0 the kernel returns at once (finished CG)
   int nx, ny, nz;
   long long N;
   AxisPlan px;     // length nx
@@ -17,6 +18,7 @@ struct XYArgs {
 
 struct ZArgs {
   int v2;
+  const int* skip;
   int nx, ny, nz;
   long long N;
   AxisPlan pz;
@@ -77,6 +79,7 @@ cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* 
                               int nblk, const Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaStream_t st);
+cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st);
 cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, const Scalars* sc,
                                  cudaStream_t st);
 cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_t st);
@@ -89,9 +92,11 @@ struct MatArgs {
   const int32_t* phase;
   const double* scale;    // per-voxel multiplier of P and K, or null
 };
+// P (and K if want_K) at F, voxel averages of F and P; with moments (and
+// !want_K) also the rotation moments T, S into sc.
 cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k_f32, bool want_K,
-                                   const MatArgs& m, long long N, double* partials, int nblk,
-                                   Scalars* sc, cudaStream_t st);
+                                   bool moments, const MatArgs& m, long long N, double* partials,
+                                   int nblk, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int nblk, Scalars* sc,
                              cudaStream_t st);
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,
@@ -107,8 +112,6 @@ struct Defl {
 };
 cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool defl, long long N,
                                     double* partials, int nblk, Scalars* sc, cudaStream_t st);
-cudaError_t mf_launch_moments(const double* F, const double* P, long long N, double* partials, int nblk,
-                              Scalars* sc, cudaStream_t st);
 // Removes from y (9N, double or float) its components along the n_k:
 // y -= What F with What = sum_k (n_k . y) W_k; What is kept in sc for reuse.
 cudaError_t mf_launch_defl_project(void* y, bool f32, bool apply, const double* F, long long N,

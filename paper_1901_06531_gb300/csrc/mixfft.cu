@@ -221,6 +221,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_CUDA_ERROR
 XYArgs xy_args(const mf_ctx* c, bool f32) {
   XYArgs a;
   a.v2 = c->v2;
+  a.skip = nullptr;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
   const size_t tw = f32 ? c->otw32 : c->otw64;
@@ -277,10 +278,11 @@ int flags_status(int flags) {
 
 // P (and optionally the packed K) at the current F, voxel averages of F and
 // P; with want_H the FP32 H = F - I for the matrix-free tangent.
-int run_constitutive(mf_ctx* c, bool want_K, bool want_H) {
+int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false) {
   cudaError_t e = mf_launch_constitutive(c->at<double>(c->oF), c->at<double>(c->oP), c->ws + c->oK,
-                                         c->f32(), want_K, mat_args(c), c->N, c->at<double>(c->opart),
-                                         kPointwiseBlocks, c->at<Scalars>(c->osc), c->st);
+                                         c->f32(), want_K, moments, mat_args(c), c->N,
+                                         c->at<double>(c->opart), kPointwiseBlocks,
+                                         c->at<Scalars>(c->osc), c->st);
   c->have_K = want_K && e == cudaSuccess;
   if (e == cudaSuccess && want_H) e = mf_launch_make_H(c->at<double>(c->oF), c->at<float>(c->oH), c->N, c->st);
   c->have_H = want_H && e == cudaSuccess;
@@ -337,25 +339,42 @@ int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max
   const long long n9 = 9 * c->N;
   void* x = c->ws + c->ox;
   void* r = c->ws + c->or_;
-  void* pa = c->ws + c->op;    // previous direction
-  void* pb = c->ws + c->op2;   // current direction
+  void* pbuf[2] = {c->ws + c->op, c->ws + c->op2};   // iteration j reads pbuf[j%2], writes pbuf[(j+1)%2]
   void* t = c->ws + c->oAp;
   Scalars* sc = c->at<Scalars>(c->osc);
   double* part = c->at<double>(c->opart);
-  const ZArgs za = z_args(c, f32, mask, 1.0 / (double)c->N);
-  const XYArgs xa = xy_args(c, f32);
+  ZArgs za = z_args(c, f32, mask, 1.0 / (double)c->N);
+  XYArgs xa = xy_args(c, f32);
+  za.skip = &sc->stop;
+  xa.skip = &sc->stop;
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
   const int nplanes = 9 * c->nz;
-  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, pa, f32, n9, part, kPointwiseBlocks,
+  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, pbuf[0], f32, n9, part, kPointwiseBlocks,
                                     tol_cg, f32 ? cg_rel : 0.0, c->N, sc, c->st);
+  if (e == cudaSuccess) e = mf_launch_cg_batch_init(sc, max_cg, c->st);
   if (e != cudaSuccess) return MF_CUDA_ERROR;
-  *its = 0;
+  // Iterations are issued in batches; every kernel of an iteration returns at
+  // once when the device-side stop flag is set (converged, failed or capped),
+  // so the host reads the scalars once per batch instead of once per
+  // iteration and the iteration count stays exact (kept on the device).
+  const int batch = 4;
+  int launched = 0;
   Scalars h;
   for (;;) {
+    for (int b = 0; b < batch; ++b, ++launched) {
+      void* pa = pbuf[launched & 1];
+      void* pb = pbuf[(launched + 1) & 1];
+      e = mf_launch_tangent(pa, r, pb, x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc, c->st);
+      if (e == cudaSuccess) e = mf_launch_fin_alpha(part, kPointwiseBlocks, sc, c->st);
+      if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, c->st);
+      if (e == cudaSuccess) e = mf_launch_fin_beta(part, nplanes, sc, c->st);
+      if (e != cudaSuccess) return MF_CUDA_ERROR;
+    }
     int s = read_scalars(c, &h);
     if (s) return s;
-    if (f32 && (h.flags & MF_FLAG_BREAKDOWN) && !(h.flags & ~MF_FLAG_BREAKDOWN) && *its > 1) {
+    *its = h.its;
+    if (f32 && (h.flags & MF_FLAG_BREAKDOWN) && !(h.flags & ~MF_FLAG_BREAKDOWN) && h.its > 1) {
       // FP32 inner solve: a direction of non-positive curvature after some
       // progress ends the inner solve; the FP64 outer iteration continues
       // from the current iterate (alpha was set to 0 for that direction).
@@ -368,17 +387,12 @@ int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max
     s = flags_status(h.flags);
     if (s) return s;
     if (h.done) break;
-    if (*its >= max_cg) return MF_NOT_CONVERGED;
-    e = mf_launch_tangent(pa, r, pb, x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc, c->st);
-    if (e == cudaSuccess) e = mf_launch_fin_alpha(part, kPointwiseBlocks, sc, c->st);
-    if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, c->st);
-    if (e == cudaSuccess) e = mf_launch_fin_beta(part, nplanes, sc, c->st);
-    if (e != cudaSuccess) return MF_CUDA_ERROR;
-    void* tmp = pa; pa = pb; pb = tmp;
-    ++*its;
+    if (h.its >= max_cg) return MF_NOT_CONVERGED;
   }
   // the solution lags one direction behind: x += alpha p of the last iteration
-  if (*its > 0 && mf_launch_axpy_alpha(x, pa, f32, n9, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+  // (that direction sits in pbuf[its % 2])
+  if (h.its > 0 && mf_launch_axpy_alpha(x, pbuf[h.its & 1], f32, n9, sc, c->st) != cudaSuccess)
+    return MF_CUDA_ERROR;
   return MF_OK;
 }
 
@@ -447,7 +461,8 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->oscale32 = take(N * sizeof(float));
   c->otable = take((size_t)kMaxPhases * 36 * sizeof(double));
   c->otable32 = take((size_t)kMaxPhases * 36 * sizeof(float));
-  c->npart = (size_t)(kPointwiseBlocks > 9 * nz ? kPointwiseBlocks : 9 * nz) * 18;
+  // widest reduction: the constitutive pass with rotation moments, 36 columns per block
+  c->npart = (size_t)(kPointwiseBlocks > 9 * nz ? kPointwiseBlocks : 9 * nz) * 36;
   c->opart = take(c->npart * sizeof(double));
   c->osc = take(sizeof(Scalars));
   c->ores = take(9 * sizeof(double));
@@ -716,7 +731,7 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
     int s;
     for (;;) {
       const bool last = nn > 0 && ratio < tol_newton;
-      s = run_constitutive(c, !last && !c->f32(), !last && c->f32());
+      s = run_constitutive(c, !last && !c->f32(), !last && c->f32(), !last && c->f32());
       if (s) return s;
       if (last) break;
       if (nn >= max_newton) return MF_NOT_CONVERGED;
@@ -728,9 +743,7 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
         // FP32 inner solves: remove the null rigid rotations from the
         // right-hand side and from the correction (their FP64 rounding noise
         // would otherwise be amplified by a near-zero curvature)
-        if (mf_launch_moments(F, c->at<double>(c->oP), N, part, kPointwiseBlocks, sc, c->st) !=
-            cudaSuccess)
-          return MF_CUDA_ERROR;
+        // T and S come from the constitutive pass of this iteration
         s = read_scalars(c, &h);
         if (s) return s;
         defl = null_rotations(h.meanF, m, h.T, h.S, c->kappa, 1e-6);

@@ -178,16 +178,24 @@ __device__ __forceinline__ void svk(const double (&f)[9], const double* __restri
   }
 }
 
-template <typename TK>
+// P (and with WK the packed K) per voxel, and block partial sums of F and P;
+// with MOM also the rotation moments T = sum P F^T and S = sum F F^T (FP32
+// products, used only to detect null rotations).  Columns: F 0-8, P 9-17,
+// T 18-26, S 27-35.
+template <typename TK, bool WK, bool MOM>
 __global__ void __launch_bounds__(kRedThreads) k_constitutive(const double* __restrict__ F,
                                                               double* __restrict__ P, void* K45,
-                                                              bool want_K, MatArgs m, long long N,
+                                                              MatArgs m, long long N,
                                                               double* __restrict__ partials,
                                                               Scalars* sc) {
-  __shared__ double tot[18];
-  double acc[18];
+  constexpr int NC = MOM ? 36 : 18;
+  __shared__ double tot[NC];
+  double acc[NC];
 #pragma unroll
   for (int c = 0; c < 18; ++c) acc[c] = 0.0;
+  float mom[18];
+#pragma unroll
+  for (int c = 0; c < 18; ++c) mom[c] = 0.f;
   bool bad = false;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
@@ -197,9 +205,9 @@ __global__ void __launch_bounds__(kRedThreads) k_constitutive(const double* __re
     const int ph = m.phase[v];
     const double s = m.scale ? m.scale[v] : 1.0;
     if (m.model == 0) {
-      if (!neohooke<TK>(f, m.table[2 * ph], m.table[2 * ph + 1], s, p, K45, N, v, want_K)) bad = true;
+      if (!neohooke<TK>(f, m.table[2 * ph], m.table[2 * ph + 1], s, p, K45, N, v, WK)) bad = true;
     } else {
-      svk<TK>(f, m.table + 36 * ph, s, p, K45, N, v, want_K);
+      svk<TK>(f, m.table + 36 * ph, s, p, K45, N, v, WK);
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
@@ -207,10 +215,26 @@ __global__ void __launch_bounds__(kRedThreads) k_constitutive(const double* __re
       acc[c] += f[c];
       acc[9 + c] += p[c];
     }
+    if (MOM) {
+      float ff[9], pf[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) { ff[c] = (float)f[c]; pf[c] = (float)p[c]; }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          mom[3 * i + j] += pf[3 * i] * ff[3 * j] + pf[3 * i + 1] * ff[3 * j + 1] + pf[3 * i + 2] * ff[3 * j + 2];
+          mom[9 + 3 * i + j] += ff[3 * i] * ff[3 * j] + ff[3 * i + 1] * ff[3 * j + 1] + ff[3 * i + 2] * ff[3 * j + 2];
+        }
+    }
   }
   if (bad) atomicOr(&sc->flags, MF_FLAG_NONPOS_J);
-  block_sum<18>(acc, tot);
-  if (threadIdx.x < 18) partials[blockIdx.x * 18 + threadIdx.x] = tot[threadIdx.x];
+  if constexpr (MOM) {
+#pragma unroll
+    for (int c = 0; c < 18; ++c) acc[18 + c] = (double)mom[c];
+  }
+  block_sum<NC>(acc, tot);
+  if (threadIdx.x < NC) partials[blockIdx.x * NC + threadIdx.x] = tot[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_fin_means(const double* __restrict__ partials, int nblk,
@@ -220,7 +244,9 @@ __global__ void __launch_bounds__(kRedThreads) k_fin_means(const double* __restr
     const double s = column_sum(partials, nblk, ncol, col, shm);
     if (threadIdx.x == 0) {
       if (col < 9) sc->meanF[col] = s / (double)N;
-      else sc->meanP[col - 9] = s / (double)N;
+      else if (col < 18) sc->meanP[col - 9] = s / (double)N;
+      else if (col < 27) sc->T[col - 18] = s;
+      else sc->S[col - 27] = s;
     }
   }
 }
@@ -252,10 +278,12 @@ struct Load9 {
 __global__ void k_predictor(double* __restrict__ F, long long N, Load9 ld, const Scalars* sc,
                             bool after_update) {
   const double* mean = after_update ? sc->meanF_new : sc->meanF;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 9 * N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / N);
-    if (ld.mask[c] == 0) F[i] += ld.target[c] - mean[c];
+  for (int c = 0; c < 9; ++c) {
+    if (ld.mask[c]) continue;
+    const double d = ld.target[c] - mean[c];
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x)
+      F[c * N + v] += d;
   }
 }
 
@@ -295,6 +323,8 @@ __global__ void __launch_bounds__(kRedThreads) k_fin_cg_init(const double* __res
 }
 
 // F += x, or with DEFL F += x - What F (What from the projection of x).
+// Partials: columns 0-8 the sums of the correction (the new averages are the
+// old ones plus its mean), column 9 the block max of abs(dF_v)^2.
 template <typename T, bool DEFL>
 __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restrict__ F,
                                                                const T* __restrict__ x, long long N,
@@ -304,29 +334,57 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
   double acc[10];
 #pragma unroll
   for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+  float xs[9], xc[9];          // compensated FP32 sums of an FP32 correction
+#pragma unroll
+  for (int c = 0; c < 9; ++c) { xs[c] = 0.f; xc[c] = 0.f; }
   double mx = 0.0;
+  double W[9];
+  if (DEFL) {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) W[t] = sc->What[t];
+  }
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
-    double n2 = 0.0;
-    double f[9], d[9];
+    double f[9];
+    T xv[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; d[c] = (double)x[c * N + v]; }
-    if (DEFL) {
+    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; xv[c] = x[c * N + v]; }
+    if (DEFL || sizeof(T) == 8) {
+      double d[9];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+      for (int c = 0; c < 9; ++c) d[c] = (double)xv[c];
+      if (DEFL) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-          d[3 * i + j] -= sc->What[3 * i] * f[j] + sc->What[3 * i + 1] * f[3 + j] +
-                          sc->What[3 * i + 2] * f[6 + j];
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            d[3 * i + j] -= W[3 * i] * f[j] + W[3 * i + 1] * f[3 + j] + W[3 * i + 2] * f[6 + j];
+      }
+      double n2 = 0.0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        F[c * N + v] = f[c] + d[c];
+        acc[c] += d[c];
+        n2 += d[c] * d[c];
+      }
+      mx = fmax(mx, n2);
+    } else {
+      float n2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const float d = (float)xv[c];
+        F[c * N + v] = f[c] + (double)d;
+        const float tt = xs[c] + d;
+        xc[c] += (fabsf(xs[c]) >= fabsf(d)) ? ((xs[c] - tt) + d) : ((d - tt) + xs[c]);
+        xs[c] = tt;
+        n2 = fmaf(d, d, n2);
+      }
+      mx = fmax(mx, (double)n2);
     }
+  }
+  if (!(DEFL || sizeof(T) == 8)) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const double fn = f[c] + d[c];
-      F[c * N + v] = fn;
-      acc[c] += fn;
-      n2 += d[c] * d[c];
-    }
-    mx = fmax(mx, n2);
+    for (int c = 0; c < 9; ++c) acc[c] = (double)xs[c] + (double)xc[c];
   }
   block_sum<10>(acc, tot);   // column 9 unused by the sum
   // block max of |dF_v|^2
@@ -335,62 +393,11 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    partials[blockIdx.x * 10 + 9] = m;
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
+    partials[blockIdx.x * 10 + 9] = mm;
   }
   if (threadIdx.x < 9) partials[blockIdx.x * 10 + threadIdx.x] = tot[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_fin_newton(const double* __restrict__ partials, int nblk,
-                                                            long long N, Scalars* sc) {
-  __shared__ double shm[kRedThreads];
-  for (int col = 0; col < 9; ++col) {
-    const double s = column_sum(partials, nblk, 10, col, shm);
-    if (threadIdx.x == 0) sc->meanF_new[col] = s / (double)N;
-  }
-  const double m = column_max(partials, nblk, 10, 9, shm);
-  if (threadIdx.x == 0) {
-    sc->dF2max = m;
-    if (!isfinite(m)) sc->flags |= MF_FLAG_NONFINITE;
-  }
-}
-
-// Rotation moments T = sum_v P_v F_v^T and S = sum_v F_v F_v^T (row-major).
-__global__ void __launch_bounds__(kRedThreads) k_moments(const double* __restrict__ F,
-                                                         const double* __restrict__ P, long long N,
-                                                         double* __restrict__ partials) {
-  __shared__ double tot[18];
-  double acc[18];
-#pragma unroll
-  for (int c = 0; c < 18; ++c) acc[c] = 0.0;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-       v += (long long)gridDim.x * blockDim.x) {
-    double f[9], p[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; p[c] = P[c * N + v]; }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        acc[3 * i + j] += p[3 * i] * f[3 * j] + p[3 * i + 1] * f[3 * j + 1] + p[3 * i + 2] * f[3 * j + 2];
-        acc[9 + 3 * i + j] += f[3 * i] * f[3 * j] + f[3 * i + 1] * f[3 * j + 1] + f[3 * i + 2] * f[3 * j + 2];
-      }
-  }
-  block_sum<18>(acc, tot);
-  if (threadIdx.x < 18) partials[blockIdx.x * 18 + threadIdx.x] = tot[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_fin_moments(const double* __restrict__ partials,
-                                                             int nblk, Scalars* sc) {
-  __shared__ double shm[kRedThreads];
-  for (int col = 0; col < 18; ++col) {
-    const double s = column_sum(partials, nblk, 18, col, shm);
-    if (threadIdx.x == 0) {
-      if (col < 9) sc->T[col] = s;
-      else sc->S[col - 9] = s;
-    }
-  }
 }
 
 // B = sum_v y_v F_v^T, the moments that give n_k . y = W_k : B.
@@ -458,6 +465,20 @@ __global__ void k_defl_apply(T* __restrict__ y, const double* __restrict__ F, lo
   }
 }
 
+__global__ void __launch_bounds__(kRedThreads) k_fin_newton(const double* __restrict__ partials, int nblk,
+                                                            long long N, Scalars* sc) {
+  __shared__ double shm[kRedThreads];
+  for (int col = 0; col < 9; ++col) {
+    const double s = column_sum(partials, nblk, 10, col, shm);
+    if (threadIdx.x == 0) sc->meanF_new[col] = sc->meanF[col] + s / (double)N;
+  }
+  const double m = column_max(partials, nblk, 10, 9, shm);
+  if (threadIdx.x == 0) {
+    sc->dF2max = m;
+    if (!isfinite(m)) sc->flags |= MF_FLAG_NONFINITE;
+  }
+}
+
 int grid_for(long long n) {
   long long g = (n + kRedThreads - 1) / kRedThreads;
   return (int)(g < 1 ? 1 : g);
@@ -466,13 +487,17 @@ int grid_for(long long n) {
 }  // namespace
 
 cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k_f32, bool want_K,
-                                   const MatArgs& m, long long N, double* partials, int nblk,
-                                   Scalars* sc, cudaStream_t st) {
-  if (k_f32)
-    k_constitutive<float><<<nblk, kRedThreads, 0, st>>>(F, P, K45, want_K, m, N, partials, sc);
-  else
-    k_constitutive<double><<<nblk, kRedThreads, 0, st>>>(F, P, K45, want_K, m, N, partials, sc);
-  k_fin_means<<<1, kRedThreads, 0, st>>>(partials, nblk, 18, N, sc);
+                                   bool moments, const MatArgs& m, long long N, double* partials,
+                                   int nblk, Scalars* sc, cudaStream_t st) {
+  if (want_K) {
+    if (k_f32) k_constitutive<float, true, false><<<nblk, kRedThreads, 0, st>>>(F, P, K45, m, N, partials, sc);
+    else k_constitutive<double, true, false><<<nblk, kRedThreads, 0, st>>>(F, P, K45, m, N, partials, sc);
+  } else if (moments) {
+    k_constitutive<double, false, true><<<nblk, kRedThreads, 0, st>>>(F, P, K45, m, N, partials, sc);
+  } else {
+    k_constitutive<double, false, false><<<nblk, kRedThreads, 0, st>>>(F, P, K45, m, N, partials, sc);
+  }
+  k_fin_means<<<1, kRedThreads, 0, st>>>(partials, nblk, (moments && !want_K) ? 36 : 18, N, sc);
   g_mf_launches += 2;
   return cudaGetLastError();
 }
@@ -512,14 +537,6 @@ cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool def
   else if (defl) k_newton_update<double, true><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials, sc);
   else k_newton_update<double, false><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials, sc);
   k_fin_newton<<<1, kRedThreads, 0, st>>>(partials, nblk, N, sc);
-  g_mf_launches += 2;
-  return cudaGetLastError();
-}
-
-cudaError_t mf_launch_moments(const double* F, const double* P, long long N, double* partials, int nblk,
-                              Scalars* sc, cudaStream_t st) {
-  k_moments<<<nblk, kRedThreads, 0, st>>>(F, P, N, partials);
-  k_fin_moments<<<1, kRedThreads, 0, st>>>(partials, nblk, sc);
   g_mf_launches += 2;
   return cudaGetLastError();
 }

@@ -19,6 +19,9 @@
 namespace tr2 {
 
 constexpr int kThreads = 256;
+// z-pass: 288 threads divide the butterfly counts of its tiles evenly
+// (9 components x S columns x NZ/R butterflies per stage)
+constexpr int kZThreads = 288;
 
 // Asynchronous global -> shared copies of one complex element (8 or 16
 // bytes); many in flight per thread without holding registers.
@@ -55,9 +58,10 @@ __device__ __forceinline__ void load_tables(C* twx, C* twy, int* posx, const C* 
 template <typename T, int NX>
 __global__ void __launch_bounds__(kThreads) k_xyf(const T* __restrict__ in, typename CT<T>::t* __restrict__ spec,
                                                   int nz, long long N, const typename CT<T>::t* __restrict__ gtw,
-                                                  const int* __restrict__ gpos) {
+                                                  const int* __restrict__ gpos, const int* skip) {
   typedef XYShape<T, NX> Sh;
   typedef typename CT<T>::t C;
+  if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -114,9 +118,11 @@ template <typename T, int NX, int MODE>
 __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __restrict__ spec, T* __restrict__ out,
                                                   double* __restrict__ partials, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
-                                                  const int* __restrict__ gpos, const Scalars* sc) {
+                                                  const int* __restrict__ gpos, const Scalars* sc,
+                                                  const int* skip) {
   typedef XYShape<T, NX> Sh;
   typedef typename CT<T>::t C;
+  if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -126,6 +132,13 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
   int* posx = reinterpret_cast<int*>(twy + NY);
   load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
+  if (MODE == 3) {
+    // the residual plane is read only at the end: start pulling it into L2 now
+    const char* rp = reinterpret_cast<const char*>(out + c * N + (long long)z * NY * NX);
+    constexpr int kLines = (NY * NX * (int)sizeof(T)) / 128;
+    for (int i = threadIdx.x; i < kLines; i += kThreads)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + 128 * i));
+  }
   const C* src = spec + ((long long)c * nz + z) * NY * H;
   for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
     const int y = idx / H, j = idx - (idx / H) * H;
@@ -171,7 +184,20 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
   __syncthreads();
   fft2::inverse<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
   C* dst = reinterpret_cast<C*>(out + c * N + (long long)z * NY * NX);
+  // per-thread sums: FP64 for FP64 data; for FP32 data exact FP32 products
+  // with Neumaier-compensated FP32 accumulation, combined in FP64 below
   double acc = 0.0;
+  float fs = 0.f, fc = 0.f;
+  auto fadd = [&](float v) {
+    const float tt = fs + v;
+    fc += (fabsf(fs) >= fabsf(v)) ? ((fs - tt) + v) : ((v - tt) + fs);
+    fs = tt;
+  };
+  auto fsq = [&](float v) {
+    const float p = v * v;
+    fadd(p);
+    fadd(fmaf(v, v, -p));
+  };
   T alpha = (T)0;
   if (MODE == 3) alpha = (T)sc->alpha;
 #pragma unroll 8
@@ -183,12 +209,17 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
       r.x -= alpha * v.x;
       r.y -= alpha * v.y;
       dst[idx] = r;
-      acc += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
+      if (sizeof(T) == 4) { fsq((float)r.x); fsq((float)r.y); }
+      else acc += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
     } else {
       dst[idx] = v;
-      if (MODE == 2) acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      if (MODE == 2) {
+        if (sizeof(T) == 4) { fsq((float)v.x); fsq((float)v.y); }
+        else acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
     }
   }
+  if (sizeof(T) == 4) acc = (double)fs + (double)fc;
   if (MODE >= 2) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -217,20 +248,21 @@ struct ZShape {
 // MODE 0: operator (scale, mask).  MODE 1: residual (adds a.add at the null
 // frequency, records the null-frequency coefficient / N in a.mean_out).
 template <typename T, int NZ, int MODE>
-__global__ void __launch_bounds__(kThreads) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
+__global__ void __launch_bounds__(kZThreads) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
   typedef ZShape<T, NZ> Sh;
   typedef typename CT<T>::t C;
+  if (a.skip && *(volatile const int*)a.skip) return;
   constexpr int S = Sh::S, CP = Sh::CP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [9][CP]
   C* twz = buf + 9 * CP;
   int* zk = reinterpret_cast<int*>(twz + NZ);
   const C* gtwz = reinterpret_cast<const C*>(a.twz);
-  for (int i = threadIdx.x; i < NZ; i += kThreads) { twz[i] = gtwz[i]; zk[i] = a.zk[i]; }
+  for (int i = threadIdx.x; i < NZ; i += kZThreads) { twz[i] = gtwz[i]; zk[i] = a.zk[i]; }
   const int H = a.nx / 2;
   const int ncol = a.ny * H;
   const int col0 = blockIdx.x * S;
-  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kZThreads) {
     const int s = idx % S, cz = idx / S;
     const int cc = cz / NZ, z = cz - (cz / NZ) * NZ;
     cp_async_elem(buf + cc * CP + z * S + s, spec + (long long)cz * ncol + col0 + s);
@@ -239,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_zp(typename CT<T>::t* __restrict__
   __syncthreads();
   fft2::forward<C, NZ, NZ, 9 * S, S, CP, 1, S>(buf, twz);
   const T scale = (T)a.scale;
-  for (int idx = threadIdx.x; idx < NZ * S; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NZ * S; idx += kZThreads) {
     const int s = idx % S, p = idx / S;
     const int col = col0 + s;
     const int row = col / H, slot = col - (col / H) * H;
@@ -283,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_zp(typename CT<T>::t* __restrict__
   __syncthreads();
   fft2::inverse<C, NZ, NZ, 9 * S, S, CP, 1, S>(buf, twz);
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kZThreads) {
     const int s = idx % S, cz = idx / S;
     const int cc = cz / NZ, z = cz - (cz / NZ) * NZ;
     spec[(long long)cz * ncol + col0 + s] = buf[cc * CP + z * S + s];

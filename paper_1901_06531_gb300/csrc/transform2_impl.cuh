@@ -12,7 +12,7 @@ cudaError_t launch_xyf(const T* in, void* spec, const XYArgs& a, cudaStream_t st
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_xyf<T, NX><<<9 * a.nz, kThreads, sm, st>>>(in, (C*)spec, a.nz, a.N, (const C*)a.twx, a.xpos);
+  k_xyf<T, NX><<<9 * a.nz, kThreads, sm, st>>>(in, (C*)spec, a.nz, a.N, (const C*)a.twx, a.xpos, a.skip);
   ++g_mf_launches;
   return cudaGetLastError();
 }
@@ -25,7 +25,7 @@ cudaError_t launch_xyi(const void* spec, T* out, double* partials, const XYArgs&
   cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_xyi<T, NX, MODE><<<9 * a.nz, kThreads, sm, st>>>((const C*)spec, out, partials, a.nz, a.N,
-                                                     (const C*)a.twx, a.xpos, sc);
+                                                     (const C*)a.twx, a.xpos, sc, a.skip);
   ++g_mf_launches;
   return cudaGetLastError();
 }
@@ -37,7 +37,7 @@ cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_zp<T, NZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int ncol = a.ny * (a.nx / 2);
-  k_zp<T, NZ, MODE><<<ncol / ZShape<T, NZ>::S, kThreads, sm, st>>>((C*)spec, a);
+  k_zp<T, NZ, MODE><<<ncol / ZShape<T, NZ>::S, kZThreads, sm, st>>>((C*)spec, a);
   ++g_mf_launches;
   return cudaGetLastError();
 }
