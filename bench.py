@@ -355,6 +355,24 @@ def run_ours(args):
 
     time_matvec(ctx, x, y, 3)
     mv32_ms = time_matvec(ctx, x, y, 30)
+
+    def time_cufft_matvec(c, xx, yy, reps):
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.matvec_cufft(xx, yy, m0)
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ts]))
+
+    # comparison: the same operator with cuFFT transforms
+    ctx.cufft_bind()
+    time_cufft_matvec(ctx, x, y, 3)
+    cf32_ms = time_cufft_matvec(ctx, x, y, 30)
+    cf32_parts = ctx.time_cufft(m0, reps=10)
     del ctx, x, y
     torch.cuda.empty_cache()
 
@@ -377,6 +395,9 @@ def run_ours(args):
     y64 = torch.empty_like(x64)
     time_matvec(ctx64, x64, y64, 2)
     mv64_ms = time_matvec(ctx64, x64, y64, 10)
+    ctx64.cufft_bind()
+    time_cufft_matvec(ctx64, x64, y64, 2)
+    cf64_ms = time_cufft_matvec(ctx64, x64, y64, 10)
     kms64 = ctx64.time_kernels(m0, reps=5)
     del ctx64, x64, y64
 
@@ -405,6 +426,10 @@ def run_ours(args):
         "kernels_fp64": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9}
                          for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
         "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9},
+        "matvec_cufft_comparison_gvoxel_s": {
+            "fp32": N / (cf32_ms * 1e-3) / 1e9, "fp64": N / (cf64_ms * 1e-3) / 1e9,
+            "fp32_parts_ms": {"r2c": float(cf32_parts[0]), "gstar": float(cf32_parts[1]),
+                              "c2r": float(cf32_parts[2])}},
         "load_step_ms": {"fp32_inner_median": float(np.median(step_ms)),
                          "fp64_plain": fp64_ms, "fp64_steps_timed": fp64_steps},
         "iterations": {"fp32_inner_newton_cg_per_step": its,

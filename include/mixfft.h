@@ -177,6 +177,21 @@ int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
  * contexts); differences around a region count its launches. */
 long long mf_kernel_launches(void);
 
+/* ---- comparison path: cuFFT transforms (timing and cross-checks only) ----
+ * The same projected operator y = G*(K : x) as mf_matvec, with the library's
+ * tangent pass but cuFFT's 3D real-to-complex / complex-to-real transforms
+ * and a natural-order G-hat-star (Eq. eq:Gnewnew).  The solver never uses
+ * it.  mf_cufft_workspace_bytes creates the cuFFT plans (cuFFT keeps its own
+ * plan data) and returns the bytes of device buffer the caller must bind
+ * with mf_cufft_bind (natural-order spectrum and cuFFT work area), or 0 on
+ * failure.  mf_matvec_cufft: as mf_matvec.  mf_time_cufft: mean ms per
+ * launch of [0] the forward transform, [1] G-hat-star, [2] the inverse, each
+ * after an L2 flush, on the context's CG vectors. */
+size_t mf_cufft_workspace_bytes(mf_ctx* ctx);
+int mf_cufft_bind(mf_ctx* ctx, void* dev, size_t bytes);
+int mf_matvec_cufft(mf_ctx* ctx, const void* x_dev, void* y_dev, const uint8_t* mask);
+int mf_time_cufft(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
+
 /* Wait for the context's stream. */
 int mf_sync(mf_ctx* ctx);
 

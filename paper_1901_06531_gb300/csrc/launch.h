@@ -38,7 +38,7 @@ struct ZArgs {
 extern long long g_mf_launches;
 
 // transform2_f32.cu / transform2_f64.cu: fixed-size kernels for square x-y
-// planes nx = ny and z lengths in {16, 32, 64, 128}.  Their spectrum layout:
+// planes nx = ny and nx, nz in {16, 32, 48, 64, 96, 128}.  Their spectrum layout:
 // per (c, z) ny rows (digit-reversed ky, yk table of ny entries) of nx/2 slots
 // (digit-reversed kx, xk table of nx/2 entries), xpos = slot of kx.
 bool mf_v2_supported(int nx, int ny, int nz);
@@ -83,6 +83,16 @@ cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st);
 cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, const Scalars* sc,
                                  cudaStream_t st);
 cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_t st);
+
+// cufft_path.cu (comparison path)
+struct MfCufft;
+int mf_cufft_plan(MfCufft* p, int nx, int ny, int nz, bool f32, cudaStream_t st, size_t* need);
+int mf_cufft_bind(MfCufft* p, void* dev);
+int mf_cufft_project(MfCufft* p, bool f32, const void* t, void* y, int nx, int ny, int nz,
+                     const uint8_t* mask, cudaStream_t st, int which);
+void mf_cufft_destroy(MfCufft* p);
+MfCufft* mf_cufft_new();
+void mf_cufft_delete(MfCufft* p);
 
 // pointwise.cu
 struct MatArgs {

@@ -208,6 +208,8 @@ struct mf_ctx {
   bool has_scale = false;
   bool have_K = false;     // packed tangent of the current F is in the workspace
   bool have_H = false;     // FP32 H = F - I of the current F is in the workspace
+  MfCufft* cufft = nullptr;   // comparison path, created on demand
+  bool cufft_bound = false;
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   bool f32() const { return prec == MF_FP32_INNER; }
@@ -847,6 +849,70 @@ int mf_sync(mf_ctx* c) {
   return cuda_status(cudaStreamSynchronize(c->st));
 }
 
-void mf_destroy(mf_ctx* c) { delete c; }
+void mf_destroy(mf_ctx* c) {
+  if (!c) return;
+  mf_cufft_delete(c->cufft);
+  delete c;
+}
+
+size_t mf_cufft_workspace_bytes(mf_ctx* c) {
+  if (!c) return 0;
+  if (!c->cufft) c->cufft = mf_cufft_new();
+  size_t need = 0;
+  if (mf_cufft_plan(c->cufft, c->nx, c->ny, c->nz, c->f32(), c->st, &need) != MF_OK) return 0;
+  return need;
+}
+
+int mf_cufft_bind(mf_ctx* c, void* dev, size_t bytes) {
+  if (!c || !dev || ((uintptr_t)dev & 255)) return MF_INVALID_ARG;
+  const size_t need = mf_cufft_workspace_bytes(c);
+  if (need == 0) return MF_CUDA_ERROR;
+  if (bytes < need) return MF_INVALID_ARG;
+  const int s = mf_cufft_bind(c->cufft, dev);
+  c->cufft_bound = (s == MF_OK);
+  return s;
+}
+
+int mf_matvec_cufft(mf_ctx* c, const void* x_dev, void* y_dev, const uint8_t* mask) {
+  if (!c || !x_dev || !y_dev || !mask || x_dev == y_dev) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (!c->cufft_bound || !operator_ready(c)) return MF_INVALID_ARG;
+  cudaError_t e = mf_launch_tangent(x_dev, nullptr, nullptr, nullptr, c->f32(), tangent_kind(c), false,
+                                    tangent_args(c), c->ws + c->oAp, c->N, nullptr, kPointwiseBlocks,
+                                    nullptr, c->st);
+  if (e != cudaSuccess) return MF_CUDA_ERROR;
+  return mf_cufft_project(c->cufft, c->f32(), c->ws + c->oAp, y_dev, c->nx, c->ny, c->nz, mask, c->st, -1);
+}
+
+int mf_time_cufft(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
+  if (!c || !mask || !ms_out || reps < 1) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (!c->cufft_bound) return MF_INVALID_ARG;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
+  int s = MF_OK;
+  for (int which = 0; which < 3 && s == MF_OK; ++which) {
+    double tot = 0.0;
+    for (int r = 0; r < reps && s == MF_OK; ++r) {
+      cudaError_t e = cudaMemsetAsync(c->ws + c->ob, r & 0xff, 9 * c->N * sizeof(double), c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+      if (e != cudaSuccess) { s = MF_CUDA_ERROR; break; }
+      s = mf_cufft_project(c->cufft, c->f32(), c->ws + c->oAp, c->ws + c->or_, c->nx, c->ny, c->nz, mask,
+                           c->st, which);
+      if (s) break;
+      e = cudaEventRecord(e1, c->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { s = MF_CUDA_ERROR; break; }
+      tot += ms;
+    }
+    ms_out[which] = (float)(tot / reps);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
 
 }  // extern "C"

@@ -379,6 +379,6 @@ cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spe
 }
 
 bool mf_v2_supported(int nx, int ny, int nz) {
-  auto ok = [](int n) { return n == 16 || n == 32 || n == 64 || n == 128; };
+  auto ok = [](int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128; };
   return nx == ny && ok(nx) && ok(nz);
 }

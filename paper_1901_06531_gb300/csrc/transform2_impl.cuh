@@ -48,7 +48,9 @@ cudaError_t xyf(const void* in, void* spec, const XYArgs& a, cudaStream_t st) {
   switch (a.nx) {
     case 16: return launch_xyf<T, 16>(p, spec, a, st);
     case 32: return launch_xyf<T, 32>(p, spec, a, st);
+    case 48: return launch_xyf<T, 48>(p, spec, a, st);
     case 64: return launch_xyf<T, 64>(p, spec, a, st);
+    case 96: return launch_xyf<T, 96>(p, spec, a, st);
     case 128: return launch_xyf<T, 128>(p, spec, a, st);
     default: return cudaErrorInvalidValue;
   }
@@ -61,7 +63,9 @@ cudaError_t xyi_m(const void* spec, void* out, double* partials, const XYArgs& a
   switch (a.nx) {
     case 16: return launch_xyi<T, 16, MODE>(spec, o, partials, a, sc, st);
     case 32: return launch_xyi<T, 32, MODE>(spec, o, partials, a, sc, st);
+    case 48: return launch_xyi<T, 48, MODE>(spec, o, partials, a, sc, st);
     case 64: return launch_xyi<T, 64, MODE>(spec, o, partials, a, sc, st);
+    case 96: return launch_xyi<T, 96, MODE>(spec, o, partials, a, sc, st);
     case 128: return launch_xyi<T, 128, MODE>(spec, o, partials, a, sc, st);
     default: return cudaErrorInvalidValue;
   }
@@ -81,7 +85,9 @@ cudaError_t zp_m(void* spec, const ZArgs& a, cudaStream_t st) {
   switch (a.nz) {
     case 16: return launch_zp<T, 16, MODE>(spec, a, st);
     case 32: return launch_zp<T, 32, MODE>(spec, a, st);
+    case 48: return launch_zp<T, 48, MODE>(spec, a, st);
     case 64: return launch_zp<T, 64, MODE>(spec, a, st);
+    case 96: return launch_zp<T, 96, MODE>(spec, a, st);
     case 128: return launch_zp<T, 128, MODE>(spec, a, st);
     default: return cudaErrorInvalidValue;
   }

@@ -44,6 +44,11 @@ _lib.mf_matvec.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.mf_residual_noalloc.argtypes = [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.mf_time_kernels.argtypes = [_vp, _vp, _i, _vp]
+_lib.mf_cufft_workspace_bytes.argtypes = [_vp]
+_lib.mf_cufft_workspace_bytes.restype = _sz
+_lib.mf_cufft_bind.argtypes = [_vp, _vp, _sz]
+_lib.mf_matvec_cufft.argtypes = [_vp, _vp, _vp, _vp]
+_lib.mf_time_cufft.argtypes = [_vp, _vp, _i, _vp]
 _lib.mf_kernel_launches.argtypes = []
 _lib.mf_kernel_launches.restype = ctypes.c_longlong
 _lib.mf_sync.argtypes = [_vp]
@@ -54,7 +59,8 @@ _lib.mf_destroy.restype = None
 
 EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_material", "mf_set_F",
             "mf_solve", "mf_get_fields", "mf_constitutive", "mf_get_tangent", "mf_matvec",
-            "mf_residual", "mf_residual_noalloc", "mf_time_kernels", "mf_kernel_launches", "mf_sync", "mf_status_string",
+            "mf_residual", "mf_residual_noalloc", "mf_time_kernels", "mf_cufft_workspace_bytes",
+            "mf_cufft_bind", "mf_matvec_cufft", "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_status_string",
             "mf_destroy"]
 
 
@@ -201,6 +207,27 @@ class Context:
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         ms = np.zeros(4, dtype=np.float32)
         _check("mf_time_kernels", _lib.mf_time_kernels(self.h, _ptr(m), reps, _ptr(ms)))
+        return ms.astype(np.float64)
+
+    # -- cuFFT comparison path -------------------------------------------
+    def cufft_bind(self):
+        nbytes = int(_lib.mf_cufft_workspace_bytes(self.h))
+        if nbytes == 0:
+            raise MixFFTError("mf_cufft_workspace_bytes", MF_CUDA_ERROR)
+        self.cufft_buffer = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
+        aligned = (self.cufft_buffer.data_ptr() + 255) & ~255
+        _check("mf_cufft_bind", _lib.mf_cufft_bind(self.h, _vp(aligned), nbytes))
+
+    def matvec_cufft(self, x, y, mask):
+        assert x.dtype == self.inner_dtype and y.dtype == self.inner_dtype
+        assert x.is_contiguous() and y.is_contiguous() and x.numel() == 9 * self.N == y.numel()
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        _check("mf_matvec_cufft", _lib.mf_matvec_cufft(self.h, _vp(x.data_ptr()), _vp(y.data_ptr()), _ptr(m)))
+
+    def time_cufft(self, mask, reps=20):
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        ms = np.zeros(3, dtype=np.float32)
+        _check("mf_time_cufft", _lib.mf_time_cufft(self.h, _ptr(m), reps, _ptr(ms)))
         return ms.astype(np.float64)
 
     def sync(self):

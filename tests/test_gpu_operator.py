@@ -18,7 +18,8 @@ MASKS = [np.zeros(9, np.uint8), np.ones(9, np.uint8),
 # planes, a grid spanning many z-pass tiles
 SHAPES = [(4, 4, 2), (16, 16, 16), (12, 8, 6), (48, 36, 18), (24, 6, 9), (32, 64, 12)]
 # square x-y planes with z lengths the fixed-size transform kernels cover
-SHAPES_V2 = [(32, 32, 32), (64, 64, 16), (128, 128, 16), (16, 16, 128), (64, 64, 64)]
+SHAPES_V2 = [(32, 32, 32), (64, 64, 16), (128, 128, 16), (16, 16, 128), (64, 64, 64), (48, 48, 96),
+             (96, 96, 48)]
 
 
 def torch_field(a, dtype):
