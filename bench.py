@@ -252,6 +252,61 @@ def run_matvec_only(args):
                       "y_norm": float(y.double().norm())}))
 
 
+BATCH_CELLS, BATCH_SEED, BATCH_STEPS = 48, 1004, 4
+
+
+def run_batched(args):
+    """The batched workload: 48 sphere-particle cells with sizes drawn from
+    {32, 48, 64, 96}^3, random mixed control, FP32 inner / FP64 outer, all
+    solved at once (mf_solve_batch, one stream per cell), against the same
+    cells solved one after another."""
+    import torch
+    from paper_1901_06531_gb300 import inputs
+    from paper_1901_06531_gb300 import mixfft as mf
+    cells = inputs.batch_of_cells(BATCH_CELLS, BATCH_SEED, nsteps=BATCH_STEPS)
+    ctxs = []
+    for cell in cells:
+        n = cell["n"]
+        c = mf.Context(n, n, n, mf.MF_FP32_INNER, stream=torch.cuda.Stream())
+        c.set_material(mf.MF_NEOHOOKE, cell["params"], cell["phase"])
+        ctxs.append(c)
+    masks = np.stack([cell["mask"] for cell in cells])
+    targets = np.stack([cell["target"] for cell in cells])
+    voxels = sum(cell["n"] ** 3 for cell in cells)
+    # warm-up (graph instantiation, first touches), then from F = I again
+    mf.solve_batch(ctxs, masks[:, :1], targets[:, :1], TOL_NEWTON, TOL_CG, CG_REL)
+    for c in ctxs:
+        c.set_F(None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = mf.solve_batch(ctxs, masks, targets, TOL_NEWTON, TOL_CG, CG_REL)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    for c in ctxs:
+        c.set_F(None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, c in enumerate(ctxs):
+        c.solve(masks[i], targets[i], TOL_NEWTON, TOL_CG, CG_REL)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    sizes = {}
+    for cell in cells:
+        sizes[str(cell["n"])] = sizes.get(str(cell["n"]), 0) + 1
+    res = {"workload": (f"{BATCH_CELLS} sphere-particle neo-Hookean cells, sizes from {{32,48,64,96}}^3 "
+                        f"(seed {BATCH_SEED}), vf U(0.1,0.3), contrast U(5,50), random mixed control, "
+                        f"{BATCH_STEPS} load steps, FP32 inner / FP64 outer"),
+           "cells_by_size": sizes, "voxels_total": voxels,
+           "batch_s": t_batch, "sequential_s": t_seq,
+           "cell_load_steps_per_s": BATCH_CELLS * BATCH_STEPS / t_batch,
+           "gvoxel_load_steps_per_s": voxels * BATCH_STEPS / t_batch / 1e9,
+           "speedup_vs_sequential": t_seq / t_batch,
+           "newton_total": int(out["newton"].sum()), "cg_total": int(out["cg"].sum())}
+    del ctxs
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -279,6 +334,7 @@ def run_ours(args):
 
     ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    ztile, ztile_ms = ctx.autotune()
 
     def steps(c, k0, k1):
         idx = [k % nsteps_hist for k in range(k0, k1)]
@@ -401,6 +457,8 @@ def run_ours(args):
     kms64 = ctx64.time_kernels(m0, reps=5)
     del ctx64, x64, y64
 
+    batched = run_batched(args) if not args.no_batched else None
+
     peak, peak_kind = measured_peaks()
     dom = int(np.argmax(kms))
     achieved = ALGO_BYTES_F32[dom] * N / (kms[dom] * 1e-3) / 1e9
@@ -425,6 +483,8 @@ def run_ours(args):
                          for k, t, b in zip(KERNELS, kms, ALGO_BYTES_F32)},
         "kernels_fp64": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9}
                          for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
+        "autotune": {"zpass_tile_columns": ztile,
+                     "zpass_ms_by_tile": {str(w): float(m) for w, m in zip((2, 4, 8), ztile_ms)}},
         "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9},
         "matvec_cufft_comparison_gvoxel_s": {
             "fp32": N / (cf32_ms * 1e-3) / 1e9, "fp64": N / (cf64_ms * 1e-3) / 1e9,
@@ -435,6 +495,8 @@ def run_ours(args):
         "iterations": {"fp32_inner_newton_cg_per_step": its,
                        "fp64_newton": o64["newton"].tolist(), "fp64_cg": o64["cg"].tolist()},
     }
+    if batched is not None:
+        line["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         line["cpu_baseline"] = cpu_baseline_entry(oracle_sample(cores), cores)
@@ -452,6 +514,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 48-cell workload")
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: run this many projected-operator applications only")
     ap.add_argument("--kernels-only", type=int, default=0,

@@ -110,6 +110,22 @@ int mf_solve(mf_ctx* ctx, int nsteps, const uint8_t* mask, const double* target,
              double tol_newton, double tol_cg, double cg_rel, int max_newton,
              int max_cg, double* Fbar_out, double* Pbar_out, int32_t* iters_out);
 
+/* Run the same load history layout on n independent cells at once (the
+ * batched form: many RVEs of different grid sizes and control masks).  Each
+ * context must have its own workspace and should have its own CUDA stream;
+ * the cells' device work then overlaps.  One host thread drives all cells:
+ * it advances whichever cell has finished its last stretch of device work and
+ * never waits on a single cell.  Within each cell every CG solve is one graph
+ * launch (the iteration loop runs on the device).
+ *   masks, targets: host, n*nsteps*9, cell-major (cell i starts at 9*nsteps*i);
+ *   Fbar_out, Pbar_out: host, n*nsteps*9 or NULL; iters_out: n*nsteps*2 or
+ *   NULL; status_out: host, n int32 or NULL, each cell's mf_status.
+ * Returns MF_OK when every cell succeeded, else the first failing status.
+ * A context may appear only once. */
+int mf_solve_batch(int n, mf_ctx* const* ctxs, int nsteps, const uint8_t* masks, const double* targets,
+                   double tol_newton, double tol_cg, double cg_rel, int max_newton, int max_cg,
+                   double* Fbar_out, double* Pbar_out, int32_t* iters_out, int32_t* status_out);
+
 /* Copy the current F and P fields to host memory (9N doubles each; either
  * pointer may be NULL).  P is the stress at the current F. */
 int mf_get_fields(mf_ctx* ctx, double* F_host, double* P_host);
@@ -194,6 +210,21 @@ int mf_time_cufft(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
 
 /* Wait for the context's stream. */
 int mf_sync(mf_ctx* ctx);
+
+/* Autotuner: time the z-pass tile candidates (2, 4, 8 columns per block) of
+ * the fixed-size transform kernels for this context's size and precision and
+ * keep the fastest (CUDA events on the context's stream, L2 flushed before
+ * every launch).  The choice is cached per (nx, ny, nz, precision) for the
+ * process; mf_solve and mf_solve_batch run the tuner on a context's first
+ * solve if no choice is cached.  This call re-times and replaces the cached
+ * choice.  zs_out: host int32 or NULL, the chosen width; ms_out: host 3
+ * floats or NULL, mean ms per candidate (-1 when not applicable).  Contexts
+ * served by the generic kernels keep their fixed tile. */
+int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out);
+
+/* Name and description of the CUDA error behind the last MF_CUDA_ERROR
+ * returned by any context in this process ("" if none); static storage. */
+const char* mf_last_cuda_error(void);
 
 /* Static description of a status code. */
 const char* mf_status_string(int status);

@@ -282,6 +282,25 @@ __global__ void k_axpy_alpha(T* __restrict__ x, const T* __restrict__ p, long lo
     x[i] += a * p[i];
 }
 
+// End of a CG body in a graph: keep looping while the solve has not stopped.
+__global__ void k_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, *(volatile const int*)&sc->stop ? 0u : 1u);
+}
+
+// Final lagging update x += alpha p, with p the direction of the last
+// completed iteration (iteration j writes pbuf[(j+1) % 2]).
+template <typename T>
+__global__ void k_axpy_last(T* __restrict__ x, const T* __restrict__ p0, const T* __restrict__ p1, long long n,
+                            const Scalars* sc) {
+  const int its = sc->its;
+  if (its == 0) return;
+  const T* p = (its & 1) ? p1 : p0;
+  const T a = (T)sc->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] += a * p[i];
+}
+
 // H = F - I in FP32 (the state the matrix-free tangent needs).
 __global__ void k_make_H(const double* __restrict__ F, float* __restrict__ H, long long N) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
@@ -349,6 +368,21 @@ cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, 
 
 cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_t st) {
   k_make_H<<<152 * 8, kThreads, 0, st>>>(F, H, N);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_cg_cond<<<1, 1, 0, st>>>(sc, h);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_axpy_last(void* x, const void* p0, const void* p1, bool f32, long long n,
+                                const Scalars* sc, cudaStream_t st) {
+  const int g = 152 * 8;
+  if (f32) k_axpy_last<float><<<g, kThreads, 0, st>>>((float*)x, (const float*)p0, (const float*)p1, n, sc);
+  else k_axpy_last<double><<<g, kThreads, 0, st>>>((double*)x, (const double*)p0, (const double*)p1, n, sc);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

@@ -80,6 +80,9 @@ cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* 
 cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st);
+cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t mf_launch_axpy_last(void* x, const void* p0, const void* p1, bool f32, long long n,
+                                const Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, const Scalars* sc,
                                  cudaStream_t st);
 cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_t st);

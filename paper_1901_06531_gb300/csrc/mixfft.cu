@@ -2,10 +2,14 @@
 // and tables, and the host side of the Newton-CG loop of Eq. (linequil2ast)
 // under the per-component stress/strain control of Eq. (eq:mixedeqil).
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/mixfft.h"
@@ -210,6 +214,12 @@ struct mf_ctx {
   bool have_H = false;     // FP32 H = F - I of the current F is in the workspace
   MfCufft* cufft = nullptr;   // comparison path, created on demand
   bool cufft_bound = false;
+  // CG loop as one graph launch: a WHILE node whose body is two iterations
+  cudaGraph_t cg_graph = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  unsigned cg_mask = 0xffffffffu;
+  cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
+  bool tuned = false;              // z-pass tile chosen by the autotuner
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   bool f32() const { return prec == MF_FP32_INNER; }
@@ -218,7 +228,13 @@ struct mf_ctx {
 
 namespace {
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? MF_OK : MF_CUDA_ERROR; }
+char g_last_cuda_error[256] = "";
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MF_OK;
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return MF_CUDA_ERROR;
+}
 
 XYArgs xy_args(const mf_ctx* c, bool f32) {
   XYArgs a;
@@ -331,17 +347,32 @@ int run_matvec(mf_ctx* c, const void* x, void* y, const uint8_t* mask) {
   return cuda_status(e);
 }
 
-// One linear solve of Eq. (linequil2ast) by CG from dF = 0; the solution is
-// left in the x vector.  Per iteration: the tangent pass (direction update,
-// lagging solution update, K:p and p.Kp), the three transform passes whose
-// last one updates the residual, and two one-block reductions.  Returns a
-// status and the iteration count.
-int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max_cg, int* its) {
+void free_cg_graph(mf_ctx* c) {
+  if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+  if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
+  c->cg_exec = nullptr;
+  c->cg_graph = nullptr;
+  c->cg_mask = 0xffffffffu;
+}
+
+unsigned mask_bits(const uint8_t* mask) {
+  unsigned m = 0;
+  for (int k = 0; k < 9; ++k)
+    if (mask[k]) m |= 1u << k;
+  return m;
+}
+
+// The CG iteration loop of one linear solve as a graph: a WHILE conditional
+// node whose body holds two iterations (the two directions swap buffers) and
+// a one-thread kernel that keeps the condition set while the device-side stop
+// flag is clear.  The kernels of an iteration that starts after the stop
+// return at once, so the iteration count (kept on the device) is exact.
+int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
+  free_cg_graph(c);
   const bool f32 = c->f32();
-  const long long n9 = 9 * c->N;
   void* x = c->ws + c->ox;
   void* r = c->ws + c->or_;
-  void* pbuf[2] = {c->ws + c->op, c->ws + c->op2};   // iteration j reads pbuf[j%2], writes pbuf[(j+1)%2]
+  void* pbuf[2] = {c->ws + c->op, c->ws + c->op2};
   void* t = c->ws + c->oAp;
   Scalars* sc = c->at<Scalars>(c->osc);
   double* part = c->at<double>(c->opart);
@@ -352,50 +383,362 @@ int run_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
   const int nplanes = 9 * c->nz;
-  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), x, r, pbuf[0], f32, n9, part, kPointwiseBlocks,
-                                    tol_cg, f32 ? cg_rel : 0.0, c->N, sc, c->st);
-  if (e == cudaSuccess) e = mf_launch_cg_batch_init(sc, max_cg, c->st);
-  if (e != cudaSuccess) return MF_CUDA_ERROR;
-  // Iterations are issued in batches; every kernel of an iteration returns at
-  // once when the device-side stop flag is set (converged, failed or capped),
-  // so the host reads the scalars once per batch instead of once per
-  // iteration and the iteration count stays exact (kept on the device).
-  const int batch = 4;
-  int launched = 0;
-  Scalars h;
-  for (;;) {
-    for (int b = 0; b < batch; ++b, ++launched) {
-      void* pa = pbuf[launched & 1];
-      void* pb = pbuf[(launched + 1) & 1];
-      e = mf_launch_tangent(pa, r, pb, x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc, c->st);
-      if (e == cudaSuccess) e = mf_launch_fin_alpha(part, kPointwiseBlocks, sc, c->st);
-      if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, c->st);
-      if (e == cudaSuccess) e = mf_launch_fin_beta(part, nplanes, sc, c->st);
-      if (e != cudaSuccess) return MF_CUDA_ERROR;
-    }
-    int s = read_scalars(c, &h);
-    if (s) return s;
-    *its = h.its;
-    if (f32 && (h.flags & MF_FLAG_BREAKDOWN) && !(h.flags & ~MF_FLAG_BREAKDOWN) && h.its > 1) {
-      // FP32 inner solve: a direction of non-positive curvature after some
-      // progress ends the inner solve; the FP64 outer iteration continues
-      // from the current iterate (alpha was set to 0 for that direction).
-      int zero = 0;
-      if (cudaMemcpyAsync(&sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
-          cudaStreamSynchronize(c->st) != cudaSuccess)
-        return MF_CUDA_ERROR;
-      break;
-    }
-    s = flags_status(h.flags);
-    if (s) return s;
-    if (h.done) break;
-    if (h.its >= max_cg) return MF_NOT_CONVERGED;
+  if (!c->cap_st) {
+    const cudaError_t ec = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
+    if (ec != cudaSuccess) { c->cap_st = nullptr; return cuda_status(ec); }
   }
-  // the solution lags one direction behind: x += alpha p of the last iteration
-  // (that direction sits in pbuf[its % 2])
-  if (h.its > 0 && mf_launch_axpy_alpha(x, pbuf[h.its & 1], f32, n9, sc, c->st) != cudaSuccess)
+  cudaStream_t cs = c->cap_st;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e);
+  }
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_status(e);
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
+    e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc,
+                          cs);
+    if (e == cudaSuccess) e = mf_launch_fin_alpha(part, kPointwiseBlocks, sc, cs);
+    if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, cs);
+    if (e == cudaSuccess) e = mf_launch_fin_beta(part, nplanes, sc, cs);
+  }
+  if (e == cudaSuccess) e = mf_launch_cg_cond(sc, h, cs);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cg_exec, g, 0);
+  if (e != cudaSuccess) {
+    cuda_status(e);
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    c->cg_exec = nullptr;
     return MF_CUDA_ERROR;
+  }
+  c->cg_graph = g;
+  c->cg_mask = mask_bits(mask);
   return MF_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// The z-pass tile (columns per block: 2, 4 or 8 for the fixed-size kernels)
+// trades shared memory per block against blocks per SM and DRAM segment
+// length; the best choice depends on the z length and the precision.  Each
+// candidate is timed with CUDA events on the context's stream (L2 flushed
+// before every launch, one untimed launch first) and the fastest kept; the
+// choice is cached for the process per (nx, ny, nz, precision).
+struct TuneEntry { int nx, ny, nz, prec, S; float ms[3]; };
+std::vector<TuneEntry> g_tune_cache;
+std::mutex g_tune_mutex;
+
+int autotune(mf_ctx* c, int reps) {
+  if (!c->v2) { c->tuned = true; return MF_OK; }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (const TuneEntry& t : g_tune_cache)
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec) {
+        c->zS = t.S;
+        c->tuned = true;
+        return MF_OK;
+      }
+  }
+  const bool f32 = c->f32();
+  const int cands[3] = {2, 4, 8};
+  const uint8_t mask[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+  ZArgs za = z_args(c, f32, mask, 1.0 / (double)c->N);
+  const XYArgs xa = xy_args(c, f32);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
+  TuneEntry te{c->nx, c->ny, c->nz, c->prec, c->zS, {0, 0, 0}};
+  float best = 1e30f;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    za.S = cands[i];
+    if ((c->ny * (c->nx / 2)) % za.S) { te.ms[i] = -1; continue; }
+    double tot = 0.0;
+    for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+      e = cudaMemsetAsync(c->ws + c->ob, 0, 9 * c->N * sizeof(double), c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+      if (e == cudaSuccess)
+        e = mf_launch_project_part(1, f32, nullptr, c->ws + c->ospec, nullptr, nullptr, xa, za, nullptr, c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (r >= 0) tot += ms;
+    }
+    te.ms[i] = (float)(tot / reps);
+    if (e == cudaSuccess && te.ms[i] < best) { best = te.ms[i]; te.S = cands[i]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) { cudaGetLastError(); return cuda_status(e); }
+  c->zS = te.S;
+  c->tuned = true;
+  free_cg_graph(c);   // a captured loop holds the old tile
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune_cache.push_back(te);
+  return MF_OK;
+}
+
+// Enqueue one linear solve of Eq. (linequil2ast) by CG from dF = 0 (the
+// solution is left in the x vector): CG start, the graph with the device-side
+// iteration loop, and the last lagging solution update.  Per iteration: the
+// tangent pass (direction update, lagging solution update, K:p and p.Kp), the
+// three transform passes whose last one updates the residual, and two
+// one-block reductions.
+int launch_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int max_cg) {
+  const bool f32 = c->f32();
+  const long long n9 = 9 * c->N;
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  if (!c->cg_exec || c->cg_mask != mask_bits(mask)) {
+    const int s = build_cg_graph(c, mask);
+    if (s) return s;
+  }
+  cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), c->ws + c->ox, c->ws + c->or_, c->ws + c->op, f32, n9,
+                                    part, kPointwiseBlocks, tol_cg, f32 ? cg_rel : 0.0, c->N, sc, c->st);
+  if (e == cudaSuccess) e = mf_launch_cg_batch_init(sc, max_cg, c->st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(c->cg_exec, c->st);
+  if (e == cudaSuccess)
+    e = mf_launch_axpy_last(c->ws + c->ox, c->ws + c->op, c->ws + c->op2, f32, n9, sc, c->st);
+  return cuda_status(e);
+}
+
+// Outcome of the solve from the scalars read back after it.  *clear is set
+// when an FP32 inner solve ended on a direction of non-positive curvature
+// after some progress: that ends the inner solve without failing it (the FP64
+// outer iteration continues from the current iterate; alpha was 0 for that
+// direction) and the caller clears the flag.
+int cg_outcome(const mf_ctx* c, const Scalars& h, bool* clear) {
+  *clear = false;
+  if (c->f32() && (h.flags & MF_FLAG_BREAKDOWN) && !(h.flags & ~MF_FLAG_BREAKDOWN) && h.its > 1) {
+    *clear = true;
+    return MF_OK;
+  }
+  const int s = flags_status(h.flags);
+  if (s) return s;
+  if (!h.done) return MF_NOT_CONVERGED;
+  return MF_OK;
+}
+
+// ---------------------------------------------------------------- load steps
+// The Newton loop of one cell as a state machine that never blocks: every
+// advance() enqueues the next stretch of device work on the cell's stream,
+// followed by an asynchronous copy of the scalar block to pinned host memory
+// and an event, and returns.  mf_solve runs one machine; mf_solve_batch runs
+// many cells at once, advancing whichever cell's event has completed.
+struct Runner {
+  enum Phase { kStep, kAfterConst, kAfterUpdate, kAfterFinal, kDone, kFailed };
+  mf_ctx* c = nullptr;
+  int nsteps = 0;
+  const uint8_t* mask = nullptr;
+  const double* target = nullptr;
+  double tol_newton = 0, tol_cg = 0, cg_rel = 0;
+  int max_newton = 0, max_cg = 0;
+  double* Fbar_out = nullptr;
+  double* Pbar_out = nullptr;
+  int32_t* iters_out = nullptr;
+  Scalars* h = nullptr;          // pinned host copy of the scalar block
+  int* zero = nullptr;           // pinned 0 (clears a flag)
+  cudaEvent_t ev = nullptr;
+  Phase phase = kStep;
+  int status = MF_OK;
+  int k = 0, nn = 0, ncg = 0;
+  double ratio = INFINITY;
+  Defl defl;
+
+  int init() {
+    if (cudaMallocHost(&h, sizeof(Scalars)) != cudaSuccess) return MF_CUDA_ERROR;
+    if (cudaMallocHost(&zero, sizeof(int)) != cudaSuccess) return MF_CUDA_ERROR;
+    *zero = 0;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return MF_CUDA_ERROR;
+    Scalars* sc = c->at<Scalars>(c->osc);
+    if (mf_launch_mean_F(c->at<double>(c->oF), c->N, c->at<double>(c->opart), kPointwiseBlocks, sc, c->st) !=
+        cudaSuccess)
+      return MF_CUDA_ERROR;
+    defl.m = 0;
+    phase = nsteps > 0 ? kStep : kDone;
+    return MF_OK;
+  }
+  void release() {
+    if (h) cudaFreeHost(h);
+    if (zero) cudaFreeHost(zero);
+    if (ev) cudaEventDestroy(ev);
+    h = nullptr;
+    zero = nullptr;
+    ev = nullptr;
+  }
+  bool active() const { return phase != kDone && phase != kFailed; }
+  int fail(int s) { status = s; phase = kFailed; return s; }
+
+  // scalar block to pinned memory, then the event
+  int post() {
+    cudaError_t e = cudaMemcpyAsync(h, c->ws + c->osc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, c->st);
+    return cuda_status(e);
+  }
+
+  // constitutive pass: the full one (K in FP64, H and rotation moments in
+  // FP32) inside the Newton loop, P only for the final state of a step
+  int launch_constitutive(bool last) {
+    const bool f32 = c->f32();
+    return run_constitutive(c, !last && !f32, !last && f32, !last && f32);
+  }
+
+  int start_step() {
+    const uint8_t* m = mask + 9 * k;
+    const double* tgt = target + 9 * k;
+    Scalars* sc = c->at<Scalars>(c->osc);
+    if (mf_launch_predictor(c->at<double>(c->oF), c->N, m, tgt, sc, false, c->st) != cudaSuccess)
+      return MF_CUDA_ERROR;
+    nn = 0;
+    ncg = 0;
+    ratio = INFINITY;
+    int s = launch_constitutive(false);
+    if (s) return s;
+    phase = kAfterConst;
+    return post();
+  }
+
+  int newton_iteration() {
+    const uint8_t* m = mask + 9 * k;
+    const double* tgt = target + 9 * k;
+    double pbar[9];
+    for (int q = 0; q < 9; ++q) pbar[q] = m[q] ? tgt[q] : 0.0;
+    Scalars* sc = c->at<Scalars>(c->osc);
+    double* part = c->at<double>(c->opart);
+    double* F = c->at<double>(c->oF);
+    const long long N = c->N;
+    if (nn >= max_newton) return MF_NOT_CONVERGED;
+    int s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores));
+    if (s) return s;
+    defl.m = 0;
+    if (c->f32()) {
+      // FP32 inner solves: remove the null rigid rotations from the right-hand
+      // side and from the correction (their FP64 rounding noise would
+      // otherwise be amplified by a near-zero curvature); T and S come from
+      // the constitutive pass of this iteration
+      defl = null_rotations(h->meanF, m, h->T, h->S, c->kappa, 1e-6);
+      if (defl.m > 0 && mf_launch_defl_project(c->at<double>(c->ob), false, true, F, N, defl, part,
+                                               kPointwiseBlocks, sc, c->st) != cudaSuccess)
+        return MF_CUDA_ERROR;
+    }
+    s = launch_cg(c, m, tol_cg, cg_rel, max_cg);
+    if (s) return s;
+    if (defl.m > 0 && mf_launch_defl_project(c->ws + c->ox, true, false, F, N, defl, part, kPointwiseBlocks, sc,
+                                             c->st) != cudaSuccess)
+      return MF_CUDA_ERROR;
+    if (mf_launch_newton_update(F, c->ws + c->ox, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc, c->st) !=
+        cudaSuccess)
+      return MF_CUDA_ERROR;
+    // FP32 corrections carry a rounding-level average on the strain-controlled
+    // components; the FP64 outer level re-imposes F-bar there
+    if (c->f32() && mf_launch_predictor(F, N, m, tgt, sc, true, c->st) != cudaSuccess) return MF_CUDA_ERROR;
+    phase = kAfterUpdate;
+    return post();
+  }
+
+  // Called when ev has completed: consume *h, enqueue the next stretch.
+  int advance() {
+    int s = MF_OK;
+    switch (phase) {
+      case kStep:
+        s = start_step();
+        break;
+      case kAfterConst:
+        s = flags_status(h->flags);
+        if (!s) s = newton_iteration();
+        break;
+      case kAfterUpdate: {
+        bool clear = false;
+        s = cg_outcome(c, *h, &clear);
+        if (s) break;
+        if (clear && cudaMemcpyAsync(&c->at<Scalars>(c->osc)->flags, zero, sizeof(int), cudaMemcpyHostToDevice,
+                                     c->st) != cudaSuccess) {
+          s = MF_CUDA_ERROR;
+          break;
+        }
+        ncg += h->its;
+        // kernels the CG graph ran: 13 per pass of its two-iteration body
+        g_mf_launches += 13LL * (h->its == 0 ? 1 : (h->its + 1) / 2);
+        double fn = 0.0;
+        for (int q = 0; q < 9; ++q) fn += h->meanF_new[q] * h->meanF_new[q];
+        ratio = sqrt(h->dF2max) / sqrt(fn);
+        ++nn;
+        const bool last = ratio < tol_newton;
+        s = launch_constitutive(last);
+        if (!s) {
+          phase = last ? kAfterFinal : kAfterConst;
+          s = post();
+        }
+        break;
+      }
+      case kAfterFinal:
+        s = flags_status(h->flags);
+        if (s) break;
+        if (Fbar_out) memcpy(Fbar_out + 9 * k, h->meanF, 9 * sizeof(double));
+        if (Pbar_out) memcpy(Pbar_out + 9 * k, h->meanP, 9 * sizeof(double));
+        if (iters_out) { iters_out[2 * k] = nn; iters_out[2 * k + 1] = ncg; }
+        ++k;
+        if (k < nsteps) s = start_step();
+        else phase = kDone;
+        break;
+      default:
+        break;
+    }
+    if (s) return fail(s);
+    return MF_OK;
+  }
+
+  bool ready() const {
+    if (phase == kStep) return true;
+    return cudaEventQuery(ev) != cudaErrorNotReady;
+  }
+};
+
+int check_solve_args(const mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, double tol_newton,
+                     double tol_cg, double cg_rel, int max_newton, int max_cg) {
+  if (!c || nsteps < 0 || (nsteps > 0 && (!mask || !target)) || !(tol_newton > 0) || !(tol_cg > 0) ||
+      max_newton < 1 || max_cg < 1 || !(cg_rel >= 0))
+    return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (c->model < 0) return MF_INVALID_ARG;
+  for (int i = 0; i < 9 * nsteps; ++i)
+    if (mask[i] > 1 || !isfinite(target[i])) return MF_INVALID_ARG;
+  return MF_OK;
+}
+
+// Drive a set of runners to completion; a cell whose event is pending is
+// skipped, and the host sleeps briefly only when no cell can advance.
+void drive(std::vector<Runner>& rs) {
+  for (;;) {
+    bool any = false, progressed = false;
+    for (Runner& r : rs) {
+      if (!r.active()) continue;
+      any = true;
+      if (r.ready()) {
+        r.advance();
+        progressed = true;
+      }
+    }
+    if (!any) return;
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(5));
+  }
 }
 
 }  // namespace
@@ -487,6 +830,7 @@ int mf_bind_workspace(mf_ctx* c, void* dev, size_t bytes) {
   c->ws = (char*)dev;
   c->model = -1;
   c->have_K = false;
+  free_cg_graph(c);
   // host-built tables: digit-reversal maps and twiddles
   const int nx = c->nx, ny = c->ny, nz = c->nz;
   std::vector<int> xpos(nx, 0), xk(nx, 0), xe(nx, 0), yk(ny, 0), zk(nz, 0);
@@ -709,82 +1053,64 @@ int mf_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b_de
 int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, double tol_newton,
              double tol_cg, double cg_rel, int max_newton, int max_cg, double* Fbar_out,
              double* Pbar_out, int32_t* iters_out) {
-  if (!c || nsteps < 0 || (nsteps > 0 && (!mask || !target)) || !(tol_newton > 0) || !(tol_cg > 0) ||
-      max_newton < 1 || max_cg < 1 || !(cg_rel >= 0))
-    return MF_INVALID_ARG;
-  if (!c->ws) return MF_NO_WORKSPACE;
-  if (c->model < 0) return MF_INVALID_ARG;
-  for (int i = 0; i < 9 * nsteps; ++i)
-    if (mask[i] > 1 || !isfinite(target[i])) return MF_INVALID_ARG;
-  Scalars* sc = c->at<Scalars>(c->osc);
-  double* part = c->at<double>(c->opart);
-  double* F = c->at<double>(c->oF);
-  const long long N = c->N;
-  if (mf_launch_mean_F(F, N, part, kPointwiseBlocks, sc, c->st) != cudaSuccess) return MF_CUDA_ERROR;
-  Scalars h;
-  for (int k = 0; k < nsteps; ++k) {
-    const uint8_t* m = mask + 9 * k;
-    const double* tgt = target + 9 * k;
-    double pbar[9];
-    for (int q = 0; q < 9; ++q) pbar[q] = m[q] ? tgt[q] : 0.0;
-    if (mf_launch_predictor(F, N, m, tgt, sc, false, c->st) != cudaSuccess) return MF_CUDA_ERROR;
-    int nn = 0, ncg = 0;
-    double ratio = INFINITY;
-    int s;
-    for (;;) {
-      const bool last = nn > 0 && ratio < tol_newton;
-      s = run_constitutive(c, !last && !c->f32(), !last && c->f32(), !last && c->f32());
-      if (s) return s;
-      if (last) break;
-      if (nn >= max_newton) return MF_NOT_CONVERGED;
-      s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores));
-      if (s) return s;
-      Defl defl;
-      defl.m = 0;
-      if (c->f32()) {
-        // FP32 inner solves: remove the null rigid rotations from the
-        // right-hand side and from the correction (their FP64 rounding noise
-        // would otherwise be amplified by a near-zero curvature)
-        // T and S come from the constitutive pass of this iteration
-        s = read_scalars(c, &h);
-        if (s) return s;
-        defl = null_rotations(h.meanF, m, h.T, h.S, c->kappa, 1e-6);
-        if (defl.m > 0 && mf_launch_defl_project(c->at<double>(c->ob), false, true, F, N, defl, part,
-                                                 kPointwiseBlocks, sc, c->st) != cudaSuccess)
-          return MF_CUDA_ERROR;
-      }
-      int its = 0;
-      s = run_cg(c, m, tol_cg, cg_rel, max_cg, &its);
-      ncg += its;
-      if (s) return s;
-      if (defl.m > 0 && mf_launch_defl_project(c->ws + c->ox, true, false, F, N, defl, part,
-                                               kPointwiseBlocks, sc, c->st) != cudaSuccess)
-        return MF_CUDA_ERROR;
-      if (mf_launch_newton_update(F, c->ws + c->ox, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc,
-                                  c->st) != cudaSuccess)
-        return MF_CUDA_ERROR;
-      // FP32 corrections carry a rounding-level average on the strain-
-      // controlled components; the FP64 outer level re-imposes F-bar there
-      if (c->f32() && mf_launch_predictor(F, N, m, tgt, sc, true, c->st) != cudaSuccess)
-        return MF_CUDA_ERROR;
-      s = read_scalars(c, &h);
-      if (s) return s;
-      s = flags_status(h.flags);
-      if (s) return s;
-      double fn = 0.0;
-      for (int q = 0; q < 9; ++q) fn += h.meanF_new[q] * h.meanF_new[q];
-      ratio = sqrt(h.dF2max) / sqrt(fn);
-      ++nn;
-    }
-    s = read_scalars(c, &h);
-    if (s) return s;
-    s = flags_status(h.flags);
-    if (s) return s;
-    if (Fbar_out) memcpy(Fbar_out + 9 * k, h.meanF, 9 * sizeof(double));
-    if (Pbar_out) memcpy(Pbar_out + 9 * k, h.meanP, 9 * sizeof(double));
-    if (iters_out) { iters_out[2 * k] = nn; iters_out[2 * k + 1] = ncg; }
+  int s = check_solve_args(c, nsteps, mask, target, tol_newton, tol_cg, cg_rel, max_newton, max_cg);
+  if (s) return s;
+  if (!c->tuned && (s = autotune(c, 3))) return s;
+  std::vector<Runner> rs(1);
+  Runner& r = rs[0];
+  r.c = c; r.nsteps = nsteps; r.mask = mask; r.target = target;
+  r.tol_newton = tol_newton; r.tol_cg = tol_cg; r.cg_rel = cg_rel;
+  r.max_newton = max_newton; r.max_cg = max_cg;
+  r.Fbar_out = Fbar_out; r.Pbar_out = Pbar_out; r.iters_out = iters_out;
+  s = r.init();
+  if (!s) {
+    drive(rs);
+    s = r.status;
   }
-  return MF_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess && !s) s = MF_CUDA_ERROR;
+  r.release();
+  return s;
+}
+
+int mf_solve_batch(int n, mf_ctx* const* ctxs, int nsteps, const uint8_t* masks, const double* targets,
+                   double tol_newton, double tol_cg, double cg_rel, int max_newton, int max_cg,
+                   double* Fbar_out, double* Pbar_out, int32_t* iters_out, int32_t* status_out) {
+  if (n < 1 || !ctxs) return MF_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int s = check_solve_args(ctxs[i], nsteps, masks ? masks + (size_t)9 * nsteps * i : nullptr,
+                                   targets ? targets + (size_t)9 * nsteps * i : nullptr, tol_newton, tol_cg,
+                                   cg_rel, max_newton, max_cg);
+    if (s) return s;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return MF_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (ctxs[i]->tuned) continue;
+    const int s = autotune(ctxs[i], 3);
+    if (s) return s;
+  }
+  std::vector<Runner> rs(n);
+  int first = MF_OK;
+  for (int i = 0; i < n; ++i) {
+    Runner& r = rs[i];
+    r.c = ctxs[i]; r.nsteps = nsteps;
+    r.mask = masks + (size_t)9 * nsteps * i; r.target = targets + (size_t)9 * nsteps * i;
+    r.tol_newton = tol_newton; r.tol_cg = tol_cg; r.cg_rel = cg_rel;
+    r.max_newton = max_newton; r.max_cg = max_cg;
+    r.Fbar_out = Fbar_out ? Fbar_out + (size_t)9 * nsteps * i : nullptr;
+    r.Pbar_out = Pbar_out ? Pbar_out + (size_t)9 * nsteps * i : nullptr;
+    r.iters_out = iters_out ? iters_out + (size_t)2 * nsteps * i : nullptr;
+    const int s = r.init();
+    if (s) r.fail(s);
+  }
+  drive(rs);
+  for (int i = 0; i < n; ++i) {
+    if (cudaStreamSynchronize(rs[i].c->st) != cudaSuccess && !rs[i].status) rs[i].status = MF_CUDA_ERROR;
+    if (status_out) status_out[i] = rs[i].status;
+    if (rs[i].status && !first) first = rs[i].status;
+    rs[i].release();
+  }
+  return first;
 }
 
 int mf_get_fields(mf_ctx* c, double* F_host, double* P_host) {
@@ -849,8 +1175,38 @@ int mf_sync(mf_ctx* c) {
   return cuda_status(cudaStreamSynchronize(c->st));
 }
 
+const char* mf_last_cuda_error(void) { return g_last_cuda_error; }
+
+int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out) {
+  if (!c) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  c->tuned = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (size_t i = 0; i < g_tune_cache.size(); ++i) {
+      const TuneEntry& t = g_tune_cache[i];
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec) {
+        g_tune_cache.erase(g_tune_cache.begin() + i);
+        break;
+      }
+    }
+  }
+  const int s = autotune(c, 5);
+  if (s) return s;
+  if (zs_out) *zs_out = c->zS;
+  if (ms_out) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (const TuneEntry& t : g_tune_cache)
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec)
+        for (int i = 0; i < 3; ++i) ms_out[i] = t.ms[i];
+  }
+  return MF_OK;
+}
+
 void mf_destroy(mf_ctx* c) {
   if (!c) return;
+  free_cg_graph(c);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   mf_cufft_delete(c->cufft);
   delete c;
 }

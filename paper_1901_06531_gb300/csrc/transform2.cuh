@@ -19,9 +19,10 @@
 namespace tr2 {
 
 constexpr int kThreads = 256;
-// z-pass: 288 threads divide the butterfly counts of its tiles evenly
+// z-pass threads per block for a tile of S columns: 36 S (rounded up to whole
+// warps) divides the butterfly counts of the radix-16/8 stages evenly
 // (9 components x S columns x NZ/R butterflies per stage)
-constexpr int kZThreads = 288;
+__host__ __device__ constexpr int z_threads(int S) { return S >= 8 ? 288 : S == 4 ? 160 : 96; }
 
 // Asynchronous global -> shared copies of one complex element (8 or 16
 // bytes); many in flight per thread without holding registers.
@@ -235,10 +236,14 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
 // ------------------------------------------------------------------ z-pass
 // Tile: S columns (consecutive (ky, kx) slots) x NZ x 9 components, component
 // pitch CP = NZ*S + 4 complex so that component planes fall in different banks.
+// Default tile: 8 columns (FP32) or 4 (FP64); the autotuner may pick others.
 template <typename T, int NZ>
+constexpr int z_default_S() { return sizeof(typename CT<T>::t) == 8 ? (NZ >= 256 ? 4 : 8) : (NZ >= 256 ? 2 : 4); }
+
+template <typename T, int NZ, int S_ = z_default_S<T, NZ>()>
 struct ZShape {
   typedef typename CT<T>::t C;
-  static constexpr int S = (sizeof(C) == 8) ? (NZ >= 256 ? 4 : 8) : (NZ >= 256 ? 2 : 4);
+  static constexpr int S = S_;
   static constexpr int CP = NZ * S + 4;
   static constexpr size_t smem() {
     return (size_t)9 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int);
@@ -247,9 +252,10 @@ struct ZShape {
 
 // MODE 0: operator (scale, mask).  MODE 1: residual (adds a.add at the null
 // frequency, records the null-frequency coefficient / N in a.mean_out).
-template <typename T, int NZ, int MODE>
-__global__ void __launch_bounds__(kZThreads) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
-  typedef ZShape<T, NZ> Sh;
+template <typename T, int NZ, int MODE, int S_>
+__global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
+  typedef ZShape<T, NZ, S_> Sh;
+  constexpr int kZThreads = z_threads(S_);
   typedef typename CT<T>::t C;
   if (a.skip && *(volatile const int*)a.skip) return;
   constexpr int S = Sh::S, CP = Sh::CP;

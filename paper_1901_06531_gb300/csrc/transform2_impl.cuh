@@ -30,16 +30,30 @@ cudaError_t launch_xyi(const void* spec, T* out, double* partials, const XYArgs&
   return cudaGetLastError();
 }
 
-template <typename T, int NZ, int MODE>
-cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
+template <typename T, int NZ, int MODE, int S>
+cudaError_t launch_zp_s(void* spec, const ZArgs& a, cudaStream_t st) {
   typedef typename CT<T>::t C;
-  const size_t sm = ZShape<T, NZ>::smem();
-  cudaError_t e = cudaFuncSetAttribute(k_zp<T, NZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  typedef ZShape<T, NZ, S> Sh;
+  const size_t sm = Sh::smem();
+  cudaError_t e = cudaFuncSetAttribute(k_zp<T, NZ, MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int ncol = a.ny * (a.nx / 2);
-  k_zp<T, NZ, MODE><<<ncol / ZShape<T, NZ>::S, kZThreads, sm, st>>>((C*)spec, a);
+  if (ncol % S) return cudaErrorInvalidValue;
+  k_zp<T, NZ, MODE, S><<<ncol / S, z_threads(S), sm, st>>>((C*)spec, a);
   ++g_mf_launches;
   return cudaGetLastError();
+}
+
+// MODE 0 (inside the CG loop) takes the tile the autotuner chose (a.S in
+// {2, 4, 8}); the residual (MODE 1) uses the default tile.
+template <typename T, int NZ, int MODE>
+cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
+  if (MODE == 0) {
+    if (a.S == 2) return launch_zp_s<T, NZ, MODE, 2>(spec, a, st);
+    if (a.S == 4) return launch_zp_s<T, NZ, MODE, 4>(spec, a, st);
+    if (a.S == 8) return launch_zp_s<T, NZ, MODE, 8>(spec, a, st);
+  }
+  return launch_zp_s<T, NZ, MODE, z_default_S<T, NZ>()>(spec, a, st);
 }
 
 template <typename T>

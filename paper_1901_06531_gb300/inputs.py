@@ -24,7 +24,7 @@ __all__ = [
     "periodic_sphere_phase", "centred_sphere", "rsa_spheres", "voronoi",
     "random_rotations", "lognormal_scale", "random_F", "random_field",
     "history_uniaxial_stress_ramp", "history_mixed_strain11",
-    "history_cyclic_stress", "laminate_phase", "fix_rotation",
+    "history_cyclic_stress", "laminate_phase", "fix_rotation", "random_control", "batch_of_cells",
 ]
 
 
@@ -234,3 +234,46 @@ def fix_rotation(mask, target):
         mask[:, c] = 0
         target[:, c] = 0.0
     return mask, target
+
+
+def random_control(nsteps, rng, amp=0.02):
+    """Random mixed control: each component stress controlled with probability
+    1/2 (at least one strain-controlled component); a rotation plane whose two
+    off-diagonal components would both be stress controlled gets its upper
+    component (12, 13 or 23) strain controlled at zero, so that no rigid
+    rotation is left free.  Strain-controlled components ramp linearly from
+    the identity by amp * U(-1, 1) over the steps; every prescribed stress is
+    zero.  Returns (mask, target), (nsteps, 9) each."""
+    m = (rng.random(9) < 0.5).astype(np.uint8)
+    if m.all():
+        m[rng.integers(0, 9)] = 0
+    u = rng.uniform(-1.0, 1.0, 9)
+    eye = np.array([1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0])
+    zero_strain = np.zeros(9, dtype=bool)
+    for up, lo in ((1, 3), (2, 6), (5, 7)):
+        if m[up] and m[lo]:
+            m[up] = 0
+            zero_strain[up] = True
+    t = np.arange(1, nsteps + 1)[:, None] / nsteps
+    target = np.where(m[None, :] == 1, 0.0, eye[None, :] + amp * u[None, :] * t)
+    target[:, zero_strain] = 0.0
+    return np.tile(m, (nsteps, 1)), target
+
+
+def batch_of_cells(count, seed, sizes=(32, 48, 64, 96), nsteps=4):
+    """The batched workload: `count` sphere-particle neo-Hookean cells with
+    grid sizes drawn from `sizes`, particle volume fraction U(0.1, 0.3),
+    stiffness contrast U(5, 50) (matrix mu = 1, lam = 2), sphere radius n/12,
+    and random mixed control (random_control).  Returns a list of dicts."""
+    rng = np.random.default_rng(seed)
+    cells = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        vf = rng.uniform(0.1, 0.3)
+        contrast = rng.uniform(5.0, 50.0)
+        phase, _ = rsa_spheres((n, n, n), n / 12.0, vf, int(rng.integers(1 << 30)))
+        params = np.array([[1.0, 2.0], [contrast, 2.0 * contrast]])
+        mask, target = random_control(nsteps, rng)
+        cells.append({"n": n, "phase": phase, "params": params, "mask": mask, "target": target,
+                      "vf": vf, "contrast": contrast})
+    return cells

@@ -38,6 +38,7 @@ _lib.mf_set_material.argtypes = [_vp, _i, _i, _vp, _vp, _vp, _vp]
 _lib.mf_set_F.argtypes = [_vp, _vp]
 _lib.mf_solve.argtypes = [_vp, _i, _vp, _vp, _d, _d, _d, _i, _i, _vp, _vp, _vp]
 _lib.mf_get_fields.argtypes = [_vp, _vp, _vp]
+_lib.mf_solve_batch.argtypes = [_i, _vp, _i, _vp, _vp, _d, _d, _d, _i, _i, _vp, _vp, _vp, _vp]
 _lib.mf_constitutive.argtypes = [_vp]
 _lib.mf_get_tangent.argtypes = [_vp, _vp]
 _lib.mf_matvec.argtypes = [_vp, _vp, _vp, _vp]
@@ -52,15 +53,19 @@ _lib.mf_time_cufft.argtypes = [_vp, _vp, _i, _vp]
 _lib.mf_kernel_launches.argtypes = []
 _lib.mf_kernel_launches.restype = ctypes.c_longlong
 _lib.mf_sync.argtypes = [_vp]
+_lib.mf_autotune.argtypes = [_vp, _vp, _vp]
+_lib.mf_last_cuda_error.argtypes = []
+_lib.mf_last_cuda_error.restype = ctypes.c_char_p
 _lib.mf_status_string.argtypes = [_i]
 _lib.mf_status_string.restype = ctypes.c_char_p
 _lib.mf_destroy.argtypes = [_vp]
 _lib.mf_destroy.restype = None
 
 EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_material", "mf_set_F",
-            "mf_solve", "mf_get_fields", "mf_constitutive", "mf_get_tangent", "mf_matvec",
+            "mf_solve", "mf_solve_batch", "mf_get_fields", "mf_constitutive", "mf_get_tangent", "mf_matvec",
             "mf_residual", "mf_residual_noalloc", "mf_time_kernels", "mf_cufft_workspace_bytes",
-            "mf_cufft_bind", "mf_matvec_cufft", "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_status_string",
+            "mf_cufft_bind", "mf_matvec_cufft", "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_last_cuda_error",
+            "mf_status_string",
             "mf_destroy"]
 
 
@@ -87,10 +92,35 @@ def residual_noalloc(nx, ny, nz, P, mask, pbar, b, stream=None):
     return meanP
 
 
+def solve_batch(contexts, masks, targets, tol_newton=1e-8, tol_cg=1e-10, cg_rel=1e-4, max_newton=50,
+                max_cg=5000):
+    """mf_solve_batch: the same number of load steps on every context at once.
+    masks, targets: (n, nsteps, 9).  Returns a dict of (n, nsteps, ...) arrays
+    and the per-cell status; raises on the first failure after all cells
+    have been driven to their end."""
+    n = len(contexts)
+    masks = np.ascontiguousarray(masks, dtype=np.uint8).reshape(n, -1, 9)
+    targets = _c64(targets).reshape(n, -1, 9)
+    nsteps = masks.shape[1]
+    Fbar = np.zeros((n, nsteps, 9))
+    Pbar = np.zeros((n, nsteps, 9))
+    iters = np.zeros((n, nsteps, 2), dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    handles = (_vp * n)(*[c.h.value for c in contexts])
+    st = _lib.mf_solve_batch(n, ctypes.cast(handles, _vp), nsteps, _ptr(masks), _ptr(targets), tol_newton, tol_cg,
+                             cg_rel, max_newton, max_cg, _ptr(Fbar), _ptr(Pbar), _ptr(iters), _ptr(status))
+    out = {"Fbar": Fbar, "Pbar": Pbar, "newton": iters[..., 0].astype(np.int64),
+           "cg": iters[..., 1].astype(np.int64), "status": status}
+    _check("mf_solve_batch", st)
+    return out
+
+
 class MixFFTError(RuntimeError):
     def __init__(self, call, status):
         self.status = status
         msg = _lib.mf_status_string(status).decode()
+        if status == MF_CUDA_ERROR:
+            msg += " [" + _lib.mf_last_cuda_error().decode() + "]"
         super().__init__(f"{call}: {msg} (status {status})")
 
 
@@ -229,6 +259,13 @@ class Context:
         ms = np.zeros(3, dtype=np.float32)
         _check("mf_time_cufft", _lib.mf_time_cufft(self.h, _ptr(m), reps, _ptr(ms)))
         return ms.astype(np.float64)
+
+    def autotune(self):
+        """mf_autotune: returns (chosen z-pass tile width, ms per candidate 2/4/8)."""
+        zs = np.zeros(1, dtype=np.int32)
+        ms = np.zeros(3, dtype=np.float32)
+        _check("mf_autotune", _lib.mf_autotune(self.h, _ptr(zs), _ptr(ms)))
+        return int(zs[0]), ms.astype(np.float64)
 
     def sync(self):
         _check("mf_sync", _lib.mf_sync(self.h))
