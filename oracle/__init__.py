@@ -18,10 +18,13 @@ Modules
   solver     -- Eq. (linequil2ast) and (eq:mixedeqil): Newton + conjugate
                 gradients under per-component stress/strain control
   dense      -- dense assembly of the linear operator for brute-force checks
+  adjoint    -- adjoint sensitivity of the homogenized response (one CG solve
+                with the projected tangent at a converged step)
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (naive DFT sums and library FFT, the projector's algebra and the reference
 medium Green operator, energy finite differences, affine and laminate closed
-forms, dense solves).  None is "parity unpinned".
+forms, dense solves, central finite differences of full solves for the
+adjoint).  None is "parity unpinned".
 """
-from . import dft, projector, materials, solver, dense  # noqa: F401
+from . import dft, projector, materials, solver, dense, adjoint  # noqa: F401
