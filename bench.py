@@ -307,6 +307,64 @@ def run_batched(args):
     return res
 
 
+ADJ_N, ADJ_SEED = 128, 1005
+
+
+def run_adjoint(args):
+    """The adjoint workload: 128^3, two neo-Hookean phases (periodic RSA
+    spheres of radius 10 voxels to volume fraction 0.2, contrast 10), voxel
+    stiffness scale lognormal with sigma 0.3, one load step P11 = 0.05 with
+    the other stresses zero and the rotation fixed (F12 = F13 = F23 = 0).
+    Times the forward solve and the adjoint solve of d<F>_11 / d(mu, lam, s)
+    in both precisions.  256^3 is not supported by the library (one x-y plane
+    of a component exceeds shared memory)."""
+    import torch
+    from paper_1901_06531_gb300 import inputs
+    from paper_1901_06531_gb300 import mixfft as mf
+    n = ADJ_N
+    shape = (n, n, n)
+    ph, _ = inputs.rsa_spheres(shape, 10.0, 0.2, ADJ_SEED)
+    sc = inputs.lognormal_scale(shape, 0.3, ADJ_SEED + 1)
+    params = np.array([[1.0, 2.0], [10.0, 20.0]])
+    mask, target = inputs.fix_rotation(*inputs.history_uniaxial_stress_ramp(1, 0.05))
+    wF = np.zeros(9)
+    wF[0] = 1.0
+    wP = np.zeros(9)
+    stream = torch.cuda.current_stream()
+    res = {"workload": (f"{n}^3 two-phase neo-Hookean (RSA spheres r=10, vf 0.2, seed {ADJ_SEED}, contrast 10), "
+                        f"lognormal voxel scale sigma 0.3, P11 = 0.05 rotation fixed; J = <F>_11"),
+           "unsupported": "256^3 (x-y plane of one component exceeds shared memory)"}
+    for name, prec, kw, akw, reps in (
+            ("fp32_inner", mf.MF_FP32_INNER, dict(tol_newton=TOL_NEWTON, tol_cg=TOL_CG, cg_rel=CG_REL),
+             dict(tol_cg=1e-30, cg_rel=1e-6), 3),
+            ("fp64", mf.MF_FP64, dict(tol_newton=TOL_NEWTON, tol_cg=TOL_CG, cg_rel=CG_REL),
+             dict(tol_cg=1e-10, cg_rel=1e-8), 1)):
+        ctx = mf.Context(n, n, n, prec)
+        ctx.set_material(mf.MF_NEOHOOKE, params, ph, scale=sc)
+        ds = torch.empty(ctx.N, dtype=torch.float64, device=ctx.device)
+        ctx.solve(mask, target, **kw)
+        ctx.adjoint(mask[0], wF, wP, dscale=ds, max_cg=20000, **akw)
+        fwd, adj = [], []
+        for _ in range(reps):
+            ctx.set_F(None)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            o = ctx.solve(mask, target, **kw)
+            e[1].record(stream)
+            J, g, its = ctx.adjoint(mask[0], wF, wP, dscale=ds, max_cg=20000, **akw)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            fwd.append(e[0].elapsed_time(e[1]))
+            adj.append(e[1].elapsed_time(e[2]))
+        res[name] = {"forward_ms": float(np.median(fwd)), "adjoint_ms": float(np.median(adj)),
+                     "adjoint_over_forward": float(np.median(adj) / np.median(fwd)),
+                     "forward_newton_cg": [int(o["newton"][0]), int(o["cg"][0])], "adjoint_cg": its,
+                     "J": J, "dJ_dmu_lam": g.tolist(), "dJ_dscale_sum": float(ds.sum())}
+        del ctx, ds
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -458,6 +516,7 @@ def run_ours(args):
     del ctx64, x64, y64
 
     batched = run_batched(args) if not args.no_batched else None
+    adjoint = run_adjoint(args) if not args.no_adjoint else None
 
     peak, peak_kind = measured_peaks()
     dom = int(np.argmax(kms))
@@ -497,6 +556,8 @@ def run_ours(args):
     }
     if batched is not None:
         line["batched"] = batched
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         line["cpu_baseline"] = cpu_baseline_entry(oracle_sample(cores), cores)
@@ -515,6 +576,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 48-cell workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 adjoint workload")
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: run this many projected-operator applications only")
     ap.add_argument("--kernels-only", type=int, default=0,

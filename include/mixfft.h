@@ -126,6 +126,14 @@ int mf_solve_batch(int n, mf_ctx* const* ctxs, int nsteps, const uint8_t* masks,
                    double tol_newton, double tol_cg, double cg_rel, int max_newton, int max_cg,
                    double* Fbar_out, double* Pbar_out, int32_t* iters_out, int32_t* status_out);
 
+/* Device-to-device copies of the deformation gradient field (9N doubles),
+ * ordered on the context's stream (no host synchronisation): mf_save_F copies
+ * the context's F to F_dev; mf_load_F replaces it by F_dev (a checkpoint of a
+ * converged step, for example) and invalidates the stored tangent.  F_dev:
+ * device, 9N doubles, owned by the caller, not inside the workspace. */
+int mf_save_F(mf_ctx* ctx, double* F_dev);
+int mf_load_F(mf_ctx* ctx, const double* F_dev);
+
 /* Copy the current F and P fields to host memory (9N doubles each; either
  * pointer may be NULL).  P is the stress at the current F. */
 int mf_get_fields(mf_ctx* ctx, double* F_host, double* P_host);
@@ -221,6 +229,32 @@ int mf_sync(mf_ctx* ctx);
  * floats or NULL, mean ms per candidate (-1 when not applicable).  Contexts
  * served by the generic kernels keep their fixed tile. */
 int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out);
+
+/* Adjoint sensitivity of the homogenized response at the current F, which
+ * must be a converged state of a step solved with control mask `mask` (for
+ * example right after mf_solve, or after mf_set_F with a stored converged
+ * field).  The response is J = wF . <F> + wP . <P> (9 weights each).  At
+ * equilibrium G*(P - P-bar) = 0 (Eq. linequil2ast with dF = 0); differentiating
+ * it gives, with the symmetric projected tangent A = G* K G*,
+ *     A lambda = G*(W_F + K : W_P),
+ *     dJ/dtheta = (1/N) sum_v (W_P - lambda_v) : dP_v/dtheta,
+ * one linear solve by the same CG as the Newton iterations (the loop is one
+ * graph launch).  Neo-Hookean law only (MF_INVALID_ARG otherwise); nphase at
+ * most 2048 and at most 4.5 N.
+ *   mask: host 9 bytes; wF, wP: host 9 doubles;
+ *   tol_cg, cg_rel: stop when rms(r) <= max(tol_cg, cg_rel * rms(r0)), in
+ *     both precisions (cg_rel 0: tol_cg alone);
+ *   J_out: host double or NULL;
+ *   dJ_dparams: host 2*nphase doubles or NULL: (dJ/dmu_p, dJ/dlam_p) per phase;
+ *   dJ_dscale_dev: device N doubles or NULL: dJ/ds_v for the per-voxel scale
+ *     s_v of mf_set_material (P_v = s_v P(F_v; mu, lam)); with no scale bound
+ *     the derivative is taken at s = 1;
+ *   cg_its_out: host int32 or NULL, CG iterations.
+ * F is left unchanged; P and the tangent are recomputed at F; the CG vectors
+ * are overwritten.  Synchronous. */
+int mf_adjoint(mf_ctx* ctx, const uint8_t* mask, const double* wF, const double* wP, double tol_cg,
+               double cg_rel, int max_cg, double* J_out, double* dJ_dparams, double* dJ_dscale_dev,
+               int32_t* cg_its_out);
 
 /* Name and description of the CUDA error behind the last MF_CUDA_ERROR
  * returned by any context in this process ("" if none); static storage. */

@@ -130,3 +130,20 @@ cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool def
 cudaError_t mf_launch_defl_project(void* y, bool f32, bool apply, const double* F, long long N,
                                    const Defl& d, double* partials, int nblk, Scalars* sc,
                                    cudaStream_t st);
+
+// adjoint.cu: adjoint sensitivity at a converged state (neo-Hookean parameters)
+struct AdjWeights {
+  double wF[9];   // weights of <F> in the response
+  double wP[9];   // weights of <P>
+};
+// q = W_P (uniform field of the inner type)
+cudaError_t mf_launch_adj_rhs_fill(void* q, bool f32, long long N, const AdjWeights& w, cudaStream_t st);
+// t += W_F (inner type, in place)
+cudaError_t mf_launch_adj_rhs_add(void* t, bool f32, long long N, const AdjWeights& w, cudaStream_t st);
+// b (FP64) = y (inner type), n entries
+cudaError_t mf_launch_to_double(const void* y, double* b, bool f32, long long n, cudaStream_t st);
+// out[2p], out[2p+1] = dJ/dmu_p, dJ/dlam_p; dscale (if non-null) = dJ/ds_v.
+// partials: nblk * 2 * nphase doubles.
+cudaError_t mf_launch_adj_grad(const double* F, const double* P, const void* lam, bool f32, const int32_t* phase,
+                               const double* scale, long long N, int nphase, const AdjWeights& w,
+                               double* partials, int nblk, double* out, double* dscale, cudaStream_t st);

@@ -496,7 +496,8 @@ int autotune(mf_ctx* c, int reps) {
 }
 
 // Enqueue one linear solve of Eq. (linequil2ast) by CG from dF = 0 (the
-// solution is left in the x vector): CG start, the graph with the device-side
+// solution is left in the x vector; stop at rms(r) <= max(tol_cg, cg_rel *
+// rms(r0))): CG start, the graph with the device-side
 // iteration loop, and the last lagging solution update.  Per iteration: the
 // tangent pass (direction update, lagging solution update, K:p and p.Kp), the
 // three transform passes whose last one updates the residual, and two
@@ -511,7 +512,7 @@ int launch_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int 
     if (s) return s;
   }
   cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), c->ws + c->ox, c->ws + c->or_, c->ws + c->op, f32, n9,
-                                    part, kPointwiseBlocks, tol_cg, f32 ? cg_rel : 0.0, c->N, sc, c->st);
+                                    part, kPointwiseBlocks, tol_cg, cg_rel, c->N, sc, c->st);
   if (e == cudaSuccess) e = mf_launch_cg_batch_init(sc, max_cg, c->st);
   if (e == cudaSuccess) e = cudaGraphLaunch(c->cg_exec, c->st);
   if (e == cudaSuccess)
@@ -638,7 +639,7 @@ struct Runner {
                                                kPointwiseBlocks, sc, c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
     }
-    s = launch_cg(c, m, tol_cg, cg_rel, max_cg);
+    s = launch_cg(c, m, tol_cg, c->f32() ? cg_rel : 0.0, max_cg);
     if (s) return s;
     if (defl.m > 0 && mf_launch_defl_project(c->ws + c->ox, true, false, F, N, defl, part, kPointwiseBlocks, sc,
                                              c->st) != cudaSuccess)
@@ -993,6 +994,27 @@ int mf_set_F(mf_ctx* c, const double* F_host) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   c->have_K = false;
+  c->have_H = false;
+  return cuda_status(e);
+}
+
+int mf_save_F(mf_ctx* c, double* F_dev) {
+  if (!c || !F_dev) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  return cuda_status(cudaMemcpyAsync(F_dev, c->ws + c->oF, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     c->st));
+}
+
+int mf_load_F(mf_ctx* c, const double* F_dev) {
+  if (!c || !F_dev) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  const char* p = (const char*)F_dev;
+  if (p + 9 * c->N * sizeof(double) > c->ws && p < c->ws + c->ws_need) return MF_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->oF, F_dev, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                  c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
+  c->have_K = false;
+  c->have_H = false;
   return cuda_status(e);
 }
 
@@ -1166,6 +1188,82 @@ int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return cuda_status(e);
+}
+
+int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* wP, double tol_cg, double cg_rel,
+               int max_cg, double* J_out, double* dJ_dparams, double* dJ_dscale_dev, int32_t* cg_its_out) {
+  if (!c || !mask || !wF || !wP || !(tol_cg > 0) || !(cg_rel >= 0) || max_cg < 1) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (c->model != MF_NEOHOOKE || c->nphase > 2048 || 2LL * c->nphase > 9 * c->N) return MF_INVALID_ARG;
+  for (int k = 0; k < 9; ++k)
+    if (mask[k] > 1 || !isfinite(wF[k]) || !isfinite(wP[k])) return MF_INVALID_ARG;
+  int s = MF_OK;
+  if (!c->tuned && (s = autotune(c, 3))) return s;
+  const bool f32 = c->f32();
+  const long long N = c->N;
+  AdjWeights w;
+  memcpy(w.wF, wF, sizeof(w.wF));
+  memcpy(w.wP, wP, sizeof(w.wP));
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  double* F = c->at<double>(c->oF);
+  double* b = c->at<double>(c->ob);
+  // P and the tangent at F (FP32: H and the rotation moments)
+  s = run_constitutive(c, !f32, f32, f32);
+  Scalars h;
+  if (!s) s = read_scalars(c, &h);
+  if (!s) s = flags_status(h.flags);
+  if (s) return s;
+  // right-hand side G*(W_F + K : W_P)
+  const XYArgs xa = xy_args(c, f32);
+  const ZArgs za = z_args(c, f32, mask, 1.0 / (double)N);
+  cudaError_t e = mf_launch_adj_rhs_fill(c->ws + c->op, f32, N, w, c->st);
+  if (e == cudaSuccess)
+    e = mf_launch_tangent(c->ws + c->op, nullptr, nullptr, nullptr, f32, tangent_kind(c), false, tangent_args(c),
+                          c->ws + c->oAp, N, nullptr, kPointwiseBlocks, nullptr, c->st);
+  if (e == cudaSuccess) e = mf_launch_adj_rhs_add(c->ws + c->oAp, f32, N, w, c->st);
+  if (e == cudaSuccess)
+    e = mf_launch_project(f32, c->ws + c->oAp, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xa, za, nullptr,
+                          c->st);
+  if (e == cudaSuccess) e = mf_launch_to_double(c->ws + c->op2, b, f32, 9 * N, c->st);
+  // FP32: the same null-rotation deflation as the Newton iterations
+  Defl defl;
+  defl.m = 0;
+  if (e == cudaSuccess && f32) {
+    defl = null_rotations(h.meanF, mask, h.T, h.S, c->kappa, 1e-6);
+    if (defl.m > 0) e = mf_launch_defl_project(b, false, true, F, N, defl, part, kPointwiseBlocks, sc, c->st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  s = launch_cg(c, mask, tol_cg, cg_rel, max_cg);
+  Scalars hc;
+  if (!s) s = read_scalars(c, &hc);
+  if (s) return s;
+  g_mf_launches += 13LL * (hc.its == 0 ? 1 : (hc.its + 1) / 2);
+  bool clear = false;
+  s = cg_outcome(c, hc, &clear);
+  if (s) return s;
+  if (clear) e = cudaMemsetAsync(&sc->flags, 0, sizeof(int), c->st);
+  if (e == cudaSuccess && defl.m > 0)
+    e = mf_launch_defl_project(c->ws + c->ox, true, true, F, N, defl, part, kPointwiseBlocks, sc, c->st);
+  // parameter derivatives; the per-phase sums land in b (free after the CG start)
+  const int per = 2 * c->nphase;
+  int nblk = (int)(c->npart / per);
+  if (nblk > kPointwiseBlocks) nblk = kPointwiseBlocks;
+  if (e == cudaSuccess)
+    e = mf_launch_adj_grad(F, c->at<double>(c->oP), c->ws + c->ox, f32, c->at<int32_t>(c->ophase),
+                           c->has_scale ? c->at<double>(c->oscale) : nullptr, N, c->nphase, w, part, nblk, b,
+                           dJ_dscale_dev, c->st);
+  if (e == cudaSuccess && dJ_dparams)
+    e = cudaMemcpyAsync(dJ_dparams, b, per * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (J_out) {
+    double J = 0.0;
+    for (int k = 0; k < 9; ++k) J += wF[k] * h.meanF[k] + wP[k] * h.meanP[k];
+    *J_out = J;
+  }
+  if (cg_its_out) *cg_its_out = hc.its;
+  return MF_OK;
 }
 
 long long mf_kernel_launches(void) { return g_mf_launches; }

@@ -38,6 +38,8 @@ _lib.mf_set_material.argtypes = [_vp, _i, _i, _vp, _vp, _vp, _vp]
 _lib.mf_set_F.argtypes = [_vp, _vp]
 _lib.mf_solve.argtypes = [_vp, _i, _vp, _vp, _d, _d, _d, _i, _i, _vp, _vp, _vp]
 _lib.mf_get_fields.argtypes = [_vp, _vp, _vp]
+_lib.mf_save_F.argtypes = [_vp, _vp]
+_lib.mf_load_F.argtypes = [_vp, _vp]
 _lib.mf_solve_batch.argtypes = [_i, _vp, _i, _vp, _vp, _d, _d, _d, _i, _i, _vp, _vp, _vp, _vp]
 _lib.mf_constitutive.argtypes = [_vp]
 _lib.mf_get_tangent.argtypes = [_vp, _vp]
@@ -54,6 +56,7 @@ _lib.mf_kernel_launches.argtypes = []
 _lib.mf_kernel_launches.restype = ctypes.c_longlong
 _lib.mf_sync.argtypes = [_vp]
 _lib.mf_autotune.argtypes = [_vp, _vp, _vp]
+_lib.mf_adjoint.argtypes = [_vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp, _vp]
 _lib.mf_last_cuda_error.argtypes = []
 _lib.mf_last_cuda_error.restype = ctypes.c_char_p
 _lib.mf_status_string.argtypes = [_i]
@@ -62,9 +65,9 @@ _lib.mf_destroy.argtypes = [_vp]
 _lib.mf_destroy.restype = None
 
 EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_material", "mf_set_F",
-            "mf_solve", "mf_solve_batch", "mf_get_fields", "mf_constitutive", "mf_get_tangent", "mf_matvec",
+            "mf_solve", "mf_solve_batch", "mf_get_fields", "mf_save_F", "mf_load_F", "mf_constitutive", "mf_get_tangent", "mf_matvec",
             "mf_residual", "mf_residual_noalloc", "mf_time_kernels", "mf_cufft_workspace_bytes",
-            "mf_cufft_bind", "mf_matvec_cufft", "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_last_cuda_error",
+            "mf_cufft_bind", "mf_matvec_cufft", "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint", "mf_last_cuda_error",
             "mf_status_string",
             "mf_destroy"]
 
@@ -176,6 +179,7 @@ class Context:
         rot = None if rot is None else _c64(rot)
         scale = None if scale is None else _c64(scale)
         nphase = params.shape[0]
+        self.nphase = nphase
         _check("mf_set_material", _lib.mf_set_material(self.h, model, nphase, _ptr(params), _ptr(rot),
                                                        _ptr(phase), _ptr(scale)))
 
@@ -203,6 +207,19 @@ class Context:
         P = np.empty((9,) + self.shape)
         _check("mf_get_fields", _lib.mf_get_fields(self.h, _ptr(F), _ptr(P)))
         return F, P
+
+    def save_F(self, out=None):
+        """mf_save_F: the current F into a torch FP64 CUDA tensor (9, nz, ny, nx)."""
+        if out is None:
+            out = self.torch.empty((9,) + self.shape, dtype=self.torch.float64, device=self.device)
+        assert out.dtype == self.torch.float64 and out.is_contiguous() and out.numel() == 9 * self.N
+        _check("mf_save_F", _lib.mf_save_F(self.h, _vp(out.data_ptr())))
+        return out
+
+    def load_F(self, F):
+        """mf_load_F: replace the current F by a torch FP64 CUDA tensor of 9N values."""
+        assert F.dtype == self.torch.float64 and F.is_contiguous() and F.numel() == 9 * self.N
+        _check("mf_load_F", _lib.mf_load_F(self.h, _vp(F.data_ptr())))
 
     # -- operator level --------------------------------------------------
     def constitutive(self):
@@ -266,6 +283,24 @@ class Context:
         ms = np.zeros(3, dtype=np.float32)
         _check("mf_autotune", _lib.mf_autotune(self.h, _ptr(zs), _ptr(ms)))
         return int(zs[0]), ms.astype(np.float64)
+
+    def adjoint(self, mask, wF, wP, tol_cg=1e-11, cg_rel=0.0, max_cg=20000, dscale=None):
+        """mf_adjoint at the current (converged) F: returns (J, dJ/d(mu, lam)
+        per phase as an (nphase, 2) array, CG iterations).  dscale: a torch
+        FP64 CUDA tensor of N values that receives dJ/ds_v, or None."""
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        wF = _c64(wF)
+        wP = _c64(wP)
+        J = np.zeros(1)
+        nphase = getattr(self, "nphase", 0)
+        grad = np.zeros((max(nphase, 1), 2))
+        its = np.zeros(1, dtype=np.int32)
+        if dscale is not None:
+            assert dscale.dtype == self.torch.float64 and dscale.is_contiguous() and dscale.numel() == self.N
+        _check("mf_adjoint", _lib.mf_adjoint(self.h, _ptr(m), _ptr(wF), _ptr(wP), tol_cg, cg_rel, max_cg,
+                                             _ptr(J), _ptr(grad),
+                                             None if dscale is None else _vp(dscale.data_ptr()), _ptr(its)))
+        return float(J[0]), grad[:nphase], int(its[0])
 
     def sync(self):
         _check("mf_sync", _lib.mf_sync(self.h))
