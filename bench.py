@@ -224,6 +224,24 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU path
+def time_residual(ctx, mask, pbar, b, reps):
+    """Median ms of one FP64 residual (three transform kernels), L2 flushed
+    before each; a 151 MB memset of b does the flush."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        b.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.residual(mask, pbar, b)
+        e.record(stream)
+        ts.append((a, e))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(e) for a, e in ts]))
+
+
 def run_matvec_only(args):
     """Profiling driver: the 128^3 polycrystal tangent at the first load step,
     then `--matvec-only` applications of the FP32 (or FP64) projected operator,
@@ -240,8 +258,10 @@ def run_matvec_only(args):
     ctx.constitutive()
     if args.kernels_only:
         ms = ctx.time_kernels(mask[0], reps=args.kernels_only)
+        b = torch.empty(9 * n ** 3, dtype=torch.float64, device="cuda")
+        res_ms = time_residual(ctx, mask[0], target[0] * mask[0], b, args.kernels_only)
         print(json.dumps({"kernels_only": args.kernels_only, "fp64": bool(args.fp64),
-                          "ms": dict(zip(KERNELS, [float(m) for m in ms]))}))
+                          "ms": dict(zip(KERNELS, [float(m) for m in ms])), "residual_ms": res_ms}))
         return
     x = torch.randn(9 * n ** 3, dtype=ctx.inner_dtype, device="cuda")
     y = torch.empty_like(x)
@@ -452,6 +472,14 @@ def run_ours(args):
     ctx.constitutive()
     m0 = mask[0]
     kms = ctx.time_kernels(m0, reps=20)
+    bres = torch.empty(9 * N, dtype=torch.float64, device="cuda")
+    res_ms = {}
+    for name, arith in (("double_word", mf.MF_RESIDUAL_DOUBLE_WORD), ("fp64", mf.MF_RESIDUAL_FP64)):
+        ctx.set_residual_arith(arith)
+        time_residual(ctx, m0, target[0] * m0, bres, 2)
+        res_ms[name] = time_residual(ctx, m0, target[0] * m0, bres, 10)
+    ctx.set_residual_arith(mf.MF_RESIDUAL_DOUBLE_WORD)
+    del bres
     x = torch.randn(9 * N, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
 
@@ -549,6 +577,7 @@ def run_ours(args):
             "fp32": N / (cf32_ms * 1e-3) / 1e9, "fp64": N / (cf64_ms * 1e-3) / 1e9,
             "fp32_parts_ms": {"r2c": float(cf32_parts[0]), "gstar": float(cf32_parts[1]),
                               "c2r": float(cf32_parts[2])}},
+        "residual_ms": res_ms,
         "load_step_ms": {"fp32_inner_median": float(np.median(step_ms)),
                          "fp64_plain": fp64_ms, "fp64_steps_timed": fp64_steps},
         "iterations": {"fp32_inner_newton_cg_per_step": its,

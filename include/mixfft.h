@@ -52,6 +52,7 @@ typedef enum {
 
 typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
 typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
+typedef enum { MF_RESIDUAL_DOUBLE_WORD = 0, MF_RESIDUAL_FP64 = 1 } mf_residual_arith;
 
 typedef struct mf_ctx mf_ctx;
 
@@ -255,6 +256,17 @@ int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out);
 int mf_adjoint(mf_ctx* ctx, const uint8_t* mask, const double* wF, const double* wP, double tol_cg,
                double cg_rel, int max_cg, double* J_out, double* dJ_dparams, double* dJ_dscale_dev,
                int32_t* cg_its_out);
+
+/* Arithmetic of the transforms of the FP64 residual b = -G*(P - P-bar)
+ * (Eq. linequil2ast, right side) in MF_FP32_INNER contexts:
+ * MF_RESIDUAL_DOUBLE_WORD (the default) computes them with double-word FP32
+ * arithmetic (hi + lo pairs, about 48 significant bits; P is read and b
+ * written in FP64) wherever the fixed-size transform kernels serve the grid
+ * (nx = ny, nx and nz in {16, 32, 48, 64, 96, 128}), FP64 elsewhere;
+ * MF_RESIDUAL_FP64 always uses FP64.  The constitutive law, the averages,
+ * the Newton update and every reduction stay FP64.  MF_FP64 contexts ignore
+ * the setting.  Returns MF_INVALID_ARG for another value. */
+int mf_set_residual_arith(mf_ctx* ctx, int arith);
 
 /* Name and description of the CUDA error behind the last MF_CUDA_ERROR
  * returned by any context in this process ("" if none); static storage. */

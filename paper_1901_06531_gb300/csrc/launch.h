@@ -51,9 +51,17 @@ cudaError_t mf_v2_xyi_f64(int mode, const void* spec, void* out, double* partial
                           const Scalars* sc, cudaStream_t st);
 cudaError_t mf_v2_zp_f64(int mode, void* spec, const ZArgs& a, cudaStream_t st);
 
+// transform2_dw.cu: the residual transforms in double-word FP32 arithmetic
+// (P in, b out in FP64; spectrum and twiddle tables double-word complex)
+cudaError_t mf_v2_xyf_dw(const double* in, void* spec, const XYArgs& a, cudaStream_t st);
+cudaError_t mf_v2_zp_dw(void* spec, const ZArgs& a, cudaStream_t st);
+cudaError_t mf_v2_xyi_dw(const void* spec, double* out, double* partials, const XYArgs& a, cudaStream_t st);
+
 // transform.cu
+// b = -G*(P - P-bar) (null frequency per za); dw: double-word transforms
+// (fixed-size kernels only; xa, za then point at the double-word tables)
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
-                               const XYArgs& xa, const ZArgs& za, cudaStream_t st);
+                               const XYArgs& xa, const ZArgs& za, bool dw, cudaStream_t st);
 // which: 0 x-y forward of t, 1 z-pass, 2 x-y inverse with the CG residual update
 cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spec, void* r,
                                    double* partials, const XYArgs& xa, const ZArgs& za,

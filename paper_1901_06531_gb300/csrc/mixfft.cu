@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/mixfft.h"
+#include "dw.cuh"
 #include "fft2.cuh"
 #include "launch.h"
 
@@ -204,7 +205,7 @@ struct mf_ctx {
   size_t ws_need = 0;
   // offsets into the workspace
   size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
-      otable32, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32;
+      otable32, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
   size_t npart;
   // material
   int model = -1, nphase = 0;
@@ -220,9 +221,12 @@ struct mf_ctx {
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
   bool tuned = false;              // z-pass tile chosen by the autotuner
+  int residual_arith = MF_RESIDUAL_DOUBLE_WORD;
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   bool f32() const { return prec == MF_FP32_INNER; }
+  // residual transforms in double-word FP32 (FP32-inner mode, fixed-size kernels)
+  bool dw_residual() const { return f32() && v2 && residual_arith == MF_RESIDUAL_DOUBLE_WORD; }
   size_t inner_size() const { return f32() ? sizeof(float) : sizeof(double); }
 };
 
@@ -236,28 +240,34 @@ int cuda_status(cudaError_t e) {
   return MF_CUDA_ERROR;
 }
 
-XYArgs xy_args(const mf_ctx* c, bool f32) {
+// Twiddle table of an arithmetic: FP32, FP64 or double-word complex.
+size_t tw_offset(const mf_ctx* c, bool f32, bool dw, size_t* esz) {
+  *esz = f32 ? sizeof(float2) : sizeof(double2);
+  return dw ? c->otwdw : f32 ? c->otw32 : c->otw64;
+}
+
+XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   XYArgs a;
   a.v2 = c->v2;
   a.skip = nullptr;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
-  const size_t tw = f32 ? c->otw32 : c->otw64;
-  const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  size_t esz;
+  const size_t tw = tw_offset(c, f32, dw, &esz);
   a.twx = c->ws + tw;
   a.twy = c->ws + tw + esz * c->nx;
   a.xpos = c->at<int>(c->oxpos);
   return a;
 }
 
-ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale) {
+ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale, bool dw = false) {
   ZArgs a;
   memset(&a, 0, sizeof(a));
   a.v2 = c->v2;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.pz = c->pz;
-  const size_t tw = f32 ? c->otw32 : c->otw64;
-  const size_t esz = f32 ? sizeof(float2) : sizeof(double2);
+  size_t esz;
+  const size_t tw = tw_offset(c, f32, dw, &esz);
   a.twz = c->ws + tw + esz * (c->nx + c->ny);
   a.xk = c->at<int>(c->oxk);
   a.xe = c->at<int>(c->oxe);
@@ -310,11 +320,12 @@ int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false) 
 bool operator_ready(const mf_ctx* c) { return c->f32() ? c->have_H : c->have_K; }
 
 int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out) {
-  ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N);
+  const bool dw = c->dw_residual();
+  ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N, dw);
   for (int k = 0; k < 9; ++k) za.add[k] = mask[k] ? pbar[k] : 0.0;
   za.mean_out = mean_out;
   return cuda_status(mf_launch_residual(c->at<double>(c->oP), c->ws + c->ospec, b,
-                                        c->at<double>(c->opart), xy_args(c, false), za, c->st));
+                                        c->at<double>(c->opart), xy_args(c, false, dw), za, dw, c->st));
 }
 
 TangentArgs tangent_args(const mf_ctx* c) {
@@ -819,6 +830,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->ozk = take(nz * sizeof(int));
   c->otw64 = take((nx + ny + nz) * sizeof(double2));
   c->otw32 = take((nx + ny + nz) * sizeof(float2));
+  c->otwdw = take((nx + ny + nz) * sizeof(dwc));
   c->ws_need = off;
   *out = c;
   return MF_OK;
@@ -855,12 +867,15 @@ int mf_bind_workspace(mf_ctx* c, void* dev, size_t bytes) {
   }
   std::vector<double2> tw64(nx + ny + nz);
   std::vector<float2> tw32(nx + ny + nz);
+  std::vector<dwc> twdw(nx + ny + nz);
   int o = 0;
   for (int n : {nx, ny, nz}) {
     for (int t = 0; t < n; ++t) {
       const double ang = -2.0 * M_PI * (double)t / (double)n;
       tw64[o + t] = make_double2(cos(ang), sin(ang));
       tw32[o + t] = make_float2((float)tw64[o + t].x, (float)tw64[o + t].y);
+      twdw[o + t].x = dw(tw64[o + t].x);
+      twdw[o + t].y = dw(tw64[o + t].y);
     }
     o += n;
   }
@@ -875,6 +890,7 @@ int mf_bind_workspace(mf_ctx* c, void* dev, size_t bytes) {
   put(c->ozk, zk.data(), nz * sizeof(int));
   put(c->otw64, tw64.data(), tw64.size() * sizeof(double2));
   put(c->otw32, tw32.data(), tw32.size() * sizeof(float2));
+  put(c->otwdw, twdw.data(), twdw.size() * sizeof(dwc));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // host vectors go out of scope
   return cuda_status(e);
@@ -1263,6 +1279,12 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
     *J_out = J;
   }
   if (cg_its_out) *cg_its_out = hc.its;
+  return MF_OK;
+}
+
+int mf_set_residual_arith(mf_ctx* c, int arith) {
+  if (!c || (arith != MF_RESIDUAL_DOUBLE_WORD && arith != MF_RESIDUAL_FP64)) return MF_INVALID_ARG;
+  c->residual_arith = arith;
   return MF_OK;
 }
 

@@ -166,7 +166,7 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
   }
   za.scale = -1.0 / (double)N;
   za.mean_out = mean;
-  e = mf_launch_residual(P_dev, spec, b_dev, partials, xa, za, st);
+  e = mf_launch_residual(P_dev, spec, b_dev, partials, xa, za, false, st);
   if (e == cudaSuccess && meanP_host)
     e = cudaMemcpyAsync(meanP_host, mean, 9 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

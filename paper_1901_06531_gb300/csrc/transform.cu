@@ -320,7 +320,13 @@ static cudaError_t launch_zpass(void* spec, const ZArgs& a, cudaStream_t st) {
 }
 
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
-                               const XYArgs& xa, const ZArgs& za, cudaStream_t st) {
+                               const XYArgs& xa, const ZArgs& za, bool dw, cudaStream_t st) {
+  if (xa.v2 && dw) {
+    cudaError_t e = mf_v2_xyf_dw(P, spec, xa, st);
+    if (e == cudaSuccess) e = mf_v2_zp_dw(spec, za, st);
+    if (e == cudaSuccess) e = mf_v2_xyi_dw(spec, b, partials, xa, st);
+    return e;
+  }
   if (xa.v2) {
     cudaError_t e = mf_v2_xyf_f64(P, spec, xa, st);
     if (e == cudaSuccess) e = mf_v2_zp_f64(1, spec, za, st);

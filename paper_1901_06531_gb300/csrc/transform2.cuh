@@ -13,10 +13,27 @@
 // slots (digit-reversed kx), dense.
 #pragma once
 
+#include <type_traits>
+
+#include "dw.cuh"
 #include "fft2.cuh"
 #include "launch.h"
 
 namespace tr2 {
+
+// Type of the real fields a kernel reads or writes in global memory: the
+// compute type itself, except for the double-word kernels, which read P and
+// write the residual in FP64 and hold the spectrum as double-word complex
+// (16 bytes, the size of an FP64 complex).
+template <typename T> struct IOT { typedef T t; };
+template <> struct IOT<dw> { typedef double t; };
+
+__device__ __forceinline__ void io_in(float2& d, float2 s) { d = s; }
+__device__ __forceinline__ void io_in(double2& d, double2 s) { d = s; }
+__device__ __forceinline__ void io_in(dwc& d, double2 s) { d = to_dwc(s); }
+__device__ __forceinline__ float2 io_out(float2 v) { return v; }
+__device__ __forceinline__ double2 io_out(double2 v) { return v; }
+__device__ __forceinline__ double2 io_out(dwc v) { return to_double2(v); }
 
 constexpr int kThreads = 256;
 // z-pass threads per block for a tile of S columns: 36 S (rounded up to whole
@@ -57,11 +74,14 @@ __device__ __forceinline__ void load_tables(C* twx, C* twy, int* posx, const C* 
 
 // ------------------------------------------------------------------ forward
 template <typename T, int NX>
-__global__ void __launch_bounds__(kThreads) k_xyf(const T* __restrict__ in, typename CT<T>::t* __restrict__ spec,
-                                                  int nz, long long N, const typename CT<T>::t* __restrict__ gtw,
+__global__ void __launch_bounds__(kThreads) k_xyf(const typename IOT<T>::t* __restrict__ in,
+                                                  typename CT<T>::t* __restrict__ spec, int nz, long long N,
+                                                  const typename CT<T>::t* __restrict__ gtw,
                                                   const int* __restrict__ gpos, const int* skip) {
   typedef XYShape<T, NX> Sh;
   typedef typename CT<T>::t C;
+  typedef typename CT<typename IOT<T>::t>::t CI;
+  static_assert(sizeof(C) == sizeof(CI), "in-place conversion needs equal element sizes");
   if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -71,12 +91,20 @@ __global__ void __launch_bounds__(kThreads) k_xyf(const T* __restrict__ in, type
   int* posx = reinterpret_cast<int*>(twy + NY);
   load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
-  const C* src = reinterpret_cast<const C*>(in + c * N + (long long)z * NY * NX);
+  const CI* src = reinterpret_cast<const CI*>(in + c * N + (long long)z * NY * NX);
   for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
     const int y = idx / H, j = idx - (idx / H) * H;
-    cp_async_elem(buf + y * PX + j, src + idx);
+    cp_async_elem(reinterpret_cast<CI*>(buf + y * PX + j), src + idx);
   }
   cp_async_wait_all();
+  if constexpr (!std::is_same<C, CI>::value) {
+    // each thread converts the elements it copied itself
+    for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+      const int y = idx / H, j = idx - (idx / H) * H;
+      const CI v = *reinterpret_cast<const CI*>(buf + y * PX + j);
+      io_in(buf[y * PX + j], v);
+    }
+  }
   __syncthreads();
   // x: NY rows of H complex samples
   fft2::forward<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
@@ -116,13 +144,17 @@ __global__ void __launch_bounds__(kThreads) k_xyf(const T* __restrict__ in, type
 // MODE 0: out[c] = y.  MODE 2: out[c] = y, partial sum y^2.  MODE 3: out[c] -=
 // alpha y (alpha from sc), partial sum out^2.
 template <typename T, int NX, int MODE>
-__global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __restrict__ spec, T* __restrict__ out,
+__global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __restrict__ spec,
+                                                  typename IOT<T>::t* __restrict__ out,
                                                   double* __restrict__ partials, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
                                                   const int* __restrict__ gpos, const Scalars* sc,
                                                   const int* skip) {
   typedef XYShape<T, NX> Sh;
   typedef typename CT<T>::t C;
+  typedef typename IOT<T>::t TI;
+  typedef typename CT<TI>::t CI;
+  static_assert(MODE != 3 || std::is_same<C, CI>::value, "the CG update runs in the compute type");
   if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -184,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
   }
   __syncthreads();
   fft2::inverse<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
-  C* dst = reinterpret_cast<C*>(out + c * N + (long long)z * NY * NX);
+  CI* dst = reinterpret_cast<CI*>(out + c * N + (long long)z * NY * NX);
   // per-thread sums: FP64 for FP64 data; for FP32 data exact FP32 products
   // with Neumaier-compensated FP32 accumulation, combined in FP64 below
   double acc = 0.0;
@@ -205,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
   for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
     const int y = idx / H, j = idx - (idx / H) * H;
     const C v = buf[y * PX + j];
-    if (MODE == 3) {
+    if constexpr (MODE == 3) {
       C r = dst[idx];
       r.x -= alpha * v.x;
       r.y -= alpha * v.y;
@@ -213,14 +245,15 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
       if (sizeof(T) == 4) { fsq((float)r.x); fsq((float)r.y); }
       else acc += (double)r.x * (double)r.x + (double)r.y * (double)r.y;
     } else {
-      dst[idx] = v;
+      const CI w = io_out(v);
+      dst[idx] = w;
       if (MODE == 2) {
-        if (sizeof(T) == 4) { fsq((float)v.x); fsq((float)v.y); }
-        else acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        if (sizeof(TI) == 4) { fsq((float)w.x); fsq((float)w.y); }
+        else acc += (double)w.x * (double)w.x + (double)w.y * (double)w.y;
       }
     }
   }
-  if (sizeof(T) == 4) acc = (double)fs + (double)fc;
+  if (sizeof(TI) == 4) acc = (double)fs + (double)fc;
   if (MODE >= 2) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

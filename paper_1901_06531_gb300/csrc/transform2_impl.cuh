@@ -7,7 +7,7 @@
 namespace tr2 {
 
 template <typename T, int NX>
-cudaError_t launch_xyf(const T* in, void* spec, const XYArgs& a, cudaStream_t st) {
+cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a, cudaStream_t st) {
   typedef typename CT<T>::t C;
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -18,8 +18,8 @@ cudaError_t launch_xyf(const T* in, void* spec, const XYArgs& a, cudaStream_t st
 }
 
 template <typename T, int NX, int MODE>
-cudaError_t launch_xyi(const void* spec, T* out, double* partials, const XYArgs& a, const Scalars* sc,
-                       cudaStream_t st) {
+cudaError_t launch_xyi(const void* spec, typename IOT<T>::t* out, double* partials, const XYArgs& a,
+                       const Scalars* sc, cudaStream_t st) {
   typedef typename CT<T>::t C;
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -48,7 +48,7 @@ cudaError_t launch_zp_s(void* spec, const ZArgs& a, cudaStream_t st) {
 // {2, 4, 8}); the residual (MODE 1) uses the default tile.
 template <typename T, int NZ, int MODE>
 cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
-  if (MODE == 0) {
+  if constexpr (MODE == 0) {
     if (a.S == 2) return launch_zp_s<T, NZ, MODE, 2>(spec, a, st);
     if (a.S == 4) return launch_zp_s<T, NZ, MODE, 4>(spec, a, st);
     if (a.S == 8) return launch_zp_s<T, NZ, MODE, 8>(spec, a, st);
@@ -58,7 +58,7 @@ cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
 
 template <typename T>
 cudaError_t xyf(const void* in, void* spec, const XYArgs& a, cudaStream_t st) {
-  const T* p = (const T*)in;
+  const typename IOT<T>::t* p = (const typename IOT<T>::t*)in;
   switch (a.nx) {
     case 16: return launch_xyf<T, 16>(p, spec, a, st);
     case 32: return launch_xyf<T, 32>(p, spec, a, st);
@@ -73,7 +73,7 @@ cudaError_t xyf(const void* in, void* spec, const XYArgs& a, cudaStream_t st) {
 template <typename T, int MODE>
 cudaError_t xyi_m(const void* spec, void* out, double* partials, const XYArgs& a, const Scalars* sc,
                   cudaStream_t st) {
-  T* o = (T*)out;
+  typename IOT<T>::t* o = (typename IOT<T>::t*)out;
   switch (a.nx) {
     case 16: return launch_xyi<T, 16, MODE>(spec, o, partials, a, sc, st);
     case 32: return launch_xyi<T, 32, MODE>(spec, o, partials, a, sc, st);

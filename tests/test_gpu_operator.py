@@ -167,6 +167,38 @@ def test_fixed_size_kernels_fp64(shape, mi):
     np.testing.assert_allclose(meanP, P.reshape(9, -1).mean(1), rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("shape", SHAPES_V2)
+@pytest.mark.parametrize("mi", [0, 2])
+@pytest.mark.parametrize("model", ["nh", "svk"])
+def test_residual_double_word(shape, mi, model):
+    """FP32-inner contexts compute the residual transforms in double-word FP32
+    arithmetic (about 48 significant bits): the FP64 residual still agrees
+    with the oracle to 1e-12 relative (max norm) and <P> to 1e-14; the FP64
+    setting of the same context gives the same agreement."""
+    import torch
+    mf = lib()
+    ctx, om, F = make(mf, shape, mf.MF_FP32_INNER, model, seed=18)
+    ctx.constitutive()
+    nx, ny, nz = shape
+    P, _ = om.PK(F)
+    pbar = np.array([0.05, 0.01, 0.0, -0.01, 0.02, 0.0, 0.0, 0.0, -0.03])
+    refb = osolver.residual(P, MASKS[mi], pbar)
+    for arith in (mf.MF_RESIDUAL_DOUBLE_WORD, mf.MF_RESIDUAL_FP64):
+        ctx.set_residual_arith(arith)
+        b = torch.full((9 * nx * ny * nz,), float("nan"), dtype=torch.float64, device="cuda")
+        meanP = ctx.residual(MASKS[mi], pbar, b)
+        assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12, arith
+        np.testing.assert_allclose(meanP, P.reshape(9, -1).mean(1), rtol=0, atol=1e-14)
+
+
+def test_residual_arith_rejects_unknown():
+    mf = lib()
+    ctx = mf.Context(16, 16, 16, mf.MF_FP32_INNER)
+    with pytest.raises(mf.MixFFTError) as e:
+        ctx.set_residual_arith(2)
+    assert e.value.status == mf.MF_INVALID_ARG
+
+
 @pytest.mark.parametrize("shape", SHAPES_V2[:4])
 def test_fixed_size_kernels_fp32(shape):
     import torch
@@ -187,7 +219,8 @@ def test_fixed_size_kernels_fp32(shape):
 def test_full_size_polycrystal_operator_and_residual():
     """The bench's workload and launch configuration (128^3, 200-grain SVK
     polycrystal, rotation-fixed mask): FP32 operator against the FP64
-    oracle element by element, and the FP64 residual to 1e-12."""
+    oracle element by element, and the FP64 residual (double-word transforms
+    in the FP32-inner context) to 1e-12."""
     import torch
     mf = lib()
     n = 128
@@ -213,10 +246,11 @@ def test_full_size_polycrystal_operator_and_residual():
             got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-6
             assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref))
-        else:
-            b = torch.empty(9 * n ** 3, dtype=torch.float64, device="cuda")
-            ctx.residual(m0, target[0] * m0, b)
-            refb = osolver.residual(P, m0, target[0] * m0)
-            assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
+        # the FP64 residual: double-word transforms in the FP32-inner
+        # context, FP64 transforms in the FP64 one
+        b = torch.empty(9 * n ** 3, dtype=torch.float64, device="cuda")
+        ctx.residual(m0, target[0] * m0, b)
+        refb = osolver.residual(P, m0, target[0] * m0)
+        assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
         del ctx
         torch.cuda.empty_cache()
