@@ -52,7 +52,7 @@ typedef enum {
 
 typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
 typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
-typedef enum { MF_RESIDUAL_DOUBLE_WORD = 0, MF_RESIDUAL_FP64 = 1 } mf_residual_arith;
+typedef enum { MF_OUTER_DOUBLE_WORD = 0, MF_OUTER_FP64 = 1 } mf_outer_arith;
 
 typedef struct mf_ctx mf_ctx;
 
@@ -145,6 +145,12 @@ int mf_get_fields(mf_ctx* ctx, double* F_host, double* P_host);
  * in the context (45 packed entries per voxel, FP64 or FP32 by precision). */
 int mf_constitutive(mf_ctx* ctx);
 
+/* Evaluate P(F) alone (no tangent) at the current F, with its voxel
+ * averages: the constitutive pass of the last Newton step.  MF_FP32_INNER
+ * contexts use the outer arithmetic (mf_set_outer_arith), MF_FP64 contexts
+ * FP64.  meanP_host: host 9 doubles or NULL, receives <P>. */
+int mf_stress(mf_ctx* ctx, double* meanP_host);
+
 /* Copy the tangent to host memory as 45 packed symmetric entries per voxel:
  * K45_host[t*N + v], t = a*9 - a*(a-1)/2 + (b - a) for a <= b, a = 3i+j,
  * b = 3k+l, value K_ijkl (converted to double). */
@@ -220,7 +226,7 @@ int mf_time_cufft(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
 /* Wait for the context's stream. */
 int mf_sync(mf_ctx* ctx);
 
-/* Autotuner: time the z-pass tile candidates (2, 4, 8 columns per block) of
+/* Autotuner: time the z-pass tile candidates (4, 8, 16 columns per block) of
  * the fixed-size transform kernels for this context's size and precision and
  * keep the fastest (CUDA events on the context's stream, L2 flushed before
  * every launch).  The choice is cached per (nx, ny, nz, precision) for the
@@ -257,16 +263,19 @@ int mf_adjoint(mf_ctx* ctx, const uint8_t* mask, const double* wF, const double*
                double cg_rel, int max_cg, double* J_out, double* dJ_dparams, double* dJ_dscale_dev,
                int32_t* cg_its_out);
 
-/* Arithmetic of the transforms of the FP64 residual b = -G*(P - P-bar)
- * (Eq. linequil2ast, right side) in MF_FP32_INNER contexts:
- * MF_RESIDUAL_DOUBLE_WORD (the default) computes them with double-word FP32
- * arithmetic (hi + lo pairs, about 48 significant bits; P is read and b
- * written in FP64) wherever the fixed-size transform kernels serve the grid
- * (nx = ny, nx and nz in {16, 32, 48, 64, 96, 128}), FP64 elsewhere;
- * MF_RESIDUAL_FP64 always uses FP64.  The constitutive law, the averages,
- * the Newton update and every reduction stay FP64.  MF_FP64 contexts ignore
- * the setting.  Returns MF_INVALID_ARG for another value. */
-int mf_set_residual_arith(mf_ctx* ctx, int arith);
+/* Arithmetic of the outer (defect-correction) level of MF_FP32_INNER
+ * contexts: the stress P(F) of the constitutive pass (Eq. eq:lineariz) and
+ * the transforms of the residual b = -G*(P - P-bar) (Eq. linequil2ast, right
+ * side).  MF_OUTER_DOUBLE_WORD (the default) evaluates them in double-word
+ * FP32 arithmetic (hi + lo pairs, about 48 significant bits; F and P are read
+ * and written in FP64): P on every grid, the residual transforms wherever the
+ * fixed-size transform kernels serve the grid (nx = ny, nx and nz in
+ * {16, 32, 48, 64, 96, 128}), FP64 elsewhere.  MF_OUTER_FP64 evaluates both
+ * in FP64.  The averages, the Newton update, the predictor and every
+ * reduction stay FP64 in both.  MF_FP64 contexts ignore the setting; the
+ * tangent of mf_constitutive is always FP64.  Returns MF_INVALID_ARG for
+ * another value. */
+int mf_set_outer_arith(mf_ctx* ctx, int arith);
 
 /* Name and description of the CUDA error behind the last MF_CUDA_ERROR
  * returned by any context in this process ("" if none); static storage. */

@@ -1,0 +1,203 @@
+// Constitutive update P(F) (Eq. eq:lineariz's P; no tangent) in double-word
+// FP32 arithmetic for the FP32-inner mode, with the voxel averages of F and
+// P, optionally the FP32 H = F - I of the matrix-free tangent and the
+// rotation moments, in one pass over F.
+//
+// Both laws are evaluated from H = F - I, so that no large term cancels:
+//   St Venant-Kirchhoff  E = (H + H^T + H^T H)/2, S = C : E, P = S + H S;
+//   neo-Hookean          J - 1 = tr H + (tr^2 H - tr H^2)/2 + det H,
+//                        P = mu F + (lam ln J - mu) F^-T, F^-T = cof(F)/J,
+// every product and sum in double-word arithmetic (about 48 bits), ln J
+// from FP64 log1p of J - 1.  F is read and P written in FP64.
+#include "dw.cuh"
+#include "launch.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ dw half(dw a) { return dw(0.5f * a.hi, 0.5f * a.lo); }   // exact
+__device__ __forceinline__ dw twice(dw a) { return dw(2.0f * a.hi, 2.0f * a.lo); }  // exact
+__device__ __forceinline__ constexpr int vgt(int i, int j) {
+  return i == j ? i : (i + j == 3 ? 3 : (i + j == 2 ? 4 : 5));
+}
+
+__device__ __forceinline__ void svk_dw(const dw (&h)[9], const dw* __restrict__ cv, dw (&P)[9]) {
+  dw e6[6];
+  auto E = [&](int a, int b) {
+    dw s = h[3 * a + b] + h[3 * b + a];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s = s + h[3 * k + a] * h[3 * k + b];
+    return half(s);
+  };
+  e6[0] = E(0, 0); e6[1] = E(1, 1); e6[2] = E(2, 2);
+  e6[3] = twice(E(1, 2)); e6[4] = twice(E(0, 2)); e6[5] = twice(E(0, 1));
+  dw sv[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) {
+    dw acc = cv[6 * I] * e6[0];
+#pragma unroll
+    for (int J = 1; J < 6; ++J) acc = acc + cv[6 * I + J] * e6[J];
+    sv[I] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dw acc = sv[vgt(i, j)];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc = acc + h[3 * i + k] * sv[vgt(k, j)];
+      P[3 * i + j] = acc;
+    }
+}
+
+// Returns false when J <= 0 (P is then zero).
+__device__ __forceinline__ bool neohooke_dw(const dw (&h)[9], const dw (&f)[9], dw mu, dw lam, dw (&P)[9]) {
+  const dw one(1.0f, 0.0f);
+  const dw trH = h[0] + h[4] + h[8];
+  dw trH2 = h[0] * h[0] + h[4] * h[4] + h[8] * h[8];
+  trH2 = trH2 + twice(h[1] * h[3] + h[2] * h[6] + h[5] * h[7]);
+  const dw detH = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                  h[2] * (h[3] * h[7] - h[4] * h[6]);
+  const dw Jm1 = trH + half(trH * trH - trH2) + detH;
+  const dw J = Jm1 + one;
+  if (!(J.hi > 0.0f)) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) P[c] = dw(0.0f, 0.0f);
+    return false;
+  }
+  const dw iJ = one / J;
+  dw G[9];   // F^-T = cof(F) / J
+  G[0] = (f[4] * f[8] - f[5] * f[7]) * iJ;
+  G[1] = (f[5] * f[6] - f[3] * f[8]) * iJ;
+  G[2] = (f[3] * f[7] - f[4] * f[6]) * iJ;
+  G[3] = (f[2] * f[7] - f[1] * f[8]) * iJ;
+  G[4] = (f[0] * f[8] - f[2] * f[6]) * iJ;
+  G[5] = (f[1] * f[6] - f[0] * f[7]) * iJ;
+  G[6] = (f[1] * f[5] - f[2] * f[4]) * iJ;
+  G[7] = (f[2] * f[3] - f[0] * f[5]) * iJ;
+  G[8] = (f[0] * f[4] - f[1] * f[3]) * iJ;
+  const dw lnJ = dw_split(log1p(dw_join(Jm1)));
+  const dw cg = lam * lnJ - mu;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) P[c] = mu * f[c] + cg * G[c];
+  return true;
+}
+
+template <int NC>
+__device__ __forceinline__ void block_sum_dw(double (&v)[NC], double* out) {
+  __shared__ double red[NC][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double s = v[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[c][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NC) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Columns of the block partials: F 0-8, P 9-17, and with MOM T = sum P F^T
+// 18-26, S = sum F F^T 27-35 (FP32 products of the high parts: only used to
+// detect null rotations).
+template <int MODEL, bool WH, bool MOM>
+__global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __restrict__ F, double* __restrict__ P,
+                                                              float* __restrict__ H, MatArgs m,
+                                                              const dw* __restrict__ table, long long N,
+                                                              double* __restrict__ partials, Scalars* sc) {
+  constexpr int NC = MOM ? 36 : 18;
+  __shared__ double tot[NC];
+  dw acc[18];
+#pragma unroll
+  for (int c = 0; c < 18; ++c) acc[c] = dw(0.0f, 0.0f);
+  float mom[18];
+#pragma unroll
+  for (int c = 0; c < 18; ++c) mom[c] = 0.f;
+  bool bad = false;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    double fd[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) fd[c] = F[c * N + v];
+    const int ph = m.phase[v];
+    dw h[9], f[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      f[c] = dw_split(fd[c]);
+      // diagonal: hi - 1 is exact for hi in [1/2, 2] (Sterbenz)
+      h[c] = (c == 0 || c == 4 || c == 8) ? dw(f[c].hi - 1.0f, 0.0f) + dw(f[c].lo, 0.0f) : f[c];
+    }
+    dw p[9];
+    if constexpr (MODEL == 0) {
+      if (!neohooke_dw(h, f, table[2 * ph], table[2 * ph + 1], p)) bad = true;
+    } else {
+      svk_dw(h, table + 36 * ph, p);
+    }
+    if (m.scale) {
+      const dw s = dw_split(m.scale[v]);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) p[c] = s * p[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      P[c * N + v] = dw_join(p[c]);
+      if (WH) H[c * N + v] = h[c].hi;
+      acc[c] = acc[c] + f[c];
+      acc[9 + c] = acc[9 + c] + p[c];
+    }
+    if (MOM) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          mom[3 * i + j] += p[3 * i].hi * f[3 * j].hi + p[3 * i + 1].hi * f[3 * j + 1].hi +
+                            p[3 * i + 2].hi * f[3 * j + 2].hi;
+          mom[9 + 3 * i + j] += f[3 * i].hi * f[3 * j].hi + f[3 * i + 1].hi * f[3 * j + 1].hi +
+                                f[3 * i + 2].hi * f[3 * j + 2].hi;
+        }
+    }
+  }
+  if (bad) atomicOr(&sc->flags, MF_FLAG_NONPOS_J);
+  double a[NC];
+#pragma unroll
+  for (int c = 0; c < 18; ++c) a[c] = dw_join(acc[c]);
+  if constexpr (MOM) {
+#pragma unroll
+    for (int c = 0; c < 18; ++c) a[18 + c] = (double)mom[c];
+  }
+  block_sum_dw<NC>(a, tot);
+  if (threadIdx.x < NC) partials[blockIdx.x * NC + threadIdx.x] = tot[threadIdx.x];
+}
+
+template <int MODEL>
+cudaError_t launch_model(const double* F, double* P, float* H, bool moments, const MatArgs& m, const dw* table,
+                         long long N, double* partials, int nblk, Scalars* sc, cudaStream_t st) {
+  if (H && moments)
+    k_constitutive_dw<MODEL, true, true><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
+  else if (H)
+    k_constitutive_dw<MODEL, true, false><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
+  else if (moments)
+    k_constitutive_dw<MODEL, false, true><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
+  else
+    k_constitutive_dw<MODEL, false, false><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t mf_launch_constitutive_dw(const double* F, double* P, float* H, bool moments, const MatArgs& m,
+                                      const void* table_dw, long long N, double* partials, int nblk,
+                                      Scalars* sc, cudaStream_t st) {
+  const dw* table = (const dw*)table_dw;
+  cudaError_t e = m.model == 0 ? launch_model<0>(F, P, H, moments, m, table, N, partials, nblk, sc, st)
+                               : launch_model<1>(F, P, H, moments, m, table, N, partials, nblk, sc, st);
+  g_mf_launches += 1;
+  if (e != cudaSuccess) return e;
+  return mf_launch_fin_means(partials, nblk, moments ? 36 : 18, N, sc, st);
+}

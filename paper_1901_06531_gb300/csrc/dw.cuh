@@ -58,9 +58,10 @@ __device__ __forceinline__ dw neg(dw a) { return dw(-a.hi, -a.lo); }
 
 __device__ __forceinline__ dw mul(dw a, dw b) {
   const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);                       // TwoProd error
+  float e = __fmaf_rn(a.lo, b.lo, 0.0f);   // kept: for squares it has one sign (no bias in sums of squares)
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
+  e = __fadd_rn(e, __fmaf_rn(a.hi, b.hi, -p));               // TwoProd error
   return fast_two_sum(p, e);
 }
 
@@ -84,6 +85,84 @@ __device__ __forceinline__ dw& operator-=(dw& a, dw b) { a = a - b; return a; }
 
 __device__ __forceinline__ dwc cmake(dw a, dw b) { dwc r; r.x = a; r.y = b; return r; }
 
-// exact split of an FP64 complex value into double-word parts, and back
-__device__ __forceinline__ dwc to_dwc(double2 v) { dwc r; r.x = dw(v.x); r.y = dw(v.y); return r; }
-__device__ __forceinline__ double2 to_double2(dwc v) { return make_double2((double)v.x, (double)v.y); }
+// Complex products with the TwoProd errors of both real products gathered
+// before one TwoSum (fewer operations than four double-word products and
+// two double-word sums).  a b (SIGN = -1) or a conj(b) pieces are formed by
+// the callers below.
+__device__ __forceinline__ dw dot2(dw a, dw b, dw c, dw d, bool minus) {
+  // a b - c d (minus) or a b + c d
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  if (minus) { p2 = -p2; e2 = -e2; }
+  const float s = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(s, p1);
+  float e = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  e = __fadd_rn(e, __fadd_rn(e1, e2));
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  e = minus ? __fmaf_rn(-c.hi, d.lo, e) : __fmaf_rn(c.hi, d.lo, e);
+  e = minus ? __fmaf_rn(-c.lo, d.hi, e) : __fmaf_rn(c.lo, d.hi, e);
+  return dwops::fast_two_sum(s, e);
+}
+__device__ __forceinline__ dwc cmul(dwc a, dwc b) {
+  dwc r;
+  r.x = dot2(a.x, b.x, a.y, b.y, true);
+  r.y = dot2(a.x, b.y, a.y, b.x, false);
+  return r;
+}
+// a * conj(b)
+__device__ __forceinline__ dwc cmulc(dwc a, dwc b) {
+  dwc r;
+  r.x = dot2(a.x, b.x, a.y, b.y, false);
+  r.y = dot2(a.y, b.x, a.x, b.y, true);
+  return r;
+}
+
+// FP64 <-> double word by bit manipulation (no FP64 instruction on the way
+// in, one FP64 addition on the way out: FP64 and its conversions run on the
+// slow FP64 pipe of this part).
+//
+// In: hi = the FP64 value truncated to 24 significant bits (exact in FP32),
+// lo = the remaining 29 bits rounded to the nearest 24 (so that the error,
+// at most 2^-48 relative, has no bias: averages over many voxels keep FP64
+// accuracy).  Magnitudes below 2^-74 contribute no lo part; below 2^-126
+// the value becomes zero; beyond the FP32 range it becomes an infinity, and
+// infinities and NaNs pass through (so a non-finite P is still seen).
+__device__ __forceinline__ dw dw_split(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  if (e >= 897 && e <= 1150) {
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | m23);
+    float lo = 0.0f;
+    const unsigned ml = lw & 0x1fffffffu;
+    if (ml != 0u && e >= 949) {
+      lo = __fmul_rn(__uint2float_rn(ml), __uint_as_float((unsigned)(e - 948) << 23));
+      if (sign) lo = -lo;
+    }
+    return dwops::fast_two_sum(hi, lo);   // normalise: abs(lo) <= ulp(hi)/2
+  }
+  if (e < 897) return dw(sign ? -0.0f : 0.0f, 0.0f);
+  const unsigned nan = (e == 2047 && ((hw & 0xfffffu) | lw)) ? 0x400000u : 0u;
+  return dw(__uint_as_float(sign | 0x7f800000u | nan), 0.0f);
+}
+
+// An FP32 value as FP64, exactly (subnormal FP32 values flush to zero).
+__device__ __forceinline__ double f32_as_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e8 = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u;
+  if (e8 == 0u) return __hiloint2double((int)sign, 0);
+  if (e8 == 255u)
+    return __hiloint2double((int)(sign | 0x7ff00000u | ((u & 0x7fffffu) ? 0x80000u : 0u)), 0);
+  return __hiloint2double((int)(sign | ((e8 + 896u) << 20) | ((u >> 3) & 0xfffffu)), (int)(u << 29));
+}
+
+__device__ __forceinline__ double dw_join(dw a) { return f32_as_f64(a.hi) + f32_as_f64(a.lo); }
+
+__device__ __forceinline__ dwc to_dwc(double2 v) { dwc r; r.x = dw_split(v.x); r.y = dw_split(v.y); return r; }
+__device__ __forceinline__ double2 to_double2(dwc v) { return make_double2(dw_join(v.x), dw_join(v.y)); }

@@ -118,6 +118,15 @@ struct MatArgs {
 cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k_f32, bool want_K,
                                    bool moments, const MatArgs& m, long long N, double* partials,
                                    int nblk, Scalars* sc, cudaStream_t st);
+// column sums of constitutive partials into meanF, meanP (and T, S if ncol 36)
+cudaError_t mf_launch_fin_means(const double* partials, int nblk, int ncol, long long N, Scalars* sc,
+                                cudaStream_t st);
+// constitutive_dw.cu: P (no tangent) in double-word arithmetic, the averages,
+// and optionally H = F - I (FP32, H non-null) and the rotation moments;
+// table_dw: the material table as double-word values (layout of MatArgs.table)
+cudaError_t mf_launch_constitutive_dw(const double* F, double* P, float* H, bool moments, const MatArgs& m,
+                                      const void* table_dw, long long N, double* partials, int nblk,
+                                      Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int nblk, Scalars* sc,
                              cudaStream_t st);
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,

@@ -205,7 +205,7 @@ struct mf_ctx {
   size_t ws_need = 0;
   // offsets into the workspace
   size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
-      otable32, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
+      otable32, otabledw, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
   size_t npart;
   // material
   int model = -1, nphase = 0;
@@ -221,12 +221,14 @@ struct mf_ctx {
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
   bool tuned = false;              // z-pass tile chosen by the autotuner
-  int residual_arith = MF_RESIDUAL_DOUBLE_WORD;
+  int outer_arith = MF_OUTER_DOUBLE_WORD;
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   bool f32() const { return prec == MF_FP32_INNER; }
-  // residual transforms in double-word FP32 (FP32-inner mode, fixed-size kernels)
-  bool dw_residual() const { return f32() && v2 && residual_arith == MF_RESIDUAL_DOUBLE_WORD; }
+  // outer level in double-word FP32 (FP32-inner mode): P on every grid, the
+  // residual transforms where the fixed-size kernels exist
+  bool dw_outer() const { return f32() && outer_arith == MF_OUTER_DOUBLE_WORD; }
+  bool dw_residual() const { return dw_outer() && v2; }
   size_t inner_size() const { return f32() ? sizeof(float) : sizeof(double); }
 };
 
@@ -307,6 +309,16 @@ int flags_status(int flags) {
 // P (and optionally the packed K) at the current F, voxel averages of F and
 // P; with want_H the FP32 H = F - I for the matrix-free tangent.
 int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false) {
+  if (!want_K && c->dw_outer()) {
+    // P, H and the moments in one double-word pass
+    const cudaError_t e = mf_launch_constitutive_dw(c->at<double>(c->oF), c->at<double>(c->oP),
+                                                    want_H ? c->at<float>(c->oH) : nullptr, moments, mat_args(c),
+                                                    c->ws + c->otabledw, c->N, c->at<double>(c->opart),
+                                                    kPointwiseBlocks, c->at<Scalars>(c->osc), c->st);
+    c->have_K = false;
+    c->have_H = want_H && e == cudaSuccess;
+    return cuda_status(e);
+  }
   cudaError_t e = mf_launch_constitutive(c->at<double>(c->oF), c->at<double>(c->oP), c->ws + c->oK,
                                          c->f32(), want_K, moments, mat_args(c), c->N,
                                          c->at<double>(c->opart), kPointwiseBlocks,
@@ -445,7 +457,7 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
 }
 
 // ---------------------------------------------------------------- autotuner
-// The z-pass tile (columns per block: 2, 4 or 8 for the fixed-size kernels)
+// The z-pass tile (columns per block: 4, 8 or 16 for the fixed-size kernels)
 // trades shared memory per block against blocks per SM and DRAM segment
 // length; the best choice depends on the z length and the precision.  Each
 // candidate is timed with CUDA events on the context's stream (L2 flushed
@@ -467,7 +479,7 @@ int autotune(mf_ctx* c, int reps) {
       }
   }
   const bool f32 = c->f32();
-  const int cands[3] = {2, 4, 8};
+  const int cands[3] = {4, 8, 16};
   const uint8_t mask[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
   ZArgs za = z_args(c, f32, mask, 1.0 / (double)c->N);
   const XYArgs xa = xy_args(c, f32);
@@ -818,6 +830,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->oscale32 = take(N * sizeof(float));
   c->otable = take((size_t)kMaxPhases * 36 * sizeof(double));
   c->otable32 = take((size_t)kMaxPhases * 36 * sizeof(float));
+  c->otabledw = take((size_t)kMaxPhases * 36 * sizeof(dw));
   // widest reduction: the constitutive pass with rotation moments, 36 columns per block
   c->npart = (size_t)(kPointwiseBlocks > 9 * nz ? kPointwiseBlocks : 9 * nz) * 36;
   c->opart = take(c->npart * sizeof(double));
@@ -961,10 +974,14 @@ int mf_set_material(mf_ctx* c, int model, int nphase, const double* params, cons
     for (long long v = 0; v < c->N; ++v)
       if (!isfinite(scale[v])) return MF_INVALID_ARG;
   std::vector<float> table32(table.begin(), table.end());
+  std::vector<dw> tabledw(table.begin(), table.end());
   cudaError_t e = cudaMemcpyAsync(c->ws + c->otable, table.data(), table.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->ws + c->otable32, table32.data(), table32.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->ws + c->otabledw, tabledw.data(), tabledw.size() * sizeof(dw),
                         cudaMemcpyHostToDevice, c->st);
   std::vector<float> scale32;
   if (scale) scale32.assign(scale, scale + c->N);
@@ -1043,6 +1060,19 @@ int mf_constitutive(mf_ctx* c) {
   Scalars h;
   s = read_scalars(c, &h);
   if (s) return s;
+  return flags_status(h.flags);
+}
+
+int mf_stress(mf_ctx* c, double* meanP_host) {
+  if (!c) return MF_INVALID_ARG;
+  if (!c->ws) return MF_NO_WORKSPACE;
+  if (c->model < 0) return MF_INVALID_ARG;
+  int s = run_constitutive(c, false, false);
+  if (s) return s;
+  Scalars h;
+  s = read_scalars(c, &h);
+  if (s) return s;
+  if (meanP_host) memcpy(meanP_host, h.meanP, sizeof(h.meanP));
   return flags_status(h.flags);
 }
 
@@ -1282,9 +1312,9 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
   return MF_OK;
 }
 
-int mf_set_residual_arith(mf_ctx* c, int arith) {
-  if (!c || (arith != MF_RESIDUAL_DOUBLE_WORD && arith != MF_RESIDUAL_FP64)) return MF_INVALID_ARG;
-  c->residual_arith = arith;
+int mf_set_outer_arith(mf_ctx* c, int arith) {
+  if (!c || (arith != MF_OUTER_DOUBLE_WORD && arith != MF_OUTER_FP64)) return MF_INVALID_ARG;
+  c->outer_arith = arith;
   return MF_OK;
 }
 

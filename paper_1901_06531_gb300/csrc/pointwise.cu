@@ -486,6 +486,13 @@ int grid_for(long long n) {
 
 }  // namespace
 
+cudaError_t mf_launch_fin_means(const double* partials, int nblk, int ncol, long long N, Scalars* sc,
+                                cudaStream_t st) {
+  k_fin_means<<<1, kRedThreads, 0, st>>>(partials, nblk, ncol, N, sc);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k_f32, bool want_K,
                                    bool moments, const MatArgs& m, long long N, double* partials,
                                    int nblk, Scalars* sc, cudaStream_t st) {

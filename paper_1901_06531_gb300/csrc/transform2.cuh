@@ -36,10 +36,15 @@ __device__ __forceinline__ double2 io_out(double2 v) { return v; }
 __device__ __forceinline__ double2 io_out(dwc v) { return to_double2(v); }
 
 constexpr int kThreads = 256;
-// z-pass threads per block for a tile of S columns: 36 S (rounded up to whole
-// warps) divides the butterfly counts of the radix-16/8 stages evenly
-// (9 components x S columns x NZ/R butterflies per stage)
-__host__ __device__ constexpr int z_threads(int S) { return S >= 8 ? 288 : S == 4 ? 160 : 96; }
+// x-y kernels: 16-byte elements (FP64, double word) hold one 128 x 128 plane
+// in 133 KB of shared memory, one block per SM, so they run twice the threads
+template <typename T> __host__ __device__ constexpr int xy_threads() {
+  return sizeof(typename CT<T>::t) == 16 ? 512 : 256;
+}
+// z-pass threads per block for a tile of S columns of one row group (three
+// components): 24 S, one butterfly per thread in a radix-16 stage of the
+// 128-point transform and two in its radix-8 stage (3 x S x 128/R)
+__host__ __device__ constexpr int z_threads(int S) { return 24 * S; }
 
 // Asynchronous global -> shared copies of one complex element (8 or 16
 // bytes); many in flight per thread without holding registers.
@@ -74,11 +79,12 @@ __device__ __forceinline__ void load_tables(C* twx, C* twy, int* posx, const C* 
 
 // ------------------------------------------------------------------ forward
 template <typename T, int NX>
-__global__ void __launch_bounds__(kThreads) k_xyf(const typename IOT<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::t* __restrict__ in,
                                                   typename CT<T>::t* __restrict__ spec, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
                                                   const int* __restrict__ gpos, const int* skip) {
   typedef XYShape<T, NX> Sh;
+  constexpr int TPB = xy_threads<T>();
   typedef typename CT<T>::t C;
   typedef typename CT<typename IOT<T>::t>::t CI;
   static_assert(sizeof(C) == sizeof(CI), "in-place conversion needs equal element sizes");
@@ -92,14 +98,14 @@ __global__ void __launch_bounds__(kThreads) k_xyf(const typename IOT<T>::t* __re
   load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
   const CI* src = reinterpret_cast<const CI*>(in + c * N + (long long)z * NY * NX);
-  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
     const int y = idx / H, j = idx - (idx / H) * H;
     cp_async_elem(reinterpret_cast<CI*>(buf + y * PX + j), src + idx);
   }
   cp_async_wait_all();
   if constexpr (!std::is_same<C, CI>::value) {
     // each thread converts the elements it copied itself
-    for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
       const int y = idx / H, j = idx - (idx / H) * H;
       const CI v = *reinterpret_cast<const CI*>(buf + y * PX + j);
       io_in(buf[y * PX + j], v);
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_xyf(const typename IOT<T>::t* __re
   fft2::forward<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
   // split into the NX-point spectrum of each real row; pairs (k, H-k)
   constexpr int NP = H / 2 + 1;
-  for (int idx = threadIdx.x; idx < NY * NP; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NY * NP; idx += TPB) {
     const int y = idx % NY, k = idx / NY;
     const int km = (H - k) % H;
     C* row = buf + y * PX;
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_xyf(const typename IOT<T>::t* __re
   fft2::forward<C, NY, NY, H, 1, 1, 0, PX>(buf, twy);
   C* dst = spec + ((long long)c * nz + z) * NY * H;
 #pragma unroll 8
-  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
     const int y = idx / H, j = idx - (idx / H) * H;
     dst[idx] = buf[y * PX + j];
   }
@@ -144,13 +150,14 @@ __global__ void __launch_bounds__(kThreads) k_xyf(const typename IOT<T>::t* __re
 // MODE 0: out[c] = y.  MODE 2: out[c] = y, partial sum y^2.  MODE 3: out[c] -=
 // alpha y (alpha from sc), partial sum out^2.
 template <typename T, int NX, int MODE>
-__global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __restrict__ spec,
+__global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t* __restrict__ spec,
                                                   typename IOT<T>::t* __restrict__ out,
                                                   double* __restrict__ partials, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
                                                   const int* __restrict__ gpos, const Scalars* sc,
                                                   const int* skip) {
   typedef XYShape<T, NX> Sh;
+  constexpr int TPB = xy_threads<T>();
   typedef typename CT<T>::t C;
   typedef typename IOT<T>::t TI;
   typedef typename CT<TI>::t CI;
@@ -169,11 +176,11 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
     // the residual plane is read only at the end: start pulling it into L2 now
     const char* rp = reinterpret_cast<const char*>(out + c * N + (long long)z * NY * NX);
     constexpr int kLines = (NY * NX * (int)sizeof(T)) / 128;
-    for (int i = threadIdx.x; i < kLines; i += kThreads)
+    for (int i = threadIdx.x; i < kLines; i += TPB)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + 128 * i));
   }
   const C* src = spec + ((long long)c * nz + z) * NY * H;
-  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
     const int y = idx / H, j = idx - (idx / H) * H;
     cp_async_elem(buf + y * PX + j, src + idx);
   }
@@ -185,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
   // O_k = (X_k - conj X_(H-k)) conj(W_NX^k); X_H (Nyquist) is zero and the
   // x-constant coefficient keeps only its real part (real output)
   constexpr int NP = H / 2 + 1;
-  for (int idx = threadIdx.x; idx < NY * NP; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NY * NP; idx += TPB) {
     const int y = idx % NY, k = idx / NY;
     const int km = (H - k) % H;
     C* row = buf + y * PX;
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
   T alpha = (T)0;
   if (MODE == 3) alpha = (T)sc->alpha;
 #pragma unroll 8
-  for (int idx = threadIdx.x; idx < NY * H; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
     const int y = idx / H, j = idx - (idx / H) * H;
     const C v = buf[y * PX + j];
     if constexpr (MODE == 3) {
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-      double s = (threadIdx.x < (kThreads >> 5)) ? red[threadIdx.x] : 0.0;
+      double s = (threadIdx.x < (TPB >> 5)) ? red[threadIdx.x] : 0.0;
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (threadIdx.x == 0) partials[blockIdx.x] = s;
     }
@@ -267,24 +274,28 @@ __global__ void __launch_bounds__(kThreads) k_xyi(const typename CT<T>::t* __res
 }
 
 // ------------------------------------------------------------------ z-pass
-// Tile: S columns (consecutive (ky, kx) slots) x NZ x 9 components, component
-// pitch CP = NZ*S + 4 complex so that component planes fall in different banks.
-// Default tile: 8 columns (FP32) or 4 (FP64); the autotuner may pick others.
+// G-hat-star (Eq. eq:Gnewnew) mixes only the three components of one row i of
+// the tensor (out_ij = (sum_l A_il xi_l / abs(xi)^2) xi_j), so a block takes
+// one row group (components 3i, 3i+1, 3i+2) of S consecutive (ky, kx)
+// columns: three times the blocks and S-column DRAM segments three times
+// longer than with all nine components at the same shared memory.  Component
+// pitch CP = NZ*S + S puts the components a warp touches on distinct banks.
 template <typename T, int NZ>
-constexpr int z_default_S() { return sizeof(typename CT<T>::t) == 8 ? (NZ >= 256 ? 4 : 8) : (NZ >= 256 ? 2 : 4); }
+constexpr int z_default_S() { return 8; }
 
 template <typename T, int NZ, int S_ = z_default_S<T, NZ>()>
 struct ZShape {
   typedef typename CT<T>::t C;
   static constexpr int S = S_;
-  static constexpr int CP = NZ * S + 4;
+  static constexpr int CP = NZ * S + S;
   static constexpr size_t smem() {
-    return (size_t)9 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int);
+    return (size_t)3 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int);
   }
 };
 
 // MODE 0: operator (scale, mask).  MODE 1: residual (adds a.add at the null
 // frequency, records the null-frequency coefficient / N in a.mean_out).
+// Grid: 3 row groups x (ncol / S) column tiles.
 template <typename T, int NZ, int MODE, int S_>
 __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
   typedef ZShape<T, NZ, S_> Sh;
@@ -293,22 +304,25 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   if (a.skip && *(volatile const int*)a.skip) return;
   constexpr int S = Sh::S, CP = Sh::CP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);   // [9][CP]
-  C* twz = buf + 9 * CP;
+  C* buf = reinterpret_cast<C*>(smem_raw);   // [3][CP]
+  C* twz = buf + 3 * CP;
   int* zk = reinterpret_cast<int*>(twz + NZ);
   const C* gtwz = reinterpret_cast<const C*>(a.twz);
   for (int i = threadIdx.x; i < NZ; i += kZThreads) { twz[i] = gtwz[i]; zk[i] = a.zk[i]; }
   const int H = a.nx / 2;
   const int ncol = a.ny * H;
-  const int col0 = blockIdx.x * S;
-  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kZThreads) {
+  const int ntile = ncol / S;
+  const int g = blockIdx.x / ntile;                 // row group: components 3g .. 3g+2
+  const int col0 = (blockIdx.x - g * ntile) * S;
+  C* gsp = spec + (long long)(3 * g) * NZ * ncol;
+  for (int idx = threadIdx.x; idx < 3 * NZ * S; idx += kZThreads) {
     const int s = idx % S, cz = idx / S;
-    const int cc = cz / NZ, z = cz - (cz / NZ) * NZ;
-    cp_async_elem(buf + cc * CP + z * S + s, spec + (long long)cz * ncol + col0 + s);
+    const int cl = cz / NZ, z = cz - (cz / NZ) * NZ;
+    cp_async_elem(buf + cl * CP + z * S + s, gsp + (long long)cz * ncol + col0 + s);
   }
   cp_async_wait_all();
   __syncthreads();
-  fft2::forward<C, NZ, NZ, 9 * S, S, CP, 1, S>(buf, twz);
+  fft2::forward<C, NZ, NZ, 3 * S, S, CP, 1, S>(buf, twz);
   const T scale = (T)a.scale;
   for (int idx = threadIdx.x; idx < NZ * S; idx += kZThreads) {
     const int s = idx % S, p = idx / S;
@@ -321,17 +335,18 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
     const bool nyq = (2 * ky == a.ny) || ((NZ % 2 == 0) && (2 * kz == NZ));
     if (nyq) {
 #pragma unroll
-      for (int cc = 0; cc < 9; ++cc) e[cc * CP] = cmake((T)0, (T)0);
+      for (int cl = 0; cl < 3; ++cl) e[cl * CP] = cmake((T)0, (T)0);
     } else if (kx == 0 && ky == 0 && kz == 0) {
 #pragma unroll
-      for (int cc = 0; cc < 9; ++cc) {
-        const C X = e[cc * CP];
+      for (int cl = 0; cl < 3; ++cl) {
+        const int cc = 3 * g + cl;
+        const C X = e[cl * CP];
         if (MODE == 1 && a.mean_out) a.mean_out[cc] = (double)X.x / (double)a.N;
         if (a.mask & (1u << cc)) {
           const T add = (MODE == 1) ? (T)a.add[cc] : (T)0;
-          e[cc * CP] = cmake(scale * X.x + add, scale * X.y);
+          e[cl * CP] = cmake(scale * X.x + add, scale * X.y);
         } else {
-          e[cc * CP] = cmake((T)0, (T)0);
+          e[cl * CP] = cmake((T)0, (T)0);
         }
       }
     } else {
@@ -339,25 +354,22 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
       const int kzs = (2 * kz < NZ) ? kz : kz - NZ;
       const T xi0 = (T)kx / (T)a.nx, xi1 = (T)kys / (T)a.ny, xi2 = (T)kzs / (T)NZ;
       const T inv = scale / (xi0 * xi0 + xi1 * xi1 + xi2 * xi2);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const C A0 = e[(3 * i) * CP], A1 = e[(3 * i + 1) * CP], A2 = e[(3 * i + 2) * CP];
-        C q;
-        q.x = (A0.x * xi0 + A1.x * xi1 + A2.x * xi2) * inv;
-        q.y = (A0.y * xi0 + A1.y * xi1 + A2.y * xi2) * inv;
-        e[(3 * i) * CP] = cmake(q.x * xi0, q.y * xi0);
-        e[(3 * i + 1) * CP] = cmake(q.x * xi1, q.y * xi1);
-        e[(3 * i + 2) * CP] = cmake(q.x * xi2, q.y * xi2);
-      }
+      const C A0 = e[0], A1 = e[CP], A2 = e[2 * CP];
+      C q;
+      q.x = (A0.x * xi0 + A1.x * xi1 + A2.x * xi2) * inv;
+      q.y = (A0.y * xi0 + A1.y * xi1 + A2.y * xi2) * inv;
+      e[0] = cmake(q.x * xi0, q.y * xi0);
+      e[CP] = cmake(q.x * xi1, q.y * xi1);
+      e[2 * CP] = cmake(q.x * xi2, q.y * xi2);
     }
   }
   __syncthreads();
-  fft2::inverse<C, NZ, NZ, 9 * S, S, CP, 1, S>(buf, twz);
+  fft2::inverse<C, NZ, NZ, 3 * S, S, CP, 1, S>(buf, twz);
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < 9 * NZ * S; idx += kZThreads) {
+  for (int idx = threadIdx.x; idx < 3 * NZ * S; idx += kZThreads) {
     const int s = idx % S, cz = idx / S;
-    const int cc = cz / NZ, z = cz - (cz / NZ) * NZ;
-    spec[(long long)cz * ncol + col0 + s] = buf[cc * CP + z * S + s];
+    const int cl = cz / NZ, z = cz - (cz / NZ) * NZ;
+    gsp[(long long)cz * ncol + col0 + s] = buf[cl * CP + z * S + s];
   }
 }
 

@@ -12,7 +12,7 @@ cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_xyf<T, NX><<<9 * a.nz, kThreads, sm, st>>>(in, (C*)spec, a.nz, a.N, (const C*)a.twx, a.xpos, a.skip);
+  k_xyf<T, NX><<<9 * a.nz, xy_threads<T>(), sm, st>>>(in, (C*)spec, a.nz, a.N, (const C*)a.twx, a.xpos, a.skip);
   ++g_mf_launches;
   return cudaGetLastError();
 }
@@ -24,7 +24,7 @@ cudaError_t launch_xyi(const void* spec, typename IOT<T>::t* out, double* partia
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_xyi<T, NX, MODE><<<9 * a.nz, kThreads, sm, st>>>((const C*)spec, out, partials, a.nz, a.N,
+  k_xyi<T, NX, MODE><<<9 * a.nz, xy_threads<T>(), sm, st>>>((const C*)spec, out, partials, a.nz, a.N,
                                                      (const C*)a.twx, a.xpos, sc, a.skip);
   ++g_mf_launches;
   return cudaGetLastError();
@@ -39,19 +39,19 @@ cudaError_t launch_zp_s(void* spec, const ZArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int ncol = a.ny * (a.nx / 2);
   if (ncol % S) return cudaErrorInvalidValue;
-  k_zp<T, NZ, MODE, S><<<ncol / S, z_threads(S), sm, st>>>((C*)spec, a);
+  k_zp<T, NZ, MODE, S><<<3 * (ncol / S), z_threads(S), sm, st>>>((C*)spec, a);
   ++g_mf_launches;
   return cudaGetLastError();
 }
 
 // MODE 0 (inside the CG loop) takes the tile the autotuner chose (a.S in
-// {2, 4, 8}); the residual (MODE 1) uses the default tile.
+// {4, 8, 16}); the residual (MODE 1) uses the default tile.
 template <typename T, int NZ, int MODE>
 cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
   if constexpr (MODE == 0) {
-    if (a.S == 2) return launch_zp_s<T, NZ, MODE, 2>(spec, a, st);
     if (a.S == 4) return launch_zp_s<T, NZ, MODE, 4>(spec, a, st);
     if (a.S == 8) return launch_zp_s<T, NZ, MODE, 8>(spec, a, st);
+    if (a.S == 16) return launch_zp_s<T, NZ, MODE, 16>(spec, a, st);
   }
   return launch_zp_s<T, NZ, MODE, z_default_S<T, NZ>()>(spec, a, st);
 }

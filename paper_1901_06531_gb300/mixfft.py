@@ -20,7 +20,7 @@ MF_NONPOSITIVE_J, MF_CUDA_ERROR, MF_DEVICE_TIMEOUT, MF_NO_WORKSPACE = 4, 5, 6, 7
 MF_TOO_LARGE = 8
 MF_FP64, MF_FP32_INNER = 0, 1
 MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
-MF_RESIDUAL_DOUBLE_WORD, MF_RESIDUAL_FP64 = 0, 1
+MF_OUTER_DOUBLE_WORD, MF_OUTER_FP64 = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
@@ -43,6 +43,7 @@ _lib.mf_save_F.argtypes = [_vp, _vp]
 _lib.mf_load_F.argtypes = [_vp, _vp]
 _lib.mf_solve_batch.argtypes = [_i, _vp, _i, _vp, _vp, _d, _d, _d, _i, _i, _vp, _vp, _vp, _vp]
 _lib.mf_constitutive.argtypes = [_vp]
+_lib.mf_stress.argtypes = [_vp, _vp]
 _lib.mf_get_tangent.argtypes = [_vp, _vp]
 _lib.mf_matvec.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
@@ -57,7 +58,7 @@ _lib.mf_kernel_launches.argtypes = []
 _lib.mf_kernel_launches.restype = ctypes.c_longlong
 _lib.mf_sync.argtypes = [_vp]
 _lib.mf_autotune.argtypes = [_vp, _vp, _vp]
-_lib.mf_set_residual_arith.argtypes = [_vp, _i]
+_lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_adjoint.argtypes = [_vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp, _vp]
 _lib.mf_last_cuda_error.argtypes = []
 _lib.mf_last_cuda_error.restype = ctypes.c_char_p
@@ -67,11 +68,11 @@ _lib.mf_destroy.argtypes = [_vp]
 _lib.mf_destroy.restype = None
 
 EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_material", "mf_set_F",
-            "mf_solve", "mf_solve_batch", "mf_get_fields", "mf_save_F", "mf_load_F", "mf_constitutive", "mf_get_tangent", "mf_matvec",
-            "mf_residual", "mf_residual_noalloc", "mf_time_kernels", "mf_cufft_workspace_bytes",
-            "mf_cufft_bind", "mf_matvec_cufft", "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint", "mf_set_residual_arith", "mf_last_cuda_error",
-            "mf_status_string",
-            "mf_destroy"]
+            "mf_solve", "mf_solve_batch", "mf_get_fields", "mf_save_F", "mf_load_F", "mf_constitutive",
+            "mf_stress", "mf_get_tangent", "mf_matvec", "mf_residual", "mf_residual_noalloc",
+            "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
+            "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
+            "mf_set_outer_arith", "mf_last_cuda_error", "mf_status_string", "mf_destroy"]
 
 
 def kernel_launches():
@@ -227,6 +228,12 @@ class Context:
     def constitutive(self):
         _check("mf_constitutive", _lib.mf_constitutive(self.h))
 
+    def stress(self):
+        """mf_stress: P at the current F (no tangent); returns <P>."""
+        meanP = np.zeros(9)
+        _check("mf_stress", _lib.mf_stress(self.h, _ptr(meanP)))
+        return meanP
+
     def get_tangent(self):
         K = np.empty((45,) + self.shape)
         _check("mf_get_tangent", _lib.mf_get_tangent(self.h, _ptr(K)))
@@ -304,9 +311,9 @@ class Context:
                                              None if dscale is None else _vp(dscale.data_ptr()), _ptr(its)))
         return float(J[0]), grad[:nphase], int(its[0])
 
-    def set_residual_arith(self, arith):
-        """mf_set_residual_arith: MF_RESIDUAL_DOUBLE_WORD or MF_RESIDUAL_FP64."""
-        _check("mf_set_residual_arith", _lib.mf_set_residual_arith(self.h, arith))
+    def set_outer_arith(self, arith):
+        """mf_set_outer_arith: MF_OUTER_DOUBLE_WORD or MF_OUTER_FP64."""
+        _check("mf_set_outer_arith", _lib.mf_set_outer_arith(self.h, arith))
 
     def sync(self):
         _check("mf_sync", _lib.mf_sync(self.h))
