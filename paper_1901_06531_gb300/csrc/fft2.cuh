@@ -148,9 +148,15 @@ template <bool INV, typename C> struct Dft<16, INV, C> {
 // (SQ = 1 gives buf[q * SQSTR + j * ESTR]).  The twiddle table holds
 // W_NTAB^t, N | NTAB.  SEQFAST: consecutive threads take consecutive
 // sequences (else consecutive butterflies of one sequence).
+//
+// stage_io takes the butterfly inputs from ld(q, i, e) and hands its outputs
+// to st(q, i, e, value), where i is the shared-memory index and e the
+// position along the sequence; stage() is stage_io on shared memory.  The
+// first or last stage of a transform can so read from or write to global
+// memory directly.
 template <typename C, int N, int NTAB, int S, bool INV, int NSEQ, int SQ, int SQSTR, int SSTR,
-          int ESTR, bool SEQFAST>
-__device__ __forceinline__ void stage(C* __restrict__ buf, const C* __restrict__ tw) {
+          int ESTR, bool SEQFAST, typename LD, typename ST>
+__device__ __forceinline__ void stage_io(const C* __restrict__ tw, LD ld, ST st) {
   constexpr int R = rad(N, S);
   constexpr int L = len(N, S);
   constexpr int M = L / R;
@@ -163,9 +169,10 @@ __device__ __forceinline__ void stage(C* __restrict__ buf, const C* __restrict__
     const int blk = b / M;
     const int j0 = b - blk * M;
     const int base = (q / SQ) * SQSTR + (q % SQ) * SSTR + (blk * L + j0) * ESTR;
+    const int e0 = blk * L + j0;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = buf[base + r * M * ESTR];
+    for (int r = 0; r < R; ++r) v[r] = ld(q, base + r * M * ESTR, e0 + r * M);
     if (!INV) {
       Dft<R, false, C>::run(v);
       if (M > 1) {
@@ -180,8 +187,15 @@ __device__ __forceinline__ void stage(C* __restrict__ buf, const C* __restrict__
       Dft<R, true, C>::run(v);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[base + r * M * ESTR] = v[r];
+    for (int r = 0; r < R; ++r) st(q, base + r * M * ESTR, e0 + r * M, v[r]);
   }
+}
+
+template <typename C, int N, int NTAB, int S, bool INV, int NSEQ, int SQ, int SQSTR, int SSTR,
+          int ESTR, bool SEQFAST>
+__device__ __forceinline__ void stage(C* __restrict__ buf, const C* __restrict__ tw) {
+  stage_io<C, N, NTAB, S, INV, NSEQ, SQ, SQSTR, SSTR, ESTR, SEQFAST>(
+      tw, [&](int, int i, int) { return buf[i]; }, [&](int, int i, int, C v) { buf[i] = v; });
 }
 
 // Whole transform (all stages), with a barrier after each stage.  SEQFAST is
@@ -213,6 +227,37 @@ __device__ __forceinline__ void run_stages_inv(C* buf, const C* tw) {
 template <typename C, int N, int NTAB, int NSEQ, int SQ, int SQSTR, int SSTR, int ESTR>
 __device__ __forceinline__ void forward(C* buf, const C* tw) {
   run_stages_fwd<C, N, NTAB, false, NSEQ, SQ, SQSTR, SSTR, ESTR>(buf, tw);
+}
+
+// Forward transform whose last stage sends its outputs to st(q, e, value)
+// (sequence q, digit-reversed position e) instead of shared memory; no
+// barrier after it.
+template <typename C, int N, int NTAB, int NSEQ, int SQ, int SQSTR, int SSTR, int ESTR, int S = 0,
+          typename ST>
+__device__ __forceinline__ void forward_out(C* buf, const C* tw, ST st) {
+  constexpr int M = len(N, S) / rad(N, S);
+  constexpr bool SF = !(ESTR == 1 && M >= 16);
+  if constexpr (S + 1 < nst(N)) {
+    stage<C, N, NTAB, S, false, NSEQ, SQ, SQSTR, SSTR, ESTR, SF>(buf, tw);
+    __syncthreads();
+    forward_out<C, N, NTAB, NSEQ, SQ, SQSTR, SSTR, ESTR, S + 1>(buf, tw, st);
+  } else {
+    stage_io<C, N, NTAB, S, false, NSEQ, SQ, SQSTR, SSTR, ESTR, SF>(
+        tw, [&](int, int i, int) { return buf[i]; }, [&](int q, int, int e, C v) { st(q, e, v); });
+  }
+}
+
+// Inverse transform whose first stage reads its inputs from ld(q, e) instead
+// of shared memory; ends with a barrier like inverse().
+template <typename C, int N, int NTAB, int NSEQ, int SQ, int SQSTR, int SSTR, int ESTR, typename LD>
+__device__ __forceinline__ void inverse_in(C* buf, const C* tw, LD ld) {
+  constexpr int S = nst(N) - 1;
+  constexpr int M = len(N, S) / rad(N, S);
+  constexpr bool SF = !(ESTR == 1 && M >= 16);
+  stage_io<C, N, NTAB, S, true, NSEQ, SQ, SQSTR, SSTR, ESTR, SF>(
+      tw, [&](int q, int, int e) { return ld(q, e); }, [&](int, int i, int, C v) { buf[i] = v; });
+  __syncthreads();
+  if constexpr (S > 0) run_stages_inv<C, N, NTAB, NSEQ, SQ, SQSTR, SSTR, ESTR, S - 1>(buf, tw);
 }
 template <typename C, int N, int NTAB, int NSEQ, int SQ, int SQSTR, int SSTR, int ESTR>
 __device__ __forceinline__ void inverse(C* buf, const C* tw) {

@@ -59,7 +59,9 @@ cudaError_t mf_v2_xyi_dw(const void* spec, double* out, double* partials, const 
 
 // transform.cu
 // b = -G*(P - P-bar) (null frequency per za); dw: double-word transforms
-// (fixed-size kernels only; xa, za then point at the double-word tables)
+// (fixed-size kernels only; xa, za then point at the double-word tables).
+// The generic kernels also leave block partial sums of b.b in partials; the
+// fixed-size ones do not (nothing reads them).
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
                                const XYArgs& xa, const ZArgs& za, bool dw, cudaStream_t st);
 // which: 0 x-y forward of t, 1 z-pass, 2 x-y inverse with the CG residual update

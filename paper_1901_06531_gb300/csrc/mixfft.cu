@@ -199,7 +199,8 @@ struct mf_ctx {
   int v2 = 0;              // fixed-size transform kernels and their table layout
   cudaStream_t st;
   AxisPlan px, pyh, pz;
-  int zS;
+  int zS;                  // z-pass tile of the operator (CG loop)
+  int zSr = 8;             // z-pass tile of the residual (fixed-size kernels)
   // workspace
   char* ws = nullptr;
   size_t ws_need = 0;
@@ -334,6 +335,7 @@ bool operator_ready(const mf_ctx* c) { return c->f32() ? c->have_H : c->have_K; 
 int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out) {
   const bool dw = c->dw_residual();
   ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N, dw);
+  if (c->v2) za.S = c->zSr;
   for (int k = 0; k < 9; ++k) za.add[k] = mask[k] ? pbar[k] : 0.0;
   za.mean_out = mean_out;
   return cuda_status(mf_launch_residual(c->at<double>(c->oP), c->ws + c->ospec, b,
@@ -463,17 +465,19 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
 // candidate is timed with CUDA events on the context's stream (L2 flushed
 // before every launch, one untimed launch first) and the fastest kept; the
 // choice is cached for the process per (nx, ny, nz, precision).
-struct TuneEntry { int nx, ny, nz, prec, S; float ms[3]; };
+struct TuneEntry { int nx, ny, nz, prec, dw, S, Sr; float ms[3], msr[2]; };
 std::vector<TuneEntry> g_tune_cache;
 std::mutex g_tune_mutex;
 
 int autotune(mf_ctx* c, int reps) {
   if (!c->v2) { c->tuned = true; return MF_OK; }
+  const int dwr = c->dw_residual() ? 1 : 0;
   {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     for (const TuneEntry& t : g_tune_cache)
-      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec) {
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec && t.dw == dwr) {
         c->zS = t.S;
+        c->zSr = t.Sr;
         c->tuned = true;
         return MF_OK;
       }
@@ -486,7 +490,7 @@ int autotune(mf_ctx* c, int reps) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
-  TuneEntry te{c->nx, c->ny, c->nz, c->prec, c->zS, {0, 0, 0}};
+  TuneEntry te{c->nx, c->ny, c->nz, c->prec, dwr, c->zS, c->zSr, {0, 0, 0}, {0, 0}};
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
@@ -507,10 +511,31 @@ int autotune(mf_ctx* c, int reps) {
     te.ms[i] = (float)(tot / reps);
     if (e == cudaSuccess && te.ms[i] < best) { best = te.ms[i]; te.S = cands[i]; }
   }
+  // the residual's z-pass (FP64 or double word), tiles 4 and 8
+  ZArgs zr = z_args(c, false, mask, -1.0 / (double)c->N, dwr != 0);
+  const int rcands[2] = {4, 8};
+  float bestr = 1e30f;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    zr.S = rcands[i];
+    double tot = 0.0;
+    for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+      e = cudaMemsetAsync(c->ws + c->ob, 0, 9 * c->N * sizeof(double), c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+      if (e == cudaSuccess) e = dwr ? mf_v2_zp_dw(c->ws + c->ospec, zr, c->st) : mf_v2_zp_f64(1, c->ws + c->ospec, zr, c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (r >= 0) tot += ms;
+    }
+    te.msr[i] = (float)(tot / reps);
+    if (e == cudaSuccess && te.msr[i] < bestr) { bestr = te.msr[i]; te.Sr = rcands[i]; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_status(e); }
   c->zS = te.S;
+  c->zSr = te.Sr;
   c->tuned = true;
   free_cg_graph(c);   // a captured loop holds the old tile
   std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -1314,6 +1339,7 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
 
 int mf_set_outer_arith(mf_ctx* c, int arith) {
   if (!c || (arith != MF_OUTER_DOUBLE_WORD && arith != MF_OUTER_FP64)) return MF_INVALID_ARG;
+  if (c->outer_arith != arith) c->tuned = false;   // the residual tile is tuned per arithmetic
   c->outer_arith = arith;
   return MF_OK;
 }
@@ -1335,7 +1361,8 @@ int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     for (size_t i = 0; i < g_tune_cache.size(); ++i) {
       const TuneEntry& t = g_tune_cache[i];
-      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec) {
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec &&
+          t.dw == (c->dw_residual() ? 1 : 0)) {
         g_tune_cache.erase(g_tune_cache.begin() + i);
         break;
       }
@@ -1347,7 +1374,8 @@ int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out) {
   if (ms_out) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     for (const TuneEntry& t : g_tune_cache)
-      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec)
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec &&
+          t.dw == (c->dw_residual() ? 1 : 0))
         for (int i = 0; i < 3; ++i) ms_out[i] = t.ms[i];
   }
   return MF_OK;

@@ -330,7 +330,7 @@ cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* p
   if (xa.v2) {
     cudaError_t e = mf_v2_xyf_f64(P, spec, xa, st);
     if (e == cudaSuccess) e = mf_v2_zp_f64(1, spec, za, st);
-    if (e == cudaSuccess) e = mf_v2_xyi_f64(2, spec, b, partials, xa, nullptr, st);
+    if (e == cudaSuccess) e = mf_v2_xyi_f64(0, spec, b, partials, xa, nullptr, st);
     return e;
   }
   cudaError_t e = launch_xy_forward<double, 1>(P, nullptr, spec, xa, st);

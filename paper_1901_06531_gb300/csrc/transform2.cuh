@@ -136,14 +136,10 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
     row[pa] = xa;
   }
   __syncthreads();
-  // y: H columns of NY samples, stride PX
-  fft2::forward<C, NY, NY, H, 1, 1, 0, PX>(buf, twy);
+  // y: H columns of NY samples, stride PX; the last stage stores the
+  // spectrum rows (consecutive threads take consecutive columns)
   C* dst = spec + ((long long)c * nz + z) * NY * H;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
-    const int y = idx / H, j = idx - (idx / H) * H;
-    dst[idx] = buf[y * PX + j];
-  }
+  fft2::forward_out<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e, C v) { dst[e * H + q] = v; });
 }
 
 // ------------------------------------------------------------------ inverse
@@ -180,13 +176,9 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
       asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + 128 * i));
   }
   const C* src = spec + ((long long)c * nz + z) * NY * H;
-  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
-    const int y = idx / H, j = idx - (idx / H) * H;
-    cp_async_elem(buf + y * PX + j, src + idx);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  fft2::inverse<C, NY, NY, H, 1, 1, 0, PX>(buf, twy);
+  __syncthreads();   // tables
+  // y: the first inverse stage reads the spectrum rows from global memory
+  fft2::inverse_in<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e) { return src[e * H + q]; });
   // merge each row's spectrum into H complex samples (the adjoint of the
   // split, times 2): Z_k = E_k + i O_k with E_k = X_k + conj X_(H-k),
   // O_k = (X_k - conj X_(H-k)) conj(W_NX^k); X_H (Nyquist) is zero and the
@@ -277,9 +269,14 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
 // G-hat-star (Eq. eq:Gnewnew) mixes only the three components of one row i of
 // the tensor (out_ij = (sum_l A_il xi_l / abs(xi)^2) xi_j), so a block takes
 // one row group (components 3i, 3i+1, 3i+2) of S consecutive (ky, kx)
-// columns: three times the blocks and S-column DRAM segments three times
-// longer than with all nine components at the same shared memory.  Component
-// pitch CP = NZ*S + S puts the components a warp touches on distinct banks.
+// columns.  The transform along z passes through shared memory only between
+// stages: the first forward stage reads the spectrum from global memory, the
+// last forward stage, G-hat-star and the first inverse stage run together in
+// registers (a thread holds the three components of R positions of one
+// column; the last DIF stage and the first DIT stage have no twiddles), and
+// the last inverse stage writes global memory.  Element (component cl,
+// position z, column s) lives at cl*CP + z*ZS + s; the paddings of ZS and CP
+// were chosen with a wavefront model of these access patterns.
 template <typename T, int NZ>
 constexpr int z_default_S() { return 8; }
 
@@ -287,7 +284,9 @@ template <typename T, int NZ, int S_ = z_default_S<T, NZ>()>
 struct ZShape {
   typedef typename CT<T>::t C;
   static constexpr int S = S_;
-  static constexpr int CP = NZ * S + S;
+  static constexpr bool E8 = sizeof(C) == 8;
+  static constexpr int ZS = S + ((E8 && S < 16) ? 1 : 0);
+  static constexpr int CP = NZ * ZS + (E8 ? (S == 8 ? 1 : 0) : (S == 4 ? 4 : 0));
   static constexpr size_t smem() {
     return (size_t)3 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int);
   }
@@ -302,7 +301,9 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   constexpr int kZThreads = z_threads(S_);
   typedef typename CT<T>::t C;
   if (a.skip && *(volatile const int*)a.skip) return;
-  constexpr int S = Sh::S, CP = Sh::CP;
+  constexpr int S = Sh::S, CP = Sh::CP, ZS = Sh::ZS;
+  constexpr int NST = fft2::nst(NZ);
+  constexpr int RL = fft2::rad(NZ, NST - 1);   // radix of the last DIF stage (its M is 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);   // [3][CP]
   C* twz = buf + 3 * CP;
@@ -314,39 +315,43 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   const int ntile = ncol / S;
   const int g = blockIdx.x / ntile;                 // row group: components 3g .. 3g+2
   const int col0 = (blockIdx.x - g * ntile) * S;
-  C* gsp = spec + (long long)(3 * g) * NZ * ncol;
-  for (int idx = threadIdx.x; idx < 3 * NZ * S; idx += kZThreads) {
-    const int s = idx % S, cz = idx / S;
-    const int cl = cz / NZ, z = cz - (cz / NZ) * NZ;
-    cp_async_elem(buf + cl * CP + z * S + s, gsp + (long long)cz * ncol + col0 + s);
-  }
-  cp_async_wait_all();
+  C* gsp = spec + (long long)(3 * g) * NZ * ncol + col0;
+  // global element of (sequence q = cl*S + s, position z)
+  auto gidx = [&](int q, int z) { return ((long long)(q / S) * NZ + z) * ncol + (q % S); };
   __syncthreads();
-  fft2::forward<C, NZ, NZ, 3 * S, S, CP, 1, S>(buf, twz);
+  if constexpr (NST > 1) {
+    // first forward stage: global -> registers -> shared
+    fft2::stage_io<C, NZ, NZ, 0, false, 3 * S, S, CP, 1, ZS, true>(
+        twz, [&](int q, int, int z) { return gsp[gidx(q, z)]; }, [&](int, int i, int, C v) { buf[i] = v; });
+    __syncthreads();
+    if constexpr (NST > 2) {
+      fft2::stage<C, NZ, NZ, 1, false, 3 * S, S, CP, 1, ZS, true>(buf, twz);
+      __syncthreads();
+    }
+  }
   const T scale = (T)a.scale;
-  for (int idx = threadIdx.x; idx < NZ * S; idx += kZThreads) {
-    const int s = idx % S, p = idx / S;
+  // G-hat-star on the three components (v0, v1, v2) at column s, position z
+  auto gstar = [&](int s, int z, C& v0, C& v1, C& v2) {
     const int col = col0 + s;
     const int row = col / H, slot = col - (col / H) * H;
     const int kx = a.xk[slot];
     const int ky = a.yk[row];
-    const int kz = zk[p];
-    C* e = buf + p * S + s;
-    const bool nyq = (2 * ky == a.ny) || ((NZ % 2 == 0) && (2 * kz == NZ));
-    if (nyq) {
+    const int kz = zk[z];
+    C* v[3] = {&v0, &v1, &v2};
+    if ((2 * ky == a.ny) || ((NZ % 2 == 0) && (2 * kz == NZ))) {
 #pragma unroll
-      for (int cl = 0; cl < 3; ++cl) e[cl * CP] = cmake((T)0, (T)0);
+      for (int cl = 0; cl < 3; ++cl) *v[cl] = cmake((T)0, (T)0);
     } else if (kx == 0 && ky == 0 && kz == 0) {
 #pragma unroll
       for (int cl = 0; cl < 3; ++cl) {
         const int cc = 3 * g + cl;
-        const C X = e[cl * CP];
+        const C X = *v[cl];
         if (MODE == 1 && a.mean_out) a.mean_out[cc] = (double)X.x / (double)a.N;
         if (a.mask & (1u << cc)) {
           const T add = (MODE == 1) ? (T)a.add[cc] : (T)0;
-          e[cl * CP] = cmake(scale * X.x + add, scale * X.y);
+          *v[cl] = cmake(scale * X.x + add, scale * X.y);
         } else {
-          e[cl * CP] = cmake((T)0, (T)0);
+          *v[cl] = cmake((T)0, (T)0);
         }
       }
     } else {
@@ -354,22 +359,80 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
       const int kzs = (2 * kz < NZ) ? kz : kz - NZ;
       const T xi0 = (T)kx / (T)a.nx, xi1 = (T)kys / (T)a.ny, xi2 = (T)kzs / (T)NZ;
       const T inv = scale / (xi0 * xi0 + xi1 * xi1 + xi2 * xi2);
-      const C A0 = e[0], A1 = e[CP], A2 = e[2 * CP];
       C q;
-      q.x = (A0.x * xi0 + A1.x * xi1 + A2.x * xi2) * inv;
-      q.y = (A0.y * xi0 + A1.y * xi1 + A2.y * xi2) * inv;
-      e[0] = cmake(q.x * xi0, q.y * xi0);
-      e[CP] = cmake(q.x * xi1, q.y * xi1);
-      e[2 * CP] = cmake(q.x * xi2, q.y * xi2);
+      q.x = (v0.x * xi0 + v1.x * xi1 + v2.x * xi2) * inv;
+      q.y = (v0.y * xi0 + v1.y * xi1 + v2.y * xi2) * inv;
+      v0 = cmake(q.x * xi0, q.y * xi0);
+      v1 = cmake(q.x * xi1, q.y * xi1);
+      v2 = cmake(q.x * xi2, q.y * xi2);
+    }
+  };
+  if constexpr (sizeof(C) == 8) {
+    // FP32: last forward stage, G-hat-star and first inverse stage in
+    // registers (three components of RL positions of one column per thread)
+    constexpr int NB = NZ / RL;
+    for (int t = threadIdx.x; t < S * NB; t += kZThreads) {
+      const int s = t % S, blk = t / S;
+      C v[3][RL];
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int z = blk * RL + r;
+          v[cl][r] = (NST > 1) ? buf[cl * CP + z * ZS + s] : gsp[gidx(cl * S + s, z)];
+        }
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl) fft2::Dft<RL, false, C>::run(v[cl]);
+#pragma unroll
+      for (int r = 0; r < RL; ++r) gstar(s, blk * RL + r, v[0][r], v[1][r], v[2][r]);
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl) fft2::Dft<RL, true, C>::run(v[cl]);
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int z = blk * RL + r;
+          if (NST > 1) buf[cl * CP + z * ZS + s] = v[cl][r];
+          else gsp[gidx(cl * S + s, z)] = v[cl][r];
+        }
+    }
+  } else {
+    // 16-byte types (FP64, double word): registers are scarcer, so the last
+    // forward stage, G-hat-star and the first inverse stage are separate
+    // passes over shared memory
+    if constexpr (NST == 1) {
+      for (int idx = threadIdx.x; idx < 3 * NZ * S; idx += kZThreads) {
+        const int s2 = idx % S, cz = idx / S, cl = cz / NZ, z = cz - cl * NZ;
+        buf[cl * CP + z * ZS + s2] = gsp[gidx(cl * S + s2, z)];
+      }
+      __syncthreads();
+    }
+    fft2::stage<C, NZ, NZ, NST - 1, false, 3 * S, S, CP, 1, ZS, true>(buf, twz);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NZ * S; idx += kZThreads) {
+      const int s2 = idx % S, z = idx / S;
+      C* e = buf + z * ZS + s2;
+      gstar(s2, z, e[0], e[CP], e[2 * CP]);
+    }
+    __syncthreads();
+    fft2::stage<C, NZ, NZ, NST - 1, true, 3 * S, S, CP, 1, ZS, true>(buf, twz);
+    if constexpr (NST == 1) {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 3 * NZ * S; idx += kZThreads) {
+        const int s2 = idx % S, cz = idx / S, cl = cz / NZ, z = cz - cl * NZ;
+        gsp[gidx(cl * S + s2, z)] = buf[cl * CP + z * ZS + s2];
+      }
     }
   }
-  __syncthreads();
-  fft2::inverse<C, NZ, NZ, 3 * S, S, CP, 1, S>(buf, twz);
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < 3 * NZ * S; idx += kZThreads) {
-    const int s = idx % S, cz = idx / S;
-    const int cl = cz / NZ, z = cz - (cz / NZ) * NZ;
-    gsp[(long long)cz * ncol + col0 + s] = buf[cl * CP + z * S + s];
+  if constexpr (NST > 1) {
+    __syncthreads();
+    if constexpr (NST > 2) {
+      fft2::stage<C, NZ, NZ, 1, true, 3 * S, S, CP, 1, ZS, true>(buf, twz);
+      __syncthreads();
+    }
+    // last inverse stage: shared -> registers -> global
+    fft2::stage_io<C, NZ, NZ, 0, true, 3 * S, S, CP, 1, ZS, true>(
+        twz, [&](int, int i, int) { return buf[i]; }, [&](int q, int, int z, C v) { gsp[gidx(q, z)] = v; });
   }
 }
 

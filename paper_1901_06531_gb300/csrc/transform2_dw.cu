@@ -10,5 +10,5 @@ cudaError_t mf_v2_zp_dw(void* spec, const ZArgs& a, cudaStream_t st) {
   return tr2::zp_m<dw, 1>(spec, a, st);
 }
 cudaError_t mf_v2_xyi_dw(const void* spec, double* out, double* partials, const XYArgs& a, cudaStream_t st) {
-  return tr2::xyi_m<dw, 2>(spec, out, partials, a, nullptr, st);
+  return tr2::xyi_m<dw, 0>(spec, out, partials, a, nullptr, st);
 }

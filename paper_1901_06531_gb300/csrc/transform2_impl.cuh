@@ -44,16 +44,15 @@ cudaError_t launch_zp_s(void* spec, const ZArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// MODE 0 (inside the CG loop) takes the tile the autotuner chose (a.S in
-// {4, 8, 16}); the residual (MODE 1) uses the default tile.
+// The tile the autotuner chose: a.S in {4, 8, 16} for the operator (MODE 0,
+// inside the CG loop), {4, 8} for the residual (MODE 1); else the default.
 template <typename T, int NZ, int MODE>
 cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
+  if (a.S == 4) return launch_zp_s<T, NZ, MODE, 4>(spec, a, st);
   if constexpr (MODE == 0) {
-    if (a.S == 4) return launch_zp_s<T, NZ, MODE, 4>(spec, a, st);
-    if (a.S == 8) return launch_zp_s<T, NZ, MODE, 8>(spec, a, st);
     if (a.S == 16) return launch_zp_s<T, NZ, MODE, 16>(spec, a, st);
   }
-  return launch_zp_s<T, NZ, MODE, z_default_S<T, NZ>()>(spec, a, st);
+  return launch_zp_s<T, NZ, MODE, 8>(spec, a, st);
 }
 
 template <typename T>

@@ -25,6 +25,7 @@ __all__ = [
     "random_rotations", "lognormal_scale", "random_F", "random_field",
     "history_uniaxial_stress_ramp", "history_mixed_strain11",
     "history_cyclic_stress", "laminate_phase", "fix_rotation", "random_control", "batch_of_cells",
+    "particle_rve", "history_case1", "history_case2", "history_case3", "history_case4",
 ]
 
 
@@ -277,3 +278,67 @@ def batch_of_cells(count, seed, sizes=(32, 48, 64, 96), nsteps=4):
         cells.append({"n": n, "phase": phase, "params": params, "mask": mask, "target": target,
                       "vf": vf, "contrast": contrast})
     return cells
+
+
+# ----------------------------------------------------------------------------
+# The load cases of the paper's Sec. 3 (control cases (1)-(4)) and its
+# particle-reinforced cell.
+
+def particle_rve(n, seed, count=4, vf=0.2):
+    """Stand-in for the paper's particle-reinforced cell (Sec. 3.1): `count`
+    non-overlapping periodic spheres of equal radius whose volumes add up to
+    the fraction `vf` of an n^3 cell (radius n (3 vf / (4 pi count))^(1/3)),
+    placed by random sequential addition.  Returns the phase map (1 inside
+    the particles)."""
+    r = n * (3.0 * vf / (4.0 * np.pi * count)) ** (1.0 / 3.0)
+    rng = np.random.default_rng(seed)
+    lengths = np.array([n, n, n], dtype=np.float64)
+    centres = []
+    attempts = 0
+    while len(centres) < count:
+        attempts += 1
+        if attempts > 100000:
+            raise RuntimeError("particle_rve: could not place the particles")
+        c = rng.random(3) * lengths
+        if centres:
+            d = np.abs(np.asarray(centres) - c)
+            d = np.minimum(d, lengths - d)
+            if np.min(np.sum(d * d, axis=1)) < (2.0 * r) ** 2:
+                continue
+        centres.append(c)
+    return periodic_sphere_phase((n, n, n), [tuple(c) for c in centres], r)
+
+
+def history_case1(nsteps, lambda_end):
+    """Case (1), a uniaxial stress test in mixed control: F11 ramps to
+    1 + lambda_end (lambda_end read as an engineering strain), F12 = F13 =
+    F23 = 0 are prescribed, P21, P22, P31, P32, P33 are zero."""
+    return fix_rotation(*history_mixed_strain11(nsteps, 1.0 + lambda_end))
+
+
+def history_case2(P_end, nsteps):
+    """Case (2), full stress control: P-bar = P_end t / t_end (P_end: 9
+    values, the final stress of case (1))."""
+    t = np.arange(1, nsteps + 1)[:, None] / nsteps
+    return np.ones((nsteps, 9), dtype=np.uint8), np.asarray(P_end, dtype=np.float64)[None, :] * t
+
+
+def history_case3(F_end, nsteps):
+    """Case (3), full strain control to the final F-bar of case (1), read as
+    F-bar = I + (F_end - I) t / t_end (the printed F_end t / t_end would start
+    from F = 0)."""
+    eye = np.array([1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0])
+    t = np.arange(1, nsteps + 1)[:, None] / nsteps
+    return (np.zeros((nsteps, 9), dtype=np.uint8),
+            eye[None, :] + (np.asarray(F_end, dtype=np.float64) - eye)[None, :] * t)
+
+
+def history_case4(nsteps, lambda_end):
+    """Case (4), the pseudo-uniaxial test of Sec. 3.2: full strain control
+    F-bar = I + t/t_end diag(lambda_end, s, s), s = sqrt(1/(1 + lambda_end)) - 1
+    (isochoric at the end in the transverse directions)."""
+    s = np.sqrt(1.0 / (1.0 + lambda_end)) - 1.0
+    d = np.array([lambda_end, 0, 0, 0, s, 0, 0, 0, s])
+    eye = np.array([1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0])
+    t = np.arange(1, nsteps + 1)[:, None] / nsteps
+    return np.zeros((nsteps, 9), dtype=np.uint8), eye[None, :] + d[None, :] * t

@@ -1,0 +1,89 @@
+"""The paper's load cases (Sec. 3) as a GPU regression suite: case (1)
+mixed control (uniaxial stress test), case (2) full stress control to the
+final stress of (1), case (3) full strain control to the final F-bar of (1)
+on the particle-reinforced stand-in (St Venant-Kirchhoff, matrix mu = 28,
+k = 140/3, particles ten times stiffer), and case (4), the pseudo-uniaxial
+strain-controlled test of Sec. 3.2, on a polycrystal stand-in."""
+import numpy as np
+import pytest
+
+from oracle import materials as omat, solver as osolver
+from paper_1901_06531_gb300 import inputs
+
+from gpu_util import lib, rel
+
+pytestmark = pytest.mark.gpu
+
+# isotropic SVK as cubic constants: C11 = k + 4 mu/3, C12 = k - 2 mu/3, C44 = mu
+MAT = np.array([[84.0, 28.0, 28.0], [840.0, 280.0, 280.0]])
+ROT2 = np.tile(np.eye(3), (2, 1, 1))
+TIGHT = dict(tol_newton=1e-10, tol_cg=1e-12, max_cg=20000)
+
+
+def particle_ctx(mf, n, prec):
+    ph = inputs.particle_rve(n, 1001)
+    ctx = mf.Context(n, n, n, prec)
+    ctx.set_material(mf.MF_SVK_CUBIC, MAT, ph, rot=ROT2)
+    return ctx, ph
+
+
+def invariants(F, P):
+    Fm = F.reshape((3, 3) + F.shape[1:])
+    Pm = P.reshape((3, 3) + P.shape[1:])
+    return (np.einsum("ki...,kj...->ij...", Fm, Fm), np.einsum("ki...,kj...->ij...", Fm, Pm))
+
+
+def test_case1_matches_oracle():
+    """Case (1) at 16^3, lambda_end = 0.1 in 4 steps, FP64: fields to 1e-10,
+    Newton counts equal, CG totals within 2 per Newton iteration."""
+    mf = lib()
+    ctx, ph = particle_ctx(mf, 16, mf.MF_FP64)
+    mask, target = inputs.history_case1(4, 0.1)
+    out = ctx.solve(mask, target, **TIGHT)
+    om = omat.Material(ph, omat.SVK_CUBIC, MAT, ROT2)
+    ref = osolver.solve(om, mask, target, tol_newton=1e-10, tol_cg=1e-12)
+    F, P = ctx.get_fields()
+    assert rel(F, ref["F"]) < 1e-10
+    assert rel(P, ref["P"]) < 1e-10
+    np.testing.assert_array_equal(out["newton"], ref["newton"])
+    assert np.all(np.abs(out["cg"] - ref["cg"]) <= 2 * out["newton"])
+
+
+def test_cases_1_2_3_share_the_endpoint():
+    """32^3, lambda_end = 0.2 in 8 steps, FP64 at tight tolerances: the three
+    control cases end at the same state (hyperelastic path independence,
+    Sec. 3.1); compared through F^T F and F^T P, which a rigid rotation left
+    free by full stress control does not change."""
+    mf = lib()
+    ctx, _ = particle_ctx(mf, 32, mf.MF_FP64)
+    m1, t1 = inputs.history_case1(8, 0.2)
+    o1 = ctx.solve(m1, t1, **TIGHT)
+    C1, S1 = invariants(*ctx.get_fields())
+    P_end, F_end = o1["Pbar"][-1], o1["Fbar"][-1]
+    for m, t in (inputs.history_case2(P_end, 8), inputs.history_case3(F_end, 8)):
+        ctx.set_F(None)
+        ctx.solve(m, t, **TIGHT)
+        C, S = invariants(*ctx.get_fields())
+        assert rel(C, C1) < 1e-8
+        assert rel(S, S1) < 1e-8
+
+
+def test_case4_pseudo_uniaxial():
+    """Case (4) on a 20-grain cubic SVK polycrystal (168/121/75), lambda_end =
+    0.02 in 2 steps, FP32 inner: F-bar exactly as prescribed at every step,
+    <P> within 1e-9 of the FP64 oracle at 16^3, and the transverse stresses
+    compressive at the end (the paper's Sec. 3.2 observation on case (4))."""
+    mf = lib()
+    n = 16
+    g, _ = inputs.voronoi((n, n, n), 20, 7)
+    R = inputs.random_rotations(20, 8)
+    params = np.tile([168.0, 121.0, 75.0], (20, 1))
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    mask, target = inputs.history_case4(2, 0.02)
+    out = ctx.solve(mask, target, tol_newton=1e-10, tol_cg=1e-12, cg_rel=1e-4, max_cg=20000)
+    assert np.max(np.abs(out["Fbar"] - target)) < 1e-14
+    ref = osolver.solve(omat.Material(g, omat.SVK_CUBIC, params, R), mask, target, tol_newton=1e-10,
+                        tol_cg=1e-12)
+    assert rel(out["Pbar"], ref["Pbar"]) < 1e-9
+    assert out["Pbar"][-1][4] < 0 and out["Pbar"][-1][8] < 0
