@@ -374,11 +374,22 @@ def run_paper_cases(args):
         torch.cuda.synchronize()
         return o, a.elapsed_time(b)
 
-    def summary(o, ms, ref_ms=None):
+    def run_case(ctx, m, t):
+        try:
+            o, ms = timed(ctx, m, t)
+            return {"o": o, "ms": ms}
+        except mf.MixFFTError as e:
+            return {"error": str(e)}
+
+    def summary(r, ref):
+        if "error" in r:
+            return {"status": r["error"]}
+        o, ms = r["o"], r["ms"]
         d = {"ms": ms, "newton_total": int(o["newton"].sum()), "cg_total": int(o["cg"].sum()),
              "cg_per_step": o["cg"].tolist(), "newton_per_step": o["newton"].tolist()}
-        if ref_ms:
-            d["time_vs_case3"] = ms / ref_ms
+        if "o" in ref:
+            d["time_vs_case3"] = ms / ref["ms"]
+            d["cg_vs_case3"] = o["cg"].sum() / ref["o"]["cg"].sum()
         return d
 
     res = {}
@@ -389,15 +400,16 @@ def run_paper_cases(args):
     ctx.set_material(mf.MF_SVK_CUBIC, mat, ph, rot=np.tile(np.eye(3), (2, 1, 1)))
     m1, t1 = inputs.history_case1(100, 0.2)
     timed(ctx, m1[:2], t1[:2])   # warm-up (tuner, graph capture)
-    o1, ms1 = timed(ctx, m1, t1)
-    o2, ms2 = timed(ctx, *inputs.history_case2(o1["Pbar"][-1], 100))
-    o3, ms3 = timed(ctx, *inputs.history_case3(o1["Fbar"][-1], 100))
-    res["particle"] = {
-        "workload": f"{n}^3 four-particle cell (seed {CASES_SEED}, vf 0.2), SVK matrix 84/28/28, particles x10, "
-                    "lambda_end 0.2 in 100 increments",
-        "case1": summary(o1, ms1, ms3), "case2": summary(o2, ms2, ms3), "case3": summary(o3, ms3, ms3),
-        "cg_ratio_case1_vs_case3": o1["cg"].sum() / o3["cg"].sum(),
-        "cg_ratio_case2_vs_case3": o2["cg"].sum() / o3["cg"].sum()}
+    r1 = run_case(ctx, m1, t1)
+    part = {"workload": f"{n}^3 four-particle cell (seed {CASES_SEED}, vf 0.2), SVK matrix 84/28/28, "
+                        "particles x10, lambda_end 0.2 in 100 increments"}
+    if "o" in r1:
+        r2 = run_case(ctx, *inputs.history_case2(r1["o"]["Pbar"][-1], 100))
+        r3 = run_case(ctx, *inputs.history_case3(r1["o"]["Fbar"][-1], 100))
+        part.update({"case1": summary(r1, r3), "case2": summary(r2, r3), "case3": summary(r3, r3)})
+    else:
+        part["case1"] = summary(r1, {})
+    res["particle"] = part
     del ctx
     # polycrystal, cases (1)-(4)
     g, _ = inputs.voronoi((n, n, n), 200, CASES_SEED + 1)
@@ -406,19 +418,21 @@ def run_paper_cases(args):
     ctx.set_material(mf.MF_SVK_CUBIC, np.tile([168.0, 121.0, 75.0], (200, 1)), g, rot=R)
     m1, t1 = inputs.history_case1(20, 0.02)
     timed(ctx, m1[:2], t1[:2])
-    o1, ms1 = timed(ctx, m1, t1)
-    o2, ms2 = timed(ctx, *inputs.history_case2(o1["Pbar"][-1], 20))
-    o3, ms3 = timed(ctx, *inputs.history_case3(o1["Fbar"][-1], 20))
-    o4, ms4 = timed(ctx, *inputs.history_case4(20, 0.02))
-    res["polycrystal"] = {
-        "workload": f"{n}^3 200-grain Voronoi (seed {CASES_SEED + 1}), SVK cubic 168/121/75 GPa, "
-                    "lambda_end 0.02 in 20 increments",
-        "case1": summary(o1, ms1, ms3), "case2": summary(o2, ms2, ms3), "case3": summary(o3, ms3, ms3),
-        "case4": summary(o4, ms4, ms3),
-        "case4_final_Pbar_diag": [float(o4["Pbar"][-1][i]) for i in (0, 4, 8)],
-        "case1_final_Pbar_diag": [float(o1["Pbar"][-1][i]) for i in (0, 4, 8)],
-        "cg_ratio_case1_vs_case3": o1["cg"].sum() / o3["cg"].sum(),
-        "cg_ratio_case2_vs_case3": o2["cg"].sum() / o3["cg"].sum()}
+    r1 = run_case(ctx, m1, t1)
+    poly = {"workload": f"{n}^3 200-grain Voronoi (seed {CASES_SEED + 1}), SVK cubic 168/121/75 GPa, "
+                        "lambda_end 0.02 in 20 increments"}
+    r4 = run_case(ctx, *inputs.history_case4(20, 0.02))
+    if "o" in r1:
+        r2 = run_case(ctx, *inputs.history_case2(r1["o"]["Pbar"][-1], 20))
+        r3 = run_case(ctx, *inputs.history_case3(r1["o"]["Fbar"][-1], 20))
+        poly.update({"case1": summary(r1, r3), "case2": summary(r2, r3), "case3": summary(r3, r3),
+                     "case4": summary(r4, r3),
+                     "case1_final_Pbar_diag": [float(r1["o"]["Pbar"][-1][i]) for i in (0, 4, 8)]})
+    else:
+        poly.update({"case1": summary(r1, {}), "case4": summary(r4, {})})
+    if "o" in r4:
+        poly["case4_final_Pbar_diag"] = [float(r4["o"]["Pbar"][-1][i]) for i in (0, 4, 8)]
+    res["polycrystal"] = poly
     del ctx
     # C2: 64^3 random spheres, F11 ramp with eight stress-free components
     phs, _ = inputs.rsa_spheres((n, n, n), 4.0, 0.25, 1002)
@@ -429,23 +443,28 @@ def run_paper_cases(args):
     for name, prec in (("fp32_inner", mf.MF_FP32_INNER), ("fp64", mf.MF_FP64)):
         ctx = mf.Context(n, n, n, prec)
         ctx.set_material(mf.MF_NEOHOOKE, params, phs)
-        timed(ctx, mask[:1], target[:1])
-        per = []
-        ctx.set_F(None)
-        its = []
-        for k in range(mask.shape[0]):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            o = ctx.solve(mask[k:k + 1], target[k:k + 1], TOL_NEWTON, TOL_CG, CG_REL)
-            b.record(stream)
-            torch.cuda.synchronize()
-            per.append(a.elapsed_time(b))
-            its.append([int(o["newton"][0]), int(o["cg"][0])])
-        c2[name] = {"load_step_ms_median": float(np.median(per)), "newton_cg_per_step": its,
-                    "final_Pbar11": float(o["Pbar"][-1][0])}
+        try:
+            timed(ctx, mask[:1], target[:1])
+            per = []
+            ctx.set_F(None)
+            its = []
+            for k in range(mask.shape[0]):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                o = ctx.solve(mask[k:k + 1], target[k:k + 1], TOL_NEWTON, TOL_CG, CG_REL)
+                b.record(stream)
+                torch.cuda.synchronize()
+                per.append(a.elapsed_time(b))
+                its.append([int(o["newton"][0]), int(o["cg"][0])])
+            c2[name] = {"load_step_ms_median": float(np.median(per)), "newton_cg_per_step": its,
+                        "final_Pbar11": float(o["Pbar"][-1][0])}
+        except mf.MixFFTError as e:
+            c2[name] = {"status": str(e)}
         del ctx
-    c2["fp64_over_fp32_inner"] = c2["fp64"]["load_step_ms_median"] / c2["fp32_inner"]["load_step_ms_median"]
+    if "load_step_ms_median" in c2["fp64"] and "load_step_ms_median" in c2["fp32_inner"]:
+        c2["fp64_over_fp32_inner"] = (c2["fp64"]["load_step_ms_median"] /
+                                      c2["fp32_inner"]["load_step_ms_median"])
     res["c2"] = c2
     torch.cuda.empty_cache()
     return res

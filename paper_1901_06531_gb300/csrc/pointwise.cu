@@ -4,6 +4,9 @@
 // update with its max |dF| test (Sec. 4).  Every reduction writes one
 // partial per block and is finished by a single block in a fixed order, so
 // results are bitwise reproducible run to run.
+#include <string.h>
+
+#include "dw.cuh"
 #include "launch.h"
 
 namespace {
@@ -237,17 +240,18 @@ __global__ void __launch_bounds__(kRedThreads) k_constitutive(const double* __re
   if (threadIdx.x < NC) partials[blockIdx.x * NC + threadIdx.x] = tot[threadIdx.x];
 }
 
+// One block per column (grid ncol): the column sums of the block partials in
+// a fixed order.
 __global__ void __launch_bounds__(kRedThreads) k_fin_means(const double* __restrict__ partials, int nblk,
                                                            int ncol, long long N, Scalars* sc) {
   __shared__ double shm[kRedThreads];
-  for (int col = 0; col < ncol; ++col) {
-    const double s = column_sum(partials, nblk, ncol, col, shm);
-    if (threadIdx.x == 0) {
-      if (col < 9) sc->meanF[col] = s / (double)N;
-      else if (col < 18) sc->meanP[col - 9] = s / (double)N;
-      else if (col < 27) sc->T[col - 18] = s;
-      else sc->S[col - 27] = s;
-    }
+  const int col = blockIdx.x;
+  const double s = column_sum(partials, nblk, ncol, col, shm);
+  if (threadIdx.x == 0) {
+    if (col < 9) sc->meanF[col] = s / (double)N;
+    else if (col < 18) sc->meanP[col - 9] = s / (double)N;
+    else if (col < 27) sc->T[col - 18] = s;
+    else sc->S[col - 27] = s;
   }
 }
 
@@ -287,20 +291,40 @@ __global__ void k_predictor(double* __restrict__ F, long long N, Load9 ld, const
   }
 }
 
+// r = b rounded to the inner type, x = p' = 0, and the block partials of
+// r.r.  FP32: b is rounded through its double-word split (no FP64
+// instruction, the FP64 pipe being slow on this part) and r.r is summed
+// from exact FP32 products with Neumaier compensation, thread totals in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_cg_init(const double* __restrict__ b, T* __restrict__ x,
                                                          T* __restrict__ r, T* __restrict__ p, long long n9,
                                                          double* __restrict__ partials) {
   __shared__ double tot[1];
   double acc[1] = {0.0};
+  float fs = 0.f, fc = 0.f;
+  auto fadd = [&](float v) {
+    const float t = fs + v;
+    fc += (fabsf(fs) >= fabsf(v)) ? ((fs - t) + v) : ((v - t) + fs);
+    fs = t;
+  };
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n9;
        i += (long long)gridDim.x * blockDim.x) {
-    const T v = (T)b[i];
-    r[i] = v;
+    if constexpr (sizeof(T) == 4) {
+      const dw d = dw_split(b[i]);
+      const float v = __fadd_rn(d.hi, d.lo);
+      r[i] = v;
+      const float pr = v * v;
+      fadd(pr);
+      fadd(fmaf(v, v, -pr));
+    } else {
+      const T v = (T)b[i];
+      r[i] = v;
+      acc[0] += (double)v * (double)v;
+    }
     p[i] = (T)0;    // previous direction of the first iteration
     x[i] = (T)0;
-    acc[0] += (double)v * (double)v;
   }
+  if constexpr (sizeof(T) == 4) acc[0] = (double)fs + (double)fc;
   block_sum<1>(acc, tot);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
 }
@@ -325,11 +349,11 @@ __global__ void __launch_bounds__(kRedThreads) k_fin_cg_init(const double* __res
 // F += x, or with DEFL F += x - What F (What from the projection of x).
 // Partials: columns 0-8 the sums of the correction (the new averages are the
 // old ones plus its mean), column 9 the block max of abs(dF_v)^2.
-template <typename T, bool DEFL>
+template <typename T, bool DEFL, bool NYQ>
 __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restrict__ F,
                                                                const T* __restrict__ x, long long N,
                                                                double* __restrict__ partials,
-                                                               const Scalars* sc) {
+                                                               const Scalars* sc, NyqArgs nq) {
   __shared__ double tot[10];
   double acc[10];
 #pragma unroll
@@ -349,10 +373,27 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
     T xv[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; xv[c] = x[c * N + v]; }
+    // Nyquist projection of the correction at this voxel
+    float ny9[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ny9[c] = 0.f;
+    if constexpr (NYQ) {
+      const unsigned vv = (unsigned)v;   // N < 2^31 for every admissible grid
+      const unsigned r = vv / (unsigned)nq.nx;
+      const int xx = (int)(vv - r * (unsigned)nq.nx);
+      const unsigned zq = r / (unsigned)nq.ny;
+      const int y = (int)(r - zq * (unsigned)nq.ny), z = (int)zq;
+      const float sx = (xx & 1) ? -1.f : 1.f, sy = (y & 1) ? -1.f : 1.f, sz = (z & 1) ? -1.f : 1.f;
+#pragma unroll
+      for (int c = 0; c < 9; ++c)
+        ny9[c] = sx * nq.Rx[((long long)c * nq.nz + z) * nq.ny + y] +
+                 sy * nq.Ry[((long long)c * nq.nz + z) * nq.nx + xx] +
+                 sz * nq.Rz[((long long)c * nq.ny + y) * nq.nx + xx];
+    }
     if (DEFL || sizeof(T) == 8) {
       double d[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) d[c] = (double)xv[c];
+      for (int c = 0; c < 9; ++c) d[c] = NYQ ? (double)xv[c] - (double)ny9[c] : (double)xv[c];
       if (DEFL) {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -373,7 +414,8 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         const float d = (float)xv[c];
-        F[c * N + v] = f[c] + (double)d;
+        if (NYQ) F[c * N + v] = (f[c] + f32_as_f64(d)) - f32_as_f64(ny9[c]);
+        else F[c * N + v] = f[c] + f32_as_f64(d);
         const float tt = xs[c] + d;
         xc[c] += (fabsf(xs[c]) >= fabsf(d)) ? ((xs[c] - tt) + d) : ((d - tt) + xs[c]);
         xs[c] = tt;
@@ -465,17 +507,21 @@ __global__ void k_defl_apply(T* __restrict__ y, const double* __restrict__ F, lo
   }
 }
 
+// One block per column (grid 10): columns 0-8 the new averages, column 9
+// the max of abs(dF_v)^2.
 __global__ void __launch_bounds__(kRedThreads) k_fin_newton(const double* __restrict__ partials, int nblk,
                                                             long long N, Scalars* sc) {
   __shared__ double shm[kRedThreads];
-  for (int col = 0; col < 9; ++col) {
+  const int col = blockIdx.x;
+  if (col < 9) {
     const double s = column_sum(partials, nblk, 10, col, shm);
     if (threadIdx.x == 0) sc->meanF_new[col] = sc->meanF[col] + s / (double)N;
-  }
-  const double m = column_max(partials, nblk, 10, 9, shm);
-  if (threadIdx.x == 0) {
-    sc->dF2max = m;
-    if (!isfinite(m)) sc->flags |= MF_FLAG_NONFINITE;
+  } else {
+    const double m = column_max(partials, nblk, 10, 9, shm);
+    if (threadIdx.x == 0) {
+      sc->dF2max = m;
+      if (!isfinite(m)) atomicOr(&sc->flags, MF_FLAG_NONFINITE);
+    }
   }
 }
 
@@ -488,7 +534,7 @@ int grid_for(long long n) {
 
 cudaError_t mf_launch_fin_means(const double* partials, int nblk, int ncol, long long N, Scalars* sc,
                                 cudaStream_t st) {
-  k_fin_means<<<1, kRedThreads, 0, st>>>(partials, nblk, ncol, N, sc);
+  k_fin_means<<<ncol, kRedThreads, 0, st>>>(partials, nblk, ncol, N, sc);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
@@ -504,7 +550,10 @@ cudaError_t mf_launch_constitutive(const double* F, double* P, void* K45, bool k
   } else {
     k_constitutive<double, false, false><<<nblk, kRedThreads, 0, st>>>(F, P, K45, m, N, partials, sc);
   }
-  k_fin_means<<<1, kRedThreads, 0, st>>>(partials, nblk, (moments && !want_K) ? 36 : 18, N, sc);
+  {
+    const int ncol = (moments && !want_K) ? 36 : 18;
+    k_fin_means<<<ncol, kRedThreads, 0, st>>>(partials, nblk, ncol, N, sc);
+  }
   g_mf_launches += 2;
   return cudaGetLastError();
 }
@@ -513,7 +562,7 @@ cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int
                              cudaStream_t st) {
   k_mean_F<<<nblk, kRedThreads, 0, st>>>(F, N, partials);
   // columns 0..8 of a 9-column table
-  k_fin_means<<<1, kRedThreads, 0, st>>>(partials, nblk, 9, N, sc);
+  k_fin_means<<<9, kRedThreads, 0, st>>>(partials, nblk, 9, N, sc);
   g_mf_launches += 2;
   return cudaGetLastError();
 }
@@ -538,12 +587,26 @@ cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f
 }
 
 cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool defl, long long N,
-                                    double* partials, int nblk, Scalars* sc, cudaStream_t st) {
-  if (f32 && defl) k_newton_update<float, true><<<nblk, kRedThreads, 0, st>>>(F, (const float*)x, N, partials, sc);
-  else if (f32) k_newton_update<float, false><<<nblk, kRedThreads, 0, st>>>(F, (const float*)x, N, partials, sc);
-  else if (defl) k_newton_update<double, true><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials, sc);
-  else k_newton_update<double, false><<<nblk, kRedThreads, 0, st>>>(F, (const double*)x, N, partials, sc);
-  k_fin_newton<<<1, kRedThreads, 0, st>>>(partials, nblk, N, sc);
+                                    double* partials, int nblk, Scalars* sc, cudaStream_t st,
+                                    const NyqArgs* nyq) {
+  NyqArgs nq;
+  memset(&nq, 0, sizeof(nq));
+  if (nyq) nq = *nyq;
+  const float* xf = (const float*)x;
+  const double* xd = (const double*)x;
+  if (f32 && nyq) {
+    if (defl) k_newton_update<float, true, true><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
+    else k_newton_update<float, false, true><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
+  } else if (f32 && defl) {
+    k_newton_update<float, true, false><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
+  } else if (f32) {
+    k_newton_update<float, false, false><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
+  } else if (defl) {
+    k_newton_update<double, true, false><<<nblk, kRedThreads, 0, st>>>(F, xd, N, partials, sc, nq);
+  } else {
+    k_newton_update<double, false, false><<<nblk, kRedThreads, 0, st>>>(F, xd, N, partials, sc, nq);
+  }
+  k_fin_newton<<<10, kRedThreads, 0, st>>>(partials, nblk, N, sc);
   g_mf_launches += 2;
   return cudaGetLastError();
 }
