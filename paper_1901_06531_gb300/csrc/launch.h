@@ -142,21 +142,8 @@ struct Defl {
   int m;
   double W[3][9];
 };
-// nyquist.cu: the Nyquist content of an FP32 correction, as the three
-// grouped terms Rx(z, y), Ry(z, x), Rz(y, x) of its projection
-// (Pi x)(x, y, z) = (-1)^x Rx + (-1)^y Ry + (-1)^z Rz, per component.
-struct NyqArgs {
-  int nx, ny, nz;
-  double *Sx, *Sy, *Sxy, *Sz;   // alternating sums (scratch)
-  float *Rx, *Ry, *Rz;          // grouped terms
-};
-size_t mf_nyquist_scratch_bytes(int nx, int ny, int nz);
-NyqArgs mf_nyquist_args(void* scratch, int nx, int ny, int nz);
-cudaError_t mf_launch_nyquist_terms(const float* x, const NyqArgs& a, long long N, cudaStream_t st);
-// F += x (FP32 x: minus its Nyquist projection when nyq is non-null)
 cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool defl, long long N,
-                                    double* partials, int nblk, Scalars* sc, cudaStream_t st,
-                                    const NyqArgs* nyq = nullptr);
+                                    double* partials, int nblk, Scalars* sc, cudaStream_t st);
 // Removes from y (9N, double or float) its components along the n_k:
 // y -= What F with What = sum_k (n_k . y) W_k; What is kept in sc for reuse.
 cudaError_t mf_launch_defl_project(void* y, bool f32, bool apply, const double* F, long long N,

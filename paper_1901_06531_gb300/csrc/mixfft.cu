@@ -206,7 +206,7 @@ struct mf_ctx {
   size_t ws_need = 0;
   // offsets into the workspace
   size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
-      otable32, otabledw, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw, onyq;
+      otable32, otabledw, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
   size_t npart;
   // material
   int model = -1, nphase = 0;
@@ -690,26 +690,23 @@ struct Runner {
     s = launch_cg(c, m, tol_cg, c->f32() ? cg_rel : 0.0, max_cg);
     if (s) return s;
     void* corr = c->ws + c->ox;
-    NyqArgs na = mf_nyquist_args(c->ws + c->onyq, c->nx, c->ny, c->nz);
     if (c->f32()) {
       // The FP32 correction, projected once more onto the range of G*: its
-      // rounding leaves incompatible components (and Nyquist ones) that the
+      // rounding leaves incompatible and Nyquist components that the
       // residual cannot see but that shift the equilibrium through the
       // nonlinear law; after the projection only the projection's own
-      // rounding is left, and the Nyquist part of that is removed exactly
-      // by the update.
+      // rounding is left of them.
       const ZArgs za = z_args(c, true, m, 1.0 / (double)N);
       if (mf_launch_project(true, c->ws + c->ox, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xy_args(c, true), za,
                             nullptr, c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
       corr = c->ws + c->op2;
-      if (mf_launch_nyquist_terms((const float*)corr, na, N, c->st) != cudaSuccess) return MF_CUDA_ERROR;
     }
     if (defl.m > 0 && mf_launch_defl_project(corr, true, false, F, N, defl, part, kPointwiseBlocks, sc, c->st) !=
                           cudaSuccess)
       return MF_CUDA_ERROR;
-    if (mf_launch_newton_update(F, corr, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc, c->st,
-                                c->f32() ? &na : nullptr) != cudaSuccess)
+    if (mf_launch_newton_update(F, corr, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc, c->st) !=
+        cudaSuccess)
       return MF_CUDA_ERROR;
     // FP32 corrections carry a rounding-level average on the strain-controlled
     // components; the FP64 outer level re-imposes F-bar there
@@ -885,7 +882,6 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->otw64 = take((nx + ny + nz) * sizeof(double2));
   c->otw32 = take((nx + ny + nz) * sizeof(float2));
   c->otwdw = take((nx + ny + nz) * sizeof(dwc));
-  c->onyq = take(mf_nyquist_scratch_bytes(nx, ny, nz));
   c->ws_need = off;
   *out = c;
   return MF_OK;

@@ -349,11 +349,11 @@ __global__ void __launch_bounds__(kRedThreads) k_fin_cg_init(const double* __res
 // F += x, or with DEFL F += x - What F (What from the projection of x).
 // Partials: columns 0-8 the sums of the correction (the new averages are the
 // old ones plus its mean), column 9 the block max of abs(dF_v)^2.
-template <typename T, bool DEFL, bool NYQ>
+template <typename T, bool DEFL>
 __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restrict__ F,
                                                                const T* __restrict__ x, long long N,
                                                                double* __restrict__ partials,
-                                                               const Scalars* sc, NyqArgs nq) {
+                                                               const Scalars* sc) {
   __shared__ double tot[10];
   double acc[10];
 #pragma unroll
@@ -373,27 +373,10 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
     T xv[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; xv[c] = x[c * N + v]; }
-    // Nyquist projection of the correction at this voxel
-    float ny9[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) ny9[c] = 0.f;
-    if constexpr (NYQ) {
-      const unsigned vv = (unsigned)v;   // N < 2^31 for every admissible grid
-      const unsigned r = vv / (unsigned)nq.nx;
-      const int xx = (int)(vv - r * (unsigned)nq.nx);
-      const unsigned zq = r / (unsigned)nq.ny;
-      const int y = (int)(r - zq * (unsigned)nq.ny), z = (int)zq;
-      const float sx = (xx & 1) ? -1.f : 1.f, sy = (y & 1) ? -1.f : 1.f, sz = (z & 1) ? -1.f : 1.f;
-#pragma unroll
-      for (int c = 0; c < 9; ++c)
-        ny9[c] = sx * nq.Rx[((long long)c * nq.nz + z) * nq.ny + y] +
-                 sy * nq.Ry[((long long)c * nq.nz + z) * nq.nx + xx] +
-                 sz * nq.Rz[((long long)c * nq.ny + y) * nq.nx + xx];
-    }
     if (DEFL || sizeof(T) == 8) {
       double d[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) d[c] = NYQ ? (double)xv[c] - (double)ny9[c] : (double)xv[c];
+      for (int c = 0; c < 9; ++c) d[c] = (double)xv[c];
       if (DEFL) {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -414,8 +397,7 @@ __global__ void __launch_bounds__(kRedThreads) k_newton_update(double* __restric
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         const float d = (float)xv[c];
-        if (NYQ) F[c * N + v] = (f[c] + f32_as_f64(d)) - f32_as_f64(ny9[c]);
-        else F[c * N + v] = f[c] + f32_as_f64(d);
+        F[c * N + v] = f[c] + f32_as_f64(d);
         const float tt = xs[c] + d;
         xc[c] += (fabsf(xs[c]) >= fabsf(d)) ? ((xs[c] - tt) + d) : ((d - tt) + xs[c]);
         xs[c] = tt;
@@ -587,25 +569,13 @@ cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f
 }
 
 cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool defl, long long N,
-                                    double* partials, int nblk, Scalars* sc, cudaStream_t st,
-                                    const NyqArgs* nyq) {
-  NyqArgs nq;
-  memset(&nq, 0, sizeof(nq));
-  if (nyq) nq = *nyq;
+                                    double* partials, int nblk, Scalars* sc, cudaStream_t st) {
   const float* xf = (const float*)x;
   const double* xd = (const double*)x;
-  if (f32 && nyq) {
-    if (defl) k_newton_update<float, true, true><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
-    else k_newton_update<float, false, true><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
-  } else if (f32 && defl) {
-    k_newton_update<float, true, false><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
-  } else if (f32) {
-    k_newton_update<float, false, false><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc, nq);
-  } else if (defl) {
-    k_newton_update<double, true, false><<<nblk, kRedThreads, 0, st>>>(F, xd, N, partials, sc, nq);
-  } else {
-    k_newton_update<double, false, false><<<nblk, kRedThreads, 0, st>>>(F, xd, N, partials, sc, nq);
-  }
+  if (f32 && defl) k_newton_update<float, true><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc);
+  else if (f32) k_newton_update<float, false><<<nblk, kRedThreads, 0, st>>>(F, xf, N, partials, sc);
+  else if (defl) k_newton_update<double, true><<<nblk, kRedThreads, 0, st>>>(F, xd, N, partials, sc);
+  else k_newton_update<double, false><<<nblk, kRedThreads, 0, st>>>(F, xd, N, partials, sc);
   k_fin_newton<<<10, kRedThreads, 0, st>>>(partials, nblk, N, sc);
   g_mf_launches += 2;
   return cudaGetLastError();

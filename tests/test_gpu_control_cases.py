@@ -71,8 +71,7 @@ def test_cases_1_2_3_share_the_endpoint_symmetric_cell(prec):
     """Cases (1), (2) and (3) on a mirror-symmetric cell (one centred sphere,
     vf 0.2, the same SVK phases), 32^3, lambda_end = 0.2 in 8 steps: the same
     endpoint, compared through F^T F and F^T P (full stress control leaves a
-    rigid rotation free).  FP64 to 1e-8; FP32 inner to 1e-6 (its field noise
-    in the Nyquist modes, which G* cannot see, grows with the strain).  The
+    rigid rotation free).  FP64 to 1e-8; FP32 inner to 3e-7.  The
     symmetric cell keeps case (1)'s final shear stresses P12, P13 at zero; in
     an asymmetric cell they are not, and full stress control to them leaves
     the rotation about e1 with a curvature of rounding size and either sign
@@ -89,7 +88,7 @@ def test_cases_1_2_3_share_the_endpoint_symmetric_cell(prec):
     C1, S1 = invariants(*ctx.get_fields())
     P_end, F_end = o1["Pbar"][-1], o1["Fbar"][-1]
     assert np.max(np.abs(P_end[[1, 2]])) < 1e-9 * np.abs(P_end[0])
-    tol = 1e-8 if prec == mf.MF_FP64 else 1e-6
+    tol = 1e-8 if prec == mf.MF_FP64 else 3e-7
     for m, t in (inputs.history_case2(P_end, 8), inputs.history_case3(F_end, 8)):
         ctx.set_F(None)
         o = ctx.solve(m, t, **kw)

@@ -110,16 +110,15 @@ def test_fp32_inner_matches_fp64_oracle():
     assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
     assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-9
     # full stress control leaves the rotation about the load axis free: F is
-    # unique up to that rotation, F^T F and F^T P are unique.  FP32 rounding
-    # in the inner solves also leaves noise of relative size ~1e-8 in the
-    # Nyquist modes of F, which G* annihilates and the FP64 residual therefore
-    # cannot see; the stated FP32-inner field tolerance is 3e-7 (max-norm).
+    # unique up to that rotation, F^T F and F^T P are unique.  Each FP32
+    # correction is projected once more onto range(G*) before the update, so
+    # the only components the FP64 residual cannot see are the rounding of
+    # that projection; the stated FP32-inner field tolerance is 3e-8
+    # (max-norm; stress-like fields times the largest stiffness, mu = 10).
     C, S = invariants(F, P)
     Cr, Sr = invariants(ref["F"], ref["P"])
-    assert rel(C, Cr) < 3e-7
-    # stress-like fields: the same noise times the stiffness (max mu = 10)
-    assert np.max(np.abs(S - Sr)) < 3e-7 * 10.0
-    assert rel(F, ref["F"]) < 1e-6
+    errs = (rel(C, Cr), np.max(np.abs(S - Sr)) / 10.0)
+    assert max(errs) < 3e-8, errs
     check_control(out, mask, target, 1e-9, 1e-14)
 
 
@@ -135,7 +134,7 @@ def test_fp32_inner_polycrystal():
     ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
     F, _ = ctx.get_fields()
     assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
-    assert rel(F, ref["F"]) < 3e-7
+    assert rel(F, ref["F"]) < 3e-8, rel(F, ref["F"])
 
 
 def test_radix3_grid_solve():
