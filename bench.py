@@ -85,13 +85,18 @@ def src_hash(kernel):
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu summary (its ```json
+    block), if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "cg_kernels_polycrystal128_fp32inner.md")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
+        text = f.read()
+    try:
+        block = text.split("```json", 1)[1].split("```", 1)[0]
+        d = json.loads(block)
+    except (IndexError, ValueError):
+        return None
     e = d.get(kernel)
     if not e or e.get("source_sha") != src_hash(kernel):
         return None
