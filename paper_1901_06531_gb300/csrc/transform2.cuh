@@ -77,6 +77,134 @@ __device__ __forceinline__ void load_tables(C* twx, C* twy, int* posx, const C* 
   for (int i = threadIdx.x; i < h; i += blockDim.x) posx[i] = gpos[i];
 }
 
+// ------------------------------------------------------------- row spectra
+// The half-length x transform (H = NX/2 points) has one or two stages.  Its
+// last stage (radix RB, no twiddles: its M is 1) has RA = H/RB butterflies
+// per row; butterfly b holds the positions b*RB + r, i.e. the frequencies
+// k = b + RA r.  The partner H - k of (b, r) is (RA - b, RB - 1 - r) for
+// b != 0 and (0, (RB - r) % RB) for b = 0.  A task takes butterflies b and
+// RA - b of one row, so both members of every pair of the split (forward) or
+// merge (inverse) are in its registers, and that step is fused with the last
+// forward (first inverse) stage.
+template <int H> struct RowPlan {
+  static constexpr int NST = fft2::nst(H);
+  static constexpr int RB = fft2::rad(H, NST - 1);
+  static constexpr int RA = H / RB;
+  static constexpr int NT = RA / 2 + 1;   // tasks per row
+};
+
+// X_k = E_k + W_NX^k O_k, E_k = (Z_k + conj Z_(H-k)) / 2, O_k = (Z_k - conj Z_(H-k)) / 2i
+template <typename T, typename C>
+__device__ __forceinline__ C split_one(C za, C zb, C w) {
+  C e, o;
+  e.x = (T)0.5 * (za.x + zb.x); e.y = (T)0.5 * (za.y - zb.y);
+  o.x = (T)0.5 * (za.y + zb.y); o.y = (T)-0.5 * (za.x - zb.x);
+  return cadd(e, cmul(o, w));
+}
+
+// Z_k = E_k + i O_k, E_k = X_k + conj X_(H-k), O_k = (X_k - conj X_(H-k)) conj(W_NX^k)
+// (the adjoint of the split, times 2)
+template <typename T, typename C>
+__device__ __forceinline__ C merge_one(C xa, C xb, C w) {
+  C e, d;
+  e.x = xa.x + xb.x; e.y = xa.y - xb.y;
+  d.x = xa.x - xb.x; d.y = xa.y + xb.y;
+  const C o = cmulc(d, w);
+  C z;
+  z.x = e.x - o.y; z.y = e.y + o.x;
+  return z;
+}
+
+// Last x stage + split.  ld(y, pos): input at position pos of row y; the
+// outputs go to buf (row pitch PX).
+template <typename T, int NX, int TPB, typename LD>
+__device__ __forceinline__ void x_last_split(typename CT<T>::t* buf, const typename CT<T>::t* twx, LD ld) {
+  typedef typename CT<T>::t C;
+  typedef RowPlan<NX / 2> RP;
+  constexpr int RA = RP::RA, RB = RP::RB, PX = NX / 2 + 1, NY = NX;
+  for (int task = threadIdx.x; task < NY * RP::NT; task += TPB) {
+    const int y = task % NY, t = task / NY;
+    const int b0 = t, b1 = (t == 0) ? 0 : RA - t;
+    C u[RB], w[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) u[r] = ld(y, b0 * RB + r);
+    fft2::Dft<RB, false, C>::run(u);
+    C* row = buf + y * PX;
+    if (b1 != b0) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) w[r] = ld(y, b1 * RB + r);
+      fft2::Dft<RB, false, C>::run(w);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int rp = RB - 1 - r;
+        const int k = b0 + RA * r, km = b1 + RA * rp;
+        row[b0 * RB + r] = split_one<T>(u[r], w[rp], twx[k]);
+        row[b1 * RB + rp] = split_one<T>(w[rp], u[r], twx[km]);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int rp = (b0 == 0) ? (RB - r) % RB : RB - 1 - r;
+        if (rp < r) continue;
+        const int k = b0 + RA * r, km = b0 + RA * rp;
+        const C za = u[r], zb = u[rp];
+        row[b0 * RB + r] = split_one<T>(za, zb, twx[k]);
+        if (rp != r) row[b0 * RB + rp] = split_one<T>(zb, za, twx[km]);
+      }
+    }
+  }
+}
+
+// Merge + first inverse x stage (in place in buf).  The x-constant
+// coefficient keeps only its real part and X_H (Nyquist) is zero, so
+// Z_0 = x0 + i x0 with x0 = Re X_0.
+template <typename T, int NX, int TPB>
+__device__ __forceinline__ void x_merge_first(typename CT<T>::t* buf, const typename CT<T>::t* twx) {
+  typedef typename CT<T>::t C;
+  typedef RowPlan<NX / 2> RP;
+  constexpr int RA = RP::RA, RB = RP::RB, PX = NX / 2 + 1, NY = NX;
+  for (int task = threadIdx.x; task < NY * RP::NT; task += TPB) {
+    const int y = task % NY, t = task / NY;
+    const int b0 = t, b1 = (t == 0) ? 0 : RA - t;
+    C* row = buf + y * PX;
+    C u[RB], w[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) u[r] = row[b0 * RB + r];
+    if (b1 != b0) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) w[r] = row[b1 * RB + r];
+      C zu[RB], zw[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int rp = RB - 1 - r;
+        const int k = b0 + RA * r, km = b1 + RA * rp;
+        zu[r] = merge_one<T>(u[r], w[rp], twx[k]);
+        zw[rp] = merge_one<T>(w[rp], u[r], twx[km]);
+      }
+      fft2::Dft<RB, true, C>::run(zu);
+      fft2::Dft<RB, true, C>::run(zw);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) { row[b0 * RB + r] = zu[r]; row[b1 * RB + r] = zw[r]; }
+    } else {
+      C zu[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int rp = (b0 == 0) ? (RB - r) % RB : RB - 1 - r;
+        const int k = b0 + RA * r;
+        if (k == 0) {
+          const T x0 = u[r].x;
+          zu[r].x = x0; zu[r].y = x0;
+        } else {
+          zu[r] = merge_one<T>(u[r], u[rp], twx[k]);
+        }
+      }
+      fft2::Dft<RB, true, C>::run(zu);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) row[b0 * RB + r] = zu[r];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ forward
 template <typename T, int NX>
 __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::t* __restrict__ in,
@@ -87,7 +215,6 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   constexpr int TPB = xy_threads<T>();
   typedef typename CT<T>::t C;
   typedef typename CT<typename IOT<T>::t>::t CI;
-  static_assert(sizeof(C) == sizeof(CI), "in-place conversion needs equal element sizes");
   if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -98,42 +225,53 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
   const CI* src = reinterpret_cast<const CI*>(in + c * N + (long long)z * NY * NX);
-  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
-    const int y = idx / H, j = idx - (idx / H) * H;
-    cp_async_elem(reinterpret_cast<CI*>(buf + y * PX + j), src + idx);
-  }
-  cp_async_wait_all();
-  if constexpr (!std::is_same<C, CI>::value) {
-    // each thread converts the elements it copied itself
+  // row y, sample j (the real values 2j, 2j+1 as one complex sample)
+  auto gload = [&](int y, int j) {
+    C v;
+    io_in(v, src[(long long)y * H + j]);
+    return v;
+  };
+  if constexpr (sizeof(C) == 8) {
+    // FP32: the x transform touches shared memory twice per sample
+    __syncthreads();   // tables
+    if constexpr (RowPlan<H>::NST == 2) {
+      // first x stage straight from global memory (consecutive threads take
+      // consecutive butterflies of a row: 64-byte row segments per warp access)
+      fft2::stage_io<C, H, NX, 0, false, NY, 1, PX, 0, 1, false>(
+          twx, [&](int q, int, int e) { return gload(q, e); }, [&](int, int i, int, C v) { buf[i] = v; });
+      __syncthreads();
+      x_last_split<T, NX, TPB>(buf, twx, [&](int y, int pos) { return buf[y * PX + pos]; });
+    } else {
+      x_last_split<T, NX, TPB>(buf, twx, gload);
+    }
+  } else {
+    // 16-byte types (FP64, double word) are arithmetic bound: the plane is
+    // copied in asynchronously (and converted in place), then the stages and
+    // the split run over shared memory
     for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
       const int y = idx / H, j = idx - (idx / H) * H;
-      const CI v = *reinterpret_cast<const CI*>(buf + y * PX + j);
-      io_in(buf[y * PX + j], v);
+      cp_async_elem(reinterpret_cast<CI*>(buf + y * PX + j), src + idx);
     }
-  }
-  __syncthreads();
-  // x: NY rows of H complex samples
-  fft2::forward<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
-  // split into the NX-point spectrum of each real row; pairs (k, H-k)
-  constexpr int NP = H / 2 + 1;
-  for (int idx = threadIdx.x; idx < NY * NP; idx += TPB) {
-    const int y = idx % NY, k = idx / NY;
-    const int km = (H - k) % H;
-    C* row = buf + y * PX;
-    const int pa = posx[k], pb = posx[km];
-    const C za = row[pa], zb = row[pb];
-    // X_k from (Z_k, Z_(H-k)); X_(H-k) from (Z_(H-k), Z_k)
-    C ea, oa, eb, ob;
-    ea.x = (T)0.5 * (za.x + zb.x); ea.y = (T)0.5 * (za.y - zb.y);
-    oa.x = (T)0.5 * (za.y + zb.y); oa.y = (T)-0.5 * (za.x - zb.x);
-    eb.x = ea.x; eb.y = -ea.y;
-    ob.x = oa.x; ob.y = -oa.y;
-    const C xa = cadd(ea, cmul(oa, twx[k]));
-    if (km != k) {
-      const C xb = cadd(eb, cmul(ob, twx[km]));
-      row[pb] = xb;
+    cp_async_wait_all();
+    if constexpr (!std::is_same<C, CI>::value) {
+      for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {   // each thread converts its own copies
+        const int y = idx / H, j = idx - (idx / H) * H;
+        const CI v = *reinterpret_cast<const CI*>(buf + y * PX + j);
+        io_in(buf[y * PX + j], v);
+      }
     }
-    row[pa] = xa;
+    __syncthreads();
+    fft2::forward<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
+    constexpr int NP = H / 2 + 1;
+    for (int idx = threadIdx.x; idx < NY * NP; idx += TPB) {
+      const int y = idx % NY, k = idx / NY;
+      const int km = (H - k) % H;
+      C* row = buf + y * PX;
+      const int pa = posx[k], pb = posx[km];
+      const C za = row[pa], zb = row[pb];
+      if (km != k) row[pb] = split_one<T>(zb, za, twx[km]);
+      row[pa] = split_one<T>(za, zb, twx[k]);
+    }
   }
   __syncthreads();
   // y: H columns of NY samples, stride PX; the last stage stores the
@@ -179,42 +317,30 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   __syncthreads();   // tables
   // y: the first inverse stage reads the spectrum rows from global memory
   fft2::inverse_in<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e) { return src[e * H + q]; });
-  // merge each row's spectrum into H complex samples (the adjoint of the
-  // split, times 2): Z_k = E_k + i O_k with E_k = X_k + conj X_(H-k),
-  // O_k = (X_k - conj X_(H-k)) conj(W_NX^k); X_H (Nyquist) is zero and the
-  // x-constant coefficient keeps only its real part (real output)
-  constexpr int NP = H / 2 + 1;
-  for (int idx = threadIdx.x; idx < NY * NP; idx += TPB) {
-    const int y = idx % NY, k = idx / NY;
-    const int km = (H - k) % H;
-    C* row = buf + y * PX;
-    const int pa = posx[k], pb = posx[km];
-    C xa = row[pa], xb = row[pb];
-    C za, zb;
-    if (k == 0) {
-      // X_0 real, X_H = 0
-      const T x0 = xa.x;   // E = x0, O = x0: Z = x0 + i x0
-      za.x = x0; za.y = x0;
-      row[pa] = za;
-      continue;
+  if constexpr (sizeof(C) == 8) {
+    // merge of each row's spectrum, fused with the first inverse x stage
+    x_merge_first<T, NX, TPB>(buf, twx);
+  } else {
+    constexpr int NP = H / 2 + 1;
+    for (int idx = threadIdx.x; idx < NY * NP; idx += TPB) {
+      const int y = idx % NY, k = idx / NY;
+      const int km = (H - k) % H;
+      C* row = buf + y * PX;
+      const int pa = posx[k], pb = posx[km];
+      const C xa = row[pa], xb = row[pb];
+      if (k == 0) {
+        const T x0 = xa.x;
+        C z0; z0.x = x0; z0.y = x0;
+        row[pa] = z0;
+        continue;
+      }
+      if (km != k) row[pb] = merge_one<T>(xb, xa, twx[km]);
+      row[pa] = merge_one<T>(xa, xb, twx[k]);
     }
-    // E_a = xa + conj(xb), D_a = xa - conj(xb)
-    C ea, da, eb, db;
-    ea.x = xa.x + xb.x; ea.y = xa.y - xb.y;
-    da.x = xa.x - xb.x; da.y = xa.y + xb.y;
-    const C oa = cmulc(da, twx[k]);
-    za.x = ea.x - oa.y; za.y = ea.y + oa.x;
-    if (km != k) {
-      eb.x = xb.x + xa.x; eb.y = xb.y - xa.y;
-      db.x = xb.x - xa.x; db.y = xb.y + xa.y;
-      const C ob = cmulc(db, twx[km]);
-      zb.x = eb.x - ob.y; zb.y = eb.y + ob.x;
-      row[pb] = zb;
-    }
-    row[pa] = za;
+    __syncthreads();
+    fft2::inverse<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
   }
   __syncthreads();
-  fft2::inverse<C, H, NX, NY, 1, PX, 0, 1>(buf, twx);
   CI* dst = reinterpret_cast<CI*>(out + c * N + (long long)z * NY * NX);
   // per-thread sums: FP64 for FP64 data; for FP32 data exact FP32 products
   // with Neumaier-compensated FP32 accumulation, combined in FP64 below
@@ -232,10 +358,8 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   };
   T alpha = (T)0;
   if (MODE == 3) alpha = (T)sc->alpha;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
-    const int y = idx / H, j = idx - (idx / H) * H;
-    const C v = buf[y * PX + j];
+  // the output of sample (row y, j): y = G*(.) stored, or r -= alpha y
+  auto emit = [&](long long idx, C v) {
     if constexpr (MODE == 3) {
       C r = dst[idx];
       r.x -= alpha * v.x;
@@ -250,6 +374,19 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
         if (sizeof(TI) == 4) { fsq((float)w.x); fsq((float)w.y); }
         else acc += (double)w.x * (double)w.x + (double)w.y * (double)w.y;
       }
+    }
+  };
+  if constexpr (sizeof(C) == 8 && RowPlan<H>::NST == 2) {
+    // last inverse x stage straight to global memory (consecutive threads
+    // take consecutive butterflies of a row: 64-byte row segments)
+    fft2::stage_io<C, H, NX, 0, true, NY, 1, PX, 0, 1, false>(
+        twx, [&](int, int i, int) { return buf[i]; },
+        [&](int q, int, int e, C v) { emit((long long)q * H + e, v); });
+  } else {
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
+      const int y = idx / H, j = idx - (idx / H) * H;
+      emit(idx, buf[y * PX + j]);
     }
   }
   if (sizeof(TI) == 4) acc = (double)fs + (double)fc;
