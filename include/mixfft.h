@@ -58,12 +58,14 @@ typedef struct mf_ctx mf_ctx;
 
 /* Create a context for one cell of nx*ny*nz voxels on the current CUDA device.
  * nx, ny: even, of the form 2^a 3^b, 4..256; nz: 2^a 3^b, 2..256.  The x-y
- * plane of one component must fit in shared memory: nx*ny <= 16384 for
- * MF_FP64 and for MF_FP32_INNER (the FP64 residual uses the same plane).
+ * plane of one component must fit in shared memory (nx*ny <= 16384), except
+ * for nx = ny = 256 with nz in {16, 32, 48, 64, 96, 128, 256}, which the
+ * separate row and column kernels serve (mf_set_xy_split).
  * precision MF_FP64: every step in FP64.  MF_FP32_INNER: the CG iterations
  * (transforms, projection, tangent apply, vector updates) run in FP32 with
- * FP64 dot products, while P, K, the residual, the null-frequency control and
- * the Newton update stay FP64 (defect correction).
+ * FP64-combined dot products, while P, the residual, the null-frequency
+ * control and the Newton update keep FP64 accuracy (defect correction; see
+ * mf_set_outer_arith).
  * stream: a cudaStream_t (NULL = legacy default stream) used for every launch
  * and copy of this context.  *out is NULL on failure. */
 int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream);
@@ -262,6 +264,15 @@ int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out);
 int mf_adjoint(mf_ctx* ctx, const uint8_t* mask, const double* wF, const double* wP, double tol_cg,
                double cg_rel, int max_cg, double* J_out, double* dJ_dparams, double* dJ_dscale_dev,
                int32_t* cg_its_out);
+
+/* x-y transform kernels of a context on the fixed-size path: 0 = one kernel
+ * per (component, z) plane holding the whole x-y plane in shared memory (the
+ * default where the plane fits); 1 = separate row (x) and column (y) kernels
+ * through global memory (the default, and the only choice, for nx = ny =
+ * 256; available for nx = ny = 32 as well, for testing).  Results agree to
+ * rounding.  MF_INVALID_ARG for a choice the context's size does not
+ * support. */
+int mf_set_xy_split(mf_ctx* ctx, int split);
 
 /* Arithmetic of the outer (defect-correction) level of MF_FP32_INNER
  * contexts: the stress P(F) of the constitutive pass (Eq. eq:lineariz) and

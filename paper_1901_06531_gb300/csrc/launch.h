@@ -6,6 +6,7 @@
 
 struct XYArgs {
   int v2;          // 1: fixed-size kernels (transform2*.cu), tables of that layout
+  int split;       // with v2: separate row (x) and column (y) kernels (transform3.cuh)
   const int* skip; // if non-null and *skip != 0 the kernel returns at once (finished CG)
   int nx, ny, nz;
   long long N;
@@ -42,6 +43,11 @@ extern long long g_mf_launches;
 // per (c, z) ny rows (digit-reversed ky, yk table of ny entries) of nx/2 slots
 // (digit-reversed kx, xk table of nx/2 entries), xpos = slot of kx.
 bool mf_v2_supported(int nx, int ny, int nz);
+// the split row/column x-y kernels exist for these plane sizes (nx = ny)
+bool mf_split_supported(int nx);
+// x-y kernel blocks of one pass, i.e. the block partials the inverse pass
+// writes (one per (c, z) plane fused, one per row block split)
+int mf_xy_blocks(int ny, int nz, bool split);
 cudaError_t mf_v2_xyf_f32(const void* in, void* spec, const XYArgs& a, cudaStream_t st);
 cudaError_t mf_v2_xyi_f32(int mode, const void* spec, void* out, double* partials, const XYArgs& a,
                           const Scalars* sc, cudaStream_t st);

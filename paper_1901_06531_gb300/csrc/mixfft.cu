@@ -197,6 +197,7 @@ struct mf_ctx {
   long long N;
   int prec;
   int v2 = 0;              // fixed-size transform kernels and their table layout
+  int xy_split = 0;        // with v2: separate row and column kernels for the x-y transform
   cudaStream_t st;
   AxisPlan px, pyh, pz;
   int zS;                  // z-pass tile of the operator (CG loop)
@@ -252,6 +253,7 @@ size_t tw_offset(const mf_ctx* c, bool f32, bool dw, size_t* esz) {
 XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   XYArgs a;
   a.v2 = c->v2;
+  a.split = c->xy_split;
   a.skip = nullptr;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
@@ -407,7 +409,7 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   xa.skip = &sc->stop;
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
-  const int nplanes = 9 * c->nz;
+  const int nplanes = mf_xy_blocks(c->ny, c->nz, c->xy_split != 0);
   if (!c->cap_st) {
     const cudaError_t ec = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
     if (ec != cudaSuccess) { c->cap_st = nullptr; return cuda_status(ec); }
@@ -829,15 +831,17 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   if (nx < 4 || ny < 4 || nz < 2 || nx > 256 || ny > 256 || nz > 256) return MF_INVALID_ARG;
   if ((nx & 1) || (ny & 1) || !smooth_size(nx) || !smooth_size(ny) || !smooth_size(nz))
     return MF_INVALID_ARG;
-  // one component's x-y plane must fit in shared memory (FP64 residual)
-  if ((size_t)(ny / 2) * nx * sizeof(double2) + (size_t)(nx + ny) * 20 > 200 * 1024)
-    return MF_INVALID_ARG;
+  // one component's x-y plane must fit in shared memory (FP64 residual),
+  // unless the split row/column kernels serve the plane
+  const bool big_plane = (size_t)(ny / 2) * nx * sizeof(double2) + (size_t)(nx + ny) * 20 > 200 * 1024;
+  if (big_plane && !(mf_v2_supported(nx, ny, nz) && mf_split_supported(nx))) return MF_INVALID_ARG;
   mf_ctx* c = new (std::nothrow) mf_ctx();
   if (!c) return MF_INVALID_ARG;
   c->nx = nx; c->ny = ny; c->nz = nz;
   c->N = (long long)nx * ny * nz;
   c->prec = precision;
   c->v2 = mf_v2_supported(nx, ny, nz) ? 1 : 0;
+  c->xy_split = big_plane ? 1 : 0;
   c->st = (cudaStream_t)stream;
   if (!make_plan(nx, &c->px) || !make_plan(ny / 2, &c->pyh) || !make_plan(nz, &c->pz)) {
     delete c;
@@ -1347,6 +1351,16 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
     *J_out = J;
   }
   if (cg_its_out) *cg_its_out = hc.its;
+  return MF_OK;
+}
+
+int mf_set_xy_split(mf_ctx* c, int split) {
+  if (!c || (split != 0 && split != 1)) return MF_INVALID_ARG;
+  if (split && !(c->v2 && mf_split_supported(c->nx))) return MF_INVALID_ARG;
+  const bool big_plane = (size_t)(c->ny / 2) * c->nx * sizeof(double2) + (size_t)(c->nx + c->ny) * 20 > 200 * 1024;
+  if (!split && big_plane) return MF_INVALID_ARG;
+  if (c->xy_split != split) free_cg_graph(c);   // the captured loop holds the old kernels
+  c->xy_split = split;
   return MF_OK;
 }
 

@@ -141,6 +141,7 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
 
   XYArgs xa;
   xa.v2 = 0;
+  xa.split = 0;
   xa.skip = nullptr;
   xa.nx = nx; xa.ny = ny; xa.nz = nz; xa.N = N;
   xa.px = px; xa.pyh = pyh;

@@ -385,6 +385,10 @@ cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spe
 }
 
 bool mf_v2_supported(int nx, int ny, int nz) {
-  auto ok = [](int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128; };
+  auto ok = [](int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 256; };
   return nx == ny && ok(nx) && ok(nz);
 }
+
+bool mf_split_supported(int nx) { return nx == 32 || nx == 256; }
+
+int mf_xy_blocks(int ny, int nz, bool split) { return split ? 9 * nz * (ny / 16) : 9 * nz; }

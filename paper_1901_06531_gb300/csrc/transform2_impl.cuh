@@ -3,6 +3,7 @@
 #pragma once
 
 #include "transform2.cuh"
+#include "transform3.cuh"
 
 namespace tr2 {
 
@@ -58,6 +59,13 @@ cudaError_t launch_zp(void* spec, const ZArgs& a, cudaStream_t st) {
 template <typename T>
 cudaError_t xyf(const void* in, void* spec, const XYArgs& a, cudaStream_t st) {
   const typename IOT<T>::t* p = (const typename IOT<T>::t*)in;
+  if (a.split) {
+    switch (a.nx) {
+      case 32: return tr3::xyf<T, 32>(in, spec, a, st);
+      case 256: return tr3::xyf<T, 256>(in, spec, a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.nx) {
     case 16: return launch_xyf<T, 16>(p, spec, a, st);
     case 32: return launch_xyf<T, 32>(p, spec, a, st);
@@ -73,6 +81,13 @@ template <typename T, int MODE>
 cudaError_t xyi_m(const void* spec, void* out, double* partials, const XYArgs& a, const Scalars* sc,
                   cudaStream_t st) {
   typename IOT<T>::t* o = (typename IOT<T>::t*)out;
+  if (a.split) {
+    switch (a.nx) {
+      case 32: return tr3::xyi<T, 32, MODE>(spec, out, partials, a, sc, st);
+      case 256: return tr3::xyi<T, 256, MODE>(spec, out, partials, a, sc, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.nx) {
     case 16: return launch_xyi<T, 16, MODE>(spec, o, partials, a, sc, st);
     case 32: return launch_xyi<T, 32, MODE>(spec, o, partials, a, sc, st);
@@ -102,6 +117,7 @@ cudaError_t zp_m(void* spec, const ZArgs& a, cudaStream_t st) {
     case 64: return launch_zp<T, 64, MODE>(spec, a, st);
     case 96: return launch_zp<T, 96, MODE>(spec, a, st);
     case 128: return launch_zp<T, 128, MODE>(spec, a, st);
+    case 256: return launch_zp<T, 256, MODE>(spec, a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -232,3 +232,39 @@ def test_adjoint_full_size_directional_derivative():
             pm = PARAMS.copy(); pm[a, b] *= 1 - h
             fd = (J_of(pp, sc) - J_of(pm, sc)) / (2 * h * PARAMS[a, b])
             assert abs(fd - g[a, b]) <= 2e-3 * max(abs(fd), 1e-3 * np.max(np.abs(g))), (a, b, fd, g[a, b])
+
+
+@pytest.mark.slow
+def test_adjoint_256_directional_derivative():
+    """256^3 (split x-y kernels), two phases, lognormal (sigma 0.3) voxel
+    scale, P11 = 0.05 with the rotation fixed, FP32 inner: the adjoint's
+    dJ/ds . e against the central difference of two full solves along a
+    random scale direction e, and dJ/dmu of the inclusion phase likewise."""
+    import torch
+    mf = lib()
+    n = 256
+    shape = (n, n, n)
+    ph = inputs.periodic_sphere_phase(shape, [(n / 2, n / 2, n / 2)], 0.3 * n)
+    sc = inputs.lognormal_scale(shape, 0.3, 12)
+    mask, target, wF, wP = uniaxial()
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    kw = dict(tol_newton=1e-10, tol_cg=1e-12, cg_rel=1e-4, max_cg=20000)
+
+    def J_of(params, s):
+        ctx.set_material(mf.MF_NEOHOOKE, params, ph, scale=s)
+        out = ctx.solve(mask, target, **kw)
+        return float(np.dot(wF, out["Fbar"][-1]) + np.dot(wP, out["Pbar"][-1]))
+
+    J0 = J_of(PARAMS, sc)
+    ds = torch.zeros(ctx.N, dtype=torch.float64, device=ctx.device)
+    J, g, its = ctx.adjoint(mask[-1], wF, wP, tol_cg=1e-30, cg_rel=1e-6, max_cg=20000, dscale=ds)
+    assert abs(J - J0) < 1e-12 * max(1.0, abs(J0))
+    e = np.random.default_rng(4).normal(size=shape) * sc
+    h = 1e-3
+    fd = (J_of(PARAMS, sc + h * e) - J_of(PARAMS, sc - h * e)) / (2 * h)
+    ad = float(np.sum(ds.cpu().numpy().reshape(shape) * e))
+    assert abs(fd - ad) <= 2e-3 * abs(fd), (fd, ad)
+    pp = PARAMS.copy(); pp[1, 0] *= 1 + h
+    pm = PARAMS.copy(); pm[1, 0] *= 1 - h
+    fd = (J_of(pp, sc) - J_of(pm, sc)) / (2 * h * PARAMS[1, 0])
+    assert abs(fd - g[1, 0]) <= 2e-3 * abs(fd), (fd, g[1, 0])

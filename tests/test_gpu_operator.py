@@ -277,3 +277,75 @@ def test_full_size_polycrystal_operator_and_residual():
         assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
         del ctx
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_split_xy_kernels_match_oracle(prec):
+    """The separate row (x) and column (y) kernels of large planes, forced on
+    a 32^3 cell: operator and residual against the oracle, FP64 to 1e-12,
+    FP32 operator to 3e-6 (norm)."""
+    import torch
+    mf = lib()
+    shape = (32, 32, 32)
+    ctx, om, F = make(mf, shape, prec, "svk", seed=31, scale=True)
+    ctx.set_xy_split(1)
+    ctx.constitutive()
+    P, K = om.PK(F)
+    x = inputs.random_field((32, 32, 32), 32)
+    dt = torch.float32 if prec else torch.float64
+    xt = torch_field(x, dt)
+    yt = torch.full_like(xt, float("nan"))
+    ctx.matvec(xt, yt, MASKS[2])
+    xin = x.astype(np.float32).astype(np.float64) if prec else x
+    ref = osolver.matvec(K, xin, MASKS[2])
+    got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
+    if prec:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-6
+    else:
+        assert rel(got, ref) < 1e-12
+    pbar = np.array([0.05, 0.01, 0.0, -0.01, 0.02, 0.0, 0.0, 0.0, -0.03])
+    b = torch.full((9 * 32 ** 3,), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.residual(MASKS[2], pbar, b)
+    refb = osolver.residual(P, MASKS[2], pbar)
+    assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
+
+
+def test_split_xy_choice_is_validated():
+    mf = lib()
+    ctx = mf.Context(48, 48, 48, mf.MF_FP32_INNER)
+    with pytest.raises(mf.MixFFTError):
+        ctx.set_xy_split(1)          # no split kernels for 48^2 planes
+    big = mf.Context(256, 256, 16, mf.MF_FP32_INNER)
+    with pytest.raises(mf.MixFFTError):
+        big.set_xy_split(0)          # a 256^2 plane does not fit one block
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_256_plane_operator_matches_oracle(prec):
+    """256 x 256 x 16 cell (split x-y kernels): the operator against the
+    oracle, FP64 to 1e-12, FP32 to 3e-6 (norm); the FP64 residual (double-word
+    transforms in the FP32-inner context) to 1e-12."""
+    import torch
+    mf = lib()
+    shape = (256, 256, 16)
+    ctx, om, F = make(mf, shape, prec, "nh", seed=33)
+    ctx.constitutive()
+    P, K = om.PK(F)
+    nx, ny, nz = shape
+    x = inputs.random_field((nz, ny, nx), 34)
+    dt = torch.float32 if prec else torch.float64
+    xt = torch_field(x, dt)
+    yt = torch.full_like(xt, float("nan"))
+    ctx.matvec(xt, yt, MASKS[0])
+    xin = x.astype(np.float32).astype(np.float64) if prec else x
+    ref = osolver.matvec(K, xin, MASKS[0])
+    got = yt.cpu().numpy().astype(np.float64).reshape(ref.shape)
+    if prec:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-6
+    else:
+        assert rel(got, ref) < 1e-12
+    pbar = np.zeros(9)
+    b = torch.empty(9 * nx * ny * nz, dtype=torch.float64, device="cuda")
+    ctx.residual(MASKS[0], pbar, b)
+    refb = osolver.residual(P, MASKS[0], pbar)
+    assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
