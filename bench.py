@@ -103,6 +103,20 @@ def ncu_traffic(kernel):
     return e.get("bytes_per_launch")
 
 
+def replica_throughput(total_ms, steps, dist=None, device="cpu"):
+    """Replicas (one independent cell per rank, no data-path collective): the
+    job's time is the slowest rank's, its throughput all ranks' load steps
+    over that time.  Returns (max_ms, load steps/s)."""
+    world = 1
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -616,11 +630,7 @@ def run_ours(args):
     launches = mf.kernel_launches() - l0
     total_ms = ev0.elapsed_time(ev1)
     step_ms = [a.elapsed_time(b) for a, b in per_step]
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, value = replica_throughput(total_ms, args.steps, dist, "cuda")
     clocks = clk.summary()
 
     # end to end through the C ABI with host buffers: step inputs go in as
