@@ -70,6 +70,11 @@ cudaError_t mf_v2_xyi_dw(const void* spec, double* out, double* partials, const 
 // fixed-size ones do not (nothing reads them).
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
                                const XYArgs& xa, const ZArgs& za, bool dw, cudaStream_t st);
+// The same residual with FP32 transforms (fixed-size kernels; xa, za with the
+// FP32 tables): P rounded into Pf, b through bf, both 9N floats of scratch.
+// Accurate to FP32 relative to abs(P): for residuals far from convergence.
+cudaError_t mf_launch_residual_f32(const double* P, float* Pf, void* spec, float* bf, double* b,
+                                   const XYArgs& xa, const ZArgs& za, cudaStream_t st);
 // which: 0 x-y forward of t, 1 z-pass, 2 x-y inverse with the CG residual update
 cudaError_t mf_launch_project_part(int which, bool f32, const void* t, void* spec, void* r,
                                    double* partials, const XYArgs& xa, const ZArgs& za,

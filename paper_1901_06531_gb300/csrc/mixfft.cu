@@ -334,7 +334,18 @@ int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false) 
 
 bool operator_ready(const mf_ctx* c) { return c->f32() ? c->have_H : c->have_K; }
 
-int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out) {
+// fp32: the residual with FP32 transforms (double-word outer arithmetic on
+// the fixed-size kernels only); its error is FP32 rounding relative to abs(P),
+// harmless while the residual is large
+int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out,
+                 bool fp32 = false) {
+  if (fp32 && c->dw_residual()) {
+    ZArgs za = z_args(c, true, mask, -1.0 / (double)c->N);
+    for (int k = 0; k < 9; ++k) za.add[k] = mask[k] ? pbar[k] : 0.0;
+    za.mean_out = mean_out;
+    return cuda_status(mf_launch_residual_f32(c->at<double>(c->oP), c->at<float>(c->oAp), c->ws + c->ospec,
+                                              c->at<float>(c->op2), b, xy_args(c, true), za, c->st));
+  }
   const bool dw = c->dw_residual();
   ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N, dw);
   if (c->v2) za.S = c->zSr;
@@ -611,6 +622,7 @@ struct Runner {
   int status = MF_OK;
   int k = 0, nn = 0, ncg = 0;
   double ratio = INFINITY;
+  bool res_f32 = false;          // the last residual came from FP32 transforms
   Defl defl;
 
   int init() {
@@ -676,7 +688,11 @@ struct Runner {
     double* F = c->at<double>(c->oF);
     const long long N = c->N;
     if (nn >= max_newton) return MF_NOT_CONVERGED;
-    int s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores));
+    // the first residual of a load step is large (the predictor moved F-bar):
+    // FP32 transforms are accurate enough for its correction; the later ones,
+    // which decide convergence, keep FP64 accuracy
+    res_f32 = (nn == 0) && c->dw_residual();
+    int s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores), res_f32);
     if (s) return s;
     defl.m = 0;
     if (c->f32()) {
@@ -744,7 +760,8 @@ struct Runner {
         for (int q = 0; q < 9; ++q) fn += h->meanF_new[q] * h->meanF_new[q];
         ratio = sqrt(h->dF2max) / sqrt(fn);
         ++nn;
-        const bool last = ratio < tol_newton;
+        // never stop on a correction from an FP32 residual
+        const bool last = ratio < tol_newton && !res_f32;
         s = launch_constitutive(last);
         if (!s) {
           phase = last ? kAfterFinal : kAfterConst;

@@ -20,6 +20,7 @@
 //   plane position p holds z-frequency kz = zk(p) during the z-pass.
 // The 1/N of the forward transform is applied once, in the z-pass.
 #include "common.cuh"
+#include "dw.cuh"
 
 #include "launch.h"
 
@@ -338,6 +339,42 @@ cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* p
   e = launch_zpass<double, 1>(spec, za, st);
   if (e != cudaSuccess) return e;
   return launch_xy_inverse<double, 2>(spec, b, nullptr, partials, 1.0, xa, st);
+}
+
+namespace {
+
+// FP64 -> FP32 rounded through the double-word split (no FP64 instruction)
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const dw d = dw_split(a[i]);
+    b[i] = __fadd_rn(d.hi, d.lo);
+  }
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = f32_as_f64(a[i]);
+}
+
+}  // namespace
+
+cudaError_t mf_launch_residual_f32(const double* P, float* Pf, void* spec, float* bf, double* b,
+                                   const XYArgs& xa, const ZArgs& za, cudaStream_t st) {
+  if (!xa.v2) return cudaErrorInvalidValue;
+  const long long n9 = 9 * xa.N;
+  k_d2f<<<152 * 8, 256, 0, st>>>(P, Pf, n9);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = mf_v2_xyf_f32(Pf, spec, xa, st);
+  if (e == cudaSuccess) e = mf_v2_zp_f32(1, spec, za, st);
+  if (e == cudaSuccess) e = mf_v2_xyi_f32(0, spec, bf, nullptr, xa, nullptr, st);
+  if (e == cudaSuccess) {
+    k_f2d<<<152 * 8, 256, 0, st>>>(bf, b, n9);
+    e = cudaGetLastError();
+  }
+  g_mf_launches += 2;
+  return e;
 }
 
 cudaError_t mf_launch_project(bool f32, const void* t, void* spec, void* out, int inv_mode,
