@@ -103,6 +103,9 @@ int mf_set_F(mf_ctx* ctx, const double* F_host);
  *   tol_cg: CG stops when sqrt(sum_v |r_v|^2 / N) <= tol_cg (MF_FP64), or
  *           <= max(tol_cg, cg_rel * initial value) (MF_FP32_INNER);
  *   cg_rel: relative CG forcing term for MF_FP32_INNER (ignored for MF_FP64);
+ *           the first Newton iteration of each step uses sqrt(cg_rel), and
+ *           its residual is computed with FP32 transforms (it is always
+ *           followed by another iteration: a step never ends on it);
  *   Fbar_out, Pbar_out: host, nsteps*9 doubles or NULL: <F>, <P> per step;
  *   iters_out: host, nsteps*2 int32 or NULL: Newton iterations and total CG
  *              iterations per step.

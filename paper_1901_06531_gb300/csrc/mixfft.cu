@@ -705,7 +705,10 @@ struct Runner {
                                                kPointwiseBlocks, sc, c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
     }
-    s = launch_cg(c, m, tol_cg, c->f32() ? cg_rel : 0.0, max_cg);
+    // FP32 inner solves: forcing sqrt(cg_rel) for the first Newton iteration
+    // of a step (its correction is followed by at least one more), cg_rel
+    // for the others
+    s = launch_cg(c, m, tol_cg, c->f32() ? (nn == 0 ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
     if (s) return s;
     void* corr = c->ws + c->ox;
     if (c->f32()) {
