@@ -655,7 +655,10 @@ def run_ours(args):
     steps(ctx, 0, 1)
     ctx.constitutive()
     m0 = mask[0]
-    kms = ctx.time_kernels(m0, reps=20)
+    # per-kernel times: as back-to-back graph nodes (what the CG graph runs)
+    # and with events around every single launch
+    kms = ctx.time_kernels(m0, reps=20, graph=True)
+    kms_single = ctx.time_kernels(m0, reps=20)
     bres = torch.empty(9 * N, dtype=torch.float64, device="cuda")
     res_ms = {}
     for name, arith in (("double_word", mf.MF_OUTER_DOUBLE_WORD), ("fp64", mf.MF_OUTER_FP64)):
@@ -766,8 +769,11 @@ def run_ours(args):
                      "traffic": ncu_traffic(KERNELS[dom]),
                      "algorithmic_bytes_per_voxel": ALGO_BYTES_F32[dom]},
         "kernels_fp32": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9,
-                             "frac": b * N / (t * 1e-3) / 1e9 / peak}
-                         for k, t, b in zip(KERNELS, kms, ALGO_BYTES_F32)},
+                             "frac": b * N / (t * 1e-3) / 1e9 / peak, "ms_single_launch": float(t1)}
+                         for k, t, t1, b in zip(KERNELS, kms, kms_single, ALGO_BYTES_F32)},
+        "kernel_timing": ("ms: 20 (L2 flush, launch) pairs as one CUDA graph, events around it, minus the "
+                          "graph of the flushes alone, per launch; ms_single_launch: events around each "
+                          "launch after its flush"),
         "kernels_fp64": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9}
                          for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
         "autotune": {"zpass_tile_columns": ztile,

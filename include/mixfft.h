@@ -206,8 +206,13 @@ int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, const uint8
  * and solution updates, K:p, p.Kp), [1] the x-y forward transform, [2] the
  * z-pass with G-hat-star, [3] the x-y inverse transform with the residual
  * update.  Operands are the context's CG vectors; needs the operator of the
- * last mf_constitutive.  ms_out: host, 4 floats, mean milliseconds per launch. */
-int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
+ * last mf_constitutive.  graph 0: events around every launch (the time
+ * includes the launch's own start-up on the device); graph 1: the reps
+ * (flush, launch) pairs run as one CUDA graph, events around the graph, minus
+ * the same graph without the launches (the kernels as they run back to back
+ * inside the CG graph, plus the write-back of their dirty lines).  ms_out:
+ * host, 4 floats, mean milliseconds per launch. */
+int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, int graph, float* ms_out);
 
 /* Number of kernel launches the library has issued in this process (all
  * contexts); differences around a region count its launches. */

@@ -152,11 +152,14 @@ __device__ __forceinline__ void neohooke_apply(const float (&h)[9], float mu, fl
 
 // TAN 0: packed tangent K45 of type T; 1: neo-Hookean from H; 2: SVK from H.
 // CG true: p = r + beta p', x += alpha' p' first (p' = pin); false: p = pin.
-template <typename T, int TAN, bool CG>
+// FIN (with CG): the last block to finish sums the partials of p.t and sets
+// alpha (the work of k_fin_alpha, without its launch).
+template <typename T, int TAN, bool CG, bool FIN>
 __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin, const T* __restrict__ r,
                                                       T* __restrict__ pout, T* __restrict__ x,
                                                       TangentArgs ta, T* __restrict__ t, long long N,
-                                                      double* __restrict__ partials, const Scalars* sc) {
+                                                      double* __restrict__ partials, Scalars* sc) {
+  static_assert(!FIN || CG, "the fused finish belongs to the CG pass");
   __shared__ double tot[1];
   T beta = (T)0, alpha = (T)0;
   if (CG) {
@@ -225,6 +228,10 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
     double acc[1] = {sizeof(T) == 4 ? acc32.value() : acc64};
     block_sum_cg<1>(acc, tot);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
+    if constexpr (FIN) {
+      double pAp;
+      if (last_block_total(partials, &sc->arrive, &pAp) && threadIdx.x == 0) cg_finish_alpha(pAp, sc);
+    }
   }
 }
 
@@ -247,16 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_fin_alpha(const double* __restrict
   __shared__ double shm[kThreads];
   if (*(volatile const int*)&sc->stop) return;
   const double pAp = col_sum(partials, n, shm);
-  if (threadIdx.x == 0) {
-    sc->pAp = pAp;
-    if (!(pAp > 0.0) || !isfinite(pAp)) {
-      sc->flags |= MF_FLAG_BREAKDOWN;
-      sc->alpha = 0.0;
-      sc->stop = 1;
-    } else {
-      sc->alpha = sc->rr / pAp;
-    }
-  }
+  if (threadIdx.x == 0) cg_finish_alpha(pAp, sc);
 }
 
 __global__ void __launch_bounds__(kThreads) k_fin_beta(const double* __restrict__ partials, int n,
@@ -264,14 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_fin_beta(const double* __restrict_
   __shared__ double shm[kThreads];
   if (*(volatile const int*)&sc->stop) return;
   const double rr = col_sum(partials, n, shm);
-  if (threadIdx.x == 0) {
-    if (!isfinite(rr)) sc->flags |= MF_FLAG_NONFINITE;
-    sc->beta = rr / sc->rr;
-    sc->rr = rr;
-    sc->done = (rr <= sc->thr2N) ? 1 : 0;
-    sc->its += 1;
-    sc->stop = (sc->done || sc->flags || sc->its >= sc->max_its) ? 1 : 0;
-  }
+  if (threadIdx.x == 0) cg_finish_beta(rr, sc);
 }
 
 template <typename T>
@@ -317,17 +308,24 @@ __global__ void k_make_H(const double* __restrict__ F, float* __restrict__ H, lo
 
 cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* x, bool f32, int tan,
                               bool cg, const TangentArgs& ta, void* t, long long N, double* partials,
-                              int nblk, const Scalars* sc, cudaStream_t st) {
-#define MF_TAN(T, K, CGV)                                                                          \
-  k_tangent<T, K, CGV><<<nblk, kThreads, 0, st>>>((const T*)pin, (const T*)r, (T*)pout, (T*)x, ta, \
-                                                  (T*)t, N, partials, sc)
+                              int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha) {
+#define MF_TAN(T, K, CGV, FV)                                                                          \
+  k_tangent<T, K, CGV, FV><<<nblk, kThreads, 0, st>>>((const T*)pin, (const T*)r, (T*)pout, (T*)x, ta, \
+                                                      (T*)t, N, partials, sc)
+#define MF_TAN_CG(T, K)                                       \
+  do {                                                        \
+    if (!cg) MF_TAN(T, K, false, false);                      \
+    else if (fin_alpha && partials) MF_TAN(T, K, true, true); \
+    else MF_TAN(T, K, true, false);                           \
+  } while (0)
   if (f32) {
-    if (tan == 0) { if (cg) MF_TAN(float, 0, true); else MF_TAN(float, 0, false); }
-    else if (tan == 1) { if (cg) MF_TAN(float, 1, true); else MF_TAN(float, 1, false); }
-    else { if (cg) MF_TAN(float, 2, true); else MF_TAN(float, 2, false); }
+    if (tan == 0) MF_TAN_CG(float, 0);
+    else if (tan == 1) MF_TAN_CG(float, 1);
+    else MF_TAN_CG(float, 2);
   } else {
-    if (cg) MF_TAN(double, 0, true); else MF_TAN(double, 0, false);
+    MF_TAN_CG(double, 0);
   }
+#undef MF_TAN_CG
 #undef MF_TAN
   g_mf_launches += 1;
   return cudaGetLastError();
@@ -341,6 +339,7 @@ cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cuda
 
 __global__ void k_cg_batch_init(Scalars* sc, int max_its) {
   sc->its = 0;
+  sc->arrive = 0u;
   sc->max_its = max_its;
   sc->stop = (sc->done || sc->flags) ? 1 : 0;
 }

@@ -175,9 +175,62 @@ struct Scalars {
   int its;            // CG iterations completed
   int stop;           // CG finished (converged, failed or capped): iteration kernels return at once
   int max_its;
-  int pad;
+  unsigned arrive;    // blocks of the current pass that have stored their partial sum
 };
+
+// Grid-wide sum finished by the last block to arrive: every block has stored
+// its partial sum in partials[blockIdx.x] (thread 0 wrote it); thread 0
+// publishes it and counts the block in *arrive.  The block that arrives last
+// adds all partials in a fixed order, leaves the total in *total (read by
+// every thread), resets the counter and returns true; the others return
+// false.  No block waits on another.
+__device__ __forceinline__ bool last_block_total(const double* partials, unsigned* arrive, double* total) {
+  __shared__ unsigned s_last;
+  __shared__ double s_red[32];
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(arrive, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(partials + b);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? s_red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) { s_red[0] = t; *arrive = 0u; }
+  }
+  __syncthreads();
+  *total = s_red[0];
+  return true;
+}
 
 #define MF_FLAG_BREAKDOWN 1
 #define MF_FLAG_NONPOS_J 2
 #define MF_FLAG_NONFINITE 4
+
+// CG scalar updates after the curvature p.Ap and after the new r.r (shared by
+// the one-block finishing kernels and the last blocks of fused passes).
+__device__ __forceinline__ void cg_finish_alpha(double pAp, Scalars* sc) {
+  sc->pAp = pAp;
+  if (!(pAp > 0.0) || !isfinite(pAp)) {
+    sc->flags |= MF_FLAG_BREAKDOWN;
+    sc->alpha = 0.0;
+    sc->stop = 1;
+  } else {
+    sc->alpha = sc->rr / pAp;
+  }
+}
+
+__device__ __forceinline__ void cg_finish_beta(double rr, Scalars* sc) {
+  if (!isfinite(rr)) sc->flags |= MF_FLAG_NONFINITE;
+  sc->beta = rr / sc->rr;
+  sc->rr = rr;
+  sc->done = (rr <= sc->thr2N) ? 1 : 0;
+  sc->its += 1;
+  sc->stop = (sc->done || sc->flags || sc->its >= sc->max_its) ? 1 : 0;
+}

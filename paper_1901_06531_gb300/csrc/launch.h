@@ -8,6 +8,7 @@ struct XYArgs {
   int v2;          // 1: fixed-size kernels (transform2*.cu), tables of that layout
   int split;       // with v2: separate row (x) and column (y) kernels (transform3.cuh)
   const int* skip; // if non-null and *skip != 0 the kernel returns at once (finished CG)
+  int fin;         // fused (v2, not split) inverse pass with the CG update: finish beta in its last block
   int nx, ny, nz;
   long long N;
   AxisPlan px;     // length nx
@@ -95,9 +96,11 @@ struct TangentArgs {
   const float* scale;    // per-voxel scale or null
 };
 // tan: 0 packed K (FP64 or FP32), 1 neo-Hookean from H, 2 SVK from H (FP32).
+// fin_alpha (cg, partials non-null): the pass also finishes alpha (last block),
+// so no k_fin_alpha follows it.
 cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* x, bool f32, int tan,
                               bool cg, const TangentArgs& ta, void* t, long long N, double* partials,
-                              int nblk, const Scalars* sc, cudaStream_t st);
+                              int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha = false);
 cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st);

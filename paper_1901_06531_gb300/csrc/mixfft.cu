@@ -219,6 +219,7 @@ struct mf_ctx {
   bool cufft_bound = false;
   // CG loop as one graph launch: a WHILE node whose body is two iterations
   cudaGraph_t cg_graph = nullptr;
+  int cg_body_kernels = 0;      // kernel launches per pass of the CG graph's body
   cudaGraphExec_t cg_exec = nullptr;
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
@@ -255,6 +256,7 @@ XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   a.v2 = c->v2;
   a.split = c->xy_split;
   a.skip = nullptr;
+  a.fin = 0;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
   size_t esz;
@@ -418,6 +420,9 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   XYArgs xa = xy_args(c, f32);
   za.skip = &sc->stop;
   xa.skip = &sc->stop;
+  // the fused x-y inverse kernel finishes beta itself; the split and generic
+  // kernels leave it to k_fin_beta
+  xa.fin = (xa.v2 && !xa.split) ? 1 : 0;
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
   const int nplanes = mf_xy_blocks(c->ny, c->nz, c->xy_split != 0);
@@ -449,11 +454,13 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
     e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc,
-                          cs);
-    if (e == cudaSuccess) e = mf_launch_fin_alpha(part, kPointwiseBlocks, sc, cs);
+                          cs, true);
     if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, cs);
-    if (e == cudaSuccess) e = mf_launch_fin_beta(part, nplanes, sc, cs);
+    if (e == cudaSuccess && !xa.fin) e = mf_launch_fin_beta(part, nplanes, sc, cs);
   }
+  // per iteration: tangent, the transform passes (two more for the split x-y
+  // kernels), k_fin_beta unless fused; k_cg_cond once per body
+  c->cg_body_kernels = 2 * (1 + ((xa.v2 && xa.split) ? 5 : 3) + (xa.fin ? 0 : 1)) + 1;
   if (e == cudaSuccess) e = mf_launch_cg_cond(sc, h, cs);
   cudaGraph_t captured = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
@@ -757,8 +764,8 @@ struct Runner {
           break;
         }
         ncg += h->its;
-        // kernels the CG graph ran: 13 per pass of its two-iteration body
-        g_mf_launches += 13LL * (h->its == 0 ? 1 : (h->its + 1) / 2);
+        // kernels the CG graph ran: cg_body_kernels per pass of its two-iteration body
+        g_mf_launches += (long long)c->cg_body_kernels * (h->its == 0 ? 1 : (h->its + 1) / 2);
         double fn = 0.0;
         for (int q = 0; q < 9; ++q) fn += h->meanF_new[q] * h->meanF_new[q];
         ratio = sqrt(h->dF2max) / sqrt(fn);
@@ -1255,8 +1262,8 @@ int mf_get_fields(mf_ctx* c, double* F_host, double* P_host) {
   return cuda_status(e);
 }
 
-int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
-  if (!c || !mask || !ms_out || reps < 1) return MF_INVALID_ARG;
+int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, int graph, float* ms_out) {
+  if (!c || !mask || !ms_out || reps < 1 || (graph != 0 && graph != 1)) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   if (!operator_ready(c)) return MF_INVALID_ARG;
   const bool f32 = c->f32();
@@ -1268,23 +1275,62 @@ int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
   // operands: a CG state made of the context's vectors (values are not used
   // for anything but timing); alpha = beta = 0 keeps them bounded
   cudaError_t e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
+  if (e == cudaSuccess && graph && !c->cap_st) {
+    e = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) c->cap_st = nullptr;
+  }
   cudaEvent_t e0, e1;
   if (e != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
+  auto flush = [&](cudaStream_t s, int r) {   // L2 flush: a memset larger than L2
+    return cudaMemsetAsync(c->ws + c->ob, r & 0xff, 9 * c->N * sizeof(double), s);
+  };
+  auto kernel = [&](cudaStream_t s, int which) {
+    if (which == 0)
+      return mf_launch_tangent(c->ws + c->op, c->ws + c->or_, c->ws + c->op2, c->ws + c->ox, f32, tangent_kind(c),
+                               true, ta, c->ws + c->oAp, c->N, part, kPointwiseBlocks, sc, s);
+    return mf_launch_project_part(which - 1, f32, c->ws + c->oAp, c->ws + c->ospec, c->ws + c->or_, part, xa, za,
+                                  sc, s);
+  };
+  // graph mode: `reps` (flush, kernel) pairs captured as one graph, timed
+  // with events around one launch of it, minus the same graph of flushes
+  // alone; what is left is the kernels and their share of the gaps between
+  // graph nodes (and the write-back of their dirty lines by the next flush)
+  auto graph_ms = [&](int which, float* ms) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t ee = cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeRelaxed);
+    for (int r = 0; r < reps && ee == cudaSuccess; ++r) {
+      ee = flush(c->cap_st, r);
+      if (ee == cudaSuccess && which >= 0) ee = kernel(c->cap_st, which);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_st, &g);
+    if (ee == cudaSuccess) ee = ec;
+    if (ee == cudaSuccess) ee = cudaGraphInstantiate(&ge, g, 0);
+    if (ee == cudaSuccess) ee = cudaGraphLaunch(ge, c->st);   // untimed: first touches
+    if (ee == cudaSuccess) ee = cudaEventRecord(e0, c->st);
+    if (ee == cudaSuccess) ee = cudaGraphLaunch(ge, c->st);
+    if (ee == cudaSuccess) ee = cudaEventRecord(e1, c->st);
+    if (ee == cudaSuccess) ee = cudaEventSynchronize(e1);
+    if (ee == cudaSuccess) ee = cudaEventElapsedTime(ms, e0, e1);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    return ee;
+  };
+  float base = 0.f;
+  if (graph) e = graph_ms(-1, &base);
   for (int which = 0; which < 4 && e == cudaSuccess; ++which) {
+    if (graph) {
+      float ms = 0.f;
+      e = graph_ms(which, &ms);
+      ms_out[which] = (ms - base) / (float)reps;
+      continue;
+    }
     double tot = 0.0;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-      e = cudaMemsetAsync(c->ws + c->ob, r & 0xff, 9 * c->N * sizeof(double), c->st);   // L2 flush
+      e = flush(c->st, r);
       if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
-      if (e == cudaSuccess) {
-        if (which == 0)
-          e = mf_launch_tangent(c->ws + c->op, c->ws + c->or_, c->ws + c->op2, c->ws + c->ox, f32,
-                                tangent_kind(c), true, ta, c->ws + c->oAp, c->N, part, kPointwiseBlocks,
-                                sc, c->st);
-        else
-          e = mf_launch_project_part(which - 1, f32, c->ws + c->oAp, c->ws + c->ospec, c->ws + c->or_,
-                                     part, xa, za, sc, c->st);
-      }
+      if (e == cudaSuccess) e = kernel(c->st, which);
       if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -1295,6 +1341,7 @@ int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, float* ms_out) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (e != cudaSuccess) cudaGetLastError();
   return cuda_status(e);
 }
 
@@ -1346,7 +1393,7 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
   Scalars hc;
   if (!s) s = read_scalars(c, &hc);
   if (s) return s;
-  g_mf_launches += 13LL * (hc.its == 0 ? 1 : (hc.its + 1) / 2);
+  g_mf_launches += (long long)c->cg_body_kernels * (hc.its == 0 ? 1 : (hc.its + 1) / 2);
   bool clear = false;
   s = cg_outcome(c, hc, &clear);
   if (s) return s;

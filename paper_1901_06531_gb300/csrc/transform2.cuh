@@ -283,14 +283,16 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
 
 // ------------------------------------------------------------------ inverse
 // MODE 0: out[c] = y.  MODE 2: out[c] = y, partial sum y^2.  MODE 3: out[c] -=
-// alpha y (alpha from sc), partial sum out^2.
+// alpha y (alpha from sc), partial sum out^2; with fin the last block to
+// finish also sums the partials and updates beta, r.r and the stop flag (the
+// work of k_fin_beta, without its launch).
 template <typename T, int NX, int MODE>
 __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t* __restrict__ spec,
                                                   typename IOT<T>::t* __restrict__ out,
                                                   double* __restrict__ partials, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
-                                                  const int* __restrict__ gpos, const Scalars* sc,
-                                                  const int* skip) {
+                                                  const int* __restrict__ gpos, Scalars* sc,
+                                                  const int* skip, int fin) {
   typedef XYShape<T, NX> Sh;
   constexpr int TPB = xy_threads<T>();
   typedef typename CT<T>::t C;
@@ -377,13 +379,24 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
       }
     }
   };
-  if constexpr (sizeof(C) == 8 && RowPlan<H>::NST == 2) {
-    // last inverse x stage straight to global memory (consecutive threads
-    // take consecutive butterflies of a row: 64-byte row segments)
+  // The last inverse x stage writes global memory directly when the outputs
+  // one butterfly step r covers (e = j0 + M0 r, M0 consecutive elements of a
+  // row per step) fill whole 32-byte sectors.  Otherwise (H = 24, 48: M0 = 3)
+  // the read-modify-write of r (MODE 3) would load sectors that the previous
+  // step has just stored, and every load would wait for those stores; the
+  // stage then runs in shared memory and a coalesced loop does the update.
+  constexpr int M0 = H / fft2::rad(H, 0);
+  constexpr bool kDirect = sizeof(C) == 8 && RowPlan<H>::NST == 2 && (MODE != 3 || (M0 * 8) % 32 == 0);
+  if constexpr (kDirect) {
+    // consecutive threads take consecutive butterflies of a row
     fft2::stage_io<C, H, NX, 0, true, NY, 1, PX, 0, 1, false>(
         twx, [&](int, int i, int) { return buf[i]; },
         [&](int q, int, int e, C v) { emit((long long)q * H + e, v); });
   } else {
+    if constexpr (sizeof(C) == 8 && RowPlan<H>::NST == 2) {
+      fft2::stage<C, H, NX, 0, true, NY, 1, PX, 0, 1, false>(buf, twx);
+      __syncthreads();
+    }
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
       const int y = idx / H, j = idx - (idx / H) * H;
@@ -399,6 +412,10 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
       double s = (threadIdx.x < (TPB >> 5)) ? red[threadIdx.x] : 0.0;
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    }
+    if (MODE == 3 && fin) {
+      double rr;
+      if (last_block_total(partials, &sc->arrive, &rr) && threadIdx.x == 0) cg_finish_beta(rr, sc);
     }
   }
 }

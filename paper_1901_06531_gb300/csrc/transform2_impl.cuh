@@ -25,8 +25,10 @@ cudaError_t launch_xyi(const void* spec, typename IOT<T>::t* out, double* partia
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  // the scalar block is written only by the fused finish (a.fin, MODE 3)
   k_xyi<T, NX, MODE><<<9 * a.nz, xy_threads<T>(), sm, st>>>((const C*)spec, out, partials, a.nz, a.N,
-                                                     (const C*)a.twx, a.xpos, sc, a.skip);
+                                                     (const C*)a.twx, a.xpos, const_cast<Scalars*>(sc),
+                                                     a.skip, MODE == 3 ? a.fin : 0);
   ++g_mf_launches;
   return cudaGetLastError();
 }

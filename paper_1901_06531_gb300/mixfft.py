@@ -48,7 +48,7 @@ _lib.mf_get_tangent.argtypes = [_vp, _vp]
 _lib.mf_matvec.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.mf_residual_noalloc.argtypes = [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]
-_lib.mf_time_kernels.argtypes = [_vp, _vp, _i, _vp]
+_lib.mf_time_kernels.argtypes = [_vp, _vp, _i, _i, _vp]
 _lib.mf_cufft_workspace_bytes.argtypes = [_vp]
 _lib.mf_cufft_workspace_bytes.restype = _sz
 _lib.mf_cufft_bind.argtypes = [_vp, _vp, _sz]
@@ -257,13 +257,14 @@ class Context:
                                                _ptr(meanP)))
         return meanP
 
-    def time_kernels(self, mask, reps=20):
+    def time_kernels(self, mask, reps=20, graph=False):
         """Mean ms per launch of the four kernels of a CG iteration (tangent
         pass, x-y forward, z-pass, x-y inverse with residual update), each
-        after an L2 flush."""
+        after an L2 flush; graph: timed as back-to-back graph nodes (see
+        mf_time_kernels)."""
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         ms = np.zeros(4, dtype=np.float32)
-        _check("mf_time_kernels", _lib.mf_time_kernels(self.h, _ptr(m), reps, _ptr(ms)))
+        _check("mf_time_kernels", _lib.mf_time_kernels(self.h, _ptr(m), reps, 1 if graph else 0, _ptr(ms)))
         return ms.astype(np.float64)
 
     # -- cuFFT comparison path -------------------------------------------

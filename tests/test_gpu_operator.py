@@ -222,7 +222,7 @@ def test_outer_arith_rejects_unknown():
     assert e.value.status == mf.MF_INVALID_ARG
 
 
-@pytest.mark.parametrize("shape", SHAPES_V2[:4])
+@pytest.mark.parametrize("shape", SHAPES_V2)
 def test_fixed_size_kernels_fp32(shape):
     import torch
     mf = lib()
@@ -349,3 +349,19 @@ def test_256_plane_operator_matches_oracle(prec):
     ctx.residual(MASKS[0], pbar, b)
     refb = osolver.residual(P, MASKS[0], pbar)
     assert rel(b.cpu().numpy().reshape(refb.shape), refb) < 1e-12
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_time_kernels_modes(graph):
+    """Both timing modes of mf_time_kernels return four positive finite
+    per-launch times; an unknown mode is rejected."""
+    mf = lib()
+    ctx, _, _ = make(mf, (32, 32, 32), mf.MF_FP32_INNER, model="svk")
+    ctx.constitutive()
+    mask = np.array([1, 0, 0, 0, 1, 0, 0, 0, 1], dtype=np.uint8)
+    ms = ctx.time_kernels(mask, reps=3, graph=graph)
+    assert ms.shape == (4,) and np.all(np.isfinite(ms)) and np.all(ms > 0)
+    m = np.ascontiguousarray(mask)
+    out = np.zeros(4, dtype=np.float32)
+    st = mf._lib.mf_time_kernels(ctx.h, m.ctypes.data, 3, 2, out.ctypes.data)
+    assert st == mf.MF_INVALID_ARG

@@ -137,6 +137,22 @@ def test_fp32_inner_polycrystal():
     assert rel(F, ref["F"]) < 3e-8, rel(F, ref["F"])
 
 
+@pytest.mark.parametrize("n", [48, 96])
+def test_fp32_inner_cg_radix3_sizes(n):
+    """FP32-inner solves on 48^3 and 96^3 cells (the CG update of the x-y
+    inverse pass takes its shared-memory route there) against the FP64
+    solve of the same cell: averages to 1e-9."""
+    mf = lib()
+    cell = inputs.batch_of_cells(1, 5, sizes=(n,), nsteps=2)[0]
+    outs = []
+    for prec in (mf.MF_FP32_INNER, mf.MF_FP64):
+        ctx = mf.Context(n, n, n, prec)
+        ctx.set_material(mf.MF_NEOHOOKE, cell["params"], cell["phase"])
+        outs.append(ctx.solve(cell["mask"], cell["target"], 1e-9, 1e-11, cg_rel=1e-4))
+    assert rel(outs[0]["Fbar"], outs[1]["Fbar"]) < 1e-9
+    assert np.max(np.abs(outs[0]["Pbar"] - outs[1]["Pbar"])) < 1e-9
+
+
 def test_radix3_grid_solve():
     mf = lib()
     nx, ny, nz = 24, 12, 18
