@@ -136,22 +136,22 @@ __global__ void __launch_bounds__(kThreads) k_adj_fin(const double* __restrict__
 }  // namespace
 
 cudaError_t mf_launch_adj_rhs_fill(void* q, bool f32, long long N, const AdjWeights& w, cudaStream_t st) {
-  if (f32) k_fill_uniform<float><<<152 * 8, kThreads, 0, st>>>((float*)q, N, w);
-  else k_fill_uniform<double><<<152 * 8, kThreads, 0, st>>>((double*)q, N, w);
+  if (f32) k_fill_uniform<float><<<stride_grid(N), kThreads, 0, st>>>((float*)q, N, w);
+  else k_fill_uniform<double><<<stride_grid(N), kThreads, 0, st>>>((double*)q, N, w);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t mf_launch_adj_rhs_add(void* t, bool f32, long long N, const AdjWeights& w, cudaStream_t st) {
-  if (f32) k_add_uniform<float><<<152 * 8, kThreads, 0, st>>>((float*)t, N, w);
-  else k_add_uniform<double><<<152 * 8, kThreads, 0, st>>>((double*)t, N, w);
+  if (f32) k_add_uniform<float><<<stride_grid(N), kThreads, 0, st>>>((float*)t, N, w);
+  else k_add_uniform<double><<<stride_grid(N), kThreads, 0, st>>>((double*)t, N, w);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t mf_launch_to_double(const void* y, double* b, bool f32, long long n, cudaStream_t st) {
-  if (f32) k_to_double<float><<<152 * 8, kThreads, 0, st>>>((const float*)y, b, n);
-  else k_to_double<double><<<152 * 8, kThreads, 0, st>>>((const double*)y, b, n);
+  if (f32) k_to_double<float><<<stride_grid(n), kThreads, 0, st>>>((const float*)y, b, n);
+  else k_to_double<double><<<stride_grid(n), kThreads, 0, st>>>((const double*)y, b, n);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

@@ -358,7 +358,7 @@ cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaS
 
 cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, const Scalars* sc,
                                  cudaStream_t st) {
-  const int g = 152 * 8;
+  const int g = stride_grid(n, kThreads);
   if (f32) k_axpy_alpha<float><<<g, kThreads, 0, st>>>((float*)x, (const float*)p, n, sc);
   else k_axpy_alpha<double><<<g, kThreads, 0, st>>>((double*)x, (const double*)p, n, sc);
   g_mf_launches += 1;
@@ -366,7 +366,7 @@ cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, 
 }
 
 cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_t st) {
-  k_make_H<<<152 * 8, kThreads, 0, st>>>(F, H, N);
+  k_make_H<<<stride_grid(N, kThreads), kThreads, 0, st>>>(F, H, N);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
@@ -379,7 +379,7 @@ cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, c
 
 cudaError_t mf_launch_axpy_last(void* x, const void* p0, const void* p1, bool f32, long long n,
                                 const Scalars* sc, cudaStream_t st) {
-  const int g = 152 * 8;
+  const int g = stride_grid(n, kThreads);
   if (f32) k_axpy_last<float><<<g, kThreads, 0, st>>>((float*)x, (const float*)p0, (const float*)p1, n, sc);
   else k_axpy_last<double><<<g, kThreads, 0, st>>>((double*)x, (const double*)p0, (const double*)p1, n, sc);
   g_mf_launches += 1;

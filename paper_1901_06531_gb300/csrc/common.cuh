@@ -14,6 +14,14 @@
 
 #define MF_MAX_STAGES 10
 
+// Grid of a grid-stride elementwise pass over n items with `threads` per
+// block: one item per thread for small passes, at most 8 blocks per SM (152
+// SMs) otherwise.
+inline int stride_grid(long long n, int threads = 256) {
+  const long long b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b < 152 * 8 ? b : 152 * 8));
+}
+
 struct AxisPlan {
   int n;                     // transform length
   int nst;                   // number of stages

@@ -220,6 +220,7 @@ struct mf_ctx {
   // CG loop as one graph launch: a WHILE node whose body is two iterations
   cudaGraph_t cg_graph = nullptr;
   int cg_body_kernels = 0;      // kernel launches per pass of the CG graph's body
+  int pw_blocks = 1;            // blocks of the grid-stride pointwise passes (one voxel per thread at most)
   cudaGraphExec_t cg_exec = nullptr;
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
@@ -319,14 +320,14 @@ int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false) 
     const cudaError_t e = mf_launch_constitutive_dw(c->at<double>(c->oF), c->at<double>(c->oP),
                                                     want_H ? c->at<float>(c->oH) : nullptr, moments, mat_args(c),
                                                     c->ws + c->otabledw, c->N, c->at<double>(c->opart),
-                                                    kPointwiseBlocks, c->at<Scalars>(c->osc), c->st);
+                                                    c->pw_blocks, c->at<Scalars>(c->osc), c->st);
     c->have_K = false;
     c->have_H = want_H && e == cudaSuccess;
     return cuda_status(e);
   }
   cudaError_t e = mf_launch_constitutive(c->at<double>(c->oF), c->at<double>(c->oP), c->ws + c->oK,
                                          c->f32(), want_K, moments, mat_args(c), c->N,
-                                         c->at<double>(c->opart), kPointwiseBlocks,
+                                         c->at<double>(c->opart), c->pw_blocks,
                                          c->at<Scalars>(c->osc), c->st);
   c->have_K = want_K && e == cudaSuccess;
   if (e == cudaSuccess && want_H) e = mf_launch_make_H(c->at<double>(c->oF), c->at<float>(c->oH), c->N, c->st);
@@ -379,7 +380,7 @@ int run_matvec(mf_ctx* c, const void* x, void* y, const uint8_t* mask) {
   const ZArgs za = z_args(c, c->f32(), mask, 1.0 / (double)c->N);
   const XYArgs xa = xy_args(c, c->f32());
   cudaError_t e = mf_launch_tangent(x, nullptr, nullptr, nullptr, c->f32(), tangent_kind(c), false,
-                                    tangent_args(c), c->ws + c->oAp, c->N, nullptr, kPointwiseBlocks,
+                                    tangent_args(c), c->ws + c->oAp, c->N, nullptr, c->pw_blocks,
                                     nullptr, c->st);
   if (e == cudaSuccess)
     e = mf_launch_project(c->f32(), c->ws + c->oAp, c->ws + c->ospec, y, 0, nullptr, xa, za, nullptr,
@@ -453,7 +454,7 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
-    e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, kPointwiseBlocks, sc,
+    e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, c->pw_blocks, sc,
                           cs, true);
     if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, cs);
     if (e == cudaSuccess && !xa.fin) e = mf_launch_fin_beta(part, nplanes, sc, cs);
@@ -580,7 +581,7 @@ int launch_cg(mf_ctx* c, const uint8_t* mask, double tol_cg, double cg_rel, int 
     if (s) return s;
   }
   cudaError_t e = mf_launch_cg_init(c->at<double>(c->ob), c->ws + c->ox, c->ws + c->or_, c->ws + c->op, f32, n9,
-                                    part, kPointwiseBlocks, tol_cg, cg_rel, c->N, sc, c->st);
+                                    part, c->pw_blocks, tol_cg, cg_rel, c->N, sc, c->st);
   if (e == cudaSuccess) e = mf_launch_cg_batch_init(sc, max_cg, c->st);
   if (e == cudaSuccess) e = cudaGraphLaunch(c->cg_exec, c->st);
   if (e == cudaSuccess)
@@ -638,7 +639,7 @@ struct Runner {
     *zero = 0;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return MF_CUDA_ERROR;
     Scalars* sc = c->at<Scalars>(c->osc);
-    if (mf_launch_mean_F(c->at<double>(c->oF), c->N, c->at<double>(c->opart), kPointwiseBlocks, sc, c->st) !=
+    if (mf_launch_mean_F(c->at<double>(c->oF), c->N, c->at<double>(c->opart), c->pw_blocks, sc, c->st) !=
         cudaSuccess)
       return MF_CUDA_ERROR;
     defl.m = 0;
@@ -709,7 +710,7 @@ struct Runner {
       // the constitutive pass of this iteration
       defl = null_rotations(h->meanF, m, h->T, h->S, c->kappa, 1e-6);
       if (defl.m > 0 && mf_launch_defl_project(c->at<double>(c->ob), false, true, F, N, defl, part,
-                                               kPointwiseBlocks, sc, c->st) != cudaSuccess)
+                                               c->pw_blocks, sc, c->st) != cudaSuccess)
         return MF_CUDA_ERROR;
     }
     // FP32 inner solves: forcing sqrt(cg_rel) for the first Newton iteration
@@ -730,10 +731,10 @@ struct Runner {
         return MF_CUDA_ERROR;
       corr = c->ws + c->op2;
     }
-    if (defl.m > 0 && mf_launch_defl_project(corr, true, false, F, N, defl, part, kPointwiseBlocks, sc, c->st) !=
+    if (defl.m > 0 && mf_launch_defl_project(corr, true, false, F, N, defl, part, c->pw_blocks, sc, c->st) !=
                           cudaSuccess)
       return MF_CUDA_ERROR;
-    if (mf_launch_newton_update(F, corr, c->f32(), defl.m > 0, N, part, kPointwiseBlocks, sc, c->st) !=
+    if (mf_launch_newton_update(F, corr, c->f32(), defl.m > 0, N, part, c->pw_blocks, sc, c->st) !=
         cudaSuccess)
       return MF_CUDA_ERROR;
     // FP32 corrections carry a rounding-level average on the strain-controlled
@@ -878,6 +879,8 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   int S = 16;
   while (S > 1 && (size_t)9 * nz * S * sizeof(double2) > 150 * 1024) S /= 2;
   c->zS = S;
+  // pointwise passes: one voxel per thread for small cells, else 8 blocks per SM
+  c->pw_blocks = (int)((c->N + 255) / 256 < kPointwiseBlocks ? (c->N + 255) / 256 : kPointwiseBlocks);
 
   const long long N = c->N;
   const size_t isz = c->inner_size();
@@ -1288,7 +1291,7 @@ int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, int graph, float* 
   auto kernel = [&](cudaStream_t s, int which) {
     if (which == 0)
       return mf_launch_tangent(c->ws + c->op, c->ws + c->or_, c->ws + c->op2, c->ws + c->ox, f32, tangent_kind(c),
-                               true, ta, c->ws + c->oAp, c->N, part, kPointwiseBlocks, sc, s);
+                               true, ta, c->ws + c->oAp, c->N, part, c->pw_blocks, sc, s);
     return mf_launch_project_part(which - 1, f32, c->ws + c->oAp, c->ws + c->ospec, c->ws + c->or_, part, xa, za,
                                   sc, s);
   };
@@ -1375,7 +1378,7 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
   cudaError_t e = mf_launch_adj_rhs_fill(c->ws + c->op, f32, N, w, c->st);
   if (e == cudaSuccess)
     e = mf_launch_tangent(c->ws + c->op, nullptr, nullptr, nullptr, f32, tangent_kind(c), false, tangent_args(c),
-                          c->ws + c->oAp, N, nullptr, kPointwiseBlocks, nullptr, c->st);
+                          c->ws + c->oAp, N, nullptr, c->pw_blocks, nullptr, c->st);
   if (e == cudaSuccess) e = mf_launch_adj_rhs_add(c->ws + c->oAp, f32, N, w, c->st);
   if (e == cudaSuccess)
     e = mf_launch_project(f32, c->ws + c->oAp, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xa, za, nullptr,
@@ -1386,7 +1389,7 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
   defl.m = 0;
   if (e == cudaSuccess && f32) {
     defl = null_rotations(h.meanF, mask, h.T, h.S, c->kappa, 1e-6);
-    if (defl.m > 0) e = mf_launch_defl_project(b, false, true, F, N, defl, part, kPointwiseBlocks, sc, c->st);
+    if (defl.m > 0) e = mf_launch_defl_project(b, false, true, F, N, defl, part, c->pw_blocks, sc, c->st);
   }
   if (e != cudaSuccess) return cuda_status(e);
   s = launch_cg(c, mask, tol_cg, cg_rel, max_cg);
@@ -1399,11 +1402,11 @@ int mf_adjoint(mf_ctx* c, const uint8_t* mask, const double* wF, const double* w
   if (s) return s;
   if (clear) e = cudaMemsetAsync(&sc->flags, 0, sizeof(int), c->st);
   if (e == cudaSuccess && defl.m > 0)
-    e = mf_launch_defl_project(c->ws + c->ox, true, true, F, N, defl, part, kPointwiseBlocks, sc, c->st);
+    e = mf_launch_defl_project(c->ws + c->ox, true, true, F, N, defl, part, c->pw_blocks, sc, c->st);
   // parameter derivatives; the per-phase sums land in b (free after the CG start)
   const int per = 2 * c->nphase;
   int nblk = (int)(c->npart / per);
-  if (nblk > kPointwiseBlocks) nblk = kPointwiseBlocks;
+  if (nblk > c->pw_blocks) nblk = c->pw_blocks;
   if (e == cudaSuccess)
     e = mf_launch_adj_grad(F, c->at<double>(c->oP), c->ws + c->ox, f32, c->at<int32_t>(c->ophase),
                            c->has_scale ? c->at<double>(c->oscale) : nullptr, N, c->nphase, w, part, nblk, b,
@@ -1506,7 +1509,7 @@ int mf_matvec_cufft(mf_ctx* c, const void* x_dev, void* y_dev, const uint8_t* ma
   if (!c->ws) return MF_NO_WORKSPACE;
   if (!c->cufft_bound || !operator_ready(c)) return MF_INVALID_ARG;
   cudaError_t e = mf_launch_tangent(x_dev, nullptr, nullptr, nullptr, c->f32(), tangent_kind(c), false,
-                                    tangent_args(c), c->ws + c->oAp, c->N, nullptr, kPointwiseBlocks,
+                                    tangent_args(c), c->ws + c->oAp, c->N, nullptr, c->pw_blocks,
                                     nullptr, c->st);
   if (e != cudaSuccess) return MF_CUDA_ERROR;
   return mf_cufft_project(c->cufft, c->f32(), c->ws + c->oAp, y_dev, c->nx, c->ny, c->nz, mask, c->st, -1);
