@@ -143,14 +143,22 @@ __device__ __forceinline__ void x_last_split(typename CT<T>::t* buf, const typen
         row[b1 * RB + rp] = split_one<T>(w[rp], u[r], twx[km]);
       }
     } else {
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int rp = (b0 == 0) ? (RB - r) % RB : RB - 1 - r;
-        if (rp < r) continue;
+      // b0 = b1 (b0 = 0 or RA/2): the pairs lie within u; the partner index
+      // is a compile-time function of r in each case, so u stays in registers
+      auto pair = [&](int r, int rp) {
         const int k = b0 + RA * r, km = b0 + RA * rp;
         const C za = u[r], zb = u[rp];
         row[b0 * RB + r] = split_one<T>(za, zb, twx[k]);
         if (rp != r) row[b0 * RB + rp] = split_one<T>(zb, za, twx[km]);
+      };
+      if (b0 == 0) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if ((RB - r) % RB >= r) pair(r, (RB - r) % RB);
+      } else {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (RB - 1 - r >= r) pair(r, RB - 1 - r);
       }
     }
   }
@@ -187,17 +195,21 @@ __device__ __forceinline__ void x_merge_first(typename CT<T>::t* buf, const type
 #pragma unroll
       for (int r = 0; r < RB; ++r) { row[b0 * RB + r] = zu[r]; row[b1 * RB + r] = zw[r]; }
     } else {
+      // b0 = b1 (b0 = 0 or RA/2): partner indices fixed at compile time per case
       C zu[RB];
+      if (b0 == 0) {
 #pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int rp = (b0 == 0) ? (RB - r) % RB : RB - 1 - r;
-        const int k = b0 + RA * r;
-        if (k == 0) {
-          const T x0 = u[r].x;
-          zu[r].x = x0; zu[r].y = x0;
-        } else {
-          zu[r] = merge_one<T>(u[r], u[rp], twx[k]);
+        for (int r = 0; r < RB; ++r) {
+          if (r == 0) {
+            const T x0 = u[0].x;
+            zu[0].x = x0; zu[0].y = x0;
+          } else {
+            zu[r] = merge_one<T>(u[r], u[(RB - r) % RB], twx[RA * r]);
+          }
         }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) zu[r] = merge_one<T>(u[r], u[RB - 1 - r], twx[b0 + RA * r]);
       }
       fft2::Dft<RB, true, C>::run(zu);
 #pragma unroll
