@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
   static_assert(!FIN || CG, "the fused finish belongs to the CG pass");
   __shared__ double tot[1];
   T beta = (T)0, alpha = (T)0;
+  pdl_wait();
   if (CG) {
     if (*(volatile const int*)&sc->stop) return;
     beta = (T)sc->beta;
@@ -275,6 +276,7 @@ __global__ void k_axpy_alpha(T* __restrict__ x, const T* __restrict__ p, long lo
 
 // End of a CG body in a graph: keep looping while the solve has not stopped.
 __global__ void k_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h) {
+  pdl_wait();
   cudaGraphSetConditional(h, *(volatile const int*)&sc->stop ? 0u : 1u);
 }
 
@@ -308,10 +310,11 @@ __global__ void k_make_H(const double* __restrict__ F, float* __restrict__ H, lo
 
 cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* x, bool f32, int tan,
                               bool cg, const TangentArgs& ta, void* t, long long N, double* partials,
-                              int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha) {
-#define MF_TAN(T, K, CGV, FV)                                                                          \
-  k_tangent<T, K, CGV, FV><<<nblk, kThreads, 0, st>>>((const T*)pin, (const T*)r, (T*)pout, (T*)x, ta, \
-                                                      (T*)t, N, partials, sc)
+                              int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha, bool pdl) {
+  cudaError_t e = cudaSuccess;
+#define MF_TAN(T, K, CGV, FV)                                                                                 \
+  e = launch_k(pdl, k_tangent<T, K, CGV, FV>, dim3(nblk), dim3(kThreads), 0, st, (const T*)pin, (const T*)r, \
+               (T*)pout, (T*)x, ta, (T*)t, N, partials, sc)
 #define MF_TAN_CG(T, K)                                       \
   do {                                                        \
     if (!cg) MF_TAN(T, K, false, false);                      \
@@ -328,7 +331,7 @@ cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* 
 #undef MF_TAN_CG
 #undef MF_TAN
   g_mf_launches += 1;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st) {
@@ -371,10 +374,9 @@ cudaError_t mf_launch_make_H(const double* F, float* H, long long N, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st) {
-  k_cg_cond<<<1, 1, 0, st>>>(sc, h);
+cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st, bool pdl) {
   g_mf_launches += 1;
-  return cudaGetLastError();
+  return launch_k(pdl, k_cg_cond, dim3(1), dim3(1), 0, st, sc, h);
 }
 
 cudaError_t mf_launch_axpy_last(void* x, const void* p0, const void* p1, bool f32, long long n,

@@ -14,6 +14,16 @@
 
 #define MF_MAX_STAGES 10
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may be scheduled as soon as the blocks of
+// its predecessor in the stream have exited, before that grid's completion
+// (its memory flush) and the launch that would normally follow it; pdl_wait()
+// returns once the predecessor grid has completed and its memory operations
+// are visible.  For a kernel launched without the attribute it returns at
+// once.  (No kernel here signals its dependents early: measured on the 128^3
+// cell, dependents resident during the predecessor's last wave slowed it.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Grid of a grid-stride elementwise pass over n items with `threads` per
 // block: one item per thread for small passes, at most 8 blocks per SM (152
 // SMs) otherwise.

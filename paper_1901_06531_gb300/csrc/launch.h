@@ -2,13 +2,38 @@
 // translation units (host code only; no torch types).
 #pragma once
 
+#include <utility>
+
 #include "common.cuh"
+
+// Launch k<<<g, b, sm, st>>>(args...), with the programmatic
+// stream-serialization attribute when pdl is set (the kernel then calls
+// pdl_wait() before it touches anything its predecessor writes).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... args) {
+  if (!pdl) {
+    k<<<g, b, sm, st>>>(std::forward<Args>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 struct XYArgs {
   int v2;          // 1: fixed-size kernels (transform2*.cu), tables of that layout
   int split;       // with v2: separate row (x) and column (y) kernels (transform3.cuh)
   const int* skip; // if non-null and *skip != 0 the kernel returns at once (finished CG)
   int fin;         // fused (v2, not split) inverse pass with the CG update: finish beta in its last block
+  int pdl;         // v2 fused kernels: launch with programmatic dependent launch (see launch_k)
   int nx, ny, nz;
   long long N;
   AxisPlan px;     // length nx
@@ -21,6 +46,7 @@ struct XYArgs {
 struct ZArgs {
   int v2;
   const int* skip;
+  int pdl;           // v2 kernels: launch with programmatic dependent launch (see launch_k)
   int nx, ny, nz;
   long long N;
   AxisPlan pz;
@@ -98,13 +124,14 @@ struct TangentArgs {
 // tan: 0 packed K (FP64 or FP32), 1 neo-Hookean from H, 2 SVK from H (FP32).
 // fin_alpha (cg, partials non-null): the pass also finishes alpha (last block),
 // so no k_fin_alpha follows it.
+// pdl: launched with programmatic dependent launch (see launch_k).
 cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* x, bool f32, int tan,
                               bool cg, const TangentArgs& ta, void* t, long long N, double* partials,
-                              int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha = false);
+                              int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha = false, bool pdl = false);
 cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st);
-cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st, bool pdl = false);
 cudaError_t mf_launch_axpy_last(void* x, const void* p0, const void* p1, bool f32, long long n,
                                 const Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_axpy_alpha(void* x, const void* p, bool f32, long long n, const Scalars* sc,

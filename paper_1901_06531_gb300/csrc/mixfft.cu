@@ -258,6 +258,7 @@ XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   a.split = c->xy_split;
   a.skip = nullptr;
   a.fin = 0;
+  a.pdl = 0;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
   size_t esz;
@@ -424,6 +425,13 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   // the fused x-y inverse kernel finishes beta itself; the split and generic
   // kernels leave it to k_fin_beta
   xa.fin = (xa.v2 && !xa.split) ? 1 : 0;
+  // programmatic dependent launch along the body (tangent, the fused
+  // transform passes, the loop condition): each kernel is scheduled as its
+  // predecessor's blocks exit, loads its constant tables, then waits for the
+  // predecessor's completion (saves the launch gap: 8 CG-bound 32^3 cells
+  // solve in half the time; neutral at 128^3)
+  const bool pdl = xa.v2 && !xa.split;
+  xa.pdl = za.pdl = pdl ? 1 : 0;
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
   const int nplanes = mf_xy_blocks(c->ny, c->nz, c->xy_split != 0);
@@ -455,14 +463,14 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
     e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, c->pw_blocks, sc,
-                          cs, true);
+                          cs, true, pdl);
     if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, cs);
     if (e == cudaSuccess && !xa.fin) e = mf_launch_fin_beta(part, nplanes, sc, cs);
   }
   // per iteration: tangent, the transform passes (two more for the split x-y
   // kernels), k_fin_beta unless fused; k_cg_cond once per body
   c->cg_body_kernels = 2 * (1 + ((xa.v2 && xa.split) ? 5 : 3) + (xa.fin ? 0 : 1)) + 1;
-  if (e == cudaSuccess) e = mf_launch_cg_cond(sc, h, cs);
+  if (e == cudaSuccess) e = mf_launch_cg_cond(sc, h, cs, pdl);
   cudaGraph_t captured = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
   if (e == cudaSuccess) e = e2;

@@ -144,6 +144,7 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
   xa.split = 0;
   xa.skip = nullptr;
   xa.fin = 0;
+  xa.pdl = 0;
   xa.nx = nx; xa.ny = ny; xa.nz = nz; xa.N = N;
   xa.px = px; xa.pyh = pyh;
   xa.twx = tab + o_tw;

@@ -228,14 +228,15 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   constexpr int TPB = xy_threads<T>();
   typedef typename CT<T>::t C;
   typedef typename CT<typename IOT<T>::t>::t CI;
-  if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* twx = buf + NY * PX;
   C* twy = twx + NX;
   int* posx = reinterpret_cast<int*>(twy + NY);
-  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);   // constant: loaded before the wait for the predecessor
+  pdl_wait();
+  if (skip && *(volatile const int*)skip) return;
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
   const CI* src = reinterpret_cast<const CI*>(in + c * N + (long long)z * NY * NX);
   // row y, sample j (the real values 2j, 2j+1 as one complex sample)
@@ -311,7 +312,6 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   typedef typename IOT<T>::t TI;
   typedef typename CT<TI>::t CI;
   static_assert(MODE != 3 || std::is_same<C, CI>::value, "the CG update runs in the compute type");
-  if (skip && *(volatile const int*)skip) return;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -319,7 +319,9 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   C* twx = buf + NY * PX;
   C* twy = twx + NX;
   int* posx = reinterpret_cast<int*>(twy + NY);
-  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);   // constant: loaded before the wait for the predecessor
+  pdl_wait();
+  if (skip && *(volatile const int*)skip) return;
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
   if (MODE == 3) {
     // the residual plane is read only at the end: start pulling it into L2 now
@@ -467,7 +469,6 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   typedef ZShape<T, NZ, S_> Sh;
   constexpr int kZThreads = z_threads(S_);
   typedef typename CT<T>::t C;
-  if (a.skip && *(volatile const int*)a.skip) return;
   constexpr int S = Sh::S, CP = Sh::CP, ZS = Sh::ZS;
   constexpr int NST = fft2::nst(NZ);
   constexpr int RL = fft2::rad(NZ, NST - 1);   // radix of the last DIF stage (its M is 1)
@@ -476,7 +477,10 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   C* twz = buf + 3 * CP;
   int* zk = reinterpret_cast<int*>(twz + NZ);
   const C* gtwz = reinterpret_cast<const C*>(a.twz);
+  // constant tables: loaded before the wait for the predecessor
   for (int i = threadIdx.x; i < NZ; i += kZThreads) { twz[i] = gtwz[i]; zk[i] = a.zk[i]; }
+  pdl_wait();
+  if (a.skip && *(volatile const int*)a.skip) return;
   const int H = a.nx / 2;
   const int ncol = a.ny * H;
   const int ntile = ncol / S;

@@ -13,9 +13,9 @@ cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_xyf<T, NX><<<9 * a.nz, xy_threads<T>(), sm, st>>>(in, (C*)spec, a.nz, a.N, (const C*)a.twx, a.xpos, a.skip);
   ++g_mf_launches;
-  return cudaGetLastError();
+  return launch_k(a.pdl != 0, k_xyf<T, NX>, dim3(9 * a.nz), dim3(xy_threads<T>()), sm, st, in, (C*)spec, a.nz, a.N,
+                  (const C*)a.twx, a.xpos, a.skip);
 }
 
 template <typename T, int NX, int MODE>
@@ -26,11 +26,10 @@ cudaError_t launch_xyi(const void* spec, typename IOT<T>::t* out, double* partia
   cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   // the scalar block is written only by the fused finish (a.fin, MODE 3)
-  k_xyi<T, NX, MODE><<<9 * a.nz, xy_threads<T>(), sm, st>>>((const C*)spec, out, partials, a.nz, a.N,
-                                                     (const C*)a.twx, a.xpos, const_cast<Scalars*>(sc),
-                                                     a.skip, MODE == 3 ? a.fin : 0);
   ++g_mf_launches;
-  return cudaGetLastError();
+  return launch_k(a.pdl != 0, k_xyi<T, NX, MODE>, dim3(9 * a.nz), dim3(xy_threads<T>()), sm, st, (const C*)spec,
+                  out, partials, a.nz, a.N, (const C*)a.twx, a.xpos, const_cast<Scalars*>(sc), a.skip,
+                  MODE == 3 ? a.fin : 0);
 }
 
 template <typename T, int NZ, int MODE, int S>
@@ -42,9 +41,8 @@ cudaError_t launch_zp_s(void* spec, const ZArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int ncol = a.ny * (a.nx / 2);
   if (ncol % S) return cudaErrorInvalidValue;
-  k_zp<T, NZ, MODE, S><<<3 * (ncol / S), z_threads(S), sm, st>>>((C*)spec, a);
   ++g_mf_launches;
-  return cudaGetLastError();
+  return launch_k(a.pdl != 0, k_zp<T, NZ, MODE, S>, dim3(3 * (ncol / S)), dim3(z_threads(S)), sm, st, (C*)spec, a);
 }
 
 // The tile the autotuner chose: a.S in {4, 8, 16} for the operator (MODE 0,
