@@ -282,6 +282,16 @@ int mf_adjoint(mf_ctx* ctx, const uint8_t* mask, const double* wF, const double*
  * support. */
 int mf_set_xy_split(mf_ctx* ctx, int split);
 
+/* The FP32 x-y forward transform of an FP32-inner context as a persistent
+ * kernel (1) or one block per (component, z) plane (0, the default): one
+ * block per SM walks the planes, each plane arriving by one bulk copy (the
+ * TMA unit) into one of two shared-memory staging buffers while the block
+ * transforms the previous one.  Same stages in the same order: results are
+ * identical.  Available for nx = ny in {48, 64, 96, 128} on the fused
+ * (non-split) kernels; MF_INVALID_ARG otherwise.  Its barrier waits are
+ * bounded; a wait that gives up makes the solve return MF_DEVICE_TIMEOUT. */
+int mf_set_xy_persistent(mf_ctx* ctx, int on);
+
 /* Arithmetic of the outer (defect-correction) level of MF_FP32_INNER
  * contexts: the stress P(F) of the constitutive pass (Eq. eq:lineariz) and
  * the transforms of the residual b = -G*(P - P-bar) (Eq. linequil2ast, right

@@ -230,6 +230,7 @@ __device__ __forceinline__ bool last_block_total(const double* partials, unsigne
 #define MF_FLAG_BREAKDOWN 1
 #define MF_FLAG_NONPOS_J 2
 #define MF_FLAG_NONFINITE 4
+#define MF_FLAG_TIMEOUT 8     // a bounded device-side wait gave up
 
 // CG scalar updates after the curvature p.Ap and after the new r.r (shared by
 // the one-block finishing kernels and the last blocks of fused passes).

@@ -221,6 +221,7 @@ struct mf_ctx {
   cudaGraph_t cg_graph = nullptr;
   int cg_body_kernels = 0;      // kernel launches per pass of the CG graph's body
   int pw_blocks = 1;            // blocks of the grid-stride pointwise passes (one voxel per thread at most)
+  int xy_persist = 0;           // FP32 x-y forward pass as the persistent bulk-copy kernel
   cudaGraphExec_t cg_exec = nullptr;
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
@@ -259,6 +260,8 @@ XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   a.skip = nullptr;
   a.fin = 0;
   a.pdl = 0;
+  a.persist = (f32 && !dw && c->xy_persist && c->v2 && !c->xy_split) ? 1 : 0;
+  a.flags = &c->at<Scalars>(c->osc)->flags;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
   size_t esz;
@@ -308,6 +311,7 @@ int read_scalars(mf_ctx* c, Scalars* h) {
 }
 
 int flags_status(int flags) {
+  if (flags & MF_FLAG_TIMEOUT) return MF_DEVICE_TIMEOUT;
   if (flags & MF_FLAG_NONPOS_J) return MF_NONPOSITIVE_J;
   if (flags & (MF_FLAG_BREAKDOWN | MF_FLAG_NONFINITE)) return MF_CG_BREAKDOWN;
   return MF_OK;
@@ -1439,6 +1443,15 @@ int mf_set_xy_split(mf_ctx* c, int split) {
   if (!split && big_plane) return MF_INVALID_ARG;
   if (c->xy_split != split) free_cg_graph(c);   // the captured loop holds the old kernels
   c->xy_split = split;
+  return MF_OK;
+}
+
+int mf_set_xy_persistent(mf_ctx* c, int on) {
+  if (!c || (on != 0 && on != 1)) return MF_INVALID_ARG;
+  if (on && !(c->prec == MF_FP32_INNER && c->v2 && !c->xy_split && mf_persist_supported(c->nx)))
+    return MF_INVALID_ARG;
+  if (c->xy_persist != on) free_cg_graph(c);   // the captured loop holds the old kernels
+  c->xy_persist = on;
   return MF_OK;
 }
 

@@ -15,6 +15,7 @@
 
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "dw.cuh"
 #include "fft2.cuh"
 #include "launch.h"
@@ -292,6 +293,95 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   // spectrum rows (consecutive threads take consecutive columns)
   C* dst = spec + ((long long)c * nz + z) * NY * H;
   fft2::forward_out<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e, C v) { dst[e * H + q] = v; });
+}
+
+// ------------------------------------------------------- persistent forward
+// The same x-y forward pass (FP32, planes whose half-length x transform has
+// two stages: NX in {48, 64, 96, 128}) as a persistent kernel: one block of
+// kPersistThreads per SM walks the (c, z) planes; each plane (NY x NX
+// contiguous reals) arrives by one bulk copy in one of two staging buffers,
+// so the copy of the block's plane i + 2 runs while plane i is transformed.
+// Results are identical to k_xyf's (same stages, same order).
+constexpr int kPersistThreads = 512;
+constexpr int kMaxPolls = 1 << 22;   // bound of every barrier wait
+
+template <int NX> struct PersistShape {
+  typedef XYShape<float, NX> Sh;
+  static constexpr int PLANE = Sh::NY * Sh::H;   // complex samples of one plane
+  static constexpr size_t smem() { return (size_t)2 * PLANE * sizeof(float2) + Sh::smem(); }
+};
+
+template <int NX>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    k_xyf_p(const float* __restrict__ in, float2* __restrict__ spec, int nz, long long N,
+            const float2* __restrict__ gtw, const int* __restrict__ gpos, const int* skip, int* flags) {
+  typedef float2 C;
+  typedef XYShape<float, NX> Sh;
+  constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY, TPB = kPersistThreads;
+  constexpr int PLANE = PersistShape<NX>::PLANE;
+  constexpr unsigned PBYTES = PLANE * sizeof(C);
+  static_assert(RowPlan<H>::NST == 2, "first x stage reads the staging buffer");
+  static_assert(PBYTES % 128 == 0, "staging buffers stay 128-byte aligned");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* stg = reinterpret_cast<C*>(smem_raw);   // [2][PLANE]
+  C* buf = stg + 2 * PLANE;
+  C* twx = buf + NY * PX;
+  C* twy = twx + NX;
+  int* posx = reinterpret_cast<int*>(twy + NY);
+  __shared__ __align__(8) uint64_t bar[2];
+  const int nplanes = 9 * nz;
+  if (threadIdx.x == 0) {
+    bulk::init(&bar[0], 1);
+    bulk::init(&bar[1], 1);
+    bulk::fence_init();
+  }
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);   // constant: loaded before the wait for the predecessor
+  pdl_wait();
+  __syncthreads();
+  if (skip && *(volatile const int*)skip) return;
+  auto plane = [&](int p) { return in + (p % 9) * N + (long long)(p / 9) * NY * NX; };
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int p = blockIdx.x + k * gridDim.x;
+      if (p < nplanes) {
+        bulk::expect_tx(&bar[k], PBYTES);
+        bulk::g2s(stg + k * PLANE, plane(p), PBYTES, &bar[k]);
+      }
+    }
+  }
+  int i = 0;
+  for (int p = blockIdx.x; p < nplanes; p += gridDim.x, ++i) {
+    const int s = i & 1;
+    const bool ok = bulk::wait(&bar[s], (unsigned)(i >> 1) & 1u, kMaxPolls);
+    if (__syncthreads_or(!ok)) {
+      // give up: record the timeout, let the copies in flight land, exit
+      if (threadIdx.x == 0) {
+        if (flags) atomicOr(flags, MF_FLAG_TIMEOUT);
+        bulk::wait(&bar[s], (unsigned)(i >> 1) & 1u, kMaxPolls);
+        if (p + gridDim.x < nplanes) bulk::wait(&bar[s ^ 1], (unsigned)((i + 1) >> 1) & 1u, kMaxPolls);
+      }
+      return;
+    }
+    const C* st = stg + s * PLANE;
+    // first x stage: staging -> working buffer (consecutive threads take
+    // consecutive butterflies of a row)
+    fft2::stage_io<C, H, NX, 0, false, NY, 1, PX, 0, 1, false>(
+        twx, [&](int q, int, int e) { return st[q * H + e]; }, [&](int, int i2, int, C v) { buf[i2] = v; });
+    __syncthreads();
+    if (threadIdx.x == 0) {   // refill the staging buffer just read with the plane after next
+      const int pn = p + 2 * gridDim.x;
+      if (pn < nplanes) {
+        bulk::fence_proxy_async();
+        bulk::expect_tx(&bar[s], PBYTES);
+        bulk::g2s(stg + s * PLANE, plane(pn), PBYTES, &bar[s]);
+      }
+    }
+    x_last_split<float, NX, TPB>(buf, twx, [&](int y, int pos) { return buf[y * PX + pos]; });
+    __syncthreads();
+    C* dst = spec + ((long long)(p % 9) * nz + p / 9) * NY * H;
+    fft2::forward_out<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e, C v) { dst[e * H + q] = v; });
+    __syncthreads();   // the working buffer is refilled by the next plane
+  }
 }
 
 // ------------------------------------------------------------------ inverse

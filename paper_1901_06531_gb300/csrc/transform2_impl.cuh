@@ -7,9 +7,37 @@
 
 namespace tr2 {
 
+inline int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 1;
+  }
+  return n;
+}
+
+template <int NX>
+cudaError_t launch_xyf_p(const float* in, void* spec, const XYArgs& a, cudaStream_t st) {
+  const size_t sm = PersistShape<NX>::smem();
+  cudaError_t e = cudaFuncSetAttribute(k_xyf_p<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int nplanes = 9 * a.nz;
+  const int grid = nplanes < num_sms() ? nplanes : num_sms();
+  ++g_mf_launches;
+  return launch_k(a.pdl != 0, k_xyf_p<NX>, dim3(grid), dim3(kPersistThreads), sm, st, in, (float2*)spec, a.nz,
+                  a.N, (const float2*)a.twx, a.xpos, a.skip, a.flags);
+}
+
 template <typename T, int NX>
 cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a, cudaStream_t st) {
   typedef typename CT<T>::t C;
+  if constexpr (std::is_same<T, float>::value && RowPlan<NX / 2>::NST == 2) {
+    if (a.persist) return launch_xyf_p<NX>(in, spec, a, st);
+  }
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;

@@ -60,6 +60,7 @@ _lib.mf_sync.argtypes = [_vp]
 _lib.mf_autotune.argtypes = [_vp, _vp, _vp]
 _lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
+_lib.mf_set_xy_persistent.argtypes = [_vp, _i]
 _lib.mf_adjoint.argtypes = [_vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp, _vp]
 _lib.mf_last_cuda_error.argtypes = []
 _lib.mf_last_cuda_error.restype = ctypes.c_char_p
@@ -73,7 +74,8 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_stress", "mf_get_tangent", "mf_matvec", "mf_residual", "mf_residual_noalloc",
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
-            "mf_set_outer_arith", "mf_set_xy_split", "mf_last_cuda_error", "mf_status_string", "mf_destroy"]
+            "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_last_cuda_error",
+            "mf_status_string", "mf_destroy"]
 
 
 def kernel_launches():
@@ -316,6 +318,10 @@ class Context:
     def set_xy_split(self, split):
         """mf_set_xy_split: 0 fused x-y plane kernels, 1 separate row/column kernels."""
         _check("mf_set_xy_split", _lib.mf_set_xy_split(self.h, int(split)))
+
+    def set_xy_persistent(self, on):
+        """mf_set_xy_persistent: 1 persistent bulk-copy FP32 x-y forward kernel, 0 one block per plane."""
+        _check("mf_set_xy_persistent", _lib.mf_set_xy_persistent(self.h, int(on)))
 
     def set_outer_arith(self, arith):
         """mf_set_outer_arith: MF_OUTER_DOUBLE_WORD or MF_OUTER_FP64."""

@@ -365,3 +365,43 @@ def test_time_kernels_modes(graph):
     out = np.zeros(4, dtype=np.float32)
     st = mf._lib.mf_time_kernels(ctx.h, m.ctypes.data, 3, 2, out.ctypes.data)
     assert st == mf.MF_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 16), (96, 96, 48), (48, 48, 96), (64, 64, 64)])
+def test_persistent_xy_forward_is_identical(shape):
+    """The persistent bulk-copy x-y forward kernel runs the same stages in the
+    same order as the per-plane kernel: the FP32 operator is bit-identical."""
+    import torch
+    mf = lib()
+    ctx, _, _ = make(mf, shape, mf.MF_FP32_INNER, "svk", seed=21)
+    ctx.constitutive()
+    nx, ny, nz = shape
+    xt = torch_field(inputs.random_field((nz, ny, nx), 22), torch.float32)
+    ys = []
+    for on in (0, 1):
+        ctx.set_xy_persistent(on)
+        y = torch.full_like(xt, float("nan"))
+        ctx.matvec(xt, y, MASKS[2])
+        ys.append(y.cpu().numpy())
+    np.testing.assert_array_equal(ys[0], ys[1])
+
+
+def test_persistent_xy_forward_solve_and_validation():
+    """A load step with the persistent kernel in the CG loop gives the same
+    fields as with the per-plane kernel; the choice is validated."""
+    mf = lib()
+    cell = inputs.batch_of_cells(1, 9, sizes=(48,), nsteps=2)[0]
+    fields = []
+    for on in (0, 1):
+        ctx = mf.Context(48, 48, 48, mf.MF_FP32_INNER)
+        ctx.set_material(mf.MF_NEOHOOKE, cell["params"], cell["phase"])
+        ctx.set_xy_persistent(on)
+        ctx.solve(cell["mask"], cell["target"], 1e-9, 1e-11)
+        fields.append(ctx.get_fields()[0])
+    np.testing.assert_array_equal(fields[0], fields[1])
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(48, 48, 48, mf.MF_FP64).set_xy_persistent(1)      # FP32 inner only
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(32, 32, 32, mf.MF_FP32_INNER).set_xy_persistent(1)   # no kernel for 32^2 planes
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(48, 48, 48, mf.MF_FP32_INNER).set_xy_persistent(2)
