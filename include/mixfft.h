@@ -104,8 +104,10 @@ int mf_set_F(mf_ctx* ctx, const double* F_host);
  *           <= max(tol_cg, cg_rel * initial value) (MF_FP32_INNER);
  *   cg_rel: relative CG forcing term for MF_FP32_INNER (ignored for MF_FP64);
  *           the first Newton iteration of each step uses sqrt(cg_rel), and
- *           its residual is computed with FP32 transforms (it is always
- *           followed by another iteration: a step never ends on it);
+ *           its residual (and the P it transforms) is computed in FP32 (it
+ *           is always followed by another iteration: a step never ends on
+ *           it); an iteration whose predecessor's correction was below
+ *           sqrt(tol_newton) (expected to be the last) uses sqrt(cg_rel) too;
  *   Fbar_out, Pbar_out: host, nsteps*9 doubles or NULL: <F>, <P> per step;
  *   iters_out: host, nsteps*2 int32 or NULL: Newton iterations and total CG
  *              iterations per step.

@@ -1,7 +1,8 @@
 // Constitutive update P(F) (Eq. eq:lineariz's P; no tangent) in double-word
 // FP32 arithmetic for the FP32-inner mode, with the voxel averages of F and
 // P, optionally the FP32 H = F - I of the matrix-free tangent and the
-// rotation moments, in one pass over F.
+// rotation moments, in one pass over F.  A variant evaluates P in plain
+// FP32 and stores it in FP32 (the first Newton iteration of a step).
 //
 // Both laws are evaluated from H = F - I, so that no large term cancels:
 //   St Venant-Kirchhoff  E = (H + H^T + H^T H)/2, S = C : E, P = S + H S;
@@ -84,6 +85,65 @@ __device__ __forceinline__ bool neohooke_dw(const dw (&h)[9], const dw (&f)[9], 
   return true;
 }
 
+// The same laws in plain FP32 from H (the first Newton iteration of a load
+// step, whose residual is taken with FP32 transforms anyway).
+__device__ __forceinline__ void svk_f32(const float (&h)[9], const float* __restrict__ cv, float (&P)[9]) {
+  auto E = [&](int a, int b) {
+    return 0.5f * (h[3 * a + b] + h[3 * b + a] + h[a] * h[b] + h[3 + a] * h[3 + b] + h[6 + a] * h[6 + b]);
+  };
+  const float e6[6] = {E(0, 0), E(1, 1), E(2, 2), 2.f * E(1, 2), 2.f * E(0, 2), 2.f * E(0, 1)};
+  float sv[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) {
+    float acc = 0.f;
+#pragma unroll
+    for (int J = 0; J < 6; ++J) acc = fmaf(cv[6 * I + J], e6[J], acc);
+    sv[I] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float acc = sv[vgt(i, j)];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc = fmaf(h[3 * i + k], sv[vgt(k, j)], acc);
+      P[3 * i + j] = acc;
+    }
+}
+
+// Returns false when J <= 0 (P is then zero).
+__device__ __forceinline__ bool neohooke_f32(const float (&h)[9], float mu, float lam, float (&P)[9]) {
+  float f[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) f[c] = (c == 0 || c == 4 || c == 8) ? 1.f + h[c] : h[c];
+  const float trH = h[0] + h[4] + h[8];
+  const float trH2 = h[0] * h[0] + h[4] * h[4] + h[8] * h[8] + 2.f * (h[1] * h[3] + h[2] * h[6] + h[5] * h[7]);
+  const float detH = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                     h[2] * (h[3] * h[7] - h[4] * h[6]);
+  const float Jm1 = trH + 0.5f * (trH * trH - trH2) + detH;
+  const float J = 1.f + Jm1;
+  if (!(J > 0.f)) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) P[c] = 0.f;
+    return false;
+  }
+  const float iJ = 1.f / J;
+  float G[9];   // F^-T = cof(F) / J
+  G[0] = (f[4] * f[8] - f[5] * f[7]) * iJ;
+  G[1] = (f[5] * f[6] - f[3] * f[8]) * iJ;
+  G[2] = (f[3] * f[7] - f[4] * f[6]) * iJ;
+  G[3] = (f[2] * f[7] - f[1] * f[8]) * iJ;
+  G[4] = (f[0] * f[8] - f[2] * f[6]) * iJ;
+  G[5] = (f[1] * f[6] - f[0] * f[7]) * iJ;
+  G[6] = (f[1] * f[5] - f[2] * f[4]) * iJ;
+  G[7] = (f[2] * f[3] - f[0] * f[5]) * iJ;
+  G[8] = (f[0] * f[4] - f[1] * f[3]) * iJ;
+  const float cg = lam * log1pf(Jm1) - mu;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) P[c] = mu * f[c] + cg * G[c];
+  return true;
+}
+
 template <int NC>
 __device__ __forceinline__ void block_sum_dw(double (&v)[NC], double* out) {
   __shared__ double red[NC][32];
@@ -105,11 +165,13 @@ __device__ __forceinline__ void block_sum_dw(double (&v)[NC], double* out) {
 
 // Columns of the block partials: F 0-8, P 9-17, and with MOM T = sum P F^T
 // 18-26, S = sum F F^T 27-35 (FP32 products of the high parts: only used to
-// detect null rotations).
-template <int MODEL, bool WH, bool MOM>
+// detect null rotations).  P32: P evaluated in FP32 from H and written, in
+// FP32, to Pf instead of P (the averages of F stay double word).
+template <int MODEL, bool WH, bool MOM, bool P32>
 __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __restrict__ F, double* __restrict__ P,
-                                                              float* __restrict__ H, MatArgs m,
-                                                              const dw* __restrict__ table, long long N,
+                                                              float* __restrict__ Pf, float* __restrict__ H,
+                                                              MatArgs m, const dw* __restrict__ table,
+                                                              const float* __restrict__ table32, long long N,
                                                               double* __restrict__ partials, Scalars* sc) {
   constexpr int NC = MOM ? 36 : 18;
   __shared__ double tot[NC];
@@ -134,19 +196,34 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
       h[c] = (c == 0 || c == 4 || c == 8) ? dw(f[c].hi - 1.0f, 0.0f) + dw(f[c].lo, 0.0f) : f[c];
     }
     dw p[9];
-    if constexpr (MODEL == 0) {
-      if (!neohooke_dw(h, f, table[2 * ph], table[2 * ph + 1], p)) bad = true;
-    } else {
-      svk_dw(h, table + 36 * ph, p);
-    }
-    if (m.scale) {
-      const dw s = dw_split(m.scale[v]);
+    if constexpr (P32) {
+      float hf[9], pf[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) p[c] = s * p[c];
+      for (int c = 0; c < 9; ++c) hf[c] = h[c].hi;
+      if constexpr (MODEL == 0) {
+        if (!neohooke_f32(hf, table32[2 * ph], table32[2 * ph + 1], pf)) bad = true;
+      } else {
+        svk_f32(hf, table32 + 36 * ph, pf);
+      }
+      const float s = m.scale ? (float)m.scale[v] : 1.f;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) p[c] = dw(s * pf[c], 0.0f);
+    } else {
+      if constexpr (MODEL == 0) {
+        if (!neohooke_dw(h, f, table[2 * ph], table[2 * ph + 1], p)) bad = true;
+      } else {
+        svk_dw(h, table + 36 * ph, p);
+      }
+      if (m.scale) {
+        const dw s = dw_split(m.scale[v]);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) p[c] = s * p[c];
+      }
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      P[c * N + v] = dw_join(p[c]);
+      if constexpr (P32) Pf[c * N + v] = p[c].hi;
+      else P[c * N + v] = dw_join(p[c]);
       if (WH) H[c * N + v] = h[c].hi;
       acc[c] = acc[c] + f[c];
       acc[9 + c] = acc[9 + c] + p[c];
@@ -176,16 +253,18 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
 }
 
 template <int MODEL>
-cudaError_t launch_model(const double* F, double* P, float* H, bool moments, const MatArgs& m, const dw* table,
-                         long long N, double* partials, int nblk, Scalars* sc, cudaStream_t st) {
-  if (H && moments)
-    k_constitutive_dw<MODEL, true, true><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
-  else if (H)
-    k_constitutive_dw<MODEL, true, false><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
-  else if (moments)
-    k_constitutive_dw<MODEL, false, true><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
-  else
-    k_constitutive_dw<MODEL, false, false><<<nblk, kThreads, 0, st>>>(F, P, H, m, table, N, partials, sc);
+cudaError_t launch_model(const double* F, double* P, float* Pf, float* H, bool moments, const MatArgs& m,
+                         const dw* table, const float* table32, long long N, double* partials, int nblk,
+                         Scalars* sc, cudaStream_t st) {
+#define MF_CDW(WH, MOM, P32)                                                                               \
+  k_constitutive_dw<MODEL, WH, MOM, P32><<<nblk, kThreads, 0, st>>>(F, P, Pf, H, m, table, table32, N, \
+                                                                    partials, sc)
+  if (Pf && H && moments) MF_CDW(true, true, true);
+  else if (H && moments) MF_CDW(true, true, false);
+  else if (H) MF_CDW(true, false, false);
+  else if (moments) MF_CDW(false, true, false);
+  else MF_CDW(false, false, false);
+#undef MF_CDW
   return cudaGetLastError();
 }
 
@@ -193,10 +272,12 @@ cudaError_t launch_model(const double* F, double* P, float* H, bool moments, con
 
 cudaError_t mf_launch_constitutive_dw(const double* F, double* P, float* H, bool moments, const MatArgs& m,
                                       const void* table_dw, long long N, double* partials, int nblk,
-                                      Scalars* sc, cudaStream_t st) {
+                                      Scalars* sc, cudaStream_t st, float* Pf, const float* table32) {
   const dw* table = (const dw*)table_dw;
-  cudaError_t e = m.model == 0 ? launch_model<0>(F, P, H, moments, m, table, N, partials, nblk, sc, st)
-                               : launch_model<1>(F, P, H, moments, m, table, N, partials, nblk, sc, st);
+  if (Pf && !(H && moments && table32)) return cudaErrorInvalidValue;   // the FP32-P pass is the full one
+  cudaError_t e = m.model == 0
+                      ? launch_model<0>(F, P, Pf, H, moments, m, table, table32, N, partials, nblk, sc, st)
+                      : launch_model<1>(F, P, Pf, H, moments, m, table, table32, N, partials, nblk, sc, st);
   g_mf_launches += 1;
   if (e != cudaSuccess) return e;
   return mf_launch_fin_means(partials, nblk, moments ? 36 : 18, N, sc, st);

@@ -102,8 +102,9 @@ cudaError_t mf_v2_xyi_dw(const void* spec, double* out, double* partials, const 
 cudaError_t mf_launch_residual(const double* P, void* spec, double* b, double* partials,
                                const XYArgs& xa, const ZArgs& za, bool dw, cudaStream_t st);
 // The same residual with FP32 transforms (fixed-size kernels; xa, za with the
-// FP32 tables): P rounded into Pf, b through bf, both 9N floats of scratch.
-// Accurate to FP32 relative to abs(P): for residuals far from convergence.
+// FP32 tables): P rounded into Pf (P null: Pf already holds P in FP32), b
+// through bf, both 9N floats of scratch.  Accurate to FP32 relative to
+// abs(P): for residuals far from convergence.
 cudaError_t mf_launch_residual_f32(const double* P, float* Pf, void* spec, float* bf, double* b,
                                    const XYArgs& xa, const ZArgs& za, cudaStream_t st);
 // which: 0 x-y forward of t, 1 z-pass, 2 x-y inverse with the CG residual update
@@ -171,9 +172,13 @@ cudaError_t mf_launch_fin_means(const double* partials, int nblk, int ncol, long
 // constitutive_dw.cu: P (no tangent) in double-word arithmetic, the averages,
 // and optionally H = F - I (FP32, H non-null) and the rotation moments;
 // table_dw: the material table as double-word values (layout of MatArgs.table)
+// Pf (with H, moments and table32, the FP32 copy of the material table):
+// P evaluated in FP32 from H and stored to Pf (9N floats) instead of P;
+// the averages of F keep double-word accuracy, those of P are FP32's.
 cudaError_t mf_launch_constitutive_dw(const double* F, double* P, float* H, bool moments, const MatArgs& m,
                                       const void* table_dw, long long N, double* partials, int nblk,
-                                      Scalars* sc, cudaStream_t st);
+                                      Scalars* sc, cudaStream_t st, float* Pf = nullptr,
+                                      const float* table32 = nullptr);
 cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int nblk, Scalars* sc,
                              cudaStream_t st);
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,

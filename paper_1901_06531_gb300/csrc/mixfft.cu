@@ -318,14 +318,20 @@ int flags_status(int flags) {
 }
 
 // P (and optionally the packed K) at the current F, voxel averages of F and
-// P; with want_H the FP32 H = F - I for the matrix-free tangent.
-int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false) {
+// P; with want_H the FP32 H = F - I for the matrix-free tangent.  p32 (the
+// double-word path, with H and moments): P evaluated in FP32 and left, in
+// FP32, in the scratch the FP32 residual transforms read (the t vector), P
+// itself untouched.
+int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false, bool p32 = false) {
   if (!want_K && c->dw_outer()) {
     // P, H and the moments in one double-word pass
+    const bool f32p = p32 && want_H && moments;
     const cudaError_t e = mf_launch_constitutive_dw(c->at<double>(c->oF), c->at<double>(c->oP),
                                                     want_H ? c->at<float>(c->oH) : nullptr, moments, mat_args(c),
                                                     c->ws + c->otabledw, c->N, c->at<double>(c->opart),
-                                                    c->pw_blocks, c->at<Scalars>(c->osc), c->st);
+                                                    c->pw_blocks, c->at<Scalars>(c->osc), c->st,
+                                                    f32p ? c->at<float>(c->oAp) : nullptr,
+                                                    c->at<float>(c->otable32));
     c->have_K = false;
     c->have_H = want_H && e == cudaSuccess;
     return cuda_status(e);
@@ -346,13 +352,15 @@ bool operator_ready(const mf_ctx* c) { return c->f32() ? c->have_H : c->have_K; 
 // the fixed-size kernels only); its error is FP32 rounding relative to abs(P),
 // harmless while the residual is large
 int run_residual(mf_ctx* c, const uint8_t* mask, const double* pbar, double* b, double* mean_out,
-                 bool fp32 = false) {
+                 bool fp32 = false, bool p_in_t = false) {
   if (fp32 && c->dw_residual()) {
+    // p_in_t: the constitutive pass left P in FP32 in the t vector
     ZArgs za = z_args(c, true, mask, -1.0 / (double)c->N);
     for (int k = 0; k < 9; ++k) za.add[k] = mask[k] ? pbar[k] : 0.0;
     za.mean_out = mean_out;
-    return cuda_status(mf_launch_residual_f32(c->at<double>(c->oP), c->at<float>(c->oAp), c->ws + c->ospec,
-                                              c->at<float>(c->op2), b, xy_args(c, true), za, c->st));
+    return cuda_status(mf_launch_residual_f32(p_in_t ? nullptr : c->at<double>(c->oP), c->at<float>(c->oAp),
+                                              c->ws + c->ospec, c->at<float>(c->op2), b, xy_args(c, true), za,
+                                              c->st));
   }
   const bool dw = c->dw_residual();
   ZArgs za = z_args(c, false, mask, -1.0 / (double)c->N, dw);
@@ -643,6 +651,7 @@ struct Runner {
   int k = 0, nn = 0, ncg = 0;
   double ratio = INFINITY;
   bool res_f32 = false;          // the last residual came from FP32 transforms
+  bool p_in_t = false;           // the last constitutive pass left P in FP32 in the t vector
   Defl defl;
 
   int init() {
@@ -677,10 +686,13 @@ struct Runner {
   }
 
   // constitutive pass: the full one (K in FP64, H and rotation moments in
-  // FP32) inside the Newton loop, P only for the final state of a step
-  int launch_constitutive(bool last) {
+  // FP32) inside the Newton loop, P only for the final state of a step.
+  // first: the pass after the predictor, whose residual uses the FP32
+  // transforms: P itself in FP32 as well (double-word outer arithmetic)
+  int launch_constitutive(bool last, bool first = false) {
     const bool f32 = c->f32();
-    return run_constitutive(c, !last && !f32, !last && f32, !last && f32);
+    p_in_t = first && f32 && c->dw_residual();
+    return run_constitutive(c, !last && !f32, !last && f32, !last && f32, p_in_t);
   }
 
   int start_step() {
@@ -692,7 +704,7 @@ struct Runner {
     nn = 0;
     ncg = 0;
     ratio = INFINITY;
-    int s = launch_constitutive(false);
+    int s = launch_constitutive(false, true);
     if (s) return s;
     phase = kAfterConst;
     return post();
@@ -712,7 +724,8 @@ struct Runner {
     // FP32 transforms are accurate enough for its correction; the later ones,
     // which decide convergence, keep FP64 accuracy
     res_f32 = (nn == 0) && c->dw_residual();
-    int s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores), res_f32);
+    int s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores), res_f32, res_f32 && p_in_t);
+    p_in_t = false;
     if (s) return s;
     defl.m = 0;
     if (c->f32()) {
@@ -726,9 +739,13 @@ struct Runner {
         return MF_CUDA_ERROR;
     }
     // FP32 inner solves: forcing sqrt(cg_rel) for the first Newton iteration
-    // of a step (its correction is followed by at least one more), cg_rel
-    // for the others
-    s = launch_cg(c, m, tol_cg, c->f32() ? (nn == 0 ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
+    // of a step (its correction is followed by at least one more) and for an
+    // iteration expected to be the last (the previous correction already
+    // below sqrt(tol_newton): with quadratic convergence this one, about its
+    // square, is below tol_newton, and a few correct digits of it leave the
+    // state accurate to a small fraction of tol_newton); cg_rel for the others
+    const bool loose = nn == 0 || ratio < sqrt(tol_newton);
+    s = launch_cg(c, m, tol_cg, c->f32() ? (loose ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
     if (s) return s;
     void* corr = c->ws + c->ox;
     if (c->f32()) {

@@ -364,8 +364,12 @@ cudaError_t mf_launch_residual_f32(const double* P, float* Pf, void* spec, float
                                    const XYArgs& xa, const ZArgs& za, cudaStream_t st) {
   if (!xa.v2) return cudaErrorInvalidValue;
   const long long n9 = 9 * xa.N;
-  k_d2f<<<stride_grid(n9), 256, 0, st>>>(P, Pf, n9);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (P) {
+    k_d2f<<<stride_grid(n9), 256, 0, st>>>(P, Pf, n9);
+    e = cudaGetLastError();
+    g_mf_launches += 1;
+  }
   if (e == cudaSuccess) e = mf_v2_xyf_f32(Pf, spec, xa, st);
   if (e == cudaSuccess) e = mf_v2_zp_f32(1, spec, za, st);
   if (e == cudaSuccess) e = mf_v2_xyi_f32(0, spec, bf, nullptr, xa, nullptr, st);
@@ -373,7 +377,7 @@ cudaError_t mf_launch_residual_f32(const double* P, float* Pf, void* spec, float
     k_f2d<<<stride_grid(n9), 256, 0, st>>>(bf, b, n9);
     e = cudaGetLastError();
   }
-  g_mf_launches += 2;
+  g_mf_launches += 1;
   return e;
 }
 
