@@ -53,6 +53,7 @@ typedef enum {
 typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
 typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
 typedef enum { MF_OUTER_DOUBLE_WORD = 0, MF_OUTER_FP64 = 1 } mf_outer_arith;
+typedef enum { MF_PROJ_FP32 = 0, MF_PROJ_OUTER = 1 } mf_projection_arith;
 
 typedef struct mf_ctx mf_ctx;
 
@@ -293,6 +294,17 @@ int mf_set_xy_split(mf_ctx* ctx, int split);
  * (non-split) kernels; MF_INVALID_ARG otherwise.  Its barrier waits are
  * bounded; a wait that gives up makes the solve return MF_DEVICE_TIMEOUT. */
 int mf_set_xy_persistent(mf_ctx* ctx, int on);
+
+/* FP32-inner contexts: arithmetic of the projection x <- G*(x) applied to
+ * every FP32 correction before the Newton update (Sec. 6 of the design
+ * notes: FP32 rounding leaves components G* annihilates, invisible to the
+ * FP64 residual).  MF_PROJ_FP32 (default): the FP32 transform kernels;
+ * MF_PROJ_OUTER: the correction widened to FP64 and projected in the outer
+ * arithmetic (double-word transforms, or FP64 with MF_OUTER_FP64): the
+ * fields then agree with FP64 solves to well below FP32 rounding, at the
+ * cost of a residual-sized transform per Newton iteration.  MF_INVALID_ARG
+ * for an unknown value or a non-FP32-inner context. */
+int mf_set_projection_arith(mf_ctx* ctx, int arith);
 
 /* Arithmetic of the outer (defect-correction) level of MF_FP32_INNER
  * contexts: the stress P(F) of the constitutive pass (Eq. eq:lineariz) and

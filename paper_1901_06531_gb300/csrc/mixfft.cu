@@ -222,6 +222,7 @@ struct mf_ctx {
   int cg_body_kernels = 0;      // kernel launches per pass of the CG graph's body
   int pw_blocks = 1;            // blocks of the grid-stride pointwise passes (one voxel per thread at most)
   int xy_persist = 0;           // FP32 x-y forward pass as the persistent bulk-copy kernel
+  int proj_arith = MF_PROJ_FP32;   // arithmetic of the projection of each FP32 correction
   cudaGraphExec_t cg_exec = nullptr;
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
@@ -748,23 +749,46 @@ struct Runner {
     s = launch_cg(c, m, tol_cg, c->f32() ? (loose ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
     if (s) return s;
     void* corr = c->ws + c->ox;
+    bool corr32 = c->f32();
     if (c->f32()) {
       // The FP32 correction, projected once more onto the range of G*: its
       // rounding leaves incompatible and Nyquist components that the
       // residual cannot see but that shift the equilibrium through the
       // nonlinear law; after the projection only the projection's own
-      // rounding is left of them.
-      const ZArgs za = z_args(c, true, m, 1.0 / (double)N);
-      if (mf_launch_project(true, c->ws + c->ox, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xy_args(c, true), za,
-                            nullptr, c->st) != cudaSuccess)
-        return MF_CUDA_ERROR;
-      corr = c->ws + c->op2;
+      // rounding is left of them (FP32's, or with MF_PROJ_OUTER the outer
+      // arithmetic's: the correction widened to FP64 in the residual buffer,
+      // free once the CG has started, and projected there).
+      if (c->proj_arith == MF_PROJ_OUTER) {
+        double* bd = c->at<double>(c->ob);
+        const bool dwp = c->dw_residual();
+        ZArgs za = z_args(c, false, m, 1.0 / (double)N, dwp);
+        if (c->v2) za.S = c->zSr;
+        cudaError_t e = mf_launch_to_double(c->ws + c->ox, bd, true, 9 * N, c->st);
+        if (e == cudaSuccess) {
+          if (dwp) {
+            const XYArgs xd = xy_args(c, false, true);
+            e = mf_v2_xyf_dw(bd, c->ws + c->ospec, xd, c->st);
+            if (e == cudaSuccess) e = mf_v2_zp_dw(c->ws + c->ospec, za, c->st);
+            if (e == cudaSuccess) e = mf_v2_xyi_dw(c->ws + c->ospec, bd, nullptr, xd, c->st);
+          } else {
+            e = mf_launch_project(false, bd, c->ws + c->ospec, bd, 0, nullptr, xy_args(c, false), za, nullptr, c->st);
+          }
+        }
+        if (e != cudaSuccess) return MF_CUDA_ERROR;
+        corr = bd;
+        corr32 = false;
+      } else {
+        const ZArgs za = z_args(c, true, m, 1.0 / (double)N);
+        if (mf_launch_project(true, c->ws + c->ox, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xy_args(c, true),
+                              za, nullptr, c->st) != cudaSuccess)
+          return MF_CUDA_ERROR;
+        corr = c->ws + c->op2;
+      }
     }
-    if (defl.m > 0 && mf_launch_defl_project(corr, true, false, F, N, defl, part, c->pw_blocks, sc, c->st) !=
+    if (defl.m > 0 && mf_launch_defl_project(corr, corr32, false, F, N, defl, part, c->pw_blocks, sc, c->st) !=
                           cudaSuccess)
       return MF_CUDA_ERROR;
-    if (mf_launch_newton_update(F, corr, c->f32(), defl.m > 0, N, part, c->pw_blocks, sc, c->st) !=
-        cudaSuccess)
+    if (mf_launch_newton_update(F, corr, corr32, defl.m > 0, N, part, c->pw_blocks, sc, c->st) != cudaSuccess)
       return MF_CUDA_ERROR;
     // FP32 corrections carry a rounding-level average on the strain-controlled
     // components; the FP64 outer level re-imposes F-bar there
@@ -1469,6 +1493,13 @@ int mf_set_xy_persistent(mf_ctx* c, int on) {
     return MF_INVALID_ARG;
   if (c->xy_persist != on) free_cg_graph(c);   // the captured loop holds the old kernels
   c->xy_persist = on;
+  return MF_OK;
+}
+
+int mf_set_projection_arith(mf_ctx* c, int arith) {
+  if (!c || (arith != MF_PROJ_FP32 && arith != MF_PROJ_OUTER)) return MF_INVALID_ARG;
+  if (arith == MF_PROJ_OUTER && c->prec != MF_FP32_INNER) return MF_INVALID_ARG;
+  c->proj_arith = arith;
   return MF_OK;
 }
 

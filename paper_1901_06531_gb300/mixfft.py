@@ -21,6 +21,7 @@ MF_TOO_LARGE = 8
 MF_FP64, MF_FP32_INNER = 0, 1
 MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
 MF_OUTER_DOUBLE_WORD, MF_OUTER_FP64 = 0, 1
+MF_PROJ_FP32, MF_PROJ_OUTER = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
@@ -61,6 +62,7 @@ _lib.mf_autotune.argtypes = [_vp, _vp, _vp]
 _lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
+_lib.mf_set_projection_arith.argtypes = [_vp, _i]
 _lib.mf_adjoint.argtypes = [_vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp, _vp]
 _lib.mf_last_cuda_error.argtypes = []
 _lib.mf_last_cuda_error.restype = ctypes.c_char_p
@@ -74,7 +76,8 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_stress", "mf_get_tangent", "mf_matvec", "mf_residual", "mf_residual_noalloc",
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
-            "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_last_cuda_error",
+            "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_projection_arith",
+            "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
 
 
@@ -318,6 +321,10 @@ class Context:
     def set_xy_split(self, split):
         """mf_set_xy_split: 0 fused x-y plane kernels, 1 separate row/column kernels."""
         _check("mf_set_xy_split", _lib.mf_set_xy_split(self.h, int(split)))
+
+    def set_projection_arith(self, arith):
+        """mf_set_projection_arith: MF_PROJ_FP32 or MF_PROJ_OUTER for the projection of each FP32 correction."""
+        _check("mf_set_projection_arith", _lib.mf_set_projection_arith(self.h, int(arith)))
 
     def set_xy_persistent(self, on):
         """mf_set_xy_persistent: 1 persistent bulk-copy FP32 x-y forward kernel, 0 one block per plane."""

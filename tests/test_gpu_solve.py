@@ -113,13 +113,46 @@ def test_fp32_inner_matches_fp64_oracle():
     # unique up to that rotation, F^T F and F^T P are unique.  Each FP32
     # correction is projected once more onto range(G*) before the update, so
     # the only components the FP64 residual cannot see are the rounding of
-    # that projection; the stated FP32-inner field tolerance is 3e-8
-    # (max-norm; stress-like fields times the largest stiffness, mu = 10).
+    # that projection; the stated FP32-inner field tolerance is 1e-8
+    # (max-norm; stress-like fields times the largest stiffness, mu = 10;
+    # measured 4.9e-9 and 7.7e-9).
     C, S = invariants(F, P)
     Cr, Sr = invariants(ref["F"], ref["P"])
     errs = (rel(C, Cr), np.max(np.abs(S - Sr)) / 10.0)
-    assert max(errs) < 3e-8, errs
+    assert max(errs) < 1e-8, errs
     check_control(out, mask, target, 1e-9, 1e-14)
+
+
+@pytest.mark.parametrize("outer", ["double_word", "fp64"])
+def test_fp32_inner_projection_in_outer_arithmetic(outer):
+    """MF_PROJ_OUTER: each FP32 correction widened to FP64 and projected in
+    the outer arithmetic (double-word transforms, or FP64 ones): the fields
+    agree with the FP64 oracle to 1e-9 (measured about 1e-10), the averages
+    to 1e-9 as in the default mode."""
+    mf = lib()
+    ctx, om = sphere_cell(mf, 16, mf.MF_FP32_INNER)
+    if outer == "fp64":
+        ctx.set_outer_arith(mf.MF_OUTER_FP64)
+    ctx.set_projection_arith(mf.MF_PROJ_OUTER)
+    mask, target = inputs.history_uniaxial_stress_ramp(5, 0.1)
+    out = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    F, P = ctx.get_fields()
+    assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
+    assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-9
+    C, S = invariants(F, P)
+    Cr, Sr = invariants(ref["F"], ref["P"])
+    errs = (rel(C, Cr), np.max(np.abs(S - Sr)) / 10.0)
+    assert max(errs) < 1e-9, errs
+    check_control(out, mask, target, 1e-9, 1e-14)
+
+
+def test_projection_arith_is_validated():
+    mf = lib()
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(8, 8, 8, mf.MF_FP64).set_projection_arith(mf.MF_PROJ_OUTER)
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(8, 8, 8, mf.MF_FP32_INNER).set_projection_arith(2)
 
 
 def test_fp32_inner_polycrystal():
@@ -134,7 +167,7 @@ def test_fp32_inner_polycrystal():
     ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
     F, _ = ctx.get_fields()
     assert rel(out["Fbar"], ref["Fbar"]) < 1e-9
-    assert rel(F, ref["F"]) < 3e-8, rel(F, ref["F"])
+    assert rel(F, ref["F"]) < 1e-8, rel(F, ref["F"])   # measured 4.4e-10
 
 
 @pytest.mark.parametrize("n", [48, 96])
