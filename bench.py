@@ -717,13 +717,18 @@ def run_ours(args):
     time_cufft_matvec(ctx, x, y, 3)
     cf32_ms = time_cufft_matvec(ctx, x, y, 30)
     cf32_parts = ctx.time_cufft(m0, reps=10)
+    # the FP32-inner state after the steps the FP64 path runs below, for the
+    # accuracy comparison
+    fp64_steps = max(1, min(args.fp64_steps, args.steps))
+    ctx.set_F(None)
+    o32 = steps(ctx, 0, fp64_steps)
+    F32 = ctx.get_fields()[0]
     del ctx, x, y
     torch.cuda.empty_cache()
 
     # plain FP64 GPU path on the same steps, for the load-step comparison
     ctx64 = mf.Context(n, n, n, mf.MF_FP64)
     ctx64.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
-    fp64_steps = max(1, min(args.fp64_steps, args.steps))
     steps(ctx64, 0, 1)
     ctx64.set_F(None)
     torch.cuda.synchronize()
@@ -734,6 +739,14 @@ def run_ours(args):
     b.record(stream)
     torch.cuda.synchronize()
     fp64_ms = a.elapsed_time(b) / fp64_steps
+    F64 = ctx64.get_fields()[0]
+    pscale = float(np.max(np.abs(o64["Pbar"])))
+    accuracy = {"steps": fp64_steps,
+                "Fbar_max_rel": float(np.max(np.abs(o32["Fbar"] - o64["Fbar"])) / np.max(np.abs(o64["Fbar"]))),
+                "Pbar_max_abs_over_max_Pbar": float(np.max(np.abs(o32["Pbar"] - o64["Pbar"])) / pscale),
+                "F_field_max_rel": float(np.max(np.abs(F32 - F64)) / np.max(np.abs(F64))),
+                "note": "FP32 inner / double-word outer against the plain FP64 path, same steps and tolerances"}
+    del F32, F64
     ctx64.constitutive()
     x64 = torch.randn(9 * N, dtype=torch.float64, device="cuda")
     y64 = torch.empty_like(x64)
@@ -787,6 +800,7 @@ def run_ours(args):
         "load_step_ms": {"fp32_inner_median": float(np.median(step_ms)),
                          "fp32_inner_fp64_outer": fp64_outer_ms,
                          "fp64_plain": fp64_ms, "fp64_steps_timed": fp64_steps},
+        "accuracy_fp32_inner_vs_fp64": accuracy,
         "iterations": {"fp32_inner_newton_cg_per_step": its,
                        "fp64_newton": o64["newton"].tolist(), "fp64_cg": o64["cg"].tolist()},
     }
