@@ -73,3 +73,39 @@ def test_calls_without_workspace_are_rejected(lib):
     lib.mf_destroy(h)
     lib.mf_status_string.restype = ctypes.c_char_p
     assert lib.mf_status_string(3).startswith(b"CG breakdown")
+
+
+def test_option_setters_validate_without_gpu(lib):
+    """Choices a context's precision or size does not support are rejected on
+    the host: the outer-arithmetic projection and the persistent x-y kernel
+    need an FP32-inner context, the persistent kernel a 48-128^2 plane."""
+    from paper_1901_06531_gb300 import mixfft
+    h = ctypes.c_void_p()
+    lib.mf_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    for name in ("mf_set_projection_arith", "mf_set_xy_persistent", "mf_set_xy_split", "mf_set_outer_arith"):
+        getattr(lib, name).argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mf_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.mf_create(ctypes.byref(h), 16, 16, 16, mixfft.MF_FP64, None) == 0
+    assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_OUTER) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_FP32) == mixfft.MF_OK
+    assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_INVALID_ARG
+    lib.mf_destroy(h)
+    assert lib.mf_create(ctypes.byref(h), 64, 64, 32, mixfft.MF_FP32_INNER, None) == 0
+    assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_OUTER) == mixfft.MF_OK
+    assert lib.mf_set_projection_arith(h, 7) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_OK
+    assert lib.mf_set_xy_persistent(h, 0) == mixfft.MF_OK
+    assert lib.mf_set_xy_persistent(h, 3) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_outer_arith(h, 5) == mixfft.MF_INVALID_ARG
+    lib.mf_destroy(h)
+    assert lib.mf_create(ctypes.byref(h), 32, 32, 32, mixfft.MF_FP32_INNER, None) == 0
+    assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_INVALID_ARG   # no persistent kernel for 32^2 planes
+    lib.mf_destroy(h)
+
+
+def test_binding_enums_match_the_header():
+    txt = open(os.path.join(ROOT, "include", "mixfft.h")).read()
+    from paper_1901_06531_gb300 import mixfft
+    for name, val in re.findall(r"\b(MF_[A-Z0-9_]+)\s*=\s*(\d+)", txt):
+        assert getattr(mixfft, name) == int(val), name
