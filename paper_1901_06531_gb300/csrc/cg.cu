@@ -16,6 +16,8 @@
 // the phase's parameters:
 //   neo-Hookean   K:q = mu q + lam (G:q) G + (mu - lam ln J) G q^T G, G = F^-T
 //   St V.-K.      K:q = q S + F (C : sym(F^T q)),  S = C : E,  E = (H + H^T + H^T H)/2
+#include <type_traits>
+
 #include "launch.h"
 
 namespace {
@@ -163,24 +165,33 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
   __shared__ double tot[1];
   T beta = (T)0, alpha = (T)0;
   pdl_wait();
+  bool first = false;   // first CG iteration: p = r, x = 0 (neither previous vector is read)
   if (CG) {
     if (*(volatile const int*)&sc->stop) return;
     beta = (T)sc->beta;
     alpha = (T)sc->alpha;
+    first = sc->its == 0;
   }
   double acc64 = 0.0;
   Dot32 acc32;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-       v += (long long)gridDim.x * blockDim.x) {
-    // every load of the voxel is issued before any arithmetic
+  // one voxel; FIRST: p = r, x = 0 without loading the previous vectors
+  // (the loop is instantiated once per case, so that in each every load of
+  // the voxel is issued before any arithmetic)
+  auto voxel = [&](long long v, auto first_tag) {
+    constexpr bool FIRST = decltype(first_tag)::value;
     T po[9], rv[9], xv[9];
     float h[9];
     int ph = 0;
+    if constexpr (FIRST) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) po[c] = pin[c * N + v];
-    if (CG) {
+      for (int c = 0; c < 9; ++c) { rv[c] = r[c * N + v]; po[c] = (T)0; xv[c] = (T)0; }
+    } else {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) { rv[c] = r[c * N + v]; xv[c] = x[c * N + v]; }
+      for (int c = 0; c < 9; ++c) po[c] = pin[c * N + v];
+      if (CG) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) { rv[c] = r[c * N + v]; xv[c] = x[c * N + v]; }
+      }
     }
     if (TAN != 0) {
 #pragma unroll
@@ -224,6 +235,13 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
       if (sizeof(T) == 4) acc32.add_prod((float)q[c], (float)o[c]);
       else acc64 += (double)q[c] * (double)o[c];
     }
+  };
+  const long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long dv = (long long)gridDim.x * blockDim.x;
+  if (CG && first) {
+    for (long long v = v0; v < N; v += dv) voxel(v, std::true_type{});
+  } else {
+    for (long long v = v0; v < N; v += dv) voxel(v, std::false_type{});
   }
   if (partials) {
     double acc[1] = {sizeof(T) == 4 ? acc32.value() : acc64};
@@ -286,7 +304,12 @@ template <typename T>
 __global__ void k_axpy_last(T* __restrict__ x, const T* __restrict__ p0, const T* __restrict__ p1, long long n,
                             const Scalars* sc) {
   const int its = sc->its;
-  if (its == 0) return;
+  if (its == 0) {   // no iteration ran (converged at the start, or stopped in the first): x = 0
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      x[i] = (T)0;
+    return;
+  }
   const T* p = (its & 1) ? p1 : p0;
   const T a = (T)sc->alpha;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;

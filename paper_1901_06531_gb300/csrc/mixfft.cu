@@ -1329,8 +1329,11 @@ int mf_time_kernels(mf_ctx* c, const uint8_t* mask, int reps, int graph, float* 
   Scalars* sc = c->at<Scalars>(c->osc);
   double* part = c->at<double>(c->opart);
   // operands: a CG state made of the context's vectors (values are not used
-  // for anything but timing); alpha = beta = 0 keeps them bounded
+  // for anything but timing); alpha = beta = 0 keeps them bounded; its = 1:
+  // a later iteration's tangent pass (the first one reads two vectors less)
+  static const int kOne = 1;
   cudaError_t e = cudaMemsetAsync(c->ws + c->osc, 0, sizeof(Scalars), c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sc->its, &kOne, sizeof(int), cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess && graph && !c->cap_st) {
     e = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
     if (e != cudaSuccess) c->cap_st = nullptr;

@@ -291,14 +291,15 @@ __global__ void k_predictor(double* __restrict__ F, long long N, Load9 ld, const
   }
 }
 
-// r = b rounded to the inner type, x = p' = 0, and the block partials of
-// r.r.  FP32: b is rounded through its double-word split (no FP64
-// instruction, the FP64 pipe being slow on this part) and r.r is summed
-// from exact FP32 products with Neumaier compensation, thread totals in FP64.
+// r = b rounded to the inner type and the block partials of r.r (x and the
+// previous direction are not touched: the first tangent pass, its = 0, takes
+// p = r and writes x = 0 without reading either).  FP32: b is rounded
+// through its double-word split (no FP64 instruction, the FP64 pipe being
+// slow on this part) and r.r is summed from exact FP32 products with
+// Neumaier compensation, thread totals in FP64.
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_cg_init(const double* __restrict__ b, T* __restrict__ x,
-                                                         T* __restrict__ r, T* __restrict__ p, long long n9,
-                                                         double* __restrict__ partials) {
+__global__ void __launch_bounds__(kRedThreads) k_cg_init(const double* __restrict__ b, T* __restrict__ r,
+                                                         long long n9, double* __restrict__ partials) {
   __shared__ double tot[1];
   double acc[1] = {0.0};
   float fs = 0.f, fc = 0.f;
@@ -321,8 +322,6 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_init(const double* __restric
       r[i] = v;
       acc[0] += (double)v * (double)v;
     }
-    p[i] = (T)0;    // previous direction of the first iteration
-    x[i] = (T)0;
   }
   if constexpr (sizeof(T) == 4) acc[0] = (double)fs + (double)fc;
   block_sum<1>(acc, tot);
@@ -561,8 +560,10 @@ cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, co
 cudaError_t mf_launch_cg_init(const double* b, void* x, void* r, void* p, bool f32, long long n9,
                               double* partials, int nblk, double tol_cg, double cg_rel, long long N,
                               Scalars* sc, cudaStream_t st) {
-  if (f32) k_cg_init<float><<<nblk, kRedThreads, 0, st>>>(b, (float*)x, (float*)r, (float*)p, n9, partials);
-  else k_cg_init<double><<<nblk, kRedThreads, 0, st>>>(b, (double*)x, (double*)r, (double*)p, n9, partials);
+  (void)x;
+  (void)p;
+  if (f32) k_cg_init<float><<<nblk, kRedThreads, 0, st>>>(b, (float*)r, n9, partials);
+  else k_cg_init<double><<<nblk, kRedThreads, 0, st>>>(b, (double*)r, n9, partials);
   k_fin_cg_init<<<1, kRedThreads, 0, st>>>(partials, nblk, tol_cg, cg_rel, N, sc);
   g_mf_launches += 2;
   return cudaGetLastError();
