@@ -46,6 +46,9 @@ METRIC = "Newton load steps/s at 128^3 (FP32-inner/FP64-outer), polycrystal cycl
 KERNELS = ["tangent_cg", "xy_forward", "zpass_projection", "xy_inverse_residual"]
 ALGO_BYTES_F32 = [4 * 36 + 4 + 3 * 36, 36 + 36, 36 + 36, 3 * 36]
 ALGO_BYTES_F64 = [3 * 72 + 360 + 3 * 72, 72 + 72, 72 + 72, 3 * 72]
+# one projected-operator application y = G*(K:x), FP32 with the matrix-free
+# tangent: K:x (x, H, phase in; t out), x-y forward, z-pass, x-y inverse
+MATVEC_BYTES_F32 = (36 + 36 + 4 + 36) + 72 + 72 + 72
 
 
 def workload(n=N1, ngrains=NGRAINS, seed=SEED):
@@ -698,7 +701,7 @@ def run_ours(args):
         return float(np.median([a.elapsed_time(b) for a, b in ts]))
 
     time_matvec(ctx, x, y, 3)
-    mv32_ms = time_matvec(ctx, x, y, 30)
+    mv32_ms = time_matvec(ctx, x, y, 100)
 
     def time_cufft_matvec(c, xx, yy, reps):
         ts = []
@@ -791,7 +794,12 @@ def run_ours(args):
                          for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
         "autotune": {"zpass_tile_columns": ztile,
                      "zpass_ms_by_tile": {str(w): float(m) for w, m in zip((4, 8, 16), ztile_ms)}},
-        "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9},
+        "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9,
+                            "reps": "median of 100 (FP32) and 10 (FP64) warm applications, events per application"},
+        "matvec_roofline_fp32": {"bytes_per_voxel": MATVEC_BYTES_F32,
+                                 "achieved_GB_s": MATVEC_BYTES_F32 * N / (mv32_ms * 1e-3) / 1e9,
+                                 "frac": MATVEC_BYTES_F32 * N / (mv32_ms * 1e-3) / 1e9 / peak,
+                                 "unit": "GB/s", "peak": peak},
         "matvec_cufft_comparison_gvoxel_s": {
             "fp32": N / (cf32_ms * 1e-3) / 1e9, "fp64": N / (cf64_ms * 1e-3) / 1e9,
             "fp32_parts_ms": {"r2c": float(cf32_parts[0]), "gstar": float(cf32_parts[1]),
