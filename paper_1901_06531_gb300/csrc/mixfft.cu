@@ -260,7 +260,9 @@ XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   a.split = c->xy_split;
   a.skip = nullptr;
   a.fin = 0;
-  a.pdl = 0;
+  // the fused fixed-size kernels wait for their predecessor themselves
+  // (pdl_wait): launch them with programmatic dependent launch everywhere
+  a.pdl = (c->v2 && !c->xy_split) ? 1 : 0;
   a.persist = (f32 && !dw && c->xy_persist && c->v2 && !c->xy_split) ? 1 : 0;
   a.flags = &c->at<Scalars>(c->osc)->flags;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
@@ -277,6 +279,7 @@ ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale, bool 
   ZArgs a;
   memset(&a, 0, sizeof(a));
   a.v2 = c->v2;
+  a.pdl = c->v2;   // the fixed-size z-pass waits for its predecessor itself
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.pz = c->pz;
   size_t esz;
@@ -395,7 +398,7 @@ int run_matvec(mf_ctx* c, const void* x, void* y, const uint8_t* mask) {
   const XYArgs xa = xy_args(c, c->f32());
   cudaError_t e = mf_launch_tangent(x, nullptr, nullptr, nullptr, c->f32(), tangent_kind(c), false,
                                     tangent_args(c), c->ws + c->oAp, c->N, nullptr, c->pw_blocks,
-                                    nullptr, c->st);
+                                    nullptr, c->st, false, true);
   if (e == cudaSuccess)
     e = mf_launch_project(c->f32(), c->ws + c->oAp, c->ws + c->ospec, y, 0, nullptr, xa, za, nullptr,
                           c->st);
@@ -444,7 +447,6 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   // predecessor's completion (saves the launch gap: 8 CG-bound 32^3 cells
   // solve in half the time; neutral at 128^3)
   const bool pdl = xa.v2 && !xa.split;
-  xa.pdl = za.pdl = pdl ? 1 : 0;
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
   const int nplanes = mf_xy_blocks(c->ny, c->nz, c->xy_split != 0);
