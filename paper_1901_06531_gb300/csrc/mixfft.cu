@@ -752,7 +752,12 @@ struct Runner {
     if (s) return s;
     void* corr = c->ws + c->ox;
     bool corr32 = c->f32();
-    if (c->f32()) {
+    // The projection matters for the large corrections (the first two of a
+    // step); a later one, below 1e-6 of F after a correction that small,
+    // carries an out-of-range rounding of ~1e-13 of F: it is applied as the
+    // CG left it (unless the projection runs in the outer arithmetic).
+    const bool project = c->proj_arith == MF_PROJ_OUTER || nn < 2 || !(ratio < 1e-6);
+    if (c->f32() && project) {
       // The FP32 correction, projected once more onto the range of G*: its
       // rounding leaves incompatible and Nyquist components that the
       // residual cannot see but that shift the equilibrium through the
