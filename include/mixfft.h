@@ -296,9 +296,9 @@ int mf_set_xy_split(mf_ctx* ctx, int split);
 int mf_set_xy_persistent(mf_ctx* ctx, int on);
 
 /* FP32-inner contexts: arithmetic of the projection x <- G*(x) applied to
- * every FP32 correction before the Newton update (Sec. 6 of the design
- * notes: FP32 rounding leaves components G* annihilates, invisible to the
- * FP64 residual).  MF_PROJ_FP32 (default): the FP32 transform kernels;
+ * every FP32 correction before the Newton update (FP32 rounding leaves in
+ * the correction components that G* annihilates: invisible to the FP64
+ * residual, they still shift the equilibrium through the nonlinear law).  MF_PROJ_FP32 (default): the FP32 transform kernels;
  * MF_PROJ_OUTER: the correction widened to FP64 and projected in the outer
  * arithmetic (double-word transforms, or FP64 with MF_OUTER_FP64): the
  * fields then agree with FP64 solves to well below FP32 rounding, at the
