@@ -239,6 +239,15 @@ int mf_time_cufft(mf_ctx* ctx, const uint8_t* mask, int reps, float* ms_out);
 /* Wait for the context's stream. */
 int mf_sync(mf_ctx* ctx);
 
+/* Failure-detection self-test: one block on the current device waits on a
+ * shared-memory barrier that nothing completes, with the bound every
+ * barrier wait of the library has (here max_polls polls, 1..2^20).  The
+ * wait gives up, the block records a device timeout and exits, and the call
+ * returns MF_DEVICE_TIMEOUT (anything else is a failure of the mechanism);
+ * the device stays usable.  Synchronous on the legacy stream; allocates
+ * nothing (the flag word is a static device variable). */
+int mf_selftest_wait_timeout(int max_polls);
+
 /* Autotuner: time the z-pass tile candidates (4, 8, 16 columns per block) of
  * the fixed-size transform kernels for this context's size and precision and
  * keep the fastest (CUDA events on the context's stream, L2 flushed before

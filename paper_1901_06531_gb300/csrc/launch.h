@@ -88,6 +88,10 @@ cudaError_t mf_v2_xyi_f64(int mode, const void* spec, void* out, double* partial
                           const Scalars* sc, cudaStream_t st);
 cudaError_t mf_v2_zp_f64(int mode, void* spec, const ZArgs& a, cudaStream_t st);
 
+// transform2_f32.cu: one block waits, at most max_polls polls, on a barrier
+// nothing arrives at, and sets MF_FLAG_TIMEOUT in *flags (device int)
+cudaError_t mf_launch_wait_selftest(int max_polls, int* flags, cudaStream_t st);
+
 // transform2_dw.cu: the residual transforms in double-word FP32 arithmetic
 // (P in, b out in FP64; spectrum and twiddle tables double-word complex)
 cudaError_t mf_v2_xyf_dw(const double* in, void* spec, const XYArgs& a, cudaStream_t st);

@@ -1527,6 +1527,23 @@ int mf_sync(mf_ctx* c) {
   return cuda_status(cudaStreamSynchronize(c->st));
 }
 
+namespace {
+__device__ int g_selftest_flags;   // the self-test's flag word (no allocation)
+}
+
+int mf_selftest_wait_timeout(int max_polls) {
+  if (max_polls < 1 || max_polls > (1 << 20)) return MF_INVALID_ARG;
+  int* flags = nullptr;
+  const int zero = 0;
+  int got = 0;
+  cudaError_t e = cudaGetSymbolAddress((void**)&flags, g_selftest_flags);
+  if (e == cudaSuccess) e = cudaMemcpy(flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = mf_launch_wait_selftest(max_polls, flags, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&got, flags, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  return flags_status(got);
+}
+
 const char* mf_last_cuda_error(void) { return g_last_cuda_error; }
 
 int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out) {

@@ -63,6 +63,7 @@ _lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
 _lib.mf_set_projection_arith.argtypes = [_vp, _i]
+_lib.mf_selftest_wait_timeout.argtypes = [_i]
 _lib.mf_adjoint.argtypes = [_vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp, _vp]
 _lib.mf_last_cuda_error.argtypes = []
 _lib.mf_last_cuda_error.restype = ctypes.c_char_p
@@ -77,7 +78,7 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
             "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_projection_arith",
-            "mf_last_cuda_error",
+            "mf_selftest_wait_timeout", "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
 
 
@@ -336,3 +337,9 @@ class Context:
 
     def sync(self):
         _check("mf_sync", _lib.mf_sync(self.h))
+
+
+def selftest_wait_timeout(max_polls=1000):
+    """mf_selftest_wait_timeout: the library's status for a bounded device
+    wait that runs out (MF_DEVICE_TIMEOUT when the mechanism works)."""
+    return int(_lib.mf_selftest_wait_timeout(int(max_polls)))

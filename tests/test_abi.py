@@ -109,3 +109,9 @@ def test_binding_enums_match_the_header():
     from paper_1901_06531_gb300 import mixfft
     for name, val in re.findall(r"\b(MF_[A-Z0-9_]+)\s*=\s*(\d+)", txt):
         assert getattr(mixfft, name) == int(val), name
+
+
+def test_wait_selftest_validates_its_bound_without_gpu(lib):
+    lib.mf_selftest_wait_timeout.argtypes = [ctypes.c_int]
+    assert lib.mf_selftest_wait_timeout(0) == 1
+    assert lib.mf_selftest_wait_timeout((1 << 20) + 1) == 1

@@ -245,3 +245,16 @@ def test_status_cg_breakdown_rotation_mode():
     with pytest.raises(mf.MixFFTError) as e:
         ctx.solve(mask, target, 1e-8, 1e-10, max_cg=2000)
     assert e.value.status in (mf.MF_CG_BREAKDOWN, mf.MF_NOT_CONVERGED)
+
+
+def test_device_wait_timeout_is_reported():
+    """Failure detection without a fault: a device barrier wait that nothing
+    completes gives up after its bound and the library reports
+    MF_DEVICE_TIMEOUT; the device keeps working (a solve runs afterwards)."""
+    mf = lib()
+    assert mf.selftest_wait_timeout(1000) == mf.MF_DEVICE_TIMEOUT
+    assert mf.selftest_wait_timeout(1) == mf.MF_DEVICE_TIMEOUT
+    ctx, om = sphere_cell(mf, 8, mf.MF_FP32_INNER)
+    mask, target = inputs.history_uniaxial_stress_ramp(1, 0.02)
+    out = ctx.solve(mask, target, 1e-8, 1e-10)
+    assert out["newton"][0] >= 1
