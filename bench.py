@@ -601,7 +601,7 @@ def run_ours(args):
 
     ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
-    ztile, ztile_ms = ctx.autotune()
+    ztile, ztile_ms, xy_persist, xy_ms = ctx.autotune()
 
     def steps(c, k0, k1):
         idx = [k % nsteps_hist for k in range(k0, k1)]
@@ -793,7 +793,9 @@ def run_ours(args):
         "kernels_fp64": {k: {"ms": float(t), "GB_s": b * N / (t * 1e-3) / 1e9}
                          for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
         "autotune": {"zpass_tile_columns": ztile,
-                     "zpass_ms_by_tile": {str(w): float(m) for w, m in zip((4, 8, 16), ztile_ms)}},
+                     "zpass_ms_by_tile": {str(w): float(m) for w, m in zip((4, 8, 16), ztile_ms)},
+                     "xy_forward_schedule": "persistent bulk-copy" if xy_persist else "one block per plane",
+                     "xy_forward_ms_by_schedule": {"per_plane": float(xy_ms[0]), "persistent": float(xy_ms[1])}},
         "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9,
                             "reps": "median of 100 (FP32) and 10 (FP64) warm applications, events per application"},
         "matvec_roofline_fp32": {"bytes_per_voxel": MATVEC_BYTES_F32,

@@ -251,13 +251,19 @@ int mf_selftest_wait_timeout(int max_polls);
 /* Autotuner: time the z-pass tile candidates (4, 8, 16 columns per block) of
  * the fixed-size transform kernels for this context's size and precision and
  * keep the fastest (CUDA events on the context's stream, L2 flushed before
- * every launch).  The choice is cached per (nx, ny, nz, precision) for the
- * process; mf_solve and mf_solve_batch run the tuner on a context's first
- * solve if no choice is cached.  This call re-times and replaces the cached
- * choice.  zs_out: host int32 or NULL, the chosen width; ms_out: host 3
- * floats or NULL, mean ms per candidate (-1 when not applicable).  Contexts
- * served by the generic kernels keep their fixed tile. */
-int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out);
+ * every launch); also the residual's z-pass tile (4, 8) and, for FP32-inner
+ * contexts whose planes have the persistent x-y kernel, the schedule of the
+ * x-y forward pass (one block per plane, or the persistent bulk-copy kernel;
+ * an explicit mf_set_xy_persistent takes precedence).  The choices are
+ * cached per (nx, ny, nz, precision, outer arithmetic) for the process;
+ * mf_solve and mf_solve_batch run the tuner on a context's first solve if
+ * nothing is cached.  This call re-times and replaces the cached choices.
+ * zs_out: host int32 or NULL, the chosen width; ms_out: host 3 floats or
+ * NULL, mean ms per width (-1 when not applicable); xy_out: host int32 or
+ * NULL, the context's x-y forward schedule after the call (1 persistent);
+ * xy_ms_out: host 2 floats or NULL, mean ms per schedule (-1 when not timed).
+ * Contexts served by the generic kernels keep their fixed tile. */
+int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out, int32_t* xy_out, float* xy_ms_out);
 
 /* Adjoint sensitivity of the homogenized response at the current F, which
  * must be a converged state of a step solved with control mask `mask` (for

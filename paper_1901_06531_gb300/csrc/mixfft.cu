@@ -222,6 +222,7 @@ struct mf_ctx {
   int cg_body_kernels = 0;      // kernel launches per pass of the CG graph's body
   int pw_blocks = 1;            // blocks of the grid-stride pointwise passes (one voxel per thread at most)
   int xy_persist = 0;           // FP32 x-y forward pass as the persistent bulk-copy kernel
+  int xy_persist_user = 0;      // set by mf_set_xy_persistent: the autotuner keeps it
   int proj_arith = MF_PROJ_FP32;   // arithmetic of the projection of each FP32 correction
   cudaGraphExec_t cg_exec = nullptr;
   unsigned cg_mask = 0xffffffffu;
@@ -509,7 +510,7 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
 // candidate is timed with CUDA events on the context's stream (L2 flushed
 // before every launch, one untimed launch first) and the fastest kept; the
 // choice is cached for the process per (nx, ny, nz, precision).
-struct TuneEntry { int nx, ny, nz, prec, dw, S, Sr; float ms[3], msr[2]; };
+struct TuneEntry { int nx, ny, nz, prec, dw, S, Sr, xyp; float ms[3], msr[2], msxy[2]; };
 std::vector<TuneEntry> g_tune_cache;
 std::mutex g_tune_mutex;
 
@@ -522,6 +523,10 @@ int autotune(mf_ctx* c, int reps) {
       if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec && t.dw == dwr) {
         c->zS = t.S;
         c->zSr = t.Sr;
+        if (!c->xy_persist_user && c->xy_persist != t.xyp) {
+          c->xy_persist = t.xyp;
+          free_cg_graph(c);
+        }
         c->tuned = true;
         return MF_OK;
       }
@@ -534,7 +539,7 @@ int autotune(mf_ctx* c, int reps) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
-  TuneEntry te{c->nx, c->ny, c->nz, c->prec, dwr, c->zS, c->zSr, {0, 0, 0}, {0, 0}};
+  TuneEntry te{c->nx, c->ny, c->nz, c->prec, dwr, c->zS, c->zSr, c->xy_persist, {0, 0, 0}, {0, 0}, {-1, -1}};
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
@@ -575,11 +580,37 @@ int autotune(mf_ctx* c, int reps) {
     te.msr[i] = (float)(tot / reps);
     if (e == cudaSuccess && te.msr[i] < bestr) { bestr = te.msr[i]; te.Sr = rcands[i]; }
   }
+  // the schedule of the FP32 x-y forward pass: one block per plane, or the
+  // persistent bulk-copy kernel (same results); the faster one is kept
+  // unless mf_set_xy_persistent chose
+  if (e == cudaSuccess && f32 && !c->xy_split && mf_persist_supported(c->nx)) {
+    float bestxy = 1e30f;
+    for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
+      XYArgs xf = xa;
+      xf.persist = form;
+      double tot = 0.0;
+      for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+        e = cudaMemsetAsync(c->ws + c->ob, 0, 9 * c->N * sizeof(double), c->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+        if (e == cudaSuccess)
+          e = mf_launch_project_part(0, f32, c->ws + c->oAp, c->ws + c->ospec, nullptr, nullptr, xf, za, nullptr,
+                                     c->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (r >= 0) tot += ms;
+      }
+      te.msxy[form] = (float)(tot / reps);
+      if (e == cudaSuccess && te.msxy[form] < bestxy) { bestxy = te.msxy[form]; te.xyp = form; }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_status(e); }
   c->zS = te.S;
   c->zSr = te.Sr;
+  if (!c->xy_persist_user) c->xy_persist = te.xyp;
   c->tuned = true;
   free_cg_graph(c);   // a captured loop holds the old tile
   std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -1503,6 +1534,7 @@ int mf_set_xy_persistent(mf_ctx* c, int on) {
     return MF_INVALID_ARG;
   if (c->xy_persist != on) free_cg_graph(c);   // the captured loop holds the old kernels
   c->xy_persist = on;
+  c->xy_persist_user = 1;
   return MF_OK;
 }
 
@@ -1546,7 +1578,7 @@ int mf_selftest_wait_timeout(int max_polls) {
 
 const char* mf_last_cuda_error(void) { return g_last_cuda_error; }
 
-int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out) {
+int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out, int32_t* xy_out, float* xy_ms_out) {
   if (!c) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   c->tuned = false;
@@ -1570,6 +1602,14 @@ int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out) {
       if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec &&
           t.dw == (c->dw_residual() ? 1 : 0))
         for (int i = 0; i < 3; ++i) ms_out[i] = t.ms[i];
+  }
+  if (xy_out) *xy_out = c->xy_persist;
+  if (xy_ms_out) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (const TuneEntry& t : g_tune_cache)
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec &&
+          t.dw == (c->dw_residual() ? 1 : 0))
+        for (int i = 0; i < 2; ++i) xy_ms_out[i] = t.msxy[i];
   }
   return MF_OK;
 }

@@ -58,7 +58,7 @@ _lib.mf_time_cufft.argtypes = [_vp, _vp, _i, _vp]
 _lib.mf_kernel_launches.argtypes = []
 _lib.mf_kernel_launches.restype = ctypes.c_longlong
 _lib.mf_sync.argtypes = [_vp]
-_lib.mf_autotune.argtypes = [_vp, _vp, _vp]
+_lib.mf_autotune.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
@@ -295,11 +295,14 @@ class Context:
         return ms.astype(np.float64)
 
     def autotune(self):
-        """mf_autotune: returns (chosen z-pass tile width, ms per candidate 2/4/8)."""
+        """mf_autotune: returns (chosen z-pass tile width, ms per width 4/8/16,
+        x-y forward schedule (1 persistent), ms per schedule)."""
         zs = np.zeros(1, dtype=np.int32)
         ms = np.zeros(3, dtype=np.float32)
-        _check("mf_autotune", _lib.mf_autotune(self.h, _ptr(zs), _ptr(ms)))
-        return int(zs[0]), ms.astype(np.float64)
+        xy = np.zeros(1, dtype=np.int32)
+        xyms = np.full(2, -1.0, dtype=np.float32)
+        _check("mf_autotune", _lib.mf_autotune(self.h, _ptr(zs), _ptr(ms), _ptr(xy), _ptr(xyms)))
+        return int(zs[0]), ms.astype(np.float64), int(xy[0]), xyms.astype(np.float64)
 
     def adjoint(self, mask, wF, wP, tol_cg=1e-11, cg_rel=0.0, max_cg=20000, dscale=None):
         """mf_adjoint at the current (converged) F: returns (J, dJ/d(mu, lam)

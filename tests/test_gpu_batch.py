@@ -92,8 +92,38 @@ def test_autotuned_tile_gives_identical_results(prec):
     mask = np.array([0, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8)
     y0 = torch.empty_like(x)
     ctx.matvec(x, y0, mask)
-    zs, ms = ctx.autotune()
+    zs, ms, xy, xyms = ctx.autotune()
     assert zs in (4, 8, 16) and np.all(ms[ms >= 0] > 0)
+    assert xy == 0 and np.all(xyms == -1.0)     # no persistent x-y kernel for 32^2 planes
     y1 = torch.empty_like(x)
     ctx.matvec(x, y1, mask)
     assert torch.equal(y0, y1)
+
+
+
+def test_autotuner_picks_the_xy_schedule():
+    """For an FP32-inner cell with 64^2 planes the autotuner times both x-y
+    forward schedules and keeps the faster; an explicit choice wins over it;
+    the operator is bitwise the same under either."""
+    import torch
+    mf = lib()
+    n = 64
+    ph, _ = inputs.rsa_spheres((n, n, n), 5.0, 0.2, 8)
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_NEOHOOKE, np.array([[1.0, 2.0], [10.0, 20.0]]), ph)
+    ctx.set_F(inputs.random_F((n, n, n), 9, 0.02))
+    ctx.constitutive()
+    zs, ms, xy, xyms = ctx.autotune()
+    assert xy in (0, 1) and np.all(xyms > 0)
+    assert xy == int(np.argmin(xyms))
+    x = torch.as_tensor(inputs.random_field((n, n, n), 10).reshape(-1), dtype=torch.float32, device="cuda")
+    mask = np.array([0, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8)
+    ys = []
+    for on in (1 - xy, xy):
+        ctx.set_xy_persistent(on)
+        _, _, xy2, _ = ctx.autotune()
+        assert xy2 == on                          # the explicit choice stays
+        y = torch.empty_like(x)
+        ctx.matvec(x, y, mask)
+        ys.append(y)
+    assert torch.equal(ys[0], ys[1])
