@@ -581,10 +581,10 @@ int autotune(mf_ctx* c, int reps) {
     if (e == cudaSuccess && te.msr[i] < bestr) { bestr = te.msr[i]; te.Sr = rcands[i]; }
   }
   // the schedule of the FP32 x-y forward pass: one block per plane, or the
-  // persistent bulk-copy kernel (same results); the faster one is kept
-  // unless mf_set_xy_persistent chose
+  // persistent bulk-copy kernel (same results); the persistent one is taken
+  // only when it is faster by more than 3% (single timed launches: a tie
+  // keeps the per-plane default), unless mf_set_xy_persistent chose
   if (e == cudaSuccess && f32 && !c->xy_split && mf_persist_supported(c->nx)) {
-    float bestxy = 1e30f;
     for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
       XYArgs xf = xa;
       xf.persist = form;
@@ -602,8 +602,8 @@ int autotune(mf_ctx* c, int reps) {
         if (r >= 0) tot += ms;
       }
       te.msxy[form] = (float)(tot / reps);
-      if (e == cudaSuccess && te.msxy[form] < bestxy) { bestxy = te.msxy[form]; te.xyp = form; }
     }
+    if (e == cudaSuccess) te.xyp = (te.msxy[1] < 0.97f * te.msxy[0]) ? 1 : 0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

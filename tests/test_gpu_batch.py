@@ -103,7 +103,8 @@ def test_autotuned_tile_gives_identical_results(prec):
 
 def test_autotuner_picks_the_xy_schedule():
     """For an FP32-inner cell with 64^2 planes the autotuner times both x-y
-    forward schedules and keeps the faster; an explicit choice wins over it;
+    forward schedules and keeps the per-plane one unless the persistent one
+    is faster by more than 3%; an explicit choice wins over it;
     the operator is bitwise the same under either."""
     import torch
     mf = lib()
@@ -115,7 +116,7 @@ def test_autotuner_picks_the_xy_schedule():
     ctx.constitutive()
     zs, ms, xy, xyms = ctx.autotune()
     assert xy in (0, 1) and np.all(xyms > 0)
-    assert xy == int(np.argmin(xyms))
+    assert xy == (1 if xyms[1] < 0.97 * xyms[0] else 0)   # the persistent kernel only when clearly faster
     x = torch.as_tensor(inputs.random_field((n, n, n), 10).reshape(-1), dtype=torch.float32, device="cuda")
     mask = np.array([0, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8)
     ys = []
