@@ -908,7 +908,13 @@ int check_solve_args(const mf_ctx* c, int nsteps, const uint8_t* mask, const dou
 
 // Drive a set of runners to completion; a cell whose event is pending is
 // skipped, and the host sleeps briefly only when no cell can advance.
+// While nothing can advance the host polls the events without sleeping for
+// up to kSpin (a sleep, however short, wakes tens of microseconds late on a
+// stock kernel, and the GPU has no queued work of that cell meanwhile), then
+// sleeps briefly between polls.
 void drive(std::vector<Runner>& rs) {
+  constexpr auto kSpin = std::chrono::milliseconds(5);
+  auto idle_since = std::chrono::steady_clock::now();
   for (;;) {
     bool any = false, progressed = false;
     for (Runner& r : rs) {
@@ -920,7 +926,11 @@ void drive(std::vector<Runner>& rs) {
       }
     }
     if (!any) return;
-    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    if (progressed) {
+      idle_since = std::chrono::steady_clock::now();
+    } else if (std::chrono::steady_clock::now() - idle_since > kSpin) {
+      std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
   }
 }
 
