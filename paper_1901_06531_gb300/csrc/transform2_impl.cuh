@@ -7,6 +7,16 @@
 
 namespace tr2 {
 
+// The shared-memory opt-in of a fixed-size kernel: its size is a constant of
+// the instantiation, so it is set once per process (on the device current at
+// the first launch; one process drives one device) instead of at every
+// launch, which for small cells costs as much host time as the launch.
+template <auto K>
+cudaError_t smem_once(size_t sm) {
+  static const cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return e;
+}
+
 inline int num_sms() {
   static int n = 0;
   if (n == 0) {
@@ -23,7 +33,7 @@ inline int num_sms() {
 template <int NX>
 cudaError_t launch_xyf_p(const float* in, void* spec, const XYArgs& a, cudaStream_t st) {
   const size_t sm = PersistShape<NX>::smem();
-  cudaError_t e = cudaFuncSetAttribute(k_xyf_p<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = smem_once<k_xyf_p<NX>>(sm);
   if (e != cudaSuccess) return e;
   const int nplanes = 9 * a.nz;
   const int grid = nplanes < num_sms() ? nplanes : num_sms();
@@ -39,7 +49,7 @@ cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a
     if (a.persist) return launch_xyf_p<NX>(in, spec, a, st);
   }
   const size_t sm = XYShape<T, NX>::smem();
-  cudaError_t e = cudaFuncSetAttribute(k_xyf<T, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = smem_once<k_xyf<T, NX>>(sm);
   if (e != cudaSuccess) return e;
   ++g_mf_launches;
   return launch_k(a.pdl != 0, k_xyf<T, NX>, dim3(9 * a.nz), dim3(xy_threads<T>()), sm, st, in, (C*)spec, a.nz, a.N,
@@ -51,7 +61,7 @@ cudaError_t launch_xyi(const void* spec, typename IOT<T>::t* out, double* partia
                        const Scalars* sc, cudaStream_t st) {
   typedef typename CT<T>::t C;
   const size_t sm = XYShape<T, NX>::smem();
-  cudaError_t e = cudaFuncSetAttribute(k_xyi<T, NX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = smem_once<k_xyi<T, NX, MODE>>(sm);
   if (e != cudaSuccess) return e;
   // the scalar block is written only by the fused finish (a.fin, MODE 3)
   ++g_mf_launches;
@@ -65,7 +75,7 @@ cudaError_t launch_zp_s(void* spec, const ZArgs& a, cudaStream_t st) {
   typedef typename CT<T>::t C;
   typedef ZShape<T, NZ, S> Sh;
   const size_t sm = Sh::smem();
-  cudaError_t e = cudaFuncSetAttribute(k_zp<T, NZ, MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = smem_once<k_zp<T, NZ, MODE, S>>(sm);
   if (e != cudaSuccess) return e;
   const int ncol = a.ny * (a.nx / 2);
   if (ncol % S) return cudaErrorInvalidValue;
