@@ -155,7 +155,7 @@ __device__ __forceinline__ void neohooke_apply(const float (&h)[9], float mu, fl
 // TAN 0: packed tangent K45 of type T; 1: neo-Hookean from H; 2: SVK from H.
 // CG true: p = r + beta p', x += alpha' p' first (p' = pin); false: p = pin.
 // FIN (with CG): the last block to finish sums the partials of p.t and sets
-// alpha (the work of k_fin_alpha, without its launch).
+// alpha (no separate finishing launch).
 template <typename T, int TAN, bool CG, bool FIN>
 __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin, const T* __restrict__ r,
                                                       T* __restrict__ pout, T* __restrict__ x,
@@ -268,14 +268,6 @@ __device__ __forceinline__ double col_sum(const double* partials, int n, double*
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads) k_fin_alpha(const double* __restrict__ partials, int n,
-                                                        Scalars* sc) {
-  __shared__ double shm[kThreads];
-  if (*(volatile const int*)&sc->stop) return;
-  const double pAp = col_sum(partials, n, shm);
-  if (threadIdx.x == 0) cg_finish_alpha(pAp, sc);
-}
-
 __global__ void __launch_bounds__(kThreads) k_fin_beta(const double* __restrict__ partials, int n,
                                                        Scalars* sc) {
   __shared__ double shm[kThreads];
@@ -355,12 +347,6 @@ cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* 
 #undef MF_TAN
   g_mf_launches += 1;
   return e;
-}
-
-cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st) {
-  k_fin_alpha<<<1, kThreads, 0, st>>>(partials, n, sc);
-  g_mf_launches += 1;
-  return cudaGetLastError();
 }
 
 __global__ void k_cg_batch_init(Scalars* sc, int max_its) {

@@ -131,13 +131,11 @@ struct TangentArgs {
   const float* scale;    // per-voxel scale or null
 };
 // tan: 0 packed K (FP64 or FP32), 1 neo-Hookean from H, 2 SVK from H (FP32).
-// fin_alpha (cg, partials non-null): the pass also finishes alpha (last block),
-// so no k_fin_alpha follows it.
+// fin_alpha (cg, partials non-null): the pass also finishes alpha (last block).
 // pdl: launched with programmatic dependent launch (see launch_k).
 cudaError_t mf_launch_tangent(const void* pin, const void* r, void* pout, void* x, bool f32, int tan,
                               bool cg, const TangentArgs& ta, void* t, long long N, double* partials,
                               int nblk, Scalars* sc, cudaStream_t st, bool fin_alpha = false, bool pdl = false);
-cudaError_t mf_launch_fin_alpha(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_fin_beta(const double* partials, int n, Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_cg_batch_init(Scalars* sc, int max_its, cudaStream_t st);
 cudaError_t mf_launch_cg_cond(const Scalars* sc, cudaGraphConditionalHandle h, cudaStream_t st, bool pdl = false);
