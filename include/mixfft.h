@@ -301,24 +301,29 @@ int mf_adjoint(mf_ctx* ctx, const uint8_t* mask, const double* wF, const double*
 int mf_set_xy_split(mf_ctx* ctx, int split);
 
 /* The FP32 x-y forward transform of an FP32-inner context as a persistent
- * kernel (1) or one block per (component, z) plane (0, the default): one
- * block per SM walks the planes, each plane arriving by one bulk copy (the
- * TMA unit) into one of two shared-memory staging buffers while the block
- * transforms the previous one.  Same stages in the same order: results are
- * identical.  Available for nx = ny in {48, 64, 96, 128} on the fused
- * (non-split) kernels; MF_INVALID_ARG otherwise.  Its barrier waits are
- * bounded; a wait that gives up makes the solve return MF_DEVICE_TIMEOUT. */
+ * kernel (1) or one block per (component, z) plane (0): one block per SM
+ * walks the planes, each plane arriving by one bulk copy (the TMA unit) into
+ * one of two shared-memory staging buffers while the block transforms the
+ * previous one.  Same stages in the same order: results are identical.
+ * Without this call the autotuner chooses (mf_autotune); with it the choice
+ * is fixed for the context.  Available for nx = ny in {48, 64, 96, 128} on
+ * the fused (non-split) kernels; MF_INVALID_ARG otherwise.  Its barrier
+ * waits are bounded; a wait that gives up makes the solve return
+ * MF_DEVICE_TIMEOUT. */
 int mf_set_xy_persistent(mf_ctx* ctx, int on);
 
 /* FP32-inner contexts: arithmetic of the projection x <- G*(x) applied to
- * every FP32 correction before the Newton update (FP32 rounding leaves in
- * the correction components that G* annihilates: invisible to the FP64
- * residual, they still shift the equilibrium through the nonlinear law).  MF_PROJ_FP32 (default): the FP32 transform kernels;
- * MF_PROJ_OUTER: the correction widened to FP64 and projected in the outer
- * arithmetic (double-word transforms, or FP64 with MF_OUTER_FP64): the
- * fields then agree with FP64 solves to well below FP32 rounding, at the
- * cost of a residual-sized transform per Newton iteration.  MF_INVALID_ARG
- * for an unknown value or a non-FP32-inner context. */
+ * the FP32 corrections before the Newton update (FP32 rounding leaves in
+ * a correction components that G* annihilates: invisible to the FP64
+ * residual, they still shift the equilibrium through the nonlinear law).
+ * MF_PROJ_FP32 (default): the FP32 transform kernels, on every correction
+ * but the late ones that follow a correction below 1e-6 of F (their
+ * out-of-range rounding is ~1e-13 of F); MF_PROJ_OUTER: every correction
+ * widened to FP64 and projected in the outer arithmetic (double-word
+ * transforms, or FP64 with MF_OUTER_FP64): the fields then agree with FP64
+ * solves to well below FP32 rounding, at the cost of a residual-sized
+ * transform per Newton iteration.  MF_INVALID_ARG for an unknown value or a
+ * non-FP32-inner context. */
 int mf_set_projection_arith(mf_ctx* ctx, int arith);
 
 /* Arithmetic of the outer (defect-correction) level of MF_FP32_INNER
