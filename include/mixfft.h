@@ -53,7 +53,7 @@ typedef enum {
 typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
 typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
 typedef enum { MF_OUTER_DOUBLE_WORD = 0, MF_OUTER_FP64 = 1 } mf_outer_arith;
-typedef enum { MF_PROJ_FP32 = 0, MF_PROJ_OUTER = 1 } mf_projection_arith;
+typedef enum { MF_PROJ_FP32 = 0, MF_PROJ_OUTER = 1, MF_PROJ_AUTO = 2 } mf_projection_arith;
 
 typedef struct mf_ctx mf_ctx;
 
@@ -192,14 +192,17 @@ int mf_residual(mf_ctx* ctx, const uint8_t* mask, const double* pbar, double* b_
  *   meanP_host: host, 9 doubles or NULL, receives <P>;
  *   stream: cudaStream_t for every copy and launch (NULL = default stream).
  * All other memory -- the half spectrum, index and twiddle tables, reduction
- * partials -- lives in one file-scope static device array of about 18.2 MiB
- * that every GPU loading the library holds until the process exits.  No
- * cudaMalloc or cudaFree is called.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call outside any stream capture.  All calls share the one array and
- * each call overwrites it, so calls that may overlap on the GPU (different
- * streams, or different host threads) race: serialise them.  The call
- * synchronises its stream before returning. */
+ * partials -- lives in one file-scope static device array of 18,958,592
+ * bytes (18.1 MiB) that every GPU loading the library holds until the
+ * process exits.  No cudaMalloc or cudaFree is called.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it for the process; make that first call
+ * outside any stream capture.  The cached address does not survive a reset
+ * of the device (cudaDeviceReset): do not call this entry point after one.
+ * stream must belong to the current device (MF_INVALID_ARG otherwise).  All
+ * calls share the one array and each call overwrites it, so calls that may
+ * overlap on the GPU (different streams, or different host threads) race:
+ * serialise them.  The call synchronises its stream before returning. */
 int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, const uint8_t* mask,
                         const double* pbar, double* b_dev, double* meanP_host, void* stream);
 
@@ -315,16 +318,36 @@ int mf_set_xy_persistent(mf_ctx* ctx, int on);
 /* FP32-inner contexts: arithmetic of the projection x <- G*(x) applied to
  * the FP32 corrections before the Newton update (FP32 rounding leaves in
  * a correction components that G* annihilates: invisible to the FP64
- * residual, they still shift the equilibrium through the nonlinear law).
- * MF_PROJ_FP32 (default): the FP32 transform kernels, on every correction
- * but the late ones that follow a correction below 1e-6 of F (their
- * out-of-range rounding is ~1e-13 of F); MF_PROJ_OUTER: every correction
- * widened to FP64 and projected in the outer arithmetic (double-word
- * transforms, or FP64 with MF_OUTER_FP64): the fields then agree with FP64
- * solves to well below FP32 rounding, at the cost of a residual-sized
- * transform per Newton iteration.  MF_INVALID_ARG for an unknown value or a
- * non-FP32-inner context. */
+ * residual, they still shift the equilibrium through the nonlinear law, by
+ * about the rounding of the projection, a few eps32 times the correction).
+ * MF_PROJ_FP32: the FP32 transform kernels, on every correction but the
+ * late ones that follow a correction below 1e-6 of F (their out-of-range
+ * rounding is ~1e-13 of F); the field error then grows with the sum of the
+ * correction sizes (about 4e-8 after a 20 % stretch in 8 steps).
+ * MF_PROJ_OUTER: every correction widened to FP64 and projected in the
+ * outer arithmetic (double-word transforms, or FP64 with MF_OUTER_FP64):
+ * the fields agree with FP64 solves to well below FP32 rounding, at the cost
+ * of a residual-sized transform per Newton iteration.  MF_PROJ_AUTO (the
+ * default): the outer arithmetic for the corrections of at least 1e-3 of F
+ * (max_v abs(dF_v) / abs(<F>); for the first correction of a step, the size
+ * of the previous step's first correction decides, and after mf_set_F,
+ * mf_set_material or mf_load_F the first step's first correction takes the
+ * outer arithmetic), FP32 for the smaller ones, whose rounding stays below
+ * about 1e-10 of F each.  MF_INVALID_ARG for an unknown value, or for a
+ * value other than MF_PROJ_FP32 on a non-FP32-inner context. */
 int mf_set_projection_arith(mf_ctx* ctx, int arith);
+
+/* Stopping rule of the CG solves of an MF_FP64 context (Sec. 4 gives the
+ * CG tolerance only as an absolute bound on the voxel-averaged residual).
+ * on = 0 (the default for MF_FP64): every Newton iteration solves to
+ * rms(r) <= tol_cg.  on = 1: the inexact-Newton forcing sequence of the
+ * FP32-inner mode, rms(r) <= max(tol_cg, f * rms(r0)) with f = sqrt(cg_rel)
+ * for the first Newton iteration of a step and for an iteration whose
+ * predecessor's correction was below sqrt(tol_newton), f = cg_rel otherwise;
+ * the converged state is the same to the Newton tolerance, with fewer CG
+ * iterations.  FP32-inner contexts always use the forcing sequence: on = 0
+ * is MF_INVALID_ARG for them, as is any other value. */
+int mf_set_inexact_newton(mf_ctx* ctx, int on);
 
 /* Arithmetic of the outer (defect-correction) level of MF_FP32_INNER
  * contexts: the stress P(F) of the constitutive pass (Eq. eq:lineariz) and

@@ -20,6 +20,9 @@
 namespace {
 
 constexpr int kMaxPhases = 65536;
+// MF_PROJ_AUTO: corrections of at least this size relative to F are projected
+// in the outer arithmetic (their FP32 projection would leave ~1e-10 of F)
+constexpr double kProjOuterAbove = 1e-3;
 constexpr int kPointwiseBlocks = 152 * 8;
 
 bool make_plan(int n, AxisPlan* p) {
@@ -223,12 +226,14 @@ struct mf_ctx {
   int pw_blocks = 1;            // blocks of the grid-stride pointwise passes (one voxel per thread at most)
   int xy_persist = 0;           // FP32 x-y forward pass as the persistent bulk-copy kernel
   int xy_persist_user = 0;      // set by mf_set_xy_persistent: the autotuner keeps it
-  int proj_arith = MF_PROJ_FP32;   // arithmetic of the projection of each FP32 correction
+  int proj_arith = MF_PROJ_AUTO;   // arithmetic of the projection of each FP32 correction
+  double first_ratio = INFINITY;   // max_v abs(dF_v)/abs(<F>) of the last step's first correction
   cudaGraphExec_t cg_exec = nullptr;
   unsigned cg_mask = 0xffffffffu;
   cudaStream_t cap_st = nullptr;   // private stream for graph capture (the legacy stream cannot capture)
   bool tuned = false;              // z-pass tile chosen by the autotuner
   int outer_arith = MF_OUTER_DOUBLE_WORD;
+  bool forcing64 = false;          // MF_FP64: inexact-Newton forcing of the FP32-inner mode
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   bool f32() const { return prec == MF_FP32_INNER; }
@@ -778,8 +783,10 @@ struct Runner {
     // below sqrt(tol_newton): with quadratic convergence this one, about its
     // square, is below tol_newton, and a few correct digits of it leave the
     // state accurate to a small fraction of tol_newton); cg_rel for the others
+    // (FP64 contexts take the same sequence with mf_set_inexact_newton)
     const bool loose = nn == 0 || ratio < sqrt(tol_newton);
-    s = launch_cg(c, m, tol_cg, c->f32() ? (loose ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
+    const bool forcing = c->f32() || c->forcing64;
+    s = launch_cg(c, m, tol_cg, forcing ? (loose ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
     if (s) return s;
     void* corr = c->ws + c->ox;
     bool corr32 = c->f32();
@@ -787,7 +794,16 @@ struct Runner {
     // step); a later one, below 1e-6 of F after a correction that small,
     // carries an out-of-range rounding of ~1e-13 of F: it is applied as the
     // CG left it (unless the projection runs in the outer arithmetic).
-    const bool project = c->proj_arith == MF_PROJ_OUTER || nn < 2 || !(ratio < 1e-6);
+    // MF_PROJ_AUTO takes the outer arithmetic for the corrections whose FP32
+    // rounding would matter: the first of a step when the last step's first
+    // correction was at least kProjOuterAbove of F (that size repeats from
+    // step to step along a load history; unknown after F was reset), a later
+    // one when its predecessor was ten times that.
+    const bool outer_proj =
+        c->proj_arith == MF_PROJ_OUTER ||
+        (c->proj_arith == MF_PROJ_AUTO &&
+         (nn == 0 ? !(c->first_ratio < kProjOuterAbove) : !(ratio < 10.0 * kProjOuterAbove)));
+    const bool project = outer_proj || nn < 2 || !(ratio < 1e-6);
     if (c->f32() && project) {
       // The FP32 correction, projected once more onto the range of G*: its
       // rounding leaves incompatible and Nyquist components that the
@@ -796,7 +812,7 @@ struct Runner {
       // rounding is left of them (FP32's, or with MF_PROJ_OUTER the outer
       // arithmetic's: the correction widened to FP64 in the residual buffer,
       // free once the CG has started, and projected there).
-      if (c->proj_arith == MF_PROJ_OUTER) {
+      if (outer_proj) {
         double* bd = c->at<double>(c->ob);
         const bool dwp = c->dw_residual();
         ZArgs za = z_args(c, false, m, 1.0 / (double)N, dwp);
@@ -862,6 +878,7 @@ struct Runner {
         for (int q = 0; q < 9; ++q) fn += h->meanF_new[q] * h->meanF_new[q];
         ratio = sqrt(h->dF2max) / sqrt(fn);
         ++nn;
+        if (nn == 1) c->first_ratio = ratio;
         // never stop on a correction from an FP32 residual
         const bool last = ratio < tol_newton && !res_f32;
         s = launch_constitutive(last);
@@ -1186,6 +1203,7 @@ int mf_set_material(mf_ctx* c, int model, int nphase, const double* params, cons
 int mf_set_F(mf_ctx* c, const double* F_host) {
   if (!c) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
+  c->first_ratio = INFINITY;
   const long long N = c->N;
   double* F = c->at<double>(c->oF);
   cudaError_t e;
@@ -1214,6 +1232,7 @@ int mf_save_F(mf_ctx* c, double* F_dev) {
 int mf_load_F(mf_ctx* c, const double* F_dev) {
   if (!c || !F_dev) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
+  c->first_ratio = INFINITY;
   const char* p = (const char*)F_dev;
   if (p + 9 * c->N * sizeof(double) > c->ws && p < c->ws + c->ws_need) return MF_INVALID_ARG;
   cudaError_t e = cudaMemcpyAsync(c->ws + c->oF, F_dev, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1549,9 +1568,16 @@ int mf_set_xy_persistent(mf_ctx* c, int on) {
 }
 
 int mf_set_projection_arith(mf_ctx* c, int arith) {
-  if (!c || (arith != MF_PROJ_FP32 && arith != MF_PROJ_OUTER)) return MF_INVALID_ARG;
-  if (arith == MF_PROJ_OUTER && c->prec != MF_FP32_INNER) return MF_INVALID_ARG;
+  if (!c || (arith != MF_PROJ_FP32 && arith != MF_PROJ_OUTER && arith != MF_PROJ_AUTO)) return MF_INVALID_ARG;
+  if (arith != MF_PROJ_FP32 && c->prec != MF_FP32_INNER) return MF_INVALID_ARG;
   c->proj_arith = arith;
+  return MF_OK;
+}
+
+int mf_set_inexact_newton(mf_ctx* c, int on) {
+  if (!c || (on != 0 && on != 1)) return MF_INVALID_ARG;
+  if (c->f32() && !on) return MF_INVALID_ARG;
+  c->forcing64 = on != 0;
   return MF_OK;
 }
 

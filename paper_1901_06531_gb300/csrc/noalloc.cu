@@ -86,9 +86,15 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
   if (!na_plan(nx, &px) || !na_plan(ny / 2, &pyh) || !na_plan(nz, &pz)) return MF_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // once per device: the device address of the scratch array
+  // once per device: the device address of the scratch array.  The address
+  // is looked up with the current device, so the stream must belong to it.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MF_CUDA_ERROR;
+  if (st) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return MF_CUDA_ERROR;
+    if (sdev != dev) return MF_INVALID_ARG;
+  }
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_mf_noalloc_scratch) != cudaSuccess || !p) return MF_CUDA_ERROR;
@@ -140,6 +146,7 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
   if (e != cudaSuccess) return MF_CUDA_ERROR;
 
   XYArgs xa;
+  memset(&xa, 0, sizeof(xa));   // persist, flags and the rest unused by the generic kernels: zero
   xa.v2 = 0;
   xa.split = 0;
   xa.skip = nullptr;

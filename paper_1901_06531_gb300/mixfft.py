@@ -21,7 +21,7 @@ MF_TOO_LARGE = 8
 MF_FP64, MF_FP32_INNER = 0, 1
 MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
 MF_OUTER_DOUBLE_WORD, MF_OUTER_FP64 = 0, 1
-MF_PROJ_FP32, MF_PROJ_OUTER = 0, 1
+MF_PROJ_FP32, MF_PROJ_OUTER, MF_PROJ_AUTO = 0, 1, 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
@@ -60,6 +60,7 @@ _lib.mf_kernel_launches.restype = ctypes.c_longlong
 _lib.mf_sync.argtypes = [_vp]
 _lib.mf_autotune.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.mf_set_outer_arith.argtypes = [_vp, _i]
+_lib.mf_set_inexact_newton.argtypes = [_vp, _i]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
 _lib.mf_set_projection_arith.argtypes = [_vp, _i]
@@ -78,7 +79,7 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
             "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_projection_arith",
-            "mf_selftest_wait_timeout", "mf_last_cuda_error",
+            "mf_set_inexact_newton", "mf_selftest_wait_timeout", "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
 
 
@@ -327,7 +328,8 @@ class Context:
         _check("mf_set_xy_split", _lib.mf_set_xy_split(self.h, int(split)))
 
     def set_projection_arith(self, arith):
-        """mf_set_projection_arith: MF_PROJ_FP32 or MF_PROJ_OUTER for the projection of each FP32 correction."""
+        """mf_set_projection_arith: MF_PROJ_FP32, MF_PROJ_OUTER or MF_PROJ_AUTO (default) for the
+        projection of each FP32 correction."""
         _check("mf_set_projection_arith", _lib.mf_set_projection_arith(self.h, int(arith)))
 
     def set_xy_persistent(self, on):
@@ -337,6 +339,11 @@ class Context:
     def set_outer_arith(self, arith):
         """mf_set_outer_arith: MF_OUTER_DOUBLE_WORD or MF_OUTER_FP64."""
         _check("mf_set_outer_arith", _lib.mf_set_outer_arith(self.h, arith))
+
+    def set_inexact_newton(self, on):
+        """mf_set_inexact_newton: the FP32-inner forcing sequence for the CG
+        solves of an FP64 context (1) or the absolute CG tolerance (0)."""
+        _check("mf_set_inexact_newton", _lib.mf_set_inexact_newton(self.h, int(on)))
 
     def sync(self):
         _check("mf_sync", _lib.mf_sync(self.h))

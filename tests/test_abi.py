@@ -83,21 +83,29 @@ def test_option_setters_validate_without_gpu(lib):
     h = ctypes.c_void_p()
     lib.mf_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
-    for name in ("mf_set_projection_arith", "mf_set_xy_persistent", "mf_set_xy_split", "mf_set_outer_arith"):
+    for name in ("mf_set_projection_arith", "mf_set_xy_persistent", "mf_set_xy_split", "mf_set_outer_arith",
+                 "mf_set_inexact_newton"):
         getattr(lib, name).argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.mf_destroy.argtypes = [ctypes.c_void_p]
     assert lib.mf_create(ctypes.byref(h), 16, 16, 16, mixfft.MF_FP64, None) == 0
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_OUTER) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_FP32) == mixfft.MF_OK
+    assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_AUTO) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_inexact_newton(h, 1) == mixfft.MF_OK
+    assert lib.mf_set_inexact_newton(h, 0) == mixfft.MF_OK
+    assert lib.mf_set_inexact_newton(h, 2) == mixfft.MF_INVALID_ARG
     lib.mf_destroy(h)
     assert lib.mf_create(ctypes.byref(h), 64, 64, 32, mixfft.MF_FP32_INNER, None) == 0
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_OUTER) == mixfft.MF_OK
     assert lib.mf_set_projection_arith(h, 7) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_AUTO) == mixfft.MF_OK
     assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_OK
     assert lib.mf_set_xy_persistent(h, 0) == mixfft.MF_OK
     assert lib.mf_set_xy_persistent(h, 3) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_outer_arith(h, 5) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_inexact_newton(h, 1) == mixfft.MF_OK
+    assert lib.mf_set_inexact_newton(h, 0) == mixfft.MF_INVALID_ARG
     lib.mf_destroy(h)
     assert lib.mf_create(ctypes.byref(h), 32, 32, 32, mixfft.MF_FP32_INNER, None) == 0
     assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_INVALID_ARG   # no persistent kernel for 32^2 planes

@@ -53,7 +53,15 @@ def test_uniaxial_stress_ramp_16_fp64():
     assert rel(out["Fbar"], ref["Fbar"]) < 1e-10
     assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) < 1e-10
     F, P = ctx.get_fields()
-    assert rel(F, ref["F"]) < 1e-8
+    # all nine components stress controlled with P-bar = diag(p, 0, 0): the
+    # rotation about e1 is a null mode (zero curvature, the residual blind to
+    # it), so F is unique up to it; F^T F and F^T P are unique and agree with
+    # the oracle to the FP64 gate 1e-10 (stress-like field over its largest
+    # stiffness, mu = 10)
+    C, S = invariants(F, P)
+    Cr, Sr = invariants(ref["F"], ref["P"])
+    errs = (rel(C, Cr), np.max(np.abs(S - Sr)) / 10.0)
+    assert max(errs) < 1e-10, errs
     np.testing.assert_array_equal(out["newton"], ref["newton"])
     assert np.all(np.abs(out["cg"] - ref["cg"]) <= 2 * out["newton"])
     # at these tolerances the control error is at the level of the last CG residual
@@ -170,20 +178,30 @@ def test_fp32_inner_polycrystal():
     assert rel(F, ref["F"]) < 1e-8, rel(F, ref["F"])   # measured 4.4e-10
 
 
-@pytest.mark.parametrize("n", [48, 96])
-def test_fp32_inner_cg_radix3_sizes(n):
-    """FP32-inner solves on 48^3 and 96^3 cells (the CG update of the x-y
-    inverse pass takes its shared-memory route there) against the FP64
-    solve of the same cell: averages to 1e-9."""
+@pytest.mark.parametrize("forcing", [0, 1])
+def test_fp64_inexact_newton_forcing(forcing):
+    """mf_set_inexact_newton: the FP64 path with the FP32-inner forcing
+    sequence reaches the oracle's converged state to the same 1e-10 as the
+    absolute CG stop, in fewer CG iterations."""
     mf = lib()
-    cell = inputs.batch_of_cells(1, 5, sizes=(n,), nsteps=2)[0]
-    outs = []
-    for prec in (mf.MF_FP32_INNER, mf.MF_FP64):
-        ctx = mf.Context(n, n, n, prec)
-        ctx.set_material(mf.MF_NEOHOOKE, cell["params"], cell["phase"])
-        outs.append(ctx.solve(cell["mask"], cell["target"], 1e-9, 1e-11, cg_rel=1e-4))
-    assert rel(outs[0]["Fbar"], outs[1]["Fbar"]) < 1e-9
-    assert np.max(np.abs(outs[0]["Pbar"] - outs[1]["Pbar"])) < 1e-9
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 31)
+    om = omat.Material(g, omat.SVK_CUBIC, params, R)
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(4, 0.2))
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    ctx = mf.Context(n, n, n, mf.MF_FP64)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    ctx.set_inexact_newton(forcing)
+    out = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+    F, P = ctx.get_fields()
+    assert rel(out["Fbar"], ref["Fbar"]) < 1e-10
+    assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) / 168.0 < 1e-10
+    assert rel(F, ref["F"]) < 1e-8
+    if forcing:
+        ctx.set_inexact_newton(0)
+        ctx.set_F(None)
+        plain = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+        assert out["cg"].sum() < plain["cg"].sum()
 
 
 def test_radix3_grid_solve():

@@ -28,12 +28,19 @@ def test_noalloc_residual_matches_context_residual_twice(shape):
     Pd = torch.as_tensor(P.reshape(-1), device="cuda")
     cases = [(np.array([0, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8), np.array([0, 0, 0, 0.02, 0.01, 0, 0, 0, -0.03])),
              (np.ones(9, np.uint8), np.array([0.05, 0.01, 0, 0.01, 0, 0, 0, 0, 0]))]
-    for mask, pbar in cases:                      # two calls in a row, different controls
+    for call, (mask, pbar) in enumerate(cases):   # two calls in a row, different controls
         b_ref = torch.empty(9 * N, dtype=torch.float64, device="cuda")
         mean_ref = ctx.residual(mask, pbar, b_ref)
         b = torch.full((9 * N,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         mean = mf.residual_noalloc(nx, ny, nz, Pd, mask, pbar, b)
         torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+        if call > 0:
+            # the first call has loaded the kernels and looked up the scratch
+            # address; from then on a call takes no device memory at all
+            assert free_after == free_before, (free_before, free_after)
         assert rel(b.cpu().numpy(), b_ref.cpu().numpy()) < 1e-12
         np.testing.assert_allclose(mean, mean_ref, rtol=0, atol=1e-14)
 
