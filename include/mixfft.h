@@ -114,18 +114,28 @@ int mf_set_F(mf_ctx* ctx, const double* F_host);
  *              iterations per step.
  * The run continues from the current F (identity after mf_set_material).
  * On a failure the outputs of the completed steps are written and the
- * status of the failing step is returned. */
+ * status of the failing step is returned.
+ * Execution: the history runs as one CUDA graph launch per stretch of steps
+ * with one control mask (at most 1024 steps per launch): the loops over
+ * steps, Newton iterations and CG iterations are conditional nodes of the
+ * graph, and every decision between them (forcing, null rotations,
+ * projection arithmetic, the Newton test, the recording of each step's
+ * averages) is taken on the device; the host waits once, at the end.  The
+ * graph is built and instantiated on the first call with a given mask and
+ * max_cg and kept by the context. */
 int mf_solve(mf_ctx* ctx, int nsteps, const uint8_t* mask, const double* target,
              double tol_newton, double tol_cg, double cg_rel, int max_newton,
              int max_cg, double* Fbar_out, double* Pbar_out, int32_t* iters_out);
 
 /* Run the same load history layout on n independent cells at once (the
  * batched form: many RVEs of different grid sizes and control masks).  Each
- * context must have its own workspace and should have its own CUDA stream;
- * the cells' device work then overlaps.  One host thread drives all cells:
- * it advances whichever cell has finished its last stretch of device work and
- * never waits on a single cell.  Within each cell every CG solve is one graph
- * launch (the iteration loop runs on the device).
+ * context must have its own workspace.  When every cell keeps one control
+ * mask over the history and nsteps <= 1024, all cells run as ONE graph
+ * launch (on the first context's stream): each cell's load history, as
+ * described for mf_solve, is an independent chain of that graph, so the
+ * cells' device work overlaps and no host round trip happens until all
+ * cells are done.  The batched graph is kept for the next call with the same
+ * contexts, masks and max_cg.  Otherwise the cells run one after another.
  *   masks, targets: host, n*nsteps*9, cell-major (cell i starts at 9*nsteps*i);
  *   Fbar_out, Pbar_out: host, n*nsteps*9 or NULL; iters_out: n*nsteps*2 or
  *   NULL; status_out: host, n int32 or NULL, each cell's mf_status.

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmixfft.so")
-SOURCES = ["transform.cu", "transform2_f32.cu", "transform2_f64.cu", "pointwise.cu", "cg.cu",
+SOURCES = ["transform.cu", "transform2_f32.cu", "transform2_f64.cu", "pointwise.cu", "cg.cu", "history.cu",
            "mixfft.cu", "noalloc.cu", "cufft_path.cu", "adjoint.cu", "transform2_dw.cu",
            "constitutive_dw.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

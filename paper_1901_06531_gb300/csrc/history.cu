@@ -1,0 +1,673 @@
+// Device-side Newton control of a load history (Sec. 2.3, Eq. linequil2ast
+// and eq:mixedeqil; Sec. 4 stopping rules).  With these kernels a whole load
+// history of a cell runs as one graph launch: a WHILE node over the load
+// steps, inside it a WHILE node over the Newton iterations, inside that the
+// WHILE node of the CG iterations.  Every decision the host used to take
+// between launches -- the forcing of the inner solve, the null rigid
+// rotations, the arithmetic of the projection of a correction, the Newton
+// convergence test, the recording of a step's averages -- is taken here by
+// one thread, which sets the graph's conditional handles.
+#include <math.h>
+
+#include "../../include/mixfft.h"
+#include "dw.cuh"
+#include "launch.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+// corrections of at least this size relative to F are projected in the outer
+// arithmetic under MF_PROJ_AUTO (their FP32 projection would leave ~1e-10 of F)
+constexpr double kProjOuterAbove = 1e-3;
+
+int grid_for(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g < 1) g = 1;
+  if (g > 4096) g = 4096;
+  return (int)g;
+}
+
+// ------------------------------------------------------------ null rotations
+// Cyclic Jacobi eigen-decomposition of a symmetric m x m matrix (m <= 3): on
+// return A holds the eigenvalues on its diagonal, V the eigenvectors.
+__device__ void jacobi3(int m, double A[3][3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += A[p][q] * A[p][q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        if (A[p][q] == 0.0) continue;
+        const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+        const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+__device__ void skew3(const double w[3], double W[9]) {
+  W[0] = 0; W[1] = -w[2]; W[2] = w[1];
+  W[3] = w[2]; W[4] = 0; W[5] = -w[0];
+  W[6] = -w[1]; W[7] = w[0]; W[8] = 0;
+}
+
+// tr(Wa^T Wb M) = sum_ij Wa_ij (Wb M)_ij
+__device__ double tr_wwm(const double* Wa, const double* Wb, const double* M) {
+  double s = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double wm = 0.0;
+      for (int k = 0; k < 3; ++k) wm += Wb[3 * i + k] * M[3 * k + j];
+      s += Wa[3 * i + j] * wm;
+    }
+  return s;
+}
+
+// Rigid rotations of the cell that the linearised problem cannot see (the
+// paper is silent on them; they arise under stress control).  A rotation
+// increment W (skew) gives the compatible field n = W F; it is admissible
+// when (W <F>)_ij = 0 on every strain-controlled component.  By objectivity
+// the curvature n_a . A n_b is tr(W_a^T W_b T), T = sum_v P_v F_v^T, and
+// n_a . n_b = tr(W_a^T W_b S), S = sum_v F_v F_v^T.  The admissible
+// rotations whose curvature is below tau * kappa are returned with the n_k
+// orthonormal.
+__device__ void null_rotations_dev(const double* meanF, const unsigned char* mask, const double* T,
+                                   const double* S, double kappa, double tau, Defl* d) {
+  d->m = 0;
+  double Wg[3][9];
+  for (int a = 0; a < 3; ++a) {
+    double w[3] = {0, 0, 0};
+    w[a] = 1.0;
+    skew3(w, Wg[a]);
+  }
+  double CtC[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int c = 0; c < 9; ++c) {
+    if (mask[c]) continue;
+    const int i = c / 3, j = c % 3;
+    double row[3];
+    for (int a = 0; a < 3; ++a)
+      row[a] = Wg[a][3 * i] * meanF[j] + Wg[a][3 * i + 1] * meanF[3 + j] + Wg[a][3 * i + 2] * meanF[6 + j];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) CtC[a][b] += row[a] * row[b];
+  }
+  double V[3][3];
+  jacobi3(3, CtC, V);
+  double Z[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  int m = 0;
+  for (int k = 0; k < 3; ++k)
+    if (fabs(CtC[k][k]) <= 1e-20) {
+      for (int a = 0; a < 3; ++a) Z[a][m] = V[a][k];
+      ++m;
+    }
+  if (m == 0) return;
+  double R[3][3], G[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      R[a][b] = 0.5 * (tr_wwm(Wg[a], Wg[b], T) + tr_wwm(Wg[b], Wg[a], T));
+      G[a][b] = tr_wwm(Wg[a], Wg[b], S);
+    }
+  double Rz[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Gz[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          Rz[p][q] += Z[a][p] * R[a][b] * Z[b][q];
+          Gz[p][q] += Z[a][p] * G[a][b] * Z[b][q];
+        }
+  // G-orthonormal eigenvectors of Rz v = lambda Gz v: Gz = Q g Q^T, then the
+  // standard problem for g^-1/2 Q^T Rz Q g^-1/2
+  double Qg[3][3];
+  jacobi3(m, Gz, Qg);
+  double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q) {
+      double s = 0.0;
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) s += Qg[a][p] * Rz[a][b] * Qg[b][q];
+      H[p][q] = s / sqrt(Gz[p][p] * Gz[q][q]);
+    }
+  double U[3][3];
+  jacobi3(m, H, U);
+  for (int k = 0; k < m; ++k) {
+    if (fabs(H[k][k]) > tau * kappa) continue;
+    double v[3] = {0, 0, 0};
+    for (int p = 0; p < m; ++p) {
+      double s = 0.0;
+      for (int q = 0; q < m; ++q) s += Qg[p][q] * U[q][k] / sqrt(Gz[q][q]);
+      v[p] = s;
+    }
+    double w[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+      for (int p = 0; p < m; ++p) w[a] += Z[a][p] * v[p];
+    skew3(w, d->W[d->m]);
+    ++d->m;
+  }
+}
+
+__device__ int flags_to_status(int flags) {
+  if (flags & MF_FLAG_TIMEOUT) return MF_DEVICE_TIMEOUT;
+  if (flags & MF_FLAG_NONPOS_J) return MF_NONPOSITIVE_J;
+  if (flags & (MF_FLAG_BREAKDOWN | MF_FLAG_NONFINITE)) return MF_CG_BREAKDOWN;
+  return MF_OK;
+}
+
+// ------------------------------------------------------------ control kernels
+__global__ void k_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, int kernels) {
+  hs->k = 0;
+  hs->status = MF_OK;
+  hs->launches = kernels;
+  cudaGraphSetConditional(h_step, hs->nsteps > 0 ? 1u : 0u);
+}
+
+// Load step k of the table: control mask, targets, P-bar (Sec. 2.3).
+__global__ void k_step_begin(HistState* hs, HistTables t) {
+  const StepIn& row = t.in[hs->k];
+  for (int c = 0; c < 9; ++c) {
+    const unsigned char m = row.mask[c];
+    const double v = row.target[c];
+    hs->mask[c] = m;
+    hs->target[c] = v;
+    hs->pbar[c] = m ? v : 0.0;
+  }
+  hs->nn = 0;
+  hs->ncg = 0;
+  hs->ratio = INFINITY;
+  hs->last = 0;
+}
+
+// Predictor of a load step (the strain-controlled components shifted
+// uniformly to the prescribed F-bar; Sec. 2.1, 2.3), with the control of the
+// current step from the history state.
+__global__ void k_predictor_hist(double* __restrict__ F, long long N, const HistState* hs, const Scalars* sc,
+                                 bool after_update) {
+  const double* mean = after_update ? sc->meanF_new : sc->meanF;
+  for (int c = 0; c < 9; ++c) {
+    if (hs->mask[c]) continue;
+    const double d = hs->target[c] - mean[c];
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x)
+      F[c * N + v] += d;
+  }
+}
+
+// Before a Newton iteration: failures of the constitutive pass end the
+// history; the iteration cap; the null rotations of the FP32 inner solves
+// (from T and S of that pass); the forcing of the inner solve: sqrt(cg_rel)
+// for the first iteration of a step and for one whose predecessor's
+// correction was below sqrt(tol_newton), cg_rel otherwise.
+__global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
+                             cudaGraphConditionalHandle h_newton, int first) {
+  int st = flags_to_status(sc->flags);
+  if (!st && hs->nn >= hs->max_newton) st = MF_NOT_CONVERGED;
+  if (st) {
+    if (!hs->status) hs->status = st;
+    cudaGraphSetConditional(h_go, 0u);
+    cudaGraphSetConditional(h_newton, 0u);
+    return;
+  }
+  hs->defl.m = 0;
+  if (hs->f32) null_rotations_dev(sc->meanF, hs->mask, sc->T, sc->S, hs->kappa, 1e-6, &hs->defl);
+  const bool loose = first || hs->ratio < sqrt(hs->tol_newton);
+  hs->cg_rel_cur = hs->forcing ? (loose ? sqrt(hs->cg_rel) : hs->cg_rel) : 0.0;
+  cudaGraphSetConditional(h_go, 1u);
+}
+
+// Projection of the FP32 correction onto the range of G* before the update:
+// 0 none (a late correction below 1e-6 of F, after one that small), 1 FP32
+// transforms, 2 outer arithmetic (MF_PROJ_OUTER, or MF_PROJ_AUTO for a
+// correction expected to be at least kProjOuterAbove of F).
+__global__ void k_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, int first) {
+  const int nn = hs->nn;
+  const double ratio = hs->ratio;
+  const bool outer =
+      hs->proj_arith == MF_PROJ_OUTER ||
+      (hs->proj_arith == MF_PROJ_AUTO &&
+       (first ? !(hs->first_ratio < kProjOuterAbove) : !(ratio < 10.0 * kProjOuterAbove)));
+  const bool project = outer || nn < 2 || !(ratio < 1e-6);
+  const int kind = !project ? 0 : (outer ? 2 : 1);
+  hs->proj_kind = kind;
+  cudaGraphSetConditional(h_proj, (unsigned)kind);
+}
+
+// After the update: the outcome of the inner solve (an FP32 inner solve that
+// ended on a direction of non-positive curvature after some progress ends
+// without failing: its flag is cleared), the iteration counts, the size of
+// the correction and the Newton stop test (Sec. 4: max_v abs(dF_v) /
+// abs(<F>) < tol_newton; never on a correction from an FP32 residual).
+__global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_last, int first_f32res) {
+  int flags = sc->flags;
+  if (hs->f32 && (flags & MF_FLAG_BREAKDOWN) && !(flags & ~MF_FLAG_BREAKDOWN) && sc->its > 1) {
+    sc->flags = 0;
+    flags = 0;
+  }
+  int st = flags_to_status(flags);
+  if (!st && !sc->done) st = MF_NOT_CONVERGED;
+  hs->ncg += sc->its;
+  double fn = 0.0;
+  for (int q = 0; q < 9; ++q) fn += sc->meanF_new[q] * sc->meanF_new[q];
+  const double ratio = sqrt(sc->dF2max) / sqrt(fn);
+  hs->ratio = ratio;
+  hs->nn += 1;
+  if (hs->nn == 1) hs->first_ratio = ratio;
+  if (st && !hs->status) hs->status = st;
+  const int last = (ratio < hs->tol_newton && !first_f32res) ? 1 : 0;
+  hs->last = last;
+  cudaGraphSetConditional(h_last, (unsigned)last);
+}
+
+// After the constitutive pass that follows an update: its failures, the
+// launch count of the iteration, and whether another Newton iteration runs.
+__global__ void k_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
+                              IterCounts cnt) {
+  const int st = flags_to_status(sc->flags);
+  if (st && !hs->status) hs->status = st;
+  const int its = sc->its;
+  hs->launches += cnt.fixed + cnt.proj[hs->proj_kind] + cnt.cons[hs->last] +
+                  (long long)cnt.cg_body * (its == 0 ? 1 : (its + 1) / 2);
+  cudaGraphSetConditional(h_newton, (!hs->last && !hs->status) ? 1u : 0u);
+}
+
+// End of a load step: record <F>, <P> (Sec. 2.2) and the iteration counts;
+// continue with the next step unless the history failed.
+__global__ void k_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
+                           int kernels) {
+  hs->launches += kernels;
+  if (!hs->status) {
+    const int k = hs->k;
+    StepOut& row = t.out[k];
+    for (int c = 0; c < 9; ++c) {
+      row.Fbar[c] = sc->meanF[c];
+      row.Pbar[c] = sc->meanP[c];
+    }
+    row.newton = hs->nn;
+    row.cg = hs->ncg;
+    hs->k = k + 1;
+  }
+  cudaGraphSetConditional(h_step, (!hs->status && hs->k < hs->nsteps) ? 1u : 0u);
+}
+
+// Start of a CG loop inside a history graph: counters reset and the loop's
+// condition set explicitly (skipped at once when the start already met the
+// tolerance or a flag is up).
+__global__ void k_cg_start_h(Scalars* sc, int max_its, cudaGraphConditionalHandle h_cg) {
+  sc->its = 0;
+  sc->arrive = 0u;
+  sc->max_its = max_its;
+  const int stop = (sc->done || sc->flags) ? 1 : 0;
+  sc->stop = stop;
+  cudaGraphSetConditional(h_cg, stop ? 0u : 1u);
+}
+
+// ------------------------------------------------------------ pass variants
+// CG start (r = b in the inner type, r.r) with the tolerance and forcing of
+// the current iteration: stop at rms(r) <= max(tol_cg, cg_rel_cur * rms(r0)).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cg_init_h(const double* __restrict__ b, T* __restrict__ r,
+                                                        long long n9, double* __restrict__ partials) {
+  __shared__ double red[kThreads / 32];
+  double acc = 0.0;
+  float fs = 0.f, fc = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n9;
+       i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) {
+      const dw d = dw_split(b[i]);
+      const float v = __fadd_rn(d.hi, d.lo);
+      r[i] = v;
+      const float pr = v * v;
+      const float e = fmaf(v, v, -pr);
+      float t = fs + pr;
+      fc += (fabsf(fs) >= fabsf(pr)) ? ((fs - t) + pr) : ((pr - t) + fs);
+      fs = t;
+      t = fs + e;
+      fc += (fabsf(fs) >= fabsf(e)) ? ((fs - t) + e) : ((e - t) + fs);
+      fs = t;
+    } else {
+      const T v = (T)b[i];
+      r[i] = v;
+      acc += (double)v * (double)v;
+    }
+  }
+  if constexpr (sizeof(T) == 4) acc = (double)fs + (double)fc;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fin_cg_init_h(const double* __restrict__ partials, int npart,
+                                                            long long N, const HistState* hs, Scalars* sc) {
+  __shared__ double shm[kThreads];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < npart; b += kThreads) s += partials[b];
+  shm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) shm[threadIdx.x] += shm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double rr = shm[0];
+    sc->rr = rr;
+    sc->rr0 = rr;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    double thr = hs->tol_cg;
+    if (hs->cg_rel_cur > 0.0) thr = fmax(hs->tol_cg, hs->cg_rel_cur * sqrt(rr / (double)N));
+    sc->thr2N = thr * thr * (double)N;
+    sc->done = (rr <= sc->thr2N) ? 1 : 0;
+  }
+}
+
+// B = sum_v y_v F_v^T (n_k . y = W_k : B); nothing when no rotation is null.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_defl_reduce_h(const T* __restrict__ y, const double* __restrict__ F,
+                                                            long long N, const HistState* hs,
+                                                            double* __restrict__ partials) {
+  if (hs->defl.m == 0) return;
+  __shared__ double red[9][kThreads / 32];
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    double f[9], q[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; q[c] = (double)y[c * N + v]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        acc[3 * i + j] += q[3 * i] * f[3 * j] + q[3 * i + 1] * f[3 * j + 1] + q[3 * i + 2] * f[3 * j + 2];
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    double s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[threadIdx.x][w];
+    partials[blockIdx.x * 9 + threadIdx.x] = s;
+  }
+}
+
+// What = sum_k (n_k . y) W_k (zero when no rotation is null).
+__global__ void __launch_bounds__(kThreads) k_defl_fin_h(const double* __restrict__ partials, int nblk,
+                                                         const HistState* hs, Scalars* sc) {
+  const Defl& d = hs->defl;
+  if (d.m == 0) {
+    if (threadIdx.x < 9) sc->What[threadIdx.x] = 0.0;
+    return;
+  }
+  __shared__ double shm[kThreads];
+  __shared__ double B[9];
+  for (int col = 0; col < 9; ++col) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += kThreads) s += partials[(long long)b * 9 + col];
+    shm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) shm[threadIdx.x] += shm[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) B[col] = shm[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < d.m; ++k) {
+      double ck = 0.0;
+      for (int t = 0; t < 9; ++t) ck += d.W[k][t] * B[t];
+      for (int t = 0; t < 9; ++t) W[t] += ck * d.W[k][t];
+    }
+    for (int t = 0; t < 9; ++t) sc->What[t] = W[t];
+  }
+}
+
+template <typename T>
+__global__ void k_defl_apply_h(T* __restrict__ y, const double* __restrict__ F, long long N, const HistState* hs,
+                               const Scalars* sc) {
+  if (hs->defl.m == 0) return;
+  double W[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) W[t] = sc->What[t];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    double f[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[c * N + v];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double corr = W[3 * i] * f[j] + W[3 * i + 1] * f[3 + j] + W[3 * i + 2] * f[6 + j];
+        y[(3 * i + j) * N + v] = (T)((double)y[(3 * i + j) * N + v] - corr);
+      }
+  }
+}
+
+// F += x (minus What F when a rotation is null).  Partials: columns 0-8 the
+// sums of the applied correction, column 9 the block max of abs(dF_v)^2.
+// An FP32 correction without deflation is widened exactly and summed with
+// Neumaier-compensated FP32 sums (no FP64 arithmetic per element).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_newton_update_h(double* __restrict__ F, const T* __restrict__ x,
+                                                              long long N, double* __restrict__ partials,
+                                                              const HistState* hs, const Scalars* sc) {
+  __shared__ double red[11][kThreads / 32];
+  const bool defl = hs->defl.m > 0;
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  float xs[9], xc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) { xs[c] = 0.f; xc[c] = 0.f; }
+  double mx = 0.0;
+  double W[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) W[t] = defl ? sc->What[t] : 0.0;
+  if (defl || sizeof(T) == 8) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+      double f[9], d[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) { f[c] = F[c * N + v]; d[c] = (double)x[c * N + v]; }
+      if (defl) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            d[3 * i + j] -= W[3 * i] * f[j] + W[3 * i + 1] * f[3 + j] + W[3 * i + 2] * f[6 + j];
+      }
+      double n2 = 0.0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        F[c * N + v] = f[c] + d[c];
+        acc[c] += d[c];
+        n2 += d[c] * d[c];
+      }
+      mx = fmax(mx, n2);
+    }
+  } else {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+      float n2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const float d = (float)x[c * N + v];
+        F[c * N + v] = F[c * N + v] + f32_as_f64(d);
+        const float tt = xs[c] + d;
+        xc[c] += (fabsf(xs[c]) >= fabsf(d)) ? ((xs[c] - tt) + d) : ((d - tt) + xs[c]);
+        xs[c] = tt;
+        n2 = fmaf(d, d, n2);
+      }
+      mx = fmax(mx, (double)n2);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = (double)xs[c] + (double)xc[c];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    double s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[c][warp] = s;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[9][warp] = mx;
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[threadIdx.x][w];
+    partials[blockIdx.x * 10 + threadIdx.x] = s;
+  } else if (threadIdx.x == 9) {
+    double m = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[9][w]);
+    partials[blockIdx.x * 10 + 9] = m;
+  }
+}
+
+// Columns 0-8: the new averages; column 9: max abs(dF_v)^2 (grid 10).
+__global__ void __launch_bounds__(kThreads) k_fin_newton_h(const double* __restrict__ partials, int nblk,
+                                                           long long N, Scalars* sc) {
+  __shared__ double shm[kThreads];
+  const int col = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kThreads) {
+    const double v = partials[(long long)b * 10 + col];
+    s = (col < 9) ? s + v : fmax(s, v);
+  }
+  shm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      shm[threadIdx.x] = (col < 9) ? shm[threadIdx.x] + shm[threadIdx.x + w] : fmax(shm[threadIdx.x], shm[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (col < 9) {
+      sc->meanF_new[col] = sc->meanF[col] + shm[0] / (double)N;
+    } else {
+      sc->dF2max = shm[0];
+      if (!isfinite(shm[0])) atomicOr(&sc->flags, MF_FLAG_NONFINITE);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t mf_launch_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, int kernels, cudaStream_t st) {
+  k_hist_init<<<1, 1, 0, st>>>(hs, h_step, kernels);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaStream_t st) {
+  k_step_begin<<<1, 1, 0, st>>>(hs, t);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_predictor_hist(double* F, long long N, const HistState* hs, const Scalars* sc,
+                                     bool after_update, cudaStream_t st) {
+  k_predictor_hist<<<grid_for(9 * N), kThreads, 0, st>>>(F, N, hs, sc, after_update);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
+                                 cudaGraphConditionalHandle h_newton, bool first, cudaStream_t st) {
+  k_newton_pre<<<1, 1, 0, st>>>(hs, sc, h_go, h_newton, first ? 1 : 0);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, bool first, cudaStream_t st) {
+  k_proj_decide<<<1, 1, 0, st>>>(hs, h_proj, first ? 1 : 0);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_last, bool first_f32res,
+                                  cudaStream_t st) {
+  k_newton_post<<<1, 1, 0, st>>>(hs, sc, h_last, first_f32res ? 1 : 0);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
+                                  IterCounts cnt, cudaStream_t st) {
+  k_newton_cond<<<1, 1, 0, st>>>(hs, sc, h_newton, cnt);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
+                               int kernels, cudaStream_t st) {
+  k_step_end<<<1, 1, 0, st>>>(hs, sc, t, h_step, kernels);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_cg_init_hist(const double* b, void* r, bool f32, long long n9, double* partials, int nblk,
+                                   long long N, const HistState* hs, Scalars* sc, cudaStream_t st) {
+  if (f32) k_cg_init_h<float><<<nblk, kThreads, 0, st>>>(b, (float*)r, n9, partials);
+  else k_cg_init_h<double><<<nblk, kThreads, 0, st>>>(b, (double*)r, n9, partials);
+  k_fin_cg_init_h<<<1, kThreads, 0, st>>>(partials, nblk, N, hs, sc);
+  g_mf_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_defl_project_hist(void* y, bool f32, bool apply, const double* F, long long N,
+                                        const HistState* hs, double* partials, int nblk, Scalars* sc,
+                                        cudaStream_t st) {
+  if (f32) k_defl_reduce_h<float><<<nblk, kThreads, 0, st>>>((const float*)y, F, N, hs, partials);
+  else k_defl_reduce_h<double><<<nblk, kThreads, 0, st>>>((const double*)y, F, N, hs, partials);
+  k_defl_fin_h<<<1, kThreads, 0, st>>>(partials, nblk, hs, sc);
+  g_mf_launches += 2;
+  if (apply) {
+    if (f32) k_defl_apply_h<float><<<grid_for(N), kThreads, 0, st>>>((float*)y, F, N, hs, sc);
+    else k_defl_apply_h<double><<<grid_for(N), kThreads, 0, st>>>((double*)y, F, N, hs, sc);
+    g_mf_launches += 1;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_newton_update_hist(double* F, const void* x, bool f32, long long N, double* partials,
+                                         int nblk, const HistState* hs, Scalars* sc, cudaStream_t st) {
+  if (f32) k_newton_update_h<float><<<nblk, kThreads, 0, st>>>(F, (const float*)x, N, partials, hs, sc);
+  else k_newton_update_h<double><<<nblk, kThreads, 0, st>>>(F, (const double*)x, N, partials, hs, sc);
+  k_fin_newton_h<<<10, kThreads, 0, st>>>(partials, nblk, N, sc);
+  g_mf_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_cg_start_hist(Scalars* sc, int max_its, cudaGraphConditionalHandle h_cg, cudaStream_t st) {
+  k_cg_start_h<<<1, 1, 0, st>>>(sc, max_its, h_cg);
+  g_mf_launches += 1;
+  return cudaGetLastError();
+}

@@ -62,6 +62,7 @@ struct ZArgs {
   double scale;      // multiplies every coefficient (1/N, or -1/N for the residual)
   double add[9];     // added at the null frequency after scaling (residual: P-bar)
   double* mean_out;  // residual: receives the null-frequency coefficient / N
+  const double* add_dev;  // if non-null: the values to add, read on the device (replaces add)
 };
 
 // Process-wide count of kernel launches issued by the library.
@@ -201,6 +202,83 @@ cudaError_t mf_launch_newton_update(double* F, const void* x, bool f32, bool def
 cudaError_t mf_launch_defl_project(void* y, bool f32, bool apply, const double* F, long long N,
                                    const Defl& d, double* partials, int nblk, Scalars* sc,
                                    cudaStream_t st);
+
+// history.cu: the Newton control of a load history on the device, so that
+// a whole history is one graph launch (steps, Newton iterations and CG
+// iterations as nested conditional nodes).  Per-step inputs come from a
+// device table, per-step outputs go to one.
+constexpr int kHistSteps = 1024;   // steps per launch (longer histories: several launches)
+struct HistState {
+  // parameters, written by the host before a launch
+  int nsteps;              // steps in the table for this launch
+  int max_newton, max_cg;
+  int forcing;             // CG forcing sequence (FP32 inner, or FP64 with inexact Newton)
+  int f32;                 // FP32-inner context: null rotations, re-imposed strain control
+  int proj_arith;          // MF_PROJ_* of the FP32 corrections
+  double tol_newton, tol_cg, cg_rel, kappa;
+  double first_ratio;      // size of the last step's first correction (persists across launches)
+  // state
+  int k;                   // step of the table being solved
+  int nn, ncg;             // Newton and CG iterations of the step so far
+  int status;              // mf_status of the history (first failure)
+  int last;                // the constitutive pass after this update ends the step
+  int proj_kind;           // projection of this correction: 0 none, 1 FP32, 2 outer arithmetic
+  double ratio;            // max_v abs(dF_v) / abs(<F>) of the last correction
+  double cg_rel_cur;       // forcing of the current CG solve (0: tol_cg alone)
+  double target[9], pbar[9];
+  unsigned char mask[9];
+  Defl defl;               // null rotations of the current Newton iteration
+  long long launches;      // kernels the graph ran (accumulated by the control kernels)
+};
+// Kernel counts of the captured pieces of one Newton iteration, for the
+// launch counter: fixed part, per projection kind, per final/next pass.
+struct IterCounts {
+  int fixed, proj[3], cons[2], cg_body;
+};
+// One row of the step table (in) and of the result table (out).
+struct StepIn {
+  double target[9];        // P-bar where mask is 1, F-bar where 0
+  unsigned char mask[9];
+  unsigned char pad[7];
+};
+struct StepOut {
+  double Fbar[9], Pbar[9]; // <F>, <P> of the converged step
+  int newton, cg;          // iterations of the step
+};
+// Device block of a history: the state, then kHistSteps result rows, then
+// kHistSteps step rows (state + results come back in one copy).
+struct HistTables {
+  const StepIn* in;
+  StepOut* out;
+};
+cudaError_t mf_launch_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, int kernels, cudaStream_t st);
+cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaStream_t st);
+cudaError_t mf_launch_predictor_hist(double* F, long long N, const HistState* hs, const Scalars* sc,
+                                     bool after_update, cudaStream_t st);
+cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
+                                 cudaGraphConditionalHandle h_newton, bool first, cudaStream_t st);
+cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, bool first, cudaStream_t st);
+cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_last, bool first_f32res,
+                                  cudaStream_t st);
+cudaError_t mf_launch_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
+                                  IterCounts cnt, cudaStream_t st);
+cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
+                               int kernels, cudaStream_t st);
+// CG start with the tolerance and forcing of the current Newton iteration read
+// from the history state
+cudaError_t mf_launch_cg_init_hist(const double* b, void* r, bool f32, long long n9, double* partials, int nblk,
+                                   long long N, const HistState* hs, Scalars* sc, cudaStream_t st);
+// CG counters reset for a loop inside a history graph; sets the loop's
+// condition (0 when the start already stopped it)
+cudaError_t mf_launch_cg_start_hist(Scalars* sc, int max_its, cudaGraphConditionalHandle h_cg, cudaStream_t st);
+// Null-rotation projection with the rotations read from the device (a pass
+// with hs->defl.m == 0 returns at once)
+cudaError_t mf_launch_defl_project_hist(void* y, bool f32, bool apply, const double* F, long long N,
+                                        const HistState* hs, double* partials, int nblk, Scalars* sc,
+                                        cudaStream_t st);
+// Newton update; the null-rotation correction is subtracted when hs->defl.m > 0
+cudaError_t mf_launch_newton_update_hist(double* F, const void* x, bool f32, long long N, double* partials,
+                                         int nblk, const HistState* hs, Scalars* sc, cudaStream_t st);
 
 // adjoint.cu: adjoint sensitivity at a converged state (neo-Hookean parameters)
 struct AdjWeights {

@@ -20,9 +20,6 @@
 namespace {
 
 constexpr int kMaxPhases = 65536;
-// MF_PROJ_AUTO: corrections of at least this size relative to F are projected
-// in the outer arithmetic (their FP32 projection would leave ~1e-10 of F)
-constexpr double kProjOuterAbove = 1e-3;
 constexpr int kPointwiseBlocks = 152 * 8;
 
 bool make_plan(int n, AxisPlan* p) {
@@ -193,6 +190,20 @@ Defl null_rotations(const double meanF[9], const uint8_t* mask, const double T[9
   return d;
 }
 
+// An instantiated load-history graph of a context, per control mask and CG cap.
+struct HistGraph {
+  unsigned mask;
+  int max_cg;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+long long g_ctx_serial = 0;   // identifies contexts in the batched-graph cache
+
+// The history state padded so that the result rows follow it (state and
+// results come back to the host in one copy).
+constexpr size_t hist_state_bytes() { return (sizeof(HistState) + 15) & ~(size_t)15; }
+
 }  // namespace
 
 struct mf_ctx {
@@ -211,6 +222,13 @@ struct mf_ctx {
   // offsets into the workspace
   size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
       otable32, otabledw, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
+  // load-history state and tables (history.cu)
+  size_t ohist, othout, othin;
+  char* pin = nullptr;              // pinned staging of the history block (cudaMallocHost)
+  std::vector<HistGraph> hist;      // instantiated history graphs
+  cudaStream_t caps[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // capture streams, one per nesting level
+  long long serial = 0;             // creation number (batched-graph cache key)
+  int gen = 0;                      // bumped whenever the captured kernels change
   size_t npart;
   // material
   int model = -1, nphase = 0;
@@ -332,27 +350,33 @@ int flags_status(int flags) {
 // double-word path, with H and moments): P evaluated in FP32 and left, in
 // FP32, in the scratch the FP32 residual transforms read (the t vector), P
 // itself untouched.
-int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false, bool p32 = false) {
+int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false, bool p32 = false,
+                     cudaStream_t cap = nullptr) {
+  // cap: the stream of a graph capture (the passes become graph nodes; the
+  // context's record of what the workspace holds is left alone)
+  cudaStream_t st = cap ? cap : c->st;
   if (!want_K && c->dw_outer()) {
     // P, H and the moments in one double-word pass
     const bool f32p = p32 && want_H && moments;
     const cudaError_t e = mf_launch_constitutive_dw(c->at<double>(c->oF), c->at<double>(c->oP),
                                                     want_H ? c->at<float>(c->oH) : nullptr, moments, mat_args(c),
                                                     c->ws + c->otabledw, c->N, c->at<double>(c->opart),
-                                                    c->pw_blocks, c->at<Scalars>(c->osc), c->st,
+                                                    c->pw_blocks, c->at<Scalars>(c->osc), st,
                                                     f32p ? c->at<float>(c->oAp) : nullptr,
                                                     c->at<float>(c->otable32));
-    c->have_K = false;
-    c->have_H = want_H && e == cudaSuccess;
+    if (!cap) {
+      c->have_K = false;
+      c->have_H = want_H && e == cudaSuccess;
+    }
     return cuda_status(e);
   }
   cudaError_t e = mf_launch_constitutive(c->at<double>(c->oF), c->at<double>(c->oP), c->ws + c->oK,
                                          c->f32(), want_K, moments, mat_args(c), c->N,
                                          c->at<double>(c->opart), c->pw_blocks,
-                                         c->at<Scalars>(c->osc), c->st);
-  c->have_K = want_K && e == cudaSuccess;
-  if (e == cudaSuccess && want_H) e = mf_launch_make_H(c->at<double>(c->oF), c->at<float>(c->oH), c->N, c->st);
-  c->have_H = want_H && e == cudaSuccess;
+                                         c->at<Scalars>(c->osc), st);
+  if (!cap) c->have_K = want_K && e == cudaSuccess;
+  if (e == cudaSuccess && want_H) e = mf_launch_make_H(c->at<double>(c->oF), c->at<float>(c->oH), c->N, st);
+  if (!cap) c->have_H = want_H && e == cudaSuccess;
   return cuda_status(e);
 }
 
@@ -411,12 +435,20 @@ int run_matvec(mf_ctx* c, const void* x, void* y, const uint8_t* mask) {
   return cuda_status(e);
 }
 
+// Drop every captured graph of the context (the CG loop, the load
+// histories): called whenever the kernels or tiles they hold change.
 void free_cg_graph(mf_ctx* c) {
   if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
   if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
   c->cg_exec = nullptr;
   c->cg_graph = nullptr;
   c->cg_mask = 0xffffffffu;
+  for (HistGraph& h : c->hist) {
+    if (h.exec) cudaGraphExecDestroy(h.exec);
+    if (h.graph) cudaGraphDestroy(h.graph);
+  }
+  c->hist.clear();
+  ++c->gen;
 }
 
 unsigned mask_bits(const uint8_t* mask) {
@@ -426,13 +458,13 @@ unsigned mask_bits(const uint8_t* mask) {
   return m;
 }
 
-// The CG iteration loop of one linear solve as a graph: a WHILE conditional
-// node whose body holds two iterations (the two directions swap buffers) and
-// a one-thread kernel that keeps the condition set while the device-side stop
-// flag is clear.  The kernels of an iteration that starts after the stop
-// return at once, so the iteration count (kept on the device) is exact.
-int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
-  free_cg_graph(c);
+// Capture the body of the CG iteration loop into `body` on stream cs: two
+// iterations (the two directions swap buffers) and a one-thread kernel that
+// keeps the loop's condition h set while the device-side stop flag is clear.
+// The kernels of an iteration that starts after the stop return at once, so
+// the iteration count (kept on the device) is exact.
+cudaError_t capture_cg_body(mf_ctx* c, cudaStream_t cs, cudaGraph_t body, const uint8_t* mask,
+                            cudaGraphConditionalHandle h) {
   const bool f32 = c->f32();
   void* x = c->ws + c->ox;
   void* r = c->ws + c->or_;
@@ -456,11 +488,30 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
   const TangentArgs ta = tangent_args(c);
   const int tk = tangent_kind(c);
   const int nplanes = mf_xy_blocks(c->ny, c->nz, c->xy_split != 0);
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
+    e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, c->pw_blocks, sc,
+                          cs, true, pdl);
+    if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, cs);
+    if (e == cudaSuccess && !xa.fin) e = mf_launch_fin_beta(part, nplanes, sc, cs);
+  }
+  // per iteration: tangent, the transform passes (two more for the split x-y
+  // kernels), k_fin_beta unless fused; k_cg_cond once per body
+  c->cg_body_kernels = 2 * (1 + ((xa.v2 && xa.split) ? 5 : 3) + (xa.fin ? 0 : 1)) + 1;
+  if (e == cudaSuccess) e = mf_launch_cg_cond(sc, h, cs, pdl);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+  return e != cudaSuccess ? e : e2;
+}
+
+// The CG iteration loop of one linear solve as a graph: a WHILE conditional
+// node whose body is capture_cg_body's.
+int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
+  free_cg_graph(c);
   if (!c->cap_st) {
     const cudaError_t ec = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
     if (ec != cudaSuccess) { c->cap_st = nullptr; return cuda_status(ec); }
   }
-  cudaStream_t cs = c->cap_st;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return cuda_status(e);
@@ -480,21 +531,9 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
     cudaGraphDestroy(g);
     return cuda_status(e);
   }
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  for (int it = 0; it < 2 && e == cudaSuccess; ++it) {
-    e = mf_launch_tangent(pbuf[it], r, pbuf[1 - it], x, f32, tk, true, ta, t, c->N, part, c->pw_blocks, sc,
-                          cs, true, pdl);
-    if (e == cudaSuccess) e = mf_launch_project(f32, t, c->ws + c->ospec, r, 3, part, xa, za, sc, cs);
-    if (e == cudaSuccess && !xa.fin) e = mf_launch_fin_beta(part, nplanes, sc, cs);
-  }
-  // per iteration: tangent, the transform passes (two more for the split x-y
-  // kernels), k_fin_beta unless fused; k_cg_cond once per body
-  c->cg_body_kernels = 2 * (1 + ((xa.v2 && xa.split) ? 5 : 3) + (xa.fin ? 0 : 1)) + 1;
-  if (e == cudaSuccess) e = mf_launch_cg_cond(sc, h, cs, pdl);
-  cudaGraph_t captured = nullptr;
-  const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
-  if (e == cudaSuccess) e = e2;
+  const long long l0 = g_mf_launches;
+  e = capture_cg_body(c, c->cap_st, np.conditional.phGraph_out[0], mask, h);
+  g_mf_launches = l0;   // captured, not launched
   if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cg_exec, g, 0);
   if (e != cudaSuccess) {
     cuda_status(e);
@@ -665,251 +704,380 @@ int cg_outcome(const mf_ctx* c, const Scalars& h, bool* clear) {
   return MF_OK;
 }
 
-// ---------------------------------------------------------------- load steps
-// The Newton loop of one cell as a state machine that never blocks: every
-// advance() enqueues the next stretch of device work on the cell's stream,
-// followed by an asynchronous copy of the scalar block to pinned host memory
-// and an event, and returns.  mf_solve runs one machine; mf_solve_batch runs
-// many cells at once, advancing whichever cell's event has completed.
-struct Runner {
-  enum Phase { kStep, kAfterConst, kAfterUpdate, kAfterFinal, kDone, kFailed };
-  mf_ctx* c = nullptr;
-  int nsteps = 0;
-  const uint8_t* mask = nullptr;
-  const double* target = nullptr;
-  double tol_newton = 0, tol_cg = 0, cg_rel = 0;
-  int max_newton = 0, max_cg = 0;
-  double* Fbar_out = nullptr;
-  double* Pbar_out = nullptr;
-  int32_t* iters_out = nullptr;
-  Scalars* h = nullptr;          // pinned host copy of the scalar block
-  int* zero = nullptr;           // pinned 0 (clears a flag)
-  cudaEvent_t ev = nullptr;
-  Phase phase = kStep;
-  int status = MF_OK;
-  int k = 0, nn = 0, ncg = 0;
-  double ratio = INFINITY;
-  bool res_f32 = false;          // the last residual came from FP32 transforms
-  bool p_in_t = false;           // the last constitutive pass left P in FP32 in the t vector
-  Defl defl;
+// ---------------------------------------------------------------- load histories
+// A load history of a cell runs as one graph launch (Sec. 2.3; Sec. 4
+// stopping rules): a WHILE node over the steps of the history table; in its
+// body the predictor, the first constitutive pass, the first Newton
+// iteration and a WHILE node over the further Newton iterations; in each
+// iteration an IF node (the iteration runs unless a failure or the cap ended
+// the step), the residual, the CG start, the WHILE node of the CG
+// iterations, a SWITCH node over the projection of an FP32 correction (none,
+// FP32, outer arithmetic; each branch ends with the Newton update) and an
+// IF/ELSE node over the following constitutive pass (P alone when the
+// correction passed the Newton test, else P with the tangent or H and the
+// rotation moments).  One-thread kernels (history.cu) take the decisions and
+// set the handles.  The graph is built by stream capture; conditional nodes
+// are added at the capture point and their bodies captured on further
+// streams, one per nesting level.
 
-  int init() {
-    if (cudaMallocHost(&h, sizeof(Scalars)) != cudaSuccess) return MF_CUDA_ERROR;
-    if (cudaMallocHost(&zero, sizeof(int)) != cudaSuccess) return MF_CUDA_ERROR;
-    *zero = 0;
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return MF_CUDA_ERROR;
-    Scalars* sc = c->at<Scalars>(c->osc);
-    if (mf_launch_mean_F(c->at<double>(c->oF), c->N, c->at<double>(c->opart), c->pw_blocks, sc, c->st) !=
-        cudaSuccess)
-      return MF_CUDA_ERROR;
-    defl.m = 0;
-    phase = nsteps > 0 ? kStep : kDone;
-    return MF_OK;
-  }
-  void release() {
-    if (h) cudaFreeHost(h);
-    if (zero) cudaFreeHost(zero);
-    if (ev) cudaEventDestroy(ev);
-    h = nullptr;
-    zero = nullptr;
-    ev = nullptr;
-  }
-  bool active() const { return phase != kDone && phase != kFailed; }
-  int fail(int s) { status = s; phase = kFailed; return s; }
+// A conditional handle on the graph that stream s is capturing into.
+cudaError_t cap_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(h, g, 0, 0);
+  return e;
+}
 
-  // scalar block to pinned memory, then the event
-  int post() {
-    cudaError_t e = cudaMemcpyAsync(h, c->ws + c->osc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev, c->st);
-    return cuda_status(e);
+// A conditional node at the capture point of s (the capture continues after
+// it); bodies receives its size body graphs.
+cudaError_t cap_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            unsigned size, cudaGraph_t* bodies) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  std::vector<cudaGraphEdgeData> ev(nd);
+  for (size_t i = 0; i < nd; ++i) {
+    if (edges) ev[i] = edges[i];
+    else memset(&ev[i], 0, sizeof(ev[i]));
   }
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = size;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, dv.data(), ev.data(), nd, &np);
+  if (e != cudaSuccess) return e;
+  for (unsigned i = 0; i < size; ++i) bodies[i] = np.conditional.phGraph_out[i];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
 
-  // constitutive pass: the full one (K in FP64, H and rotation moments in
-  // FP32) inside the Newton loop, P only for the final state of a step.
-  // first: the pass after the predictor, whose residual uses the FP32
-  // transforms: P itself in FP32 as well (double-word outer arithmetic)
-  int launch_constitutive(bool last, bool first = false) {
-    const bool f32 = c->f32();
-    p_in_t = first && f32 && c->dw_residual();
-    return run_constitutive(c, !last && !f32, !last && f32, !last && f32, p_in_t);
+cudaError_t cap_begin(cudaStream_t s, cudaGraph_t g) {
+  return cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+}
+
+cudaError_t cap_end(cudaStream_t s, cudaError_t e) {
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s, &out);
+  return e != cudaSuccess ? e : e2;
+}
+
+HistTables hist_tables(const mf_ctx* c) {
+  HistTables t;
+  t.in = c->at<StepIn>(c->othin);
+  t.out = c->at<StepOut>(c->othout);
+  return t;
+}
+
+// Capture one Newton iteration on caps[lvl] (capturing into a step body or
+// the Newton loop's body); caps[lvl + 1] and caps[lvl + 2] take the nested
+// bodies.  h_newton: the Newton loop's condition, set at the end.
+cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first, const uint8_t* mask, int max_cg,
+                              cudaGraphConditionalHandle h_newton) {
+  const bool f32 = c->f32();
+  const long long N = c->N;
+  HistState* hs = c->at<HistState>(c->ohist);
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  double* F = c->at<double>(c->oF);
+  double* b = c->at<double>(c->ob);
+  cudaStream_t s = caps[lvl], s1 = caps[lvl + 1], s2 = caps[lvl + 2];
+  const long long l0 = g_mf_launches;
+  long long in_bodies = 0;
+  IterCounts cnt;
+  memset(&cnt, 0, sizeof(cnt));
+  cudaGraphConditionalHandle h_go;
+  cudaError_t e = cap_handle(s, &h_go);
+  if (e == cudaSuccess) e = mf_launch_newton_pre(hs, sc, h_go, h_newton, first, s);
+  cudaGraph_t go_body = nullptr;
+  if (e == cudaSuccess) e = cap_conditional(s, h_go, cudaGraphCondTypeIf, 1, &go_body);
+  if (e != cudaSuccess) return e;
+  e = cap_begin(s1, go_body);
+  if (e != cudaSuccess) return e;
+  // the residual b = -G*(P - P-bar), P-bar of the step read on the device;
+  // the first iteration of a step with FP32 transforms (double-word outer level)
+  const bool res32 = first && c->dw_residual();
+  if (res32) {
+    ZArgs za = z_args(c, true, mask, -1.0 / (double)N);
+    za.add_dev = hs->pbar;
+    za.mean_out = c->at<double>(c->ores);
+    e = mf_launch_residual_f32(nullptr, c->at<float>(c->oAp), c->ws + c->ospec, c->at<float>(c->op2), b,
+                               xy_args(c, true), za, s1);
+  } else {
+    const bool dw = c->dw_residual();
+    ZArgs za = z_args(c, false, mask, -1.0 / (double)N, dw);
+    if (c->v2) za.S = c->zSr;
+    za.add_dev = hs->pbar;
+    za.mean_out = c->at<double>(c->ores);
+    e = mf_launch_residual(c->at<double>(c->oP), c->ws + c->ospec, b, part, xy_args(c, false, dw), za, dw, s1);
   }
-
-  int start_step() {
-    const uint8_t* m = mask + 9 * k;
-    const double* tgt = target + 9 * k;
-    Scalars* sc = c->at<Scalars>(c->osc);
-    if (mf_launch_predictor(c->at<double>(c->oF), c->N, m, tgt, sc, false, c->st) != cudaSuccess)
-      return MF_CUDA_ERROR;
-    nn = 0;
-    ncg = 0;
-    ratio = INFINITY;
-    int s = launch_constitutive(false, true);
-    if (s) return s;
-    phase = kAfterConst;
-    return post();
+  // FP32 inner solves: the null rotations out of the right-hand side
+  if (e == cudaSuccess && f32) e = mf_launch_defl_project_hist(b, false, true, F, N, hs, part, c->pw_blocks, sc, s1);
+  if (e == cudaSuccess)
+    e = mf_launch_cg_init_hist(b, c->ws + c->or_, f32, 9 * N, part, c->pw_blocks, N, hs, sc, s1);
+  cudaGraphConditionalHandle h_cg;
+  if (e == cudaSuccess) e = cap_handle(s1, &h_cg);
+  if (e == cudaSuccess) e = mf_launch_cg_start_hist(sc, max_cg, h_cg, s1);
+  cudaGraph_t cg_body = nullptr;
+  if (e == cudaSuccess) e = cap_conditional(s1, h_cg, cudaGraphCondTypeWhile, 1, &cg_body);
+  if (e == cudaSuccess) {
+    const long long lb = g_mf_launches;
+    e = capture_cg_body(c, s2, cg_body, mask, h_cg);
+    in_bodies += g_mf_launches - lb;
+    cnt.cg_body = c->cg_body_kernels;
   }
-
-  int newton_iteration() {
-    const uint8_t* m = mask + 9 * k;
-    const double* tgt = target + 9 * k;
-    double pbar[9];
-    for (int q = 0; q < 9; ++q) pbar[q] = m[q] ? tgt[q] : 0.0;
-    Scalars* sc = c->at<Scalars>(c->osc);
-    double* part = c->at<double>(c->opart);
-    double* F = c->at<double>(c->oF);
-    const long long N = c->N;
-    if (nn >= max_newton) return MF_NOT_CONVERGED;
-    // the first residual of a load step is large (the predictor moved F-bar):
-    // FP32 transforms are accurate enough for its correction; the later ones,
-    // which decide convergence, keep FP64 accuracy
-    res_f32 = (nn == 0) && c->dw_residual();
-    int s = run_residual(c, m, pbar, c->at<double>(c->ob), c->at<double>(c->ores), res_f32, res_f32 && p_in_t);
-    p_in_t = false;
-    if (s) return s;
-    defl.m = 0;
-    if (c->f32()) {
-      // FP32 inner solves: remove the null rigid rotations from the right-hand
-      // side and from the correction (their FP64 rounding noise would
-      // otherwise be amplified by a near-zero curvature); T and S come from
-      // the constitutive pass of this iteration
-      defl = null_rotations(h->meanF, m, h->T, h->S, c->kappa, 1e-6);
-      if (defl.m > 0 && mf_launch_defl_project(c->at<double>(c->ob), false, true, F, N, defl, part,
-                                               c->pw_blocks, sc, c->st) != cudaSuccess)
-        return MF_CUDA_ERROR;
-    }
-    // FP32 inner solves: forcing sqrt(cg_rel) for the first Newton iteration
-    // of a step (its correction is followed by at least one more) and for an
-    // iteration expected to be the last (the previous correction already
-    // below sqrt(tol_newton): with quadratic convergence this one, about its
-    // square, is below tol_newton, and a few correct digits of it leave the
-    // state accurate to a small fraction of tol_newton); cg_rel for the others
-    // (FP64 contexts take the same sequence with mf_set_inexact_newton)
-    const bool loose = nn == 0 || ratio < sqrt(tol_newton);
-    const bool forcing = c->f32() || c->forcing64;
-    s = launch_cg(c, m, tol_cg, forcing ? (loose ? sqrt(cg_rel) : cg_rel) : 0.0, max_cg);
-    if (s) return s;
-    void* corr = c->ws + c->ox;
-    bool corr32 = c->f32();
-    // The projection matters for the large corrections (the first two of a
-    // step); a later one, below 1e-6 of F after a correction that small,
-    // carries an out-of-range rounding of ~1e-13 of F: it is applied as the
-    // CG left it (unless the projection runs in the outer arithmetic).
-    // MF_PROJ_AUTO takes the outer arithmetic for the corrections whose FP32
-    // rounding would matter: the first of a step when the last step's first
-    // correction was at least kProjOuterAbove of F (that size repeats from
-    // step to step along a load history; unknown after F was reset), a later
-    // one when its predecessor was ten times that.
-    const bool outer_proj =
-        c->proj_arith == MF_PROJ_OUTER ||
-        (c->proj_arith == MF_PROJ_AUTO &&
-         (nn == 0 ? !(c->first_ratio < kProjOuterAbove) : !(ratio < 10.0 * kProjOuterAbove)));
-    const bool project = outer_proj || nn < 2 || !(ratio < 1e-6);
-    if (c->f32() && project) {
-      // The FP32 correction, projected once more onto the range of G*: its
-      // rounding leaves incompatible and Nyquist components that the
-      // residual cannot see but that shift the equilibrium through the
-      // nonlinear law; after the projection only the projection's own
-      // rounding is left of them (FP32's, or with MF_PROJ_OUTER the outer
-      // arithmetic's: the correction widened to FP64 in the residual buffer,
-      // free once the CG has started, and projected there).
-      if (outer_proj) {
-        double* bd = c->at<double>(c->ob);
+  if (e == cudaSuccess)
+    e = mf_launch_axpy_last(c->ws + c->ox, c->ws + c->op, c->ws + c->op2, f32, 9 * N, sc, s1);
+  if (e == cudaSuccess && f32) {
+    // projection of the FP32 correction onto the range of G* (its rounding
+    // leaves components the residual cannot see), then the Newton update
+    cudaGraphConditionalHandle h_proj;
+    e = cap_handle(s1, &h_proj);
+    if (e == cudaSuccess) e = mf_launch_proj_decide(hs, h_proj, first, s1);
+    cudaGraph_t pb[3] = {nullptr, nullptr, nullptr};
+    if (e == cudaSuccess) e = cap_conditional(s1, h_proj, cudaGraphCondTypeSwitch, 3, pb);
+    for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
+      const long long lb = g_mf_launches;
+      e = cap_begin(s2, pb[kind]);
+      if (e != cudaSuccess) break;
+      void* corr = c->ws + c->ox;
+      bool corr32 = true;
+      if (kind == 1) {
+        const ZArgs za = z_args(c, true, mask, 1.0 / (double)N);
+        e = mf_launch_project(true, c->ws + c->ox, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xy_args(c, true), za,
+                              nullptr, s2);
+        corr = c->ws + c->op2;
+      } else if (kind == 2) {
         const bool dwp = c->dw_residual();
-        ZArgs za = z_args(c, false, m, 1.0 / (double)N, dwp);
+        ZArgs za = z_args(c, false, mask, 1.0 / (double)N, dwp);
         if (c->v2) za.S = c->zSr;
-        cudaError_t e = mf_launch_to_double(c->ws + c->ox, bd, true, 9 * N, c->st);
+        e = mf_launch_to_double(c->ws + c->ox, b, true, 9 * N, s2);
         if (e == cudaSuccess) {
           if (dwp) {
             const XYArgs xd = xy_args(c, false, true);
-            e = mf_v2_xyf_dw(bd, c->ws + c->ospec, xd, c->st);
-            if (e == cudaSuccess) e = mf_v2_zp_dw(c->ws + c->ospec, za, c->st);
-            if (e == cudaSuccess) e = mf_v2_xyi_dw(c->ws + c->ospec, bd, nullptr, xd, c->st);
+            e = mf_v2_xyf_dw(b, c->ws + c->ospec, xd, s2);
+            if (e == cudaSuccess) e = mf_v2_zp_dw(c->ws + c->ospec, za, s2);
+            if (e == cudaSuccess) e = mf_v2_xyi_dw(c->ws + c->ospec, b, nullptr, xd, s2);
           } else {
-            e = mf_launch_project(false, bd, c->ws + c->ospec, bd, 0, nullptr, xy_args(c, false), za, nullptr, c->st);
+            e = mf_launch_project(false, b, c->ws + c->ospec, b, 0, nullptr, xy_args(c, false), za, nullptr, s2);
           }
         }
-        if (e != cudaSuccess) return MF_CUDA_ERROR;
-        corr = bd;
+        corr = b;
         corr32 = false;
-      } else {
-        const ZArgs za = z_args(c, true, m, 1.0 / (double)N);
-        if (mf_launch_project(true, c->ws + c->ox, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xy_args(c, true),
-                              za, nullptr, c->st) != cudaSuccess)
-          return MF_CUDA_ERROR;
-        corr = c->ws + c->op2;
       }
+      if (e == cudaSuccess)
+        e = mf_launch_defl_project_hist(corr, corr32, false, F, N, hs, part, c->pw_blocks, sc, s2);
+      if (e == cudaSuccess) e = mf_launch_newton_update_hist(F, corr, corr32, N, part, c->pw_blocks, hs, sc, s2);
+      e = cap_end(s2, e);
+      cnt.proj[kind] = (int)(g_mf_launches - lb);
+      in_bodies += g_mf_launches - lb;
     }
-    if (defl.m > 0 && mf_launch_defl_project(corr, corr32, false, F, N, defl, part, c->pw_blocks, sc, c->st) !=
-                          cudaSuccess)
-      return MF_CUDA_ERROR;
-    if (mf_launch_newton_update(F, corr, corr32, defl.m > 0, N, part, c->pw_blocks, sc, c->st) != cudaSuccess)
-      return MF_CUDA_ERROR;
     // FP32 corrections carry a rounding-level average on the strain-controlled
     // components; the FP64 outer level re-imposes F-bar there
-    if (c->f32() && mf_launch_predictor(F, N, m, tgt, sc, true, c->st) != cudaSuccess) return MF_CUDA_ERROR;
-    phase = kAfterUpdate;
-    return post();
+    if (e == cudaSuccess) e = mf_launch_predictor_hist(F, N, hs, sc, true, s1);
+  } else if (e == cudaSuccess) {
+    e = mf_launch_newton_update_hist(F, c->ws + c->ox, false, N, part, c->pw_blocks, hs, sc, s1);
   }
+  // the Newton test, then P alone (end of the step) or the full pass
+  cudaGraphConditionalHandle h_last;
+  if (e == cudaSuccess) e = cap_handle(s1, &h_last);
+  if (e == cudaSuccess) e = mf_launch_newton_post(hs, sc, h_last, res32, s1);
+  cudaGraph_t lb2[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cap_conditional(s1, h_last, cudaGraphCondTypeIf, 2, lb2);
+  for (int br = 0; br < 2 && e == cudaSuccess; ++br) {
+    // body 0 runs when the correction passed the test (the step ends)
+    const long long lb = g_mf_launches;
+    e = cap_begin(s2, lb2[br]);
+    if (e != cudaSuccess) break;
+    const bool last = br == 0;
+    const int st = run_constitutive(c, !last && !f32, !last && f32, !last && f32, false, s2);
+    e = cap_end(s2, st ? cudaErrorUnknown : cudaSuccess);
+    cnt.cons[last ? 1 : 0] = (int)(g_mf_launches - lb);
+    in_bodies += g_mf_launches - lb;
+  }
+  // the kernels outside the bodies, including the condition kernel below
+  cnt.fixed = (int)(g_mf_launches - l0 - in_bodies) + 1;
+  if (!f32) cnt.proj[1] = cnt.proj[2] = 0;
+  if (e == cudaSuccess) e = mf_launch_newton_cond(hs, sc, h_newton, cnt, s1);
+  return cap_end(s1, e);
+}
 
-  // Called when ev has completed: consume *h, enqueue the next stretch.
-  int advance() {
-    int s = MF_OK;
-    switch (phase) {
-      case kStep:
-        s = start_step();
-        break;
-      case kAfterConst:
-        s = flags_status(h->flags);
-        if (!s) s = newton_iteration();
-        break;
-      case kAfterUpdate: {
-        bool clear = false;
-        s = cg_outcome(c, *h, &clear);
-        if (s) break;
-        if (clear && cudaMemcpyAsync(&c->at<Scalars>(c->osc)->flags, zero, sizeof(int), cudaMemcpyHostToDevice,
-                                     c->st) != cudaSuccess) {
-          s = MF_CUDA_ERROR;
-          break;
-        }
-        ncg += h->its;
-        // kernels the CG graph ran: cg_body_kernels per pass of its two-iteration body
-        g_mf_launches += (long long)c->cg_body_kernels * (h->its == 0 ? 1 : (h->its + 1) / 2);
-        double fn = 0.0;
-        for (int q = 0; q < 9; ++q) fn += h->meanF_new[q] * h->meanF_new[q];
-        ratio = sqrt(h->dF2max) / sqrt(fn);
-        ++nn;
-        if (nn == 1) c->first_ratio = ratio;
-        // never stop on a correction from an FP32 residual
-        const bool last = ratio < tol_newton && !res_f32;
-        s = launch_constitutive(last);
-        if (!s) {
-          phase = last ? kAfterFinal : kAfterConst;
-          s = post();
-        }
-        break;
-      }
-      case kAfterFinal:
-        s = flags_status(h->flags);
-        if (s) break;
-        if (Fbar_out) memcpy(Fbar_out + 9 * k, h->meanF, 9 * sizeof(double));
-        if (Pbar_out) memcpy(Pbar_out + 9 * k, h->meanP, 9 * sizeof(double));
-        if (iters_out) { iters_out[2 * k] = nn; iters_out[2 * k + 1] = ncg; }
-        ++k;
-        if (k < nsteps) s = start_step();
-        else phase = kDone;
-        break;
-      default:
-        break;
+// Capture a whole load history of the cell into graph G (as a root chain of
+// its own: several cells can share one graph).
+cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max_cg) {
+  for (int i = 0; i < 5; ++i)
+    if (!c->caps[i]) {
+      const cudaError_t ec = cudaStreamCreateWithFlags(&c->caps[i], cudaStreamNonBlocking);
+      if (ec != cudaSuccess) { c->caps[i] = nullptr; return ec; }
     }
-    if (s) return fail(s);
-    return MF_OK;
+  const bool f32 = c->f32();
+  const long long N = c->N;
+  HistState* hs = c->at<HistState>(c->ohist);
+  Scalars* sc = c->at<Scalars>(c->osc);
+  double* part = c->at<double>(c->opart);
+  double* F = c->at<double>(c->oF);
+  const HistTables t = hist_tables(c);
+  cudaStream_t* caps = c->caps;
+  const long long l0 = g_mf_launches;
+  cudaError_t e = cap_begin(caps[0], G);
+  if (e != cudaSuccess) return e;
+  e = mf_launch_mean_F(F, N, part, c->pw_blocks, sc, caps[0]);
+  cudaGraphConditionalHandle h_step;
+  if (e == cudaSuccess) e = cap_handle(caps[0], &h_step);
+  if (e == cudaSuccess) e = mf_launch_hist_init(hs, h_step, 3, caps[0]);
+  cudaGraph_t B1 = nullptr;
+  if (e == cudaSuccess) e = cap_conditional(caps[0], h_step, cudaGraphCondTypeWhile, 1, &B1);
+  if (e == cudaSuccess) {
+    // the body of one load step
+    e = cap_begin(caps[1], B1);
+    if (e == cudaSuccess) {
+      const long long ls = g_mf_launches;
+      e = mf_launch_step_begin(hs, t, caps[1]);
+      if (e == cudaSuccess) e = mf_launch_predictor_hist(F, N, hs, sc, false, caps[1]);
+      // the pass after the predictor: FP64 P and K, or (FP32 inner) H and the
+      // rotation moments, with P itself in FP32 for the FP32 first residual
+      if (e == cudaSuccess && run_constitutive(c, !f32, f32, f32, f32 && c->dw_residual(), caps[1]))
+        e = cudaErrorUnknown;
+      const int step_kernels = (int)(g_mf_launches - ls) + 1;
+      cudaGraphConditionalHandle h_newton;
+      if (e == cudaSuccess) e = cap_handle(caps[1], &h_newton);
+      if (e == cudaSuccess) e = capture_iteration(c, caps, 1, true, mask, max_cg, h_newton);
+      cudaGraph_t B2 = nullptr;
+      if (e == cudaSuccess) e = cap_conditional(caps[1], h_newton, cudaGraphCondTypeWhile, 1, &B2);
+      if (e == cudaSuccess) {
+        e = cap_begin(caps[2], B2);
+        if (e == cudaSuccess) e = cap_end(caps[2], capture_iteration(c, caps, 2, false, mask, max_cg, h_newton));
+      }
+      if (e == cudaSuccess) e = mf_launch_step_end(hs, sc, t, h_step, step_kernels, caps[1]);
+      e = cap_end(caps[1], e);
+    }
   }
+  e = cap_end(caps[0], e);
+  g_mf_launches = l0;   // captured, not launched
+  return e;
+}
 
-  bool ready() const {
-    if (phase == kStep) return true;
-    return cudaEventQuery(ev) != cudaErrorNotReady;
+// The instantiated history graph of a context for a control mask and CG cap
+// (built on first use).
+cudaGraphExec_t history_exec(mf_ctx* c, const uint8_t* mask, int max_cg, int* status) {
+  const unsigned mb = mask_bits(mask);
+  for (const HistGraph& h : c->hist)
+    if (h.mask == mb && h.max_cg == max_cg) return h.exec;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = build_history(c, g, mask, max_cg);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (e != cudaSuccess) {
+    *status = cuda_status(e);
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return nullptr;
   }
-};
+  c->hist.push_back(HistGraph{mb, max_cg, g, ex});
+  return ex;
+}
+
+// Pinned staging of the history block: the state, kHistSteps result rows,
+// kHistSteps step rows (host memory; allocated on a context's first solve).
+int hist_staging(mf_ctx* c) {
+  if (c->pin) return MF_OK;
+  const size_t bytes = hist_state_bytes() + (size_t)kHistSteps * (sizeof(StepOut) + sizeof(StepIn));
+  if (cudaMallocHost((void**)&c->pin, bytes) != cudaSuccess) {
+    c->pin = nullptr;
+    return MF_CUDA_ERROR;
+  }
+  return MF_OK;
+}
+
+HistState* pin_state(mf_ctx* c) { return reinterpret_cast<HistState*>(c->pin); }
+StepOut* pin_out(mf_ctx* c) { return reinterpret_cast<StepOut*>(c->pin + hist_state_bytes()); }
+StepIn* pin_in(mf_ctx* c) {
+  return reinterpret_cast<StepIn*>(c->pin + hist_state_bytes() + (size_t)kHistSteps * sizeof(StepOut));
+}
+
+// The history parameters and step rows [k0, k1) to the device, on st.
+cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target, int k0, int k1, double tol_newton,
+                           double tol_cg, double cg_rel, int max_newton, int max_cg, cudaStream_t st) {
+  HistState* hh = pin_state(c);
+  memset(hh, 0, sizeof(*hh));
+  hh->nsteps = k1 - k0;
+  hh->max_newton = max_newton;
+  hh->max_cg = max_cg;
+  hh->forcing = (c->f32() || c->forcing64) ? 1 : 0;
+  hh->f32 = c->f32() ? 1 : 0;
+  hh->proj_arith = c->proj_arith;
+  hh->tol_newton = tol_newton;
+  hh->tol_cg = tol_cg;
+  hh->cg_rel = cg_rel;
+  hh->kappa = c->kappa;
+  hh->first_ratio = c->first_ratio;
+  hh->ratio = INFINITY;
+  StepIn* in = pin_in(c);
+  for (int k = k0; k < k1; ++k) {
+    StepIn& r = in[k - k0];
+    memset(&r, 0, sizeof(r));
+    memcpy(r.target, target + 9 * (size_t)k, 9 * sizeof(double));
+    memcpy(r.mask, mask + 9 * (size_t)k, 9);
+  }
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->ohist, hh, sizeof(HistState), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->ws + c->othin, in, sizeof(StepIn) * (k1 - k0), cudaMemcpyHostToDevice, st);
+  return e;
+}
+
+// The state and the result rows of n steps back to the staging block, on st.
+cudaError_t download_history(mf_ctx* c, int n, cudaStream_t st) {
+  return cudaMemcpyAsync(c->pin, c->ws + c->ohist, hist_state_bytes() + sizeof(StepOut) * n,
+                         cudaMemcpyDeviceToHost, st);
+}
+
+// After the download completed: the completed steps' rows into the caller's
+// arrays at [k0, ...); returns the history's status.
+int finish_history(mf_ctx* c, int k0, int k1, double* Fbar_out, double* Pbar_out, int32_t* iters_out) {
+  const HistState& hs = *pin_state(c);
+  const StepOut* out = pin_out(c);
+  for (int k = 0; k < hs.k && k0 + k < k1; ++k) {
+    if (Fbar_out) memcpy(Fbar_out + 9 * (size_t)(k0 + k), out[k].Fbar, 9 * sizeof(double));
+    if (Pbar_out) memcpy(Pbar_out + 9 * (size_t)(k0 + k), out[k].Pbar, 9 * sizeof(double));
+    if (iters_out) { iters_out[2 * (k0 + k)] = out[k].newton; iters_out[2 * (k0 + k) + 1] = out[k].cg; }
+  }
+  c->first_ratio = hs.first_ratio;
+  c->have_K = false;
+  c->have_H = false;
+  g_mf_launches += hs.launches;
+  return hs.status;
+}
+
+bool same_mask(const uint8_t* a, const uint8_t* b) { return memcmp(a, b, 9) == 0; }
+
+// One cell: the history in segments of constant control mask (at most
+// kHistSteps steps each), one graph launch per segment.
+int solve_cell(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, double tol_newton, double tol_cg,
+               double cg_rel, int max_newton, int max_cg, double* Fbar_out, double* Pbar_out, int32_t* iters_out) {
+  int s = hist_staging(c);
+  if (s) return s;
+  for (int k0 = 0; k0 < nsteps;) {
+    int k1 = k0 + 1;
+    while (k1 < nsteps && k1 - k0 < kHistSteps && same_mask(mask + 9 * (size_t)k1, mask + 9 * (size_t)k0)) ++k1;
+    cudaGraphExec_t ex = history_exec(c, mask + 9 * (size_t)k0, max_cg, &s);
+    if (!ex) return s;
+    cudaError_t e = upload_history(c, mask, target, k0, k1, tol_newton, tol_cg, cg_rel, max_newton, max_cg, c->st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->st);
+    if (e == cudaSuccess) e = download_history(c, k1 - k0, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    s = finish_history(c, k0, k1, Fbar_out, Pbar_out, iters_out);
+    if (s) return s;
+    k0 = k1;
+  }
+  return MF_OK;
+}
 
 int check_solve_args(const mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, double tol_newton,
                      double tol_cg, double cg_rel, int max_newton, int max_cg) {
@@ -921,34 +1089,6 @@ int check_solve_args(const mf_ctx* c, int nsteps, const uint8_t* mask, const dou
   for (int i = 0; i < 9 * nsteps; ++i)
     if (mask[i] > 1 || !isfinite(target[i])) return MF_INVALID_ARG;
   return MF_OK;
-}
-
-// Drive a set of runners to completion; a cell whose event is pending is
-// skipped, and the host sleeps briefly only when no cell can advance.
-// While nothing can advance the host polls the events without sleeping for
-// up to kSpin (a sleep, however short, wakes tens of microseconds late on a
-// stock kernel, and the GPU has no queued work of that cell meanwhile), then
-// sleeps briefly between polls.
-void drive(std::vector<Runner>& rs) {
-  constexpr auto kSpin = std::chrono::milliseconds(5);
-  auto idle_since = std::chrono::steady_clock::now();
-  for (;;) {
-    bool any = false, progressed = false;
-    for (Runner& r : rs) {
-      if (!r.active()) continue;
-      any = true;
-      if (r.ready()) {
-        r.advance();
-        progressed = true;
-      }
-    }
-    if (!any) return;
-    if (progressed) {
-      idle_since = std::chrono::steady_clock::now();
-    } else if (std::chrono::steady_clock::now() - idle_since > kSpin) {
-      std::this_thread::sleep_for(std::chrono::microseconds(5));
-    }
-  }
 }
 
 }  // namespace
@@ -986,6 +1126,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->nx = nx; c->ny = ny; c->nz = nz;
   c->N = (long long)nx * ny * nz;
   c->prec = precision;
+  c->serial = ++g_ctx_serial;
   c->v2 = mf_v2_supported(nx, ny, nz) ? 1 : 0;
   c->xy_split = big_plane ? 1 : 0;
   c->st = (cudaStream_t)stream;
@@ -1025,6 +1166,9 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->npart = (size_t)(kPointwiseBlocks > 9 * nz ? kPointwiseBlocks : 9 * nz) * 36;
   c->opart = take(c->npart * sizeof(double));
   c->osc = take(sizeof(Scalars));
+  c->ohist = take(hist_state_bytes() + (size_t)kHistSteps * sizeof(StepOut));
+  c->othout = c->ohist + hist_state_bytes();
+  c->othin = take((size_t)kHistSteps * sizeof(StepIn));
   c->ores = take(9 * sizeof(double));
   c->oxpos = take(nx * sizeof(int));
   c->oxk = take(nx * sizeof(int));
@@ -1316,21 +1460,34 @@ int mf_solve(mf_ctx* c, int nsteps, const uint8_t* mask, const double* target, d
   int s = check_solve_args(c, nsteps, mask, target, tol_newton, tol_cg, cg_rel, max_newton, max_cg);
   if (s) return s;
   if (!c->tuned && (s = autotune(c, 3))) return s;
-  std::vector<Runner> rs(1);
-  Runner& r = rs[0];
-  r.c = c; r.nsteps = nsteps; r.mask = mask; r.target = target;
-  r.tol_newton = tol_newton; r.tol_cg = tol_cg; r.cg_rel = cg_rel;
-  r.max_newton = max_newton; r.max_cg = max_cg;
-  r.Fbar_out = Fbar_out; r.Pbar_out = Pbar_out; r.iters_out = iters_out;
-  s = r.init();
-  if (!s) {
-    drive(rs);
-    s = r.status;
-  }
-  if (cudaStreamSynchronize(c->st) != cudaSuccess && !s) s = MF_CUDA_ERROR;
-  r.release();
-  return s;
+  return solve_cell(c, nsteps, mask, target, tol_newton, tol_cg, cg_rel, max_newton, max_cg, Fbar_out, Pbar_out,
+                    iters_out);
 }
+
+}  // extern "C"
+
+namespace {
+
+// The batched graph of the last mf_solve_batch call: every cell's history as
+// a root chain of one graph, reused while the same contexts (by creation
+// number and graph generation), masks and CG cap come back.
+struct BatchGraph {
+  std::vector<long long> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+BatchGraph g_batch;
+std::mutex g_batch_mutex;
+
+void drop_batch_graph() {
+  if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+  if (g_batch.graph) cudaGraphDestroy(g_batch.graph);
+  g_batch = BatchGraph();
+}
+
+}  // namespace
+
+extern "C" {
 
 int mf_solve_batch(int n, mf_ctx* const* ctxs, int nsteps, const uint8_t* masks, const double* targets,
                    double tol_newton, double tol_cg, double cg_rel, int max_newton, int max_cg,
@@ -1349,26 +1506,74 @@ int mf_solve_batch(int n, mf_ctx* const* ctxs, int nsteps, const uint8_t* masks,
     const int s = autotune(ctxs[i], 3);
     if (s) return s;
   }
-  std::vector<Runner> rs(n);
-  int first = MF_OK;
-  for (int i = 0; i < n; ++i) {
-    Runner& r = rs[i];
-    r.c = ctxs[i]; r.nsteps = nsteps;
-    r.mask = masks + (size_t)9 * nsteps * i; r.target = targets + (size_t)9 * nsteps * i;
-    r.tol_newton = tol_newton; r.tol_cg = tol_cg; r.cg_rel = cg_rel;
-    r.max_newton = max_newton; r.max_cg = max_cg;
-    r.Fbar_out = Fbar_out ? Fbar_out + (size_t)9 * nsteps * i : nullptr;
-    r.Pbar_out = Pbar_out ? Pbar_out + (size_t)9 * nsteps * i : nullptr;
-    r.iters_out = iters_out ? iters_out + (size_t)2 * nsteps * i : nullptr;
-    const int s = r.init();
-    if (s) r.fail(s);
+  if (nsteps == 0) {
+    if (status_out)
+      for (int i = 0; i < n; ++i) status_out[i] = MF_OK;
+    return MF_OK;
   }
-  drive(rs);
+  // one launch for all cells when each cell keeps one control mask over the
+  // history and the history fits the step table; otherwise cell by cell
+  bool one_launch = nsteps <= kHistSteps;
+  for (int i = 0; i < n && one_launch; ++i) {
+    const uint8_t* m = masks + (size_t)9 * nsteps * i;
+    for (int k = 1; k < nsteps && one_launch; ++k) one_launch = same_mask(m + 9 * (size_t)k, m);
+  }
+  int first = MF_OK;
+  if (!one_launch) {
+    for (int i = 0; i < n; ++i) {
+      const size_t o9 = (size_t)9 * nsteps * i;
+      const int s = solve_cell(ctxs[i], nsteps, masks + o9, targets + o9, tol_newton, tol_cg, cg_rel, max_newton,
+                               max_cg, Fbar_out ? Fbar_out + o9 : nullptr, Pbar_out ? Pbar_out + o9 : nullptr,
+                               iters_out ? iters_out + (size_t)2 * nsteps * i : nullptr);
+      if (status_out) status_out[i] = s;
+      if (s && !first) first = s;
+    }
+    return first;
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  std::vector<long long> key;
+  key.push_back(max_cg);
   for (int i = 0; i < n; ++i) {
-    if (cudaStreamSynchronize(rs[i].c->st) != cudaSuccess && !rs[i].status) rs[i].status = MF_CUDA_ERROR;
-    if (status_out) status_out[i] = rs[i].status;
-    if (rs[i].status && !first) first = rs[i].status;
-    rs[i].release();
+    key.push_back(ctxs[i]->serial);
+    key.push_back(ctxs[i]->gen);
+    key.push_back((long long)mask_bits(masks + (size_t)9 * nsteps * i));
+  }
+  cudaError_t e = cudaSuccess;
+  if (key != g_batch.key || !g_batch.exec) {
+    drop_batch_graph();
+    e = cudaGraphCreate(&g_batch.graph, 0);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+      e = build_history(ctxs[i], g_batch.graph, masks + (size_t)9 * nsteps * i, max_cg);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g_batch.exec, g_batch.graph, 0);
+    if (e != cudaSuccess) {
+      drop_batch_graph();
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    g_batch.key = key;
+  }
+  // every cell's inputs on the launch stream, one launch, every cell's outputs
+  cudaStream_t st = ctxs[0]->st;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    if (ctxs[i]->st != st) e = cudaStreamSynchronize(ctxs[i]->st);
+    if (e == cudaSuccess && hist_staging(ctxs[i])) return MF_CUDA_ERROR;
+  }
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const size_t o9 = (size_t)9 * nsteps * i;
+    e = upload_history(ctxs[i], masks + o9, targets + o9, 0, nsteps, tol_newton, tol_cg, cg_rel, max_newton, max_cg,
+                       st);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(g_batch.exec, st);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = download_history(ctxs[i], nsteps, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int i = 0; i < n; ++i) {
+    const size_t o9 = (size_t)9 * nsteps * i;
+    const int s = finish_history(ctxs[i], 0, nsteps, Fbar_out ? Fbar_out + o9 : nullptr,
+                                 Pbar_out ? Pbar_out + o9 : nullptr,
+                                 iters_out ? iters_out + (size_t)2 * nsteps * i : nullptr);
+    if (status_out) status_out[i] = s;
+    if (s && !first) first = s;
   }
   return first;
 }
@@ -1654,6 +1859,9 @@ void mf_destroy(mf_ctx* c) {
   if (!c) return;
   free_cg_graph(c);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  for (cudaStream_t s : c->caps)
+    if (s) cudaStreamDestroy(s);
+  if (c->pin) cudaFreeHost(c->pin);
   mf_cufft_delete(c->cufft);
   delete c;
 }

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(512) k_zpass(typename CT<T>::t* __restrict__ s
         const C X = e[c * zstride];
         if (MODE == 1 && a.mean_out) a.mean_out[c] = (double)X.x / (double)a.N;
         if (a.mask & (1u << c)) {
-          T add = (MODE == 1) ? (T)a.add[c] : (T)0;
+          T add = (MODE == 1) ? (T)(a.add_dev ? a.add_dev[c] : a.add[c]) : (T)0;
           e[c * zstride] = cmake(scale * X.x + add, scale * X.y);
         } else {
           e[c * zstride] = cmake((T)0, (T)0);

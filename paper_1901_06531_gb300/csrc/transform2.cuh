@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
         const C X = *v[cl];
         if (MODE == 1 && a.mean_out) a.mean_out[cc] = (double)X.x / (double)a.N;
         if (a.mask & (1u << cc)) {
-          const T add = (MODE == 1) ? (T)a.add[cc] : (T)0;
+          const T add = (MODE == 1) ? (T)(a.add_dev ? a.add_dev[cc] : a.add[cc]) : (T)0;
           *v[cl] = cmake(scale * X.x + add, scale * X.y);
         } else {
           *v[cl] = cmake((T)0, (T)0);

@@ -160,7 +160,7 @@ def test_projection_arith_is_validated():
     with pytest.raises(mf.MixFFTError):
         mf.Context(8, 8, 8, mf.MF_FP64).set_projection_arith(mf.MF_PROJ_OUTER)
     with pytest.raises(mf.MixFFTError):
-        mf.Context(8, 8, 8, mf.MF_FP32_INNER).set_projection_arith(2)
+        mf.Context(8, 8, 8, mf.MF_FP32_INNER).set_projection_arith(7)
 
 
 def test_fp32_inner_polycrystal():
