@@ -20,6 +20,7 @@ constexpr int kThreads = 256;
 // arithmetic under MF_PROJ_AUTO (their FP32 projection would leave ~1e-10 of F)
 constexpr double kProjOuterAbove = 1e-3;
 
+
 int grid_for(long long n) {
   long long g = (n + kThreads - 1) / kThreads;
   if (g < 1) g = 1;
@@ -191,6 +192,7 @@ __global__ void k_step_begin(HistState* hs, HistTables t) {
   hs->ncg = 0;
   hs->ratio = INFINITY;
   hs->last = 0;
+  hs->res32 = hs->dw_res;   // the first residual of a step uses FP32 transforms where they exist
 }
 
 // Predictor of a load step (the strain-controlled components shifted
@@ -251,8 +253,14 @@ __global__ void k_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, 
 // ended on a direction of non-positive curvature after some progress ends
 // without failing: its flag is cleared), the iteration counts, the size of
 // the correction and the Newton stop test (Sec. 4: max_v abs(dF_v) /
-// abs(<F>) < tol_newton; never on a correction from an FP32 residual).
-__global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_last, int first_f32res) {
+// abs(<F>) < tol_newton; never on a correction from the FP32 residual of a
+// step's first iteration).  Then the pass that follows: P alone (the step
+// ends), or P with what the next iteration needs and the next residual in
+// the outer arithmetic.  (FP32 residuals later in a step were tried: their
+// rounding, relative to abs(P), is no longer small against the shrinking
+// residual, and the 128^3 polycrystal needed a fourth Newton iteration per
+// step.)
+__global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_cons) {
   int flags = sc->flags;
   if (hs->f32 && (flags & MF_FLAG_BREAKDOWN) && !(flags & ~MF_FLAG_BREAKDOWN) && sc->its > 1) {
     sc->flags = 0;
@@ -268,9 +276,12 @@ __global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHa
   hs->nn += 1;
   if (hs->nn == 1) hs->first_ratio = ratio;
   if (st && !hs->status) hs->status = st;
-  const int last = (ratio < hs->tol_newton && !first_f32res) ? 1 : 0;
+  const int last = (ratio < hs->tol_newton && !hs->res32) ? 1 : 0;
+  const int kind = last ? 0 : 1;
   hs->last = last;
-  cudaGraphSetConditional(h_last, (unsigned)last);
+  hs->res32 = 0;
+  hs->cons_kind = kind;
+  cudaGraphSetConditional(h_cons, (unsigned)kind);
 }
 
 // After the constitutive pass that follows an update: its failures, the
@@ -280,7 +291,7 @@ __global__ void k_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditi
   const int st = flags_to_status(sc->flags);
   if (st && !hs->status) hs->status = st;
   const int its = sc->its;
-  hs->launches += cnt.fixed + cnt.proj[hs->proj_kind] + cnt.cons[hs->last] +
+  hs->launches += cnt.fixed + cnt.proj[hs->proj_kind] + cnt.cons[hs->cons_kind] +
                   (long long)cnt.cg_body * (its == 0 ? 1 : (its + 1) / 2);
   cudaGraphSetConditional(h_newton, (!hs->last && !hs->status) ? 1u : 0u);
 }
@@ -612,9 +623,8 @@ cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_pr
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_last, bool first_f32res,
-                                  cudaStream_t st) {
-  k_newton_post<<<1, 1, 0, st>>>(hs, sc, h_last, first_f32res ? 1 : 0);
+cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_cons, cudaStream_t st) {
+  k_newton_post<<<1, 1, 0, st>>>(hs, sc, h_cons);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

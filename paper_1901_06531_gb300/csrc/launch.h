@@ -222,6 +222,9 @@ struct HistState {
   int nn, ncg;             // Newton and CG iterations of the step so far
   int status;              // mf_status of the history (first failure)
   int last;                // the constitutive pass after this update ends the step
+  int dw_res;              // the context has the FP32 residual kernels (double-word outer level)
+  int res32;               // the current iteration's residual came from FP32 transforms
+  int cons_kind;           // pass after this update: 0 P alone, 1 P with the next residual
   int proj_kind;           // projection of this correction: 0 none, 1 FP32, 2 outer arithmetic
   double ratio;            // max_v abs(dF_v) / abs(<F>) of the last correction
   double cg_rel_cur;       // forcing of the current CG solve (0: tol_cg alone)
@@ -258,8 +261,7 @@ cudaError_t mf_launch_predictor_hist(double* F, long long N, const HistState* hs
 cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
                                  cudaGraphConditionalHandle h_newton, bool first, cudaStream_t st);
 cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, bool first, cudaStream_t st);
-cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_last, bool first_f32res,
-                                  cudaStream_t st);
+cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_cons, cudaStream_t st);
 cudaError_t mf_launch_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
                                   IterCounts cnt, cudaStream_t st);
 cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,

@@ -774,12 +774,40 @@ HistTables hist_tables(const mf_ctx* c) {
   return t;
 }
 
-// Capture one Newton iteration on caps[lvl] (capturing into a step body or
-// the Newton loop's body); caps[lvl + 1] and caps[lvl + 2] take the nested
-// bodies.  h_newton: the Newton loop's condition, set at the end.
+// The residual b = -G*(P - P-bar) of a Newton iteration, captured on st,
+// P-bar of the step read on the device.  res32: FP32 transforms of the P the
+// preceding pass left in FP32 in the t vector (double-word outer level);
+// otherwise the outer arithmetic (double word where the fixed-size kernels
+// exist, else FP64).
+cudaError_t capture_residual(mf_ctx* c, const uint8_t* mask, bool res32, cudaStream_t st) {
+  const long long N = c->N;
+  HistState* hs = c->at<HistState>(c->ohist);
+  double* b = c->at<double>(c->ob);
+  if (res32) {
+    ZArgs za = z_args(c, true, mask, -1.0 / (double)N);
+    za.add_dev = hs->pbar;
+    za.mean_out = c->at<double>(c->ores);
+    return mf_launch_residual_f32(nullptr, c->at<float>(c->oAp), c->ws + c->ospec, c->at<float>(c->op2), b,
+                                  xy_args(c, true), za, st);
+  }
+  const bool dw = c->dw_residual();
+  ZArgs za = z_args(c, false, mask, -1.0 / (double)N, dw);
+  if (c->v2) za.S = c->zSr;
+  za.add_dev = hs->pbar;
+  za.mean_out = c->at<double>(c->ores);
+  return mf_launch_residual(c->at<double>(c->oP), c->ws + c->ospec, b, c->at<double>(c->opart),
+                            xy_args(c, false, dw), za, dw, st);
+}
+
+// Capture one Newton iteration (its residual already computed) on caps[lvl]
+// (capturing into a step body or the Newton loop's body); caps[lvl + 1] and
+// caps[lvl + 2] take the nested bodies.  h_newton: the Newton loop's
+// condition, set at the end.  The iteration ends with the pass after the
+// update and, unless the step ended, the next iteration's residual.
 cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first, const uint8_t* mask, int max_cg,
                               cudaGraphConditionalHandle h_newton) {
   const bool f32 = c->f32();
+  const bool dwr = c->dw_residual();
   const long long N = c->N;
   HistState* hs = c->at<HistState>(c->ohist);
   Scalars* sc = c->at<Scalars>(c->osc);
@@ -799,25 +827,8 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   if (e != cudaSuccess) return e;
   e = cap_begin(s1, go_body);
   if (e != cudaSuccess) return e;
-  // the residual b = -G*(P - P-bar), P-bar of the step read on the device;
-  // the first iteration of a step with FP32 transforms (double-word outer level)
-  const bool res32 = first && c->dw_residual();
-  if (res32) {
-    ZArgs za = z_args(c, true, mask, -1.0 / (double)N);
-    za.add_dev = hs->pbar;
-    za.mean_out = c->at<double>(c->ores);
-    e = mf_launch_residual_f32(nullptr, c->at<float>(c->oAp), c->ws + c->ospec, c->at<float>(c->op2), b,
-                               xy_args(c, true), za, s1);
-  } else {
-    const bool dw = c->dw_residual();
-    ZArgs za = z_args(c, false, mask, -1.0 / (double)N, dw);
-    if (c->v2) za.S = c->zSr;
-    za.add_dev = hs->pbar;
-    za.mean_out = c->at<double>(c->ores);
-    e = mf_launch_residual(c->at<double>(c->oP), c->ws + c->ospec, b, part, xy_args(c, false, dw), za, dw, s1);
-  }
   // FP32 inner solves: the null rotations out of the right-hand side
-  if (e == cudaSuccess && f32) e = mf_launch_defl_project_hist(b, false, true, F, N, hs, part, c->pw_blocks, sc, s1);
+  if (f32) e = mf_launch_defl_project_hist(b, false, true, F, N, hs, part, c->pw_blocks, sc, s1);
   if (e == cudaSuccess)
     e = mf_launch_cg_init_hist(b, c->ws + c->or_, f32, 9 * N, part, c->pw_blocks, N, hs, sc, s1);
   cudaGraphConditionalHandle h_cg;
@@ -853,12 +864,11 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
                               nullptr, s2);
         corr = c->ws + c->op2;
       } else if (kind == 2) {
-        const bool dwp = c->dw_residual();
-        ZArgs za = z_args(c, false, mask, 1.0 / (double)N, dwp);
+        ZArgs za = z_args(c, false, mask, 1.0 / (double)N, dwr);
         if (c->v2) za.S = c->zSr;
         e = mf_launch_to_double(c->ws + c->ox, b, true, 9 * N, s2);
         if (e == cudaSuccess) {
-          if (dwp) {
+          if (dwr) {
             const XYArgs xd = xy_args(c, false, true);
             e = mf_v2_xyf_dw(b, c->ws + c->ospec, xd, s2);
             if (e == cudaSuccess) e = mf_v2_zp_dw(c->ws + c->ospec, za, s2);
@@ -883,21 +893,24 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   } else if (e == cudaSuccess) {
     e = mf_launch_newton_update_hist(F, c->ws + c->ox, false, N, part, c->pw_blocks, hs, sc, s1);
   }
-  // the Newton test, then P alone (end of the step) or the full pass
-  cudaGraphConditionalHandle h_last;
-  if (e == cudaSuccess) e = cap_handle(s1, &h_last);
-  if (e == cudaSuccess) e = mf_launch_newton_post(hs, sc, h_last, res32, s1);
-  cudaGraph_t lb2[2] = {nullptr, nullptr};
-  if (e == cudaSuccess) e = cap_conditional(s1, h_last, cudaGraphCondTypeIf, 2, lb2);
-  for (int br = 0; br < 2 && e == cudaSuccess; ++br) {
-    // body 0 runs when the correction passed the test (the step ends)
+  // the Newton test, then the pass after the update: 0 P alone (the step
+  // ends), 1 P with the tangent or H and the rotation moments, and the next
+  // iteration's residual in the outer arithmetic
+  cudaGraphConditionalHandle h_cons;
+  if (e == cudaSuccess) e = cap_handle(s1, &h_cons);
+  if (e == cudaSuccess) e = mf_launch_newton_post(hs, sc, h_cons, s1);
+  constexpr int nkind = 2;
+  cudaGraph_t cb[nkind] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cap_conditional(s1, h_cons, cudaGraphCondTypeSwitch, nkind, cb);
+  for (int kind = 0; kind < nkind && e == cudaSuccess; ++kind) {
     const long long lb = g_mf_launches;
-    e = cap_begin(s2, lb2[br]);
+    e = cap_begin(s2, cb[kind]);
     if (e != cudaSuccess) break;
-    const bool last = br == 0;
-    const int st = run_constitutive(c, !last && !f32, !last && f32, !last && f32, false, s2);
+    const bool more = kind != 0;
+    int st = run_constitutive(c, more && !f32, more && f32, more && f32, false, s2);
+    if (!st && more && capture_residual(c, mask, false, s2) != cudaSuccess) st = MF_CUDA_ERROR;
     e = cap_end(s2, st ? cudaErrorUnknown : cudaSuccess);
-    cnt.cons[last ? 1 : 0] = (int)(g_mf_launches - lb);
+    cnt.cons[kind] = (int)(g_mf_launches - lb);
     in_bodies += g_mf_launches - lb;
   }
   // the kernels outside the bodies, including the condition kernel below
@@ -940,9 +953,11 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
       e = mf_launch_step_begin(hs, t, caps[1]);
       if (e == cudaSuccess) e = mf_launch_predictor_hist(F, N, hs, sc, false, caps[1]);
       // the pass after the predictor: FP64 P and K, or (FP32 inner) H and the
-      // rotation moments, with P itself in FP32 for the FP32 first residual
+      // rotation moments, with P itself in FP32 for the FP32 first residual;
+      // then the first residual
       if (e == cudaSuccess && run_constitutive(c, !f32, f32, f32, f32 && c->dw_residual(), caps[1]))
         e = cudaErrorUnknown;
+      if (e == cudaSuccess) e = capture_residual(c, mask, c->dw_residual(), caps[1]);
       const int step_kernels = (int)(g_mf_launches - ls) + 1;
       cudaGraphConditionalHandle h_newton;
       if (e == cudaSuccess) e = cap_handle(caps[1], &h_newton);
@@ -1011,6 +1026,7 @@ cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target,
   hh->max_cg = max_cg;
   hh->forcing = (c->f32() || c->forcing64) ? 1 : 0;
   hh->f32 = c->f32() ? 1 : 0;
+  hh->dw_res = c->dw_residual() ? 1 : 0;
   hh->proj_arith = c->proj_arith;
   hh->tol_newton = tol_newton;
   hh->tol_cg = tol_cg;
@@ -1788,7 +1804,10 @@ int mf_set_inexact_newton(mf_ctx* c, int on) {
 
 int mf_set_outer_arith(mf_ctx* c, int arith) {
   if (!c || (arith != MF_OUTER_DOUBLE_WORD && arith != MF_OUTER_FP64)) return MF_INVALID_ARG;
-  if (c->outer_arith != arith) c->tuned = false;   // the residual tile is tuned per arithmetic
+  if (c->outer_arith != arith) {
+    c->tuned = false;    // the residual tile is tuned per arithmetic
+    free_cg_graph(c);    // the captured histories hold the outer level's kernels
+  }
   c->outer_arith = arith;
   return MF_OK;
 }

@@ -155,6 +155,31 @@ def test_fp32_inner_projection_in_outer_arithmetic(outer):
     check_control(out, mask, target, 1e-9, 1e-14)
 
 
+def test_outer_arith_switch_between_solves():
+    """A context whose outer arithmetic changes between solves gives what a
+    context created with the new setting gives, bit for bit (its captured
+    load histories hold the outer level's kernels and are rebuilt)."""
+    mf = lib()
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 41)
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(4, 0.2))
+
+    def run(ctx, arith):
+        ctx.set_outer_arith(arith)
+        ctx.set_F(None)
+        return ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    for arith in (mf.MF_OUTER_DOUBLE_WORD, mf.MF_OUTER_FP64, mf.MF_OUTER_DOUBLE_WORD):
+        o = run(ctx, arith)
+        fresh = mf.Context(n, n, n, mf.MF_FP32_INNER)
+        fresh.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+        ref = run(fresh, arith)
+        np.testing.assert_array_equal(o["Fbar"], ref["Fbar"])
+        np.testing.assert_array_equal(o["cg"], ref["cg"])
+
+
 def test_projection_arith_is_validated():
     mf = lib()
     with pytest.raises(mf.MixFFTError):
