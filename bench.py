@@ -36,7 +36,7 @@ SEED = 1003
 TOL_NEWTON, TOL_CG, CG_REL = 1e-8, 1e-10, 1e-4
 WORKLOAD = ("polycrystal 128^3, 200-grain Voronoi, SVK cubic (168/121/75 GPa) rotated per grain, "
             "cyclic stress P11 +-0.2 GPa in 20 steps (F12=F13=F23=0), FP32 inner CG / double-word outer "
-            "(FP32 first residual per step; averages, control and Newton update in FP64)")
+            "(averages, control and Newton update in FP64), extrapolated Newton start")
 METRIC = ("Newton load steps/s at 128^3 (FP32-inner CG / double-word outer), polycrystal cyclic stress "
           "control")
 # algorithmic bytes per voxel of each kernel of one CG iteration.  FP32 (matrix-
@@ -51,6 +51,10 @@ ALGO_BYTES_F64 = [3 * 72 + 360 + 3 * 72, 72 + 72, 72 + 72, 3 * 72]
 # one projected-operator application y = G*(K:x), FP32 with the matrix-free
 # tangent: K:x (x, H, phase in; t out), x-y forward, z-pass, x-y inverse
 MATVEC_BYTES_F32 = (36 + 36 + 4 + 36) + 72 + 72 + 72
+# flops per voxel of one FP64 operator application: forward and inverse 3D
+# transforms of the nine components (2.5 log2(N) flops per real point each
+# at 128^3: 945), the packed tangent apply (162), G-hat-star (about 30)
+MATVEC_FLOP_F64 = 1140
 
 
 def workload(n=N1, ngrains=NGRAINS, seed=SEED):
@@ -389,6 +393,7 @@ def run_batched(args):
         n = cell["n"]
         c = mf.Context(n, n, n, mf.MF_FP32_INNER, stream=torch.cuda.Stream())
         c.set_material(mf.MF_NEOHOOKE, cell["params"], cell["phase"])
+        c.set_predictor(mf.MF_PRED_EXTRAPOLATE)
         ctxs.append(c)
     masks = np.stack([cell["mask"] for cell in cells])
     targets = np.stack([cell["target"] for cell in cells])
@@ -415,7 +420,8 @@ def run_batched(args):
         sizes[str(cell["n"])] = sizes.get(str(cell["n"]), 0) + 1
     res = {"workload": (f"{BATCH_CELLS} sphere-particle neo-Hookean cells, sizes from {{32,48,64,96}}^3 "
                         f"(seed {BATCH_SEED}), vf U(0.1,0.3), contrast U(5,50), random mixed control, "
-                        f"{BATCH_STEPS} load steps, FP32 inner / FP64 outer"),
+                        f"{BATCH_STEPS} load steps, FP32 inner / double-word outer, extrapolated Newton starts; "
+                        "all cells one graph launch (mf_solve_batch)"),
            "cells_by_size": sizes, "voxels_total": voxels,
            "batch_s": t_batch, "sequential_s": t_seq,
            "cell_load_steps_per_s": BATCH_CELLS * BATCH_STEPS / t_batch,
@@ -525,10 +531,13 @@ def run_paper_cases(args):
     mask, target = inputs.history_mixed_strain11(10, 1.05)
     c2 = {"workload": f"{n}^3 RSA spheres r=4 vf 0.25 (seed 1002), neo-Hookean contrast 10, "
                       "F11 -> 1.05 in 10 steps, other components stress free"}
-    for name, prec, forcing in (("fp32_inner", mf.MF_FP32_INNER, None), ("fp64", mf.MF_FP64, 0),
-                                ("fp64_forcing", mf.MF_FP64, 1)):
+    for name, prec, forcing, pred in (("fp32_inner", mf.MF_FP32_INNER, None, mf.MF_PRED_EXTRAPOLATE),
+                                      ("fp32_inner_uniform_predictor", mf.MF_FP32_INNER, None, mf.MF_PRED_UNIFORM),
+                                      ("fp64", mf.MF_FP64, 0, mf.MF_PRED_UNIFORM),
+                                      ("fp64_forcing", mf.MF_FP64, 1, mf.MF_PRED_EXTRAPOLATE)):
         ctx = mf.Context(n, n, n, prec)
         ctx.set_material(mf.MF_NEOHOOKE, params, phs)
+        ctx.set_predictor(pred)
         if forcing is not None:
             ctx.set_inexact_newton(forcing)
         try:
@@ -657,6 +666,10 @@ def run_ours(args):
 
     ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    # each step starts from the last converged state extrapolated along the
+    # last load increment (mf_set_predictor); the paper's uniform start is
+    # timed beside it below
+    ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
     ztile, ztile_ms, xy_persist, xy_ms = ctx.autotune()
 
     def steps(c, k0, k1):
@@ -696,6 +709,22 @@ def run_ours(args):
         per_step.append((a, b))
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in per_step]
+    # the paper's uniform start (the last converged state, strain-controlled
+    # components shifted to the new F-bar), whole history in one call
+    ctx.set_predictor(mf.MF_PRED_UNIFORM)
+    steps(ctx, 0, 1)
+    ctx.set_F(None)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    o_uni = steps(ctx, 0, args.steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    uniform_ms = a.elapsed_time(b) / args.steps
+    its_uniform = [(int(x), int(y)) for x, y in zip(o_uni["newton"], o_uni["cg"])]
+    ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+    steps(ctx, 0, 1)
 
     # end to end through the C ABI with host buffers: step inputs go in as
     # arguments, <F>, <P> and the full F field come back to pinned host memory
@@ -793,8 +822,11 @@ def run_ours(args):
     ctx64.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
     steps(ctx64, 0, 1)
     fp64 = {}
-    for forcing in (0, 1):
+    for name, forcing, pred in (("plain", 0, mf.MF_PRED_UNIFORM), ("plain_extrapolated", 0, mf.MF_PRED_EXTRAPOLATE),
+                                ("forcing", 1, mf.MF_PRED_EXTRAPOLATE)):
         ctx64.set_inexact_newton(forcing)
+        ctx64.set_predictor(pred)
+        steps(ctx64, 0, 1)
         ctx64.set_F(None)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -803,11 +835,13 @@ def run_ours(args):
         o = steps(ctx64, 0, nacc)
         b.record(stream)
         torch.cuda.synchronize()
-        fp64["forcing" if forcing else "plain"] = {
+        fp64[name] = {
             "ms_per_step": a.elapsed_time(b) / nacc,
             "newton_cg_per_step": [(int(x), int(y)) for x, y in zip(o["newton"], o["cg"])], "steps": nacc}
-    # accuracy, lockstep: FP32 inner (double-word outer) against plain FP64
+    # accuracy, lockstep: FP32 inner (double-word outer, extrapolated
+    # starts) against plain FP64 with the paper's uniform start
     ctx64.set_inexact_newton(0)
+    ctx64.set_predictor(mf.MF_PRED_UNIFORM)
     ctx64.set_F(None)
     ctx.set_F(None)
     acc = {"Fbar": [], "Pbar": [], "F_field": []}
@@ -824,11 +858,14 @@ def run_ours(args):
                 "Fbar_max_rel": max(acc["Fbar"]), "Pbar_max_abs_over_C11": max(acc["Pbar"]),
                 "F_field_max_rel": max(acc["F_field"]),
                 "per_step": {k: [float("%.3g" % v) for v in acc[k]] for k in ("Fbar", "Pbar", "F_field")},
-                "note": ("FP32 inner with double-word outer arithmetic (the timed configuration) against the "
-                         "plain FP64 path, every step of the history, same tolerances; <P> error over C11 = 168")}
-    # the FP64 path with forcing against plain FP64 at the end of the history
+                "note": ("FP32 inner with double-word outer arithmetic and extrapolated starts (the timed "
+                         "configuration) against the plain FP64 path with uniform starts, every step of the "
+                         "history, same tolerances; <P> error over C11 = 168")}
+    # the FP64 path with forcing (and extrapolated starts) against plain FP64
+    # at the end of the history
     F64p = ctx64.get_fields()[0]
     ctx64.set_inexact_newton(1)
+    ctx64.set_predictor(mf.MF_PRED_EXTRAPOLATE)
     ctx64.set_F(None)
     of = steps(ctx64, 0, nacc)
     F64f = ctx64.get_fields()[0]
@@ -847,6 +884,10 @@ def run_ours(args):
     cf64_ms = time_cufft_matvec(ctx64, x64, y64, 10)
     kms64 = ctx64.time_kernels(m0, reps=5)
     del ctx64, x64, y64
+
+    # the arithmetic roof of the FP64 path: measured FP64 (and FP32) FMA rate
+    fp64_peak = mf.probe_fma(mf.MF_FP64)
+    fp32_peak = mf.probe_fma(mf.MF_FP32_INNER)
 
     batched = run_batched(args) if not args.no_batched else None
     adjoint = run_adjoint(args) if not args.no_adjoint else None
@@ -885,6 +926,13 @@ def run_ours(args):
                      "xy_forward_ms_by_schedule": {"per_plane": float(xy_ms[0]), "persistent": float(xy_ms[1])}},
         "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9,
                             "reps": "median of 100 (FP32) and 10 (FP64) warm applications, events per application"},
+        "fp64_roofline": {"bound": "fp64 FMA", "flop_per_voxel": MATVEC_FLOP_F64,
+                          "achieved_TFLOP_s": MATVEC_FLOP_F64 * N / (mv64_ms * 1e-3) / 1e12,
+                          "peak_TFLOP_s": fp64_peak, "peak_kind": "measured here (mf_probe_fma, FP64)",
+                          "frac": MATVEC_FLOP_F64 * N / (mv64_ms * 1e-3) / 1e12 / fp64_peak,
+                          "fp32_fma_TFLOP_s": fp32_peak,
+                          "note": ("plain FP64 projected operator: the FP64 pipe, not HBM, bounds it "
+                                   "(about 1.1 kflop per voxel per application against 504 B)")},
         "matvec_roofline_fp32": {"bytes_per_voxel": MATVEC_BYTES_F32,
                                  "achieved_GB_s": MATVEC_BYTES_F32 * N / (mv32_ms * 1e-3) / 1e9,
                                  "frac": MATVEC_BYTES_F32 * N / (mv32_ms * 1e-3) / 1e9 / peak,
@@ -900,22 +948,31 @@ def run_ours(args):
             "fp32_inner_dw_outer": total_ms / args.steps,
             "fp32_inner_dw_outer_per_call_median": float(np.median(step_ms)),
             "fp32_inner_fp64_outer": fp64_outer_ms,
+            "fp32_inner_dw_outer_uniform_predictor": uniform_ms,
             "fp64_plain": fp64["plain"]["ms_per_step"],
+            "fp64_plain_extrapolated": fp64["plain_extrapolated"]["ms_per_step"],
             "fp64_forcing": fp64["forcing"]["ms_per_step"],
             "fp64_steps_timed": nacc,
             "labels": {
                 "fp32_inner_dw_outer": ("the timed configuration: FP32 inner CG; outer level (P, residual "
-                                        "transforms) in double-word FP32 (about 48 bits), the first residual "
-                                        "of each step and its P in FP32; averages, control and Newton update "
-                                        "in FP64"),
+                                        "transforms) in double-word FP32 (about 48 bits), FP32 first residual "
+                                        "of a step that did not start extrapolated; averages, control and "
+                                        "Newton update in FP64; each step starts from the last converged state "
+                                        "extrapolated along the last load increment"),
+                "fp32_inner_dw_outer_uniform_predictor": ("the same with the paper's uniform start (last "
+                                                          "converged state, strain-controlled components "
+                                                          "shifted to the new F-bar)"),
+                "fp64_plain_extrapolated": "plain FP64, CG to the absolute tolerance, extrapolated starts",
                 "fp32_inner_fp64_outer": "FP32 inner CG, outer level (P and every residual) in strict FP64",
-                "fp64_plain": "every step in FP64, CG to the absolute tolerance (Sec. 4's rule)",
-                "fp64_forcing": ("every step in FP64 with the same inexact-Newton forcing as the FP32-inner "
-                                 "path (mf_set_inexact_newton): same stopping rule")},
+                "fp64_plain": "every step in FP64, CG to the absolute tolerance (Sec. 4's rule), uniform starts",
+                "fp64_forcing": ("every step in FP64 with the same inexact-Newton forcing and extrapolated starts "
+                                 "as the FP32-inner path (mf_set_inexact_newton): same stopping rule")},
             "ratio_fp64_plain_over_fp32_inner": fp64["plain"]["ms_per_step"] / (total_ms / args.steps),
             "ratio_fp64_forcing_over_fp32_inner": fp64["forcing"]["ms_per_step"] / (total_ms / args.steps)},
         "accuracy_fp32_inner_vs_fp64": accuracy,
         "iterations": {"fp32_inner_newton_cg_per_step": its,
+                       "fp32_inner_uniform_predictor_newton_cg_per_step": its_uniform,
+                       "fp64_plain_extrapolated_newton_cg_per_step": fp64["plain_extrapolated"]["newton_cg_per_step"],
                        "fp64_plain_newton_cg_per_step": fp64["plain"]["newton_cg_per_step"],
                        "fp64_forcing_newton_cg_per_step": fp64["forcing"]["newton_cg_per_step"]},
     }

@@ -54,6 +54,7 @@ typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
 typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
 typedef enum { MF_OUTER_DOUBLE_WORD = 0, MF_OUTER_FP64 = 1 } mf_outer_arith;
 typedef enum { MF_PROJ_FP32 = 0, MF_PROJ_OUTER = 1, MF_PROJ_AUTO = 2 } mf_projection_arith;
+typedef enum { MF_PRED_UNIFORM = 0, MF_PRED_EXTRAPOLATE = 1 } mf_predictor;
 
 typedef struct mf_ctx mf_ctx;
 
@@ -230,6 +231,14 @@ int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, const uint8
  * host, 4 floats, mean milliseconds per launch. */
 int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, int graph, float* ms_out);
 
+/* Measurement hook: the FMA throughput of the current device in TFLOP/s
+ * (2 flops per FMA), FP64 (precision MF_FP64) or FP32 (MF_FP32_INNER), from
+ * independent FMA chains on every SM with no memory traffic (CUDA events
+ * around three launches after one untimed launch, legacy stream).  The FP64
+ * path of this library is bound by this rate, not by HBM: its roofline
+ * fraction is taken against it. */
+int mf_probe_fma(int precision, double* tflops_out);
+
 /* Number of kernel launches the library has issued in this process (all
  * contexts); differences around a region count its launches. */
 long long mf_kernel_launches(void);
@@ -346,6 +355,22 @@ int mf_set_xy_persistent(mf_ctx* ctx, int on);
  * about 1e-10 of F each.  MF_INVALID_ARG for an unknown value, or for a
  * value other than MF_PROJ_FP32 on a non-FP32-inner context. */
 int mf_set_projection_arith(mf_ctx* ctx, int arith);
+
+/* Start of the Newton iterations of a load step (Sec. 2.1 writes the start
+ * as the last converged fluctuation on the new average; the paper fixes
+ * nothing more).  MF_PRED_UNIFORM (default): the last converged F with each
+ * strain-controlled component shifted uniformly to the prescribed F-bar.
+ * MF_PRED_EXTRAPOLATE: when the last two converged steps of the context had
+ * the same control mask, F is first extrapolated along the last increment,
+ * F + alpha (F - F_prev), alpha the projection of this step's increment of the
+ * prescribed values on the last one (1 along a ramp, -1 back across a
+ * reversal), then shifted as above; the first residual of such a step runs
+ * in the outer arithmetic and its inner solve to cg_rel.  The converged state
+ * is the same to the Newton tolerance; the iteration counts drop along
+ * smooth load paths.  The two converged steps are remembered across mf_solve
+ * calls (not across mf_set_F, mf_set_material, mf_load_F or a failed step).
+ * MF_INVALID_ARG for another value. */
+int mf_set_predictor(mf_ctx* ctx, int kind);
 
 /* Stopping rule of the CG solves of an MF_FP64 context (Sec. 4 gives the
  * CG tolerance only as an absolute bound on the voxel-averaged residual).

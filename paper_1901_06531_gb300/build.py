@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmixfft.so")
 SOURCES = ["transform.cu", "transform2_f32.cu", "transform2_f64.cu", "pointwise.cu", "cg.cu", "history.cu",
            "mixfft.cu", "noalloc.cu", "cufft_path.cu", "adjoint.cu", "transform2_dw.cu",
-           "constitutive_dw.cu"]
+           "constitutive_dw.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xptxas", "-v"]

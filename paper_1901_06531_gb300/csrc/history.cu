@@ -178,35 +178,78 @@ __global__ void k_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, in
   cudaGraphSetConditional(h_step, hs->nsteps > 0 ? 1u : 0u);
 }
 
-// Load step k of the table: control mask, targets, P-bar (Sec. 2.3).
-__global__ void k_step_begin(HistState* hs, HistTables t) {
+// Load step k of the table: control mask, targets, P-bar (Sec. 2.3).  With
+// the extrapolating predictor and the last two converged steps at hand (same
+// mask), the factor alpha of the increment: the projection of this step's
+// target increment on the last one, alpha = dT_k . dT_(k-1) / abs(dT_(k-1))^2
+// (1 along a ramp, -1 back across a reversal of the load).  An extrapolated
+// start is close to the solution: its first residual runs in the outer
+// arithmetic (FP32 rounding, relative to abs(P), would no longer be small
+// against it).
+__global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle h_first, int set_first) {
   const StepIn& row = t.in[hs->k];
+  bool same = hs->nprev >= 2;
   for (int c = 0; c < 9; ++c) {
     const unsigned char m = row.mask[c];
     const double v = row.target[c];
     hs->mask[c] = m;
     hs->target[c] = v;
     hs->pbar[c] = m ? v : 0.0;
+    if (m != hs->mprev[c]) same = false;
   }
+  double num = 0.0, den = 0.0;
+  for (int c = 0; c < 9; ++c) {
+    const double d1 = hs->target[c] - hs->t1[c], d0 = hs->t1[c] - hs->t2[c];
+    num += d1 * d0;
+    den += d0 * d0;
+  }
+  const int ex = (hs->extrap && same && den > 0.0) ? 1 : 0;
+  hs->extrapolated = ex;
+  hs->alpha = ex ? num / den : 0.0;
   hs->nn = 0;
   hs->ncg = 0;
   hs->ratio = INFINITY;
   hs->last = 0;
-  hs->res32 = hs->dw_res;   // the first residual of a step uses FP32 transforms where they exist
+  // the first residual of a step uses FP32 transforms where they exist,
+  // unless the start was extrapolated
+  hs->res32 = hs->dw_res && !ex;
+  if (set_first) cudaGraphSetConditional(h_first, ex ? 1u : 0u);
 }
 
-// Predictor of a load step (the strain-controlled components shifted
-// uniformly to the prescribed F-bar; Sec. 2.1, 2.3), with the control of the
-// current step from the history state.
-__global__ void k_predictor_hist(double* __restrict__ F, long long N, const HistState* hs, const Scalars* sc,
-                                 bool after_update) {
-  const double* mean = after_update ? sc->meanF_new : sc->meanF;
+// Predictor of a load step (Sec. 2.1, 2.3): with the extrapolating
+// predictor, F <- F + alpha (F - Fprev) (and Fprev <- F, the state the next
+// step extrapolates from); then every strain-controlled component shifted
+// uniformly so that its average is the prescribed F-bar.  After an FP32
+// update (after_update) only the shift, to the averages of that update.
+__global__ void k_predictor_hist(double* __restrict__ F, double* __restrict__ Fprev, long long N,
+                                 const HistState* hs, const Scalars* sc, bool after_update) {
+  double shift[9];
+  const double a = (!after_update && hs->extrapolated) ? hs->alpha : 0.0;
+  for (int c = 0; c < 9; ++c) {
+    double mean;
+    if (after_update) mean = sc->meanF_new[c];
+    else mean = sc->meanF[c] + a * (sc->meanF[c] - hs->fmean2[c]);
+    shift[c] = hs->mask[c] ? 0.0 : hs->target[c] - mean;
+  }
+  if (!after_update && Fprev != nullptr) {
+    // every component: Fprev <- F, F <- F + alpha (F - Fprev) + shift
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const double f = F[c * N + v], fp = Fprev[c * N + v];
+        Fprev[c * N + v] = f;
+        F[c * N + v] = f + a * (f - fp) + shift[c];
+      }
+    }
+    return;
+  }
+  // the strain-controlled components only
   for (int c = 0; c < 9; ++c) {
     if (hs->mask[c]) continue;
-    const double d = hs->target[c] - mean[c];
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x)
-      F[c * N + v] += d;
+      F[c * N + v] += shift[c];
   }
 }
 
@@ -227,7 +270,9 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
   }
   hs->defl.m = 0;
   if (hs->f32) null_rotations_dev(sc->meanF, hs->mask, sc->T, sc->S, hs->kappa, 1e-6, &hs->defl);
-  const bool loose = first || hs->ratio < sqrt(hs->tol_newton);
+  // the first iteration of an extrapolated step is solved to cg_rel: it is
+  // expected to be followed by one more (the test below) only
+  const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
   hs->cg_rel_cur = hs->forcing ? (loose ? sqrt(hs->cg_rel) : hs->cg_rel) : 0.0;
   cudaGraphSetConditional(h_go, 1u);
 }
@@ -299,10 +344,19 @@ __global__ void k_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditi
 // End of a load step: record <F>, <P> (Sec. 2.2) and the iteration counts;
 // continue with the next step unless the history failed.
 __global__ void k_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
-                           int kernels) {
-  hs->launches += kernels;
+                           int kernels, int kernels_ex) {
+  hs->launches += hs->extrapolated ? kernels_ex : kernels;
   if (!hs->status) {
     const int k = hs->k;
+    // the converged step joins the two the predictor extrapolates from
+    for (int c = 0; c < 9; ++c) {
+      hs->t2[c] = hs->t1[c];
+      hs->t1[c] = hs->target[c];
+      hs->fmean2[c] = hs->fmean1[c];
+      hs->fmean1[c] = sc->meanF[c];
+      hs->mprev[c] = hs->mask[c];
+    }
+    hs->nprev = hs->nprev < 2 ? hs->nprev + 1 : 2;
     StepOut& row = t.out[k];
     for (int c = 0; c < 9; ++c) {
       row.Fbar[c] = sc->meanF[c];
@@ -597,15 +651,15 @@ cudaError_t mf_launch_hist_init(HistState* hs, cudaGraphConditionalHandle h_step
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaStream_t st) {
-  k_step_begin<<<1, 1, 0, st>>>(hs, t);
+cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle* h_first, cudaStream_t st) {
+  k_step_begin<<<1, 1, 0, st>>>(hs, t, h_first ? *h_first : cudaGraphConditionalHandle(), h_first ? 1 : 0);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_predictor_hist(double* F, long long N, const HistState* hs, const Scalars* sc,
+cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, long long N, const HistState* hs, const Scalars* sc,
                                      bool after_update, cudaStream_t st) {
-  k_predictor_hist<<<grid_for(9 * N), kThreads, 0, st>>>(F, N, hs, sc, after_update);
+  k_predictor_hist<<<grid_for(N), kThreads, 0, st>>>(F, Fprev, N, hs, sc, after_update);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
@@ -637,8 +691,8 @@ cudaError_t mf_launch_newton_cond(HistState* hs, const Scalars* sc, cudaGraphCon
 }
 
 cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
-                               int kernels, cudaStream_t st) {
-  k_step_end<<<1, 1, 0, st>>>(hs, sc, t, h_step, kernels);
+                               int kernels, int kernels_ex, cudaStream_t st) {
+  k_step_end<<<1, 1, 0, st>>>(hs, sc, t, h_step, kernels, kernels_ex);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

@@ -217,6 +217,13 @@ struct HistState {
   int proj_arith;          // MF_PROJ_* of the FP32 corrections
   double tol_newton, tol_cg, cg_rel, kappa;
   double first_ratio;      // size of the last step's first correction (persists across launches)
+  int extrap;              // the predictor extrapolates from the last two converged steps
+  // persists across launches (the host keeps it between calls): the last two
+  // converged steps behind F, for the extrapolating predictor
+  int nprev;               // consecutive converged steps recorded (0, 1, 2)
+  double t1[9], t2[9];     // their targets (t1 the latest)
+  double fmean1[9], fmean2[9];   // their <F>
+  unsigned char mprev[9];  // their control mask
   // state
   int k;                   // step of the table being solved
   int nn, ncg;             // Newton and CG iterations of the step so far
@@ -228,6 +235,8 @@ struct HistState {
   int proj_kind;           // projection of this correction: 0 none, 1 FP32, 2 outer arithmetic
   double ratio;            // max_v abs(dF_v) / abs(<F>) of the last correction
   double cg_rel_cur;       // forcing of the current CG solve (0: tol_cg alone)
+  int extrapolated;        // this step started from an extrapolated F
+  double alpha;            // its extrapolation factor
   double target[9], pbar[9];
   unsigned char mask[9];
   Defl defl;               // null rotations of the current Newton iteration
@@ -255,8 +264,13 @@ struct HistTables {
   StepOut* out;
 };
 cudaError_t mf_launch_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, int kernels, cudaStream_t st);
-cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaStream_t st);
-cudaError_t mf_launch_predictor_hist(double* F, long long N, const HistState* hs, const Scalars* sc,
+// h_first: set to 1 when the step's first residual runs in the outer
+// arithmetic (an extrapolated start), 0 for the FP32 one (may be null)
+cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle* h_first, cudaStream_t st);
+// Fprev (9N, may be null when the predictor does not extrapolate): the
+// converged F before the current one; the step's predictor replaces it by
+// the current F and extrapolates F along the last increment
+cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, long long N, const HistState* hs, const Scalars* sc,
                                      bool after_update, cudaStream_t st);
 cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
                                  cudaGraphConditionalHandle h_newton, bool first, cudaStream_t st);
@@ -264,8 +278,10 @@ cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_pr
 cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_cons, cudaStream_t st);
 cudaError_t mf_launch_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
                                   IterCounts cnt, cudaStream_t st);
+// kernels, kernels_ex: the step's kernels outside its Newton iterations, for
+// a uniform and an extrapolated start (launch counter)
 cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
-                               int kernels, cudaStream_t st);
+                               int kernels, int kernels_ex, cudaStream_t st);
 // CG start with the tolerance and forcing of the current Newton iteration read
 // from the history state
 cudaError_t mf_launch_cg_init_hist(const double* b, void* r, bool f32, long long n9, double* partials, int nblk,

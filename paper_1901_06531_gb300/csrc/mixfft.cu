@@ -223,7 +223,9 @@ struct mf_ctx {
   size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
       otable32, otabledw, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
   // load-history state and tables (history.cu)
-  size_t ohist, othout, othin;
+  size_t ohist, othout, othin, oFprev;
+  int predictor = MF_PRED_UNIFORM;  // mf_set_predictor
+  HistState keep;                   // the history fields that persist between calls (nprev, t1, ...)
   char* pin = nullptr;              // pinned staging of the history block (cudaMallocHost)
   std::vector<HistGraph> hist;      // instantiated history graphs
   cudaStream_t caps[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // capture streams, one per nesting level
@@ -889,7 +891,7 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
     }
     // FP32 corrections carry a rounding-level average on the strain-controlled
     // components; the FP64 outer level re-imposes F-bar there
-    if (e == cudaSuccess) e = mf_launch_predictor_hist(F, N, hs, sc, true, s1);
+    if (e == cudaSuccess) e = mf_launch_predictor_hist(F, nullptr, N, hs, sc, true, s1);
   } else if (e == cudaSuccess) {
     e = mf_launch_newton_update_hist(F, c->ws + c->ox, false, N, part, c->pw_blocks, hs, sc, s1);
   }
@@ -950,15 +952,39 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
     e = cap_begin(caps[1], B1);
     if (e == cudaSuccess) {
       const long long ls = g_mf_launches;
-      e = mf_launch_step_begin(hs, t, caps[1]);
-      if (e == cudaSuccess) e = mf_launch_predictor_hist(F, N, hs, sc, false, caps[1]);
+      const bool extrap = c->predictor == MF_PRED_EXTRAPOLATE;
+      const bool dwr = c->dw_residual();
+      // with the extrapolating predictor on a double-word context, the first
+      // residual's arithmetic follows the start (IF: extrapolated -> outer)
+      cudaGraphConditionalHandle h_first;
+      const bool choose = extrap && dwr;
+      if (choose) e = cap_handle(caps[1], &h_first);
+      if (e == cudaSuccess) e = mf_launch_step_begin(hs, t, choose ? &h_first : nullptr, caps[1]);
+      if (e == cudaSuccess)
+        e = mf_launch_predictor_hist(F, extrap ? c->at<double>(c->oFprev) : nullptr, N, hs, sc, false, caps[1]);
       // the pass after the predictor: FP64 P and K, or (FP32 inner) H and the
-      // rotation moments, with P itself in FP32 for the FP32 first residual;
+      // rotation moments, with P itself in FP32 for an FP32 first residual;
       // then the first residual
-      if (e == cudaSuccess && run_constitutive(c, !f32, f32, f32, f32 && c->dw_residual(), caps[1]))
-        e = cudaErrorUnknown;
-      if (e == cudaSuccess) e = capture_residual(c, mask, c->dw_residual(), caps[1]);
-      const int step_kernels = (int)(g_mf_launches - ls) + 1;
+      int step_kernels = 0, step_kernels_ex = 0;
+      auto first_pass = [&](bool res32, cudaStream_t st) {
+        int r = run_constitutive(c, !f32, f32, f32, res32, st);
+        if (!r && capture_residual(c, mask, res32, st) != cudaSuccess) r = MF_CUDA_ERROR;
+        return r ? cudaErrorUnknown : cudaSuccess;
+      };
+      if (e == cudaSuccess && !choose) {
+        e = first_pass(dwr, caps[1]);
+        step_kernels = step_kernels_ex = (int)(g_mf_launches - ls) + 1;
+      } else if (e == cudaSuccess) {
+        const int base = (int)(g_mf_launches - ls) + 1;
+        cudaGraph_t fb[2] = {nullptr, nullptr};
+        e = cap_conditional(caps[1], h_first, cudaGraphCondTypeIf, 2, fb);
+        for (int br = 0; br < 2 && e == cudaSuccess; ++br) {   // body 0: extrapolated start
+          const long long lb = g_mf_launches;
+          e = cap_begin(caps[2], fb[br]);
+          if (e == cudaSuccess) e = cap_end(caps[2], first_pass(br == 1, caps[2]));
+          (br == 0 ? step_kernels_ex : step_kernels) = base + (int)(g_mf_launches - lb);
+        }
+      }
       cudaGraphConditionalHandle h_newton;
       if (e == cudaSuccess) e = cap_handle(caps[1], &h_newton);
       if (e == cudaSuccess) e = capture_iteration(c, caps, 1, true, mask, max_cg, h_newton);
@@ -968,7 +994,7 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
         e = cap_begin(caps[2], B2);
         if (e == cudaSuccess) e = cap_end(caps[2], capture_iteration(c, caps, 2, false, mask, max_cg, h_newton));
       }
-      if (e == cudaSuccess) e = mf_launch_step_end(hs, sc, t, h_step, step_kernels, caps[1]);
+      if (e == cudaSuccess) e = mf_launch_step_end(hs, sc, t, h_step, step_kernels, step_kernels_ex, caps[1]);
       e = cap_end(caps[1], e);
     }
   }
@@ -1034,6 +1060,13 @@ cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target,
   hh->kappa = c->kappa;
   hh->first_ratio = c->first_ratio;
   hh->ratio = INFINITY;
+  hh->extrap = c->predictor == MF_PRED_EXTRAPOLATE ? 1 : 0;
+  hh->nprev = c->keep.nprev;
+  memcpy(hh->t1, c->keep.t1, sizeof(hh->t1));
+  memcpy(hh->t2, c->keep.t2, sizeof(hh->t2));
+  memcpy(hh->fmean1, c->keep.fmean1, sizeof(hh->fmean1));
+  memcpy(hh->fmean2, c->keep.fmean2, sizeof(hh->fmean2));
+  memcpy(hh->mprev, c->keep.mprev, sizeof(hh->mprev));
   StepIn* in = pin_in(c);
   for (int k = k0; k < k1; ++k) {
     StepIn& r = in[k - k0];
@@ -1064,6 +1097,8 @@ int finish_history(mf_ctx* c, int k0, int k1, double* Fbar_out, double* Pbar_out
     if (iters_out) { iters_out[2 * (k0 + k)] = out[k].newton; iters_out[2 * (k0 + k) + 1] = out[k].cg; }
   }
   c->first_ratio = hs.first_ratio;
+  c->keep = hs;
+  if (hs.status) c->keep.nprev = 0;
   c->have_K = false;
   c->have_H = false;
   g_mf_launches += hs.launches;
@@ -1143,6 +1178,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->N = (long long)nx * ny * nz;
   c->prec = precision;
   c->serial = ++g_ctx_serial;
+  memset(&c->keep, 0, sizeof(c->keep));
   c->v2 = mf_v2_supported(nx, ny, nz) ? 1 : 0;
   c->xy_split = big_plane ? 1 : 0;
   c->st = (cudaStream_t)stream;
@@ -1185,6 +1221,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->ohist = take(hist_state_bytes() + (size_t)kHistSteps * sizeof(StepOut));
   c->othout = c->ohist + hist_state_bytes();
   c->othin = take((size_t)kHistSteps * sizeof(StepIn));
+  c->oFprev = take(9 * N * sizeof(double));
   c->ores = take(9 * sizeof(double));
   c->oxpos = take(nx * sizeof(int));
   c->oxk = take(nx * sizeof(int));
@@ -1364,6 +1401,7 @@ int mf_set_F(mf_ctx* c, const double* F_host) {
   if (!c) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
+  c->keep.nprev = 0;   // the extrapolating predictor starts over
   const long long N = c->N;
   double* F = c->at<double>(c->oF);
   cudaError_t e;
@@ -1393,6 +1431,7 @@ int mf_load_F(mf_ctx* c, const double* F_dev) {
   if (!c || !F_dev) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
+  c->keep.nprev = 0;   // the extrapolating predictor starts over
   const char* p = (const char*)F_dev;
   if (p + 9 * c->N * sizeof(double) > c->ws && p < c->ws + c->ws_need) return MF_INVALID_ARG;
   cudaError_t e = cudaMemcpyAsync(c->ws + c->oF, F_dev, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1792,6 +1831,13 @@ int mf_set_projection_arith(mf_ctx* c, int arith) {
   if (!c || (arith != MF_PROJ_FP32 && arith != MF_PROJ_OUTER && arith != MF_PROJ_AUTO)) return MF_INVALID_ARG;
   if (arith != MF_PROJ_FP32 && c->prec != MF_FP32_INNER) return MF_INVALID_ARG;
   c->proj_arith = arith;
+  return MF_OK;
+}
+
+int mf_set_predictor(mf_ctx* c, int kind) {
+  if (!c || (kind != MF_PRED_UNIFORM && kind != MF_PRED_EXTRAPOLATE)) return MF_INVALID_ARG;
+  if (c->predictor != kind) free_cg_graph(c);   // the captured histories hold the predictor's passes
+  c->predictor = kind;
   return MF_OK;
 }
 

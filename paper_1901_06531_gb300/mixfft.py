@@ -22,6 +22,7 @@ MF_FP64, MF_FP32_INNER = 0, 1
 MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
 MF_OUTER_DOUBLE_WORD, MF_OUTER_FP64 = 0, 1
 MF_PROJ_FP32, MF_PROJ_OUTER, MF_PROJ_AUTO = 0, 1, 2
+MF_PRED_UNIFORM, MF_PRED_EXTRAPOLATE = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
@@ -61,6 +62,8 @@ _lib.mf_sync.argtypes = [_vp]
 _lib.mf_autotune.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_set_inexact_newton.argtypes = [_vp, _i]
+_lib.mf_set_predictor.argtypes = [_vp, _i]
+_lib.mf_probe_fma.argtypes = [_i, _vp]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
 _lib.mf_set_projection_arith.argtypes = [_vp, _i]
@@ -79,8 +82,15 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
             "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_projection_arith",
-            "mf_set_inexact_newton", "mf_selftest_wait_timeout", "mf_last_cuda_error",
+            "mf_set_inexact_newton", "mf_set_predictor", "mf_probe_fma", "mf_selftest_wait_timeout", "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
+
+
+def probe_fma(precision):
+    """mf_probe_fma: measured FMA throughput of the current device, TFLOP/s."""
+    out = np.zeros(1)
+    _check("mf_probe_fma", _lib.mf_probe_fma(precision, _ptr(out)))
+    return float(out[0])
 
 
 def kernel_launches():
@@ -339,6 +349,10 @@ class Context:
     def set_outer_arith(self, arith):
         """mf_set_outer_arith: MF_OUTER_DOUBLE_WORD or MF_OUTER_FP64."""
         _check("mf_set_outer_arith", _lib.mf_set_outer_arith(self.h, arith))
+
+    def set_predictor(self, kind):
+        """mf_set_predictor: MF_PRED_UNIFORM (default) or MF_PRED_EXTRAPOLATE."""
+        _check("mf_set_predictor", _lib.mf_set_predictor(self.h, int(kind)))
 
     def set_inexact_newton(self, on):
         """mf_set_inexact_newton: the FP32-inner forcing sequence for the CG

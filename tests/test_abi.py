@@ -84,7 +84,7 @@ def test_option_setters_validate_without_gpu(lib):
     lib.mf_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     for name in ("mf_set_projection_arith", "mf_set_xy_persistent", "mf_set_xy_split", "mf_set_outer_arith",
-                 "mf_set_inexact_newton"):
+                 "mf_set_inexact_newton", "mf_set_predictor"):
         getattr(lib, name).argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.mf_destroy.argtypes = [ctypes.c_void_p]
     assert lib.mf_create(ctypes.byref(h), 16, 16, 16, mixfft.MF_FP64, None) == 0
@@ -95,6 +95,9 @@ def test_option_setters_validate_without_gpu(lib):
     assert lib.mf_set_inexact_newton(h, 1) == mixfft.MF_OK
     assert lib.mf_set_inexact_newton(h, 0) == mixfft.MF_OK
     assert lib.mf_set_inexact_newton(h, 2) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_predictor(h, mixfft.MF_PRED_EXTRAPOLATE) == mixfft.MF_OK
+    assert lib.mf_set_predictor(h, mixfft.MF_PRED_UNIFORM) == mixfft.MF_OK
+    assert lib.mf_set_predictor(h, 2) == mixfft.MF_INVALID_ARG
     lib.mf_destroy(h)
     assert lib.mf_create(ctypes.byref(h), 64, 64, 32, mixfft.MF_FP32_INNER, None) == 0
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_OUTER) == mixfft.MF_OK

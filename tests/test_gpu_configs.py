@@ -224,3 +224,52 @@ def test_fp32_inner_radix3_cells_in_one_batch_against_oracle():
         s = g["samples"][str(k)]
         idx = np.asarray(s["index"])
         assert rel(F.reshape(9, -1)[:, idx], np.asarray(s["F"]).T) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adjoint128_against_oracle(prec):
+    """The adjoint workload at 128^3 (two neo-Hookean phases, RSA spheres
+    r = 10 at 20 %, contrast 10, lognormal voxel scale sigma 0.3; one step
+    P11 = 0.05 with the rotation fixed): J = <F>_11, dJ/d(mu, lam) per phase
+    and dJ/ds_v at the sampled voxels against the oracle's adjoint gradient.
+    FP64 (forward and adjoint CG to 1e-12): 1e-8 relative; FP32 inner (the
+    adjoint solve in FP32 to cg_rel 1e-5): 1e-4, the stated accuracy of an
+    FP32 adjoint solve."""
+    import torch
+    mf = lib()
+    g = golden("c5_adjoint128")
+    n = 128
+    shape = (n, n, n)
+    ph, _ = inputs.rsa_spheres(shape, 10.0, 0.2, 1005)
+    sc = inputs.lognormal_scale(shape, 0.3, 1006)
+    params = np.array([[1.0, 2.0], [10.0, 20.0]])
+    mask = np.asarray(g["mask"], dtype=np.uint8)
+    target = np.asarray(g["target"])
+    ctx = mf.Context(n, n, n, prec)
+    ctx.set_material(mf.MF_NEOHOOKE, params, ph, scale=sc)
+    if prec == mf.MF_FP64:
+        o = ctx.solve(mask, target, 1e-10, 1e-12, max_cg=20000)
+        akw = dict(tol_cg=1e-12, cg_rel=0.0, max_cg=20000)
+        tol = 1e-8
+    else:
+        o = ctx.solve(mask, target, TOL_NEWTON, TOL_CG, CG_REL, max_cg=20000)
+        akw = dict(tol_cg=1e-30, cg_rel=1e-5, max_cg=20000)
+        tol = 1e-4
+    assert rel(o["Fbar"][0], np.asarray(g["Fbar"][0])) < 1e-9
+    ds = torch.zeros(ctx.N, dtype=torch.float64, device=ctx.device)
+    a = g["adjoint"]
+    J, grad, its = ctx.adjoint(mask[0], np.asarray(a["wF"]), np.asarray(a["wP"]), dscale=ds, **akw)
+    idx = np.asarray(g["samples"]["1"]["index"])
+    d = ds.cpu().numpy()
+    errs = {"J": abs(J - a["J"]) / max(1.0, abs(a["J"])),
+            "dJ_dmu_lam": rel(grad, np.asarray(a["dJ_dmu_lam"])),
+            "dJ_ds_sample": float(np.max(np.abs(d[idx] - np.asarray(a["dJ_dscale_sample"])))
+                                  / a["dJ_dscale_absmax"]),
+            "dJ_ds_sum": abs(float(d.sum()) - a["dJ_dscale_sum"]) / abs(a["dJ_dscale_sum"])}
+    print("adjoint128", prec, its, errs)
+    assert errs["J"] < 1e-9
+    assert errs["dJ_dmu_lam"] < tol
+    assert errs["dJ_ds_sample"] < tol
+    assert errs["dJ_ds_sum"] < tol
+    del ctx, ds
+    torch.cuda.empty_cache()

@@ -301,3 +301,60 @@ def test_device_wait_timeout_is_reported():
     mask, target = inputs.history_uniaxial_stress_ramp(1, 0.02)
     out = ctx.solve(mask, target, 1e-8, 1e-10)
     assert out["newton"][0] >= 1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_extrapolating_predictor_reaches_the_oracle(prec):
+    """mf_set_predictor(MF_PRED_EXTRAPOLATE) on a cyclic stress history (a
+    ramp, two reversals): the converged averages and fields are the oracle's
+    (uniform predictor) to the precision's tolerance, with no more Newton or
+    CG iterations in total than the uniform predictor, and fewer Newton
+    iterations on the steps along a ramp."""
+    mf = lib()
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 41)
+    om = omat.Material(g, omat.SVK_CUBIC, params, R)
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(12, 0.2))
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    outs = {}
+    for pred in (mf.MF_PRED_UNIFORM, mf.MF_PRED_EXTRAPOLATE):
+        ctx = mf.Context(n, n, n, prec)
+        ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+        ctx.set_predictor(pred)
+        out = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+        F, _ = ctx.get_fields()
+        tol_mean = 1e-10 if prec == mf.MF_FP64 else 1e-9
+        assert rel(out["Fbar"], ref["Fbar"]) < tol_mean
+        assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) / 168.0 < tol_mean
+        assert rel(F, ref["F"]) < 1e-8
+        outs[pred] = out
+    u, x = outs[mf.MF_PRED_UNIFORM], outs[mf.MF_PRED_EXTRAPOLATE]
+    print("predictor", prec, u["newton"].tolist(), x["newton"].tolist(), u["cg"].sum(), x["cg"].sum())
+    assert x["newton"].sum() < u["newton"].sum()
+    assert x["cg"].sum() <= u["cg"].sum()
+
+
+def test_extrapolating_predictor_across_calls():
+    """The predictor's two converged steps carry over between mf_solve calls:
+    a history solved one step per call gives the same iterations and the
+    same result, to rounding (a launch recomputes <F> from the field, in
+    another summation order than the constitutive pass), as the same history
+    in one call."""
+    mf = lib()
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 41)
+    mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(8, 0.2))
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+    one = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+    F1, _ = ctx.get_fields()
+    ctx.set_F(None)
+    for k in range(mask.shape[0]):
+        o = ctx.solve(mask[k:k + 1], target[k:k + 1], 1e-8, 1e-10, cg_rel=1e-4)
+        assert rel(o["Fbar"][0], one["Fbar"][k]) < 1e-14
+        np.testing.assert_array_equal(o["newton"][0], one["newton"][k])
+    F2, _ = ctx.get_fields()
+    # the FP32 inner solves carry the last-bit differences of their inputs
+    # into the fields at FP32-solve level (measured 8e-13)
+    assert rel(F2, F1) < 1e-10
