@@ -152,32 +152,36 @@ def poly128(mf, prec):
     return ctx
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_spheres64_mixed_control_against_oracle(prec):
+@pytest.mark.parametrize("prec,pred", [(0, 0), (1, 0), (1, 1)])
+def test_spheres64_mixed_control_against_oracle(prec, pred):
     """64^3 random spheres (r = 4, 25 %), neo-Hookean contrast 10, F11 -> 1.05
     in 10 steps with the other eight components stress free: every step
-    against the oracle, FP64 and FP32 inner / FP64 outer."""
+    against the oracle, FP64 and FP32 inner / FP64 outer, the latter also with
+    the extrapolating predictor of the bench."""
     mf = lib()
     g = golden("c2_spheres64")
     ctx = spheres64(mf, prec)
+    ctx.set_predictor(pred)
     tol_mean, tol_field = (1e-10, 1e-8) if prec == mf.MF_FP64 else (1e-9, 1e-8)
     errs = run_steps(mf, ctx, g, tol_mean, tol_field, kappa=10.0, rotation_free=True)
-    print("spheres64", prec, errs)
+    print("spheres64", prec, pred, errs)
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_polycrystal128_cyclic_stress_against_oracle(prec):
+@pytest.mark.parametrize("prec,pred", [(1, 1), (1, 0), (0, 0)])
+def test_polycrystal128_cyclic_stress_against_oracle(prec, pred):
     """The bench's workload (128^3 polycrystal, cyclic P11 with the rotation
     fixed), in the bench's launch configuration (FP32 inner, double-word
-    outer level, autotuned kernels) and in plain FP64: the load steps the
-    golden file holds, against the oracle."""
+    outer level, extrapolating predictor, autotuned kernels), with the
+    uniform predictor, and in plain FP64: the load steps the golden file
+    holds, against the oracle."""
     import torch
     mf = lib()
     g = golden("c3_poly128")
     ctx = poly128(mf, prec)
+    ctx.set_predictor(pred)
     tol_mean, tol_field = (1e-10, 1e-8) if prec == mf.MF_FP64 else (1e-9, 1e-8)
     errs = run_steps(mf, ctx, g, tol_mean, tol_field, kappa=168.0, rotation_free=False)
-    print("poly128", prec, g["steps_done"], errs)
+    print("poly128", prec, pred, g["steps_done"], errs)
     del ctx
     torch.cuda.empty_cache()
 
