@@ -104,12 +104,15 @@ int mf_set_F(mf_ctx* ctx, const double* F_host);
  *   tol_newton: stop when max_v |dF_v| / |<F>| < tol_newton;
  *   tol_cg: CG stops when sqrt(sum_v |r_v|^2 / N) <= tol_cg (MF_FP64), or
  *           <= max(tol_cg, cg_rel * initial value) (MF_FP32_INNER);
- *   cg_rel: relative CG forcing term for MF_FP32_INNER (ignored for MF_FP64);
- *           the first Newton iteration of each step uses sqrt(cg_rel), and
+ *   cg_rel: relative CG forcing term for MF_FP32_INNER (and for MF_FP64 with
+ *           mf_set_inexact_newton); the first Newton iteration of a step
+ *           that starts from the uniform predictor uses sqrt(cg_rel), and
  *           its residual (and the P it transforms) is computed in FP32 (it
  *           is always followed by another iteration: a step never ends on
- *           it); an iteration whose predecessor's correction was below
- *           sqrt(tol_newton) (expected to be the last) uses sqrt(cg_rel) too;
+ *           it); a step that starts extrapolated (mf_set_predictor) takes
+ *           its first residual in the outer arithmetic and cg_rel; an
+ *           iteration whose predecessor's correction was below
+ *           sqrt(tol_newton) (expected to be the last) uses sqrt(cg_rel);
  *   Fbar_out, Pbar_out: host, nsteps*9 doubles or NULL: <F>, <P> per step;
  *   iters_out: host, nsteps*2 int32 or NULL: Newton iterations and total CG
  *              iterations per step.
@@ -238,6 +241,23 @@ int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, int graph, float
  * path of this library is bound by this rate, not by HBM: its roofline
  * fraction is taken against it. */
 int mf_probe_fma(int precision, double* tflops_out);
+
+/* Bounds checks of the debug build (the library compiled with MF_DEBUG, see
+ * the package's build script): the transform, tangent and pointwise kernels
+ * check every shared- and global-memory index against its buffer; an index
+ * outside is counted and recorded (source line, index, extent) and the
+ * access is redirected to element 0 of that buffer, so nothing faults.  This
+ * call synchronises the device, returns the number of failed checks since the
+ * last call in *count_out (the first one's line, index and extent in the
+ * other outputs, each may be NULL) and clears the records.  A release build
+ * sets *count_out to -1. */
+int mf_debug_report(long long* count_out, int* line_out, long long* index_out, long long* extent_out);
+
+/* Self-test of those checks (debug build only): one thread checks index 7
+ * against a 4-element device array; the failure is recorded (mf_debug_report
+ * then returns count 1, index 7, extent 4) and the write goes to element 0.
+ * A release build launches nothing and returns MF_INVALID_ARG. */
+int mf_debug_selftest(void);
 
 /* Number of kernel launches the library has issued in this process (all
  * contexts); differences around a region count its launches. */

@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_tangent(const T* __restrict__ pin,
   // the voxel is issued before any arithmetic)
   auto voxel = [&](long long v, auto first_tag) {
     constexpr bool FIRST = decltype(first_tag)::value;
+    v = MF_AT(v, N);   // every access below is c * N + v (c < 9) or t * N + v (t < 45)
     T po[9], rv[9], xv[9];
     float h[9];
     int ph = 0;

@@ -14,6 +14,41 @@
 
 #define MF_MAX_STAGES 10
 
+// Bounds checks of the debug build (compiled with -DMF_DEBUG; release builds
+// compile them away).  MF_AT(i, n) is i when 0 <= i < n; otherwise the
+// failure is counted, the first one (source line, index, extent) recorded,
+// and element 0 -- in bounds -- is used instead, so that the kernel runs to
+// its end and the host reads the record (mf_debug_report) rather than the
+// GPU faulting.  Every translation unit has its own record and registers a
+// reader and a reset for it with the library at load time.
+#ifdef MF_DEBUG
+struct MfDebugRecord {
+  unsigned long long count;
+  long long index, extent;
+  int line, pad;
+};
+void mf_debug_register(void (*read)(MfDebugRecord*), void (*clear)());
+static __device__ MfDebugRecord g_mf_debug;
+static void mf_debug_read_tu(MfDebugRecord* r) { cudaMemcpyFromSymbol(r, g_mf_debug, sizeof(*r)); }
+static void mf_debug_clear_tu() {
+  MfDebugRecord z = {0ull, 0, 0, 0, 0};
+  cudaMemcpyToSymbol(g_mf_debug, &z, sizeof(z));
+}
+static const bool g_mf_debug_registered = (mf_debug_register(mf_debug_read_tu, mf_debug_clear_tu), true);
+__device__ __forceinline__ long long mf_dbg_check(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return i;
+  if (atomicAdd(&g_mf_debug.count, 1ull) == 0ull) {
+    g_mf_debug.index = i;
+    g_mf_debug.extent = n;
+    g_mf_debug.line = line;
+  }
+  return 0;
+}
+#define MF_AT(i, n) mf_dbg_check((long long)(i), (long long)(n), __LINE__)
+#else
+#define MF_AT(i, n) (i)
+#endif
+
 // Programmatic dependent launch: a kernel launched with the programmatic
 // stream-serialization attribute may be scheduled as soon as the blocks of
 // its predecessor in the stream have exited, before that grid's completion
@@ -104,7 +139,7 @@ template <bool INV, typename C> struct Radix<3, INV, C> {
 // (strided transforms) or butterflies (contiguous transforms).
 template <typename C, int R, bool INV, bool SEQ_FAST>
 __device__ __forceinline__ void fft_stage(C* buf, int n, int L, int nseq, int nlo, int hs,
-                                          int ls, int es, const C* tw, int ntab) {
+                                          int ls, int es, const C* tw, int ntab, int ext) {
   const int m = L / R;
   const int nb = n / R;
   const int total = nb * nseq;
@@ -118,40 +153,41 @@ __device__ __forceinline__ void fft_stage(C* buf, int n, int L, int nseq, int nl
     const int step = m * es;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = buf[base + r * step];
+    for (int r = 0; r < R; ++r) v[r] = buf[MF_AT(base + r * step, ext)];
     if (!INV) {
       Radix<R, false, C>::run(v);
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[j0 * k * tstep]);
+      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[MF_AT(j0 * k * tstep, ntab)]);
     } else {
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[j0 * k * tstep]);
+      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[MF_AT(j0 * k * tstep, ntab)]);
       Radix<R, true, C>::run(v);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[base + r * step] = v[r];
+    for (int r = 0; r < R; ++r) buf[MF_AT(base + r * step, ext)] = v[r];
   }
 }
 
 template <typename C, bool INV, bool SEQ_FAST>
 __device__ __forceinline__ void fft_stage_dispatch(int R, C* buf, int n, int L, int nseq, int nlo,
-                                                   int hs, int ls, int es, const C* tw, int ntab) {
-  if (R == 4) fft_stage<C, 4, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab);
-  else if (R == 2) fft_stage<C, 2, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab);
-  else fft_stage<C, 3, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab);
+                                                   int hs, int ls, int es, const C* tw, int ntab, int ext) {
+  if (R == 4) fft_stage<C, 4, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab, ext);
+  else if (R == 2) fft_stage<C, 2, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab, ext);
+  else fft_stage<C, 3, INV, SEQ_FAST>(buf, n, L, nseq, nlo, hs, ls, es, tw, ntab, ext);
 }
 
 // Full transform of every sequence: DIF forward (INV = false) or its adjoint
 // DIT inverse (INV = true, unnormalised).  Ends with __syncthreads(); the
-// caller synchronises before the first stage.
+// caller synchronises before the first stage.  ext: elements of buf (the
+// debug build checks every index against it).
 template <typename C, bool INV, bool SEQ_FAST>
 __device__ __forceinline__ void fft_run(C* buf, const AxisPlan& pl, int nseq, int nlo, int hs,
-                                        int ls, int es, const C* tw, int ntab) {
+                                        int ls, int es, const C* tw, int ntab, int ext) {
   if (!INV) {
     int L = pl.n;
     for (int st = 0; st < pl.nst; ++st) {
       const int R = pl.rad[st];
-      fft_stage_dispatch<C, false, SEQ_FAST>(R, buf, pl.n, L, nseq, nlo, hs, ls, es, tw, ntab);
+      fft_stage_dispatch<C, false, SEQ_FAST>(R, buf, pl.n, L, nseq, nlo, hs, ls, es, tw, ntab, ext);
       L /= R;
       __syncthreads();
     }
@@ -161,7 +197,7 @@ __device__ __forceinline__ void fft_run(C* buf, const AxisPlan& pl, int nseq, in
     for (int st = 0; st < pl.nst; ++st) { Ls[st] = L; L /= pl.rad[st]; }
     for (int st = pl.nst - 1; st >= 0; --st) {
       fft_stage_dispatch<C, true, SEQ_FAST>(pl.rad[st], buf, pl.n, Ls[st], nseq, nlo, hs, ls, es,
-                                            tw, ntab);
+                                            tw, ntab, ext);
       __syncthreads();
     }
   }

@@ -177,12 +177,12 @@ __device__ __forceinline__ void stage_io(const C* __restrict__ tw, LD ld, ST st)
       Dft<R, false, C>::run(v);
       if (M > 1) {
 #pragma unroll
-        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[j0 * k * TSTEP]);
+        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[MF_AT(j0 * k * TSTEP, NTAB)]);
       }
     } else {
       if (M > 1) {
 #pragma unroll
-        for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[j0 * k * TSTEP]);
+        for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[MF_AT(j0 * k * TSTEP, NTAB)]);
       }
       Dft<R, true, C>::run(v);
     }
@@ -191,11 +191,19 @@ __device__ __forceinline__ void stage_io(const C* __restrict__ tw, LD ld, ST st)
   }
 }
 
+// Largest shared-memory index a stage over this layout touches, plus one:
+// the extent the debug build checks stage() accesses against.
+template <int N, int NSEQ, int SQ, int SQSTR, int SSTR, int ESTR>
+__host__ __device__ constexpr int layout_extent() {
+  return ((NSEQ - 1) / SQ) * SQSTR + ((NSEQ - 1) % SQ) * SSTR + (N - 1) * ESTR + 1;
+}
+
 template <typename C, int N, int NTAB, int S, bool INV, int NSEQ, int SQ, int SQSTR, int SSTR,
           int ESTR, bool SEQFAST>
 __device__ __forceinline__ void stage(C* __restrict__ buf, const C* __restrict__ tw) {
+  constexpr int EXT = layout_extent<N, NSEQ, SQ, SQSTR, SSTR, ESTR>();
   stage_io<C, N, NTAB, S, INV, NSEQ, SQ, SQSTR, SSTR, ESTR, SEQFAST>(
-      tw, [&](int, int i, int) { return buf[i]; }, [&](int, int i, int, C v) { buf[i] = v; });
+      tw, [&](int, int i, int) { return buf[MF_AT(i, EXT)]; }, [&](int, int i, int, C v) { buf[MF_AT(i, EXT)] = v; });
 }
 
 // Whole transform (all stages), with a barrier after each stage.  SEQFAST is
@@ -242,8 +250,9 @@ __device__ __forceinline__ void forward_out(C* buf, const C* tw, ST st) {
     __syncthreads();
     forward_out<C, N, NTAB, NSEQ, SQ, SQSTR, SSTR, ESTR, S + 1>(buf, tw, st);
   } else {
+    constexpr int EXT = layout_extent<N, NSEQ, SQ, SQSTR, SSTR, ESTR>();
     stage_io<C, N, NTAB, S, false, NSEQ, SQ, SQSTR, SSTR, ESTR, SF>(
-        tw, [&](int, int i, int) { return buf[i]; }, [&](int q, int, int e, C v) { st(q, e, v); });
+        tw, [&](int, int i, int) { return buf[MF_AT(i, EXT)]; }, [&](int q, int, int e, C v) { st(q, e, v); });
   }
 }
 
@@ -254,8 +263,9 @@ __device__ __forceinline__ void inverse_in(C* buf, const C* tw, LD ld) {
   constexpr int S = nst(N) - 1;
   constexpr int M = len(N, S) / rad(N, S);
   constexpr bool SF = !(ESTR == 1 && M >= 16);
+  constexpr int EXT = layout_extent<N, NSEQ, SQ, SQSTR, SSTR, ESTR>();
   stage_io<C, N, NTAB, S, true, NSEQ, SQ, SQSTR, SSTR, ESTR, SF>(
-      tw, [&](int q, int, int e) { return ld(q, e); }, [&](int, int i, int, C v) { buf[i] = v; });
+      tw, [&](int q, int, int e) { return ld(q, e); }, [&](int, int i, int, C v) { buf[MF_AT(i, EXT)] = v; });
   __syncthreads();
   if constexpr (S > 0) run_stages_inv<C, N, NTAB, NSEQ, SQ, SQSTR, SSTR, ESTR, S - 1>(buf, tw);
 }

@@ -190,6 +190,18 @@ Defl null_rotations(const double meanF[9], const uint8_t* mask, const double T[9
   return d;
 }
 
+#ifdef MF_DEBUG
+// Readers of the per-translation-unit bounds-check records of the debug build.
+struct DebugReader {
+  void (*read)(MfDebugRecord*);
+  void (*clear)();
+};
+std::vector<DebugReader>& debug_readers() {
+  static std::vector<DebugReader> v;
+  return v;
+}
+#endif
+
 // An instantiated load-history graph of a context, per control mask and CG cap.
 struct HistGraph {
   unsigned mask;
@@ -205,6 +217,12 @@ long long g_ctx_serial = 0;   // identifies contexts in the batched-graph cache
 constexpr size_t hist_state_bytes() { return (sizeof(HistState) + 15) & ~(size_t)15; }
 
 }  // namespace
+
+#ifdef MF_DEBUG
+void mf_debug_register(void (*read)(MfDebugRecord*), void (*clear)()) {
+  debug_readers().push_back(DebugReader{read, clear});
+}
+#endif
 
 struct mf_ctx {
   int nx, ny, nz;
@@ -1859,6 +1877,37 @@ int mf_set_outer_arith(mf_ctx* c, int arith) {
 }
 
 long long mf_kernel_launches(void) { return g_mf_launches; }
+
+int mf_debug_report(long long* count_out, int* line_out, long long* index_out, long long* extent_out) {
+  if (!count_out) return MF_INVALID_ARG;
+#ifdef MF_DEBUG
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  long long total = 0;
+  bool have = false;
+  for (const DebugReader& r : debug_readers()) {
+    MfDebugRecord rec;
+    memset(&rec, 0, sizeof(rec));
+    r.read(&rec);
+    total += (long long)rec.count;
+    if (rec.count && !have) {
+      have = true;
+      if (line_out) *line_out = rec.line;
+      if (index_out) *index_out = rec.index;
+      if (extent_out) *extent_out = rec.extent;
+    }
+    r.clear();
+  }
+  *count_out = total;
+  return cuda_status(cudaGetLastError());
+#else
+  (void)line_out;
+  (void)index_out;
+  (void)extent_out;
+  *count_out = -1;
+  return MF_OK;
+#endif
+}
 
 int mf_sync(mf_ctx* c) {
   if (!c) return MF_INVALID_ARG;

@@ -75,3 +75,26 @@ extern "C" int mf_probe_fma(int precision, double* tflops_out) {
   *tflops_out = flops / (ms * 1e-3) / 1e12;
   return MF_OK;
 }
+
+// Self-test of the debug build's bounds checks: one thread evaluates a check
+// whose index (7) lies outside its 4-element array; the check records it and
+// redirects the write to element 0, inside the array.  Release builds have no
+// checks (the index would be used as is), so there the call launches nothing
+// and returns MF_INVALID_ARG.
+#ifdef MF_DEBUG
+namespace {
+__device__ int g_dbg_probe[4];
+__global__ void k_debug_selftest() { g_dbg_probe[MF_AT(7, 4)] = 1; }
+}  // namespace
+#endif
+
+extern "C" int mf_debug_selftest(void) {
+#ifdef MF_DEBUG
+  k_debug_selftest<<<1, 1>>>();
+  ++g_mf_launches;
+  const cudaError_t e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? MF_OK : MF_CUDA_ERROR;
+#else
+  return MF_INVALID_ARG;
+#endif
+}

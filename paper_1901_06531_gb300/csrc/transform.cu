@@ -53,21 +53,21 @@ __global__ void __launch_bounds__(512) k_xy_forward(const T* __restrict__ in, co
     const int q = idx / nx, j = idx - (idx / nx) * nx;
     const long long v0 = plane + (long long)q * nx + j;
     const long long v1 = v0 + (long long)hy * nx;
-    buf[idx] = cmake(in[c * N + v0], in[c * N + v1]);
+    buf[MF_AT(idx, P)] = cmake(in[MF_AT(c * N + v0, 9 * N)], in[MF_AT(c * N + v1, 9 * N)]);
   }
   __syncthreads();
 
   // x transform of the hy packed rows (contiguous sequences)
-  fft_run<C, false, false>(buf, a.px, hy, 1, nx, 0, 1, twx, nx);
+  fft_run<C, false, false>(buf, a.px, hy, 1, nx, 0, 1, twx, nx, P);
 
   // split the packed rows into the spectra of rows q and q+hy, and apply the
   // first (radix-2) stage of the y transform, which combines exactly those two
   const int hx = nx / 2;
   for (int idx = threadIdx.x; idx < hy * hx; idx += blockDim.x) {
     const int q = idx / hx, k = idx - (idx / hx) * hx;
-    const int sa = xpos[k];
-    const int sb = xpos[k == 0 ? hx : nx - k];
-    const C za = buf[q * nx + sa], zb = buf[q * nx + sb];
+    const int sa = xpos[MF_AT(k, nx)];
+    const int sb = xpos[MF_AT(k == 0 ? hx : nx - k, nx)];
+    const C za = buf[MF_AT(q * nx + sa, P)], zb = buf[MF_AT(q * nx + sb, P)];
     C xa, xb;
     if (k == 0) {
       xa = cmake(za.x, (T)0);
@@ -76,16 +76,16 @@ __global__ void __launch_bounds__(512) k_xy_forward(const T* __restrict__ in, co
       xa = cmake((T)0.5 * (za.x + zb.x), (T)0.5 * (za.y - zb.y));
       xb = cmake((T)0.5 * (za.y + zb.y), (T)-0.5 * (za.x - zb.x));
     }
-    buf[q * nx + sa] = cadd(xa, xb);
-    buf[q * nx + sb] = cmul(csub(xa, xb), twy[q]);
+    buf[MF_AT(q * nx + sa, P)] = cadd(xa, xb);
+    buf[MF_AT(q * nx + sb, P)] = cmul(csub(xa, xb), twy[MF_AT(q, ny)]);
   }
   __syncthreads();
 
   // remaining y stages: nx column sequences of length hy, stride nx
-  fft_run<C, false, true>(buf, a.pyh, nx, nx, 0, 1, nx, twy, ny);
+  fft_run<C, false, true>(buf, a.pyh, nx, nx, 0, 1, nx, twy, ny, P);
 
-  C* dst = spec + ((long long)c * a.nz + z) * P;
-  for (int idx = threadIdx.x; idx < P; idx += blockDim.x) dst[idx] = buf[idx];
+  const long long o = ((long long)c * a.nz + z) * P;
+  for (int idx = threadIdx.x; idx < P; idx += blockDim.x) spec[MF_AT(o + idx, 9LL * a.nz * P)] = buf[idx];
 }
 
 // ---------------------------------------------------------------- xy inverse
@@ -117,31 +117,31 @@ __global__ void __launch_bounds__(512) k_xy_inverse(const typename CT<T>::t* __r
   const int c = blockIdx.x % 9;
   const int z = blockIdx.x / 9;
   const long long N = a.N;
-  const C* src = spec + ((long long)c * a.nz + z) * P;
-  for (int idx = threadIdx.x; idx < P; idx += blockDim.x) buf[idx] = src[idx];
+  const long long o = ((long long)c * a.nz + z) * P;
+  for (int idx = threadIdx.x; idx < P; idx += blockDim.x) buf[MF_AT(idx, P)] = spec[MF_AT(o + idx, 9LL * a.nz * P)];
   __syncthreads();
 
-  fft_run<C, true, true>(buf, a.pyh, nx, nx, 0, 1, nx, twy, ny);
+  fft_run<C, true, true>(buf, a.pyh, nx, nx, 0, 1, nx, twy, ny, P);
 
   const int hx = nx / 2;
   for (int idx = threadIdx.x; idx < hy * hx; idx += blockDim.x) {
     const int q = idx / hx, k = idx - (idx / hx) * hx;
-    const int sa = xpos[k];
-    const int sb = xpos[k == 0 ? hx : nx - k];
-    const C y0 = buf[q * nx + sa];
-    const C t = cmulc(buf[q * nx + sb], twy[q]);
+    const int sa = xpos[MF_AT(k, nx)];
+    const int sb = xpos[MF_AT(k == 0 ? hx : nx - k, nx)];
+    const C y0 = buf[MF_AT(q * nx + sa, P)];
+    const C t = cmulc(buf[MF_AT(q * nx + sb, P)], twy[MF_AT(q, ny)]);
     const C xa = cadd(y0, t), xb = csub(y0, t);
     if (k == 0) {
-      buf[q * nx + sa] = cmake(xa.x, xb.x);
-      buf[q * nx + sb] = cmake((T)0, (T)0);
+      buf[MF_AT(q * nx + sa, P)] = cmake(xa.x, xb.x);
+      buf[MF_AT(q * nx + sb, P)] = cmake((T)0, (T)0);
     } else {
-      buf[q * nx + sa] = cmake(xa.x - xb.y, xa.y + xb.x);
-      buf[q * nx + sb] = cmake(xa.x + xb.y, xb.x - xa.y);
+      buf[MF_AT(q * nx + sa, P)] = cmake(xa.x - xb.y, xa.y + xb.x);
+      buf[MF_AT(q * nx + sb, P)] = cmake(xa.x + xb.y, xb.x - xa.y);
     }
   }
   __syncthreads();
 
-  fft_run<C, true, false>(buf, a.px, hy, 1, nx, 0, 1, twx, nx);
+  fft_run<C, true, false>(buf, a.px, hy, 1, nx, 0, 1, twx, nx, P);
 
   const long long plane = (long long)z * ny * nx;
   double acc = 0.0;
@@ -151,19 +151,20 @@ __global__ void __launch_bounds__(512) k_xy_inverse(const typename CT<T>::t* __r
     const int q = idx / nx, j = idx - (idx / nx) * nx;
     const long long v0 = plane + (long long)q * nx + j;
     const long long v1 = v0 + (long long)hy * nx;
-    const C v = buf[idx];
+    const C v = buf[MF_AT(idx, P)];
     const T o0 = v.x * oscale, o1 = v.y * oscale;
+    const long long i0 = MF_AT(c * N + v0, 9 * N), i1 = MF_AT(c * N + v1, 9 * N);
     if (DOT == 3) {
-      const T r0 = out[c * N + v0] - alpha * o0;
-      const T r1 = out[c * N + v1] - alpha * o1;
-      out[c * N + v0] = r0;
-      out[c * N + v1] = r1;
+      const T r0 = out[i0] - alpha * o0;
+      const T r1 = out[i1] - alpha * o1;
+      out[i0] = r0;
+      out[i1] = r1;
       acc += (double)r0 * (double)r0 + (double)r1 * (double)r1;
     } else {
-      out[c * N + v0] = o0;
-      out[c * N + v1] = o1;
+      out[i0] = o0;
+      out[i1] = o1;
     }
-    if (DOT == 1) acc += (double)o0 * (double)w[c * N + v0] + (double)o1 * (double)w[c * N + v1];
+    if (DOT == 1) acc += (double)o0 * (double)w[i0] + (double)o1 * (double)w[i1];
     if (DOT == 2) acc += (double)o0 * (double)o0 + (double)o1 * (double)o1;
   }
   if (DOT) {
@@ -200,11 +201,12 @@ __global__ void __launch_bounds__(512) k_zpass(typename CT<T>::t* __restrict__ s
     const int s = idx % S;
     const int cz = idx / S;          // c * nz + z
     const int col = col0 + s;
-    buf[idx] = (col < ncol) ? spec[(long long)cz * ncol + col] : cmake((T)0, (T)0);
+    buf[MF_AT(idx, tot)] =
+        (col < ncol) ? spec[MF_AT((long long)cz * ncol + col, 9LL * nz * ncol)] : cmake((T)0, (T)0);
   }
   __syncthreads();
 
-  fft_run<C, false, true>(buf, a.pz, 9 * S, S, nz * S, 1, S, twz, nz);
+  fft_run<C, false, true>(buf, a.pz, 9 * S, S, nz * S, 1, S, twz, nz, tot);
 
   const T scale = (T)a.scale;
   const int zstride = nz * S;
@@ -213,10 +215,10 @@ __global__ void __launch_bounds__(512) k_zpass(typename CT<T>::t* __restrict__ s
     const int col = col0 + s;
     if (col >= ncol) continue;
     const int qr = col / nx, slot = col - (col / nx) * nx;
-    const int kx = a.xk[slot];
-    const int ky = 2 * a.yk[qr] + a.xe[slot];
-    const int kz = zk[p];
-    C* e = buf + idx;
+    const int kx = a.xk[MF_AT(slot, nx)];
+    const int ky = 2 * a.yk[MF_AT(qr, ny / 2)] + a.xe[MF_AT(slot, nx)];
+    const int kz = zk[MF_AT(p, nz)];
+    C* e = buf + MF_AT(idx, tot - 8 * zstride);   // e[c * zstride], c < 9
     const bool nyq = (2 * ky == ny) || ((nz % 2 == 0) && (2 * kz == nz));
     if (nyq) {
 #pragma unroll
@@ -254,13 +256,13 @@ __global__ void __launch_bounds__(512) k_zpass(typename CT<T>::t* __restrict__ s
   }
   __syncthreads();
 
-  fft_run<C, true, true>(buf, a.pz, 9 * S, S, nz * S, 1, S, twz, nz);
+  fft_run<C, true, true>(buf, a.pz, 9 * S, S, nz * S, 1, S, twz, nz, tot);
 
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int s = idx % S;
     const int cz = idx / S;
     const int col = col0 + s;
-    if (col < ncol) spec[(long long)cz * ncol + col] = buf[idx];
+    if (col < ncol) spec[MF_AT((long long)cz * ncol + col, 9LL * nz * ncol)] = buf[MF_AT(idx, tot)];
   }
 }
 

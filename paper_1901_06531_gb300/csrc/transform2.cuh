@@ -140,8 +140,8 @@ __device__ __forceinline__ void x_last_split(typename CT<T>::t* buf, const typen
       for (int r = 0; r < RB; ++r) {
         const int rp = RB - 1 - r;
         const int k = b0 + RA * r, km = b1 + RA * rp;
-        row[b0 * RB + r] = split_one<T>(u[r], w[rp], twx[k]);
-        row[b1 * RB + rp] = split_one<T>(w[rp], u[r], twx[km]);
+        row[MF_AT(b0 * RB + r, NX / 2)] = split_one<T>(u[r], w[rp], twx[k]);
+        row[MF_AT(b1 * RB + rp, NX / 2)] = split_one<T>(w[rp], u[r], twx[km]);
       }
     } else {
       // b0 = b1 (b0 = 0 or RA/2): the pairs lie within u; the partner index
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   // row y, sample j (the real values 2j, 2j+1 as one complex sample)
   auto gload = [&](int y, int j) {
     C v;
-    io_in(v, src[(long long)y * H + j]);
+    io_in(v, src[MF_AT((long long)y * H + j, NY * H)]);
     return v;
   };
   if constexpr (sizeof(C) == 8) {
@@ -253,9 +253,9 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
       // first x stage straight from global memory (consecutive threads take
       // consecutive butterflies of a row: 64-byte row segments per warp access)
       fft2::stage_io<C, H, NX, 0, false, NY, 1, PX, 0, 1, false>(
-          twx, [&](int q, int, int e) { return gload(q, e); }, [&](int, int i, int, C v) { buf[i] = v; });
+          twx, [&](int q, int, int e) { return gload(q, e); }, [&](int, int i, int, C v) { buf[MF_AT(i, NY * PX)] = v; });
       __syncthreads();
-      x_last_split<T, NX, TPB>(buf, twx, [&](int y, int pos) { return buf[y * PX + pos]; });
+      x_last_split<T, NX, TPB>(buf, twx, [&](int y, int pos) { return buf[MF_AT(y * PX + pos, NY * PX)]; });
     } else {
       x_last_split<T, NX, TPB>(buf, twx, gload);
     }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   // y: H columns of NY samples, stride PX; the last stage stores the
   // spectrum rows (consecutive threads take consecutive columns)
   C* dst = spec + ((long long)c * nz + z) * NY * H;
-  fft2::forward_out<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e, C v) { dst[e * H + q] = v; });
+  fft2::forward_out<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e, C v) { dst[MF_AT(e * H + q, NY * H)] = v; });
 }
 
 // ------------------------------------------------------- persistent forward
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   const C* src = spec + ((long long)c * nz + z) * NY * H;
   __syncthreads();   // tables
   // y: the first inverse stage reads the spectrum rows from global memory
-  fft2::inverse_in<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e) { return src[e * H + q]; });
+  fft2::inverse_in<C, NY, NY, H, 1, 1, 0, PX>(buf, twy, [&](int q, int e) { return src[MF_AT(e * H + q, NY * H)]; });
   if constexpr (sizeof(C) == 8) {
     // merge of each row's spectrum, fused with the first inverse x stage
     x_merge_first<T, NX, TPB>(buf, twx);
@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   if (MODE == 3) alpha = (T)sc->alpha;
   // the output of sample (row y, j): y = G*(.) stored, or r -= alpha y
   auto emit = [&](long long idx, C v) {
+    idx = MF_AT(idx, NY * H);
     if constexpr (MODE == 3) {
       C r = dst[idx];
       r.x -= alpha * v.x;
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   if constexpr (kDirect) {
     // consecutive threads take consecutive butterflies of a row
     fft2::stage_io<C, H, NX, 0, true, NY, 1, PX, 0, 1, false>(
-        twx, [&](int, int i, int) { return buf[i]; },
+        twx, [&](int, int i, int) { return buf[MF_AT(i, NY * PX)]; },
         [&](int q, int, int e, C v) { emit((long long)q * H + e, v); });
   } else {
     if constexpr (sizeof(C) == 8 && RowPlan<H>::NST == 2) {
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < NY * H; idx += TPB) {
       const int y = idx / H, j = idx - (idx / H) * H;
-      emit(idx, buf[y * PX + j]);
+      emit(idx, buf[MF_AT(y * PX + j, NY * PX)]);
     }
   }
   if (sizeof(TI) == 4) acc = (double)fs + (double)fc;
@@ -577,13 +578,17 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   const int g = blockIdx.x / ntile;                 // row group: components 3g .. 3g+2
   const int col0 = (blockIdx.x - g * ntile) * S;
   C* gsp = spec + (long long)(3 * g) * NZ * ncol + col0;
-  // global element of (sequence q = cl*S + s, position z)
-  auto gidx = [&](int q, int z) { return ((long long)(q / S) * NZ + z) * ncol + (q % S); };
+  // global element of (sequence q = cl*S + s, position z), relative to gsp
+  // (the debug build checks it against the spectrum's 9 NZ ncol elements)
+  const long long goff = (long long)(3 * g) * NZ * ncol + col0;
+  auto gidx = [&](int q, int z) {
+    return MF_AT(goff + ((long long)(q / S) * NZ + z) * ncol + (q % S), 9LL * NZ * ncol) - goff;
+  };
   __syncthreads();
   if constexpr (NST > 1) {
     // first forward stage: global -> registers -> shared
     fft2::stage_io<C, NZ, NZ, 0, false, 3 * S, S, CP, 1, ZS, true>(
-        twz, [&](int q, int, int z) { return gsp[gidx(q, z)]; }, [&](int, int i, int, C v) { buf[i] = v; });
+        twz, [&](int q, int, int z) { return gsp[gidx(q, z)]; }, [&](int, int i, int, C v) { buf[MF_AT(i, 3 * CP)] = v; });
     __syncthreads();
     if constexpr (NST > 2) {
       fft2::stage<C, NZ, NZ, 1, false, 3 * S, S, CP, 1, ZS, true>(buf, twz);
@@ -647,7 +652,7 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int z = blk * RL + r;
-          v[cl][r] = (NST > 1) ? buf[cl * CP + z * ZS + s] : gsp[gidx(cl * S + s, z)];
+          v[cl][r] = (NST > 1) ? buf[MF_AT(cl * CP + z * ZS + s, 3 * CP)] : gsp[gidx(cl * S + s, z)];
         }
 #pragma unroll
       for (int cl = 0; cl < 3; ++cl) fft2::Dft<RL, false, C>::run(v[cl]);
@@ -660,7 +665,7 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int z = blk * RL + r;
-          if (NST > 1) buf[cl * CP + z * ZS + s] = v[cl][r];
+          if (NST > 1) buf[MF_AT(cl * CP + z * ZS + s, 3 * CP)] = v[cl][r];
           else gsp[gidx(cl * S + s, z)] = v[cl][r];
         }
     }
@@ -700,7 +705,7 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
     }
     // last inverse stage: shared -> registers -> global
     fft2::stage_io<C, NZ, NZ, 0, true, 3 * S, S, CP, 1, ZS, true>(
-        twz, [&](int, int i, int) { return buf[i]; }, [&](int q, int, int z, C v) { gsp[gidx(q, z)] = v; });
+        twz, [&](int, int i, int) { return buf[MF_AT(i, 3 * CP)]; }, [&](int q, int, int z, C v) { gsp[gidx(q, z)] = v; });
   }
 }
 

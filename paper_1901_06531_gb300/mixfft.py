@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmixfft.so")
+# MF_LIBRARY=debug selects the bounds-checking build (build.build(debug=True))
+LIB_PATH = os.path.join(_HERE, "libmixfft_debug.so" if os.environ.get("MF_LIBRARY") == "debug"
+                        else "libmixfft.so")
 
 MF_OK, MF_INVALID_ARG, MF_NOT_CONVERGED, MF_CG_BREAKDOWN = 0, 1, 2, 3
 MF_NONPOSITIVE_J, MF_CUDA_ERROR, MF_DEVICE_TIMEOUT, MF_NO_WORKSPACE = 4, 5, 6, 7
@@ -64,6 +66,8 @@ _lib.mf_set_outer_arith.argtypes = [_vp, _i]
 _lib.mf_set_inexact_newton.argtypes = [_vp, _i]
 _lib.mf_set_predictor.argtypes = [_vp, _i]
 _lib.mf_probe_fma.argtypes = [_i, _vp]
+_lib.mf_debug_report.argtypes = [_vp, _vp, _vp, _vp]
+_lib.mf_debug_selftest.argtypes = []
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
 _lib.mf_set_projection_arith.argtypes = [_vp, _i]
@@ -82,7 +86,7 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
             "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_projection_arith",
-            "mf_set_inexact_newton", "mf_set_predictor", "mf_probe_fma", "mf_selftest_wait_timeout", "mf_last_cuda_error",
+            "mf_set_inexact_newton", "mf_set_predictor", "mf_probe_fma", "mf_debug_report", "mf_debug_selftest", "mf_selftest_wait_timeout", "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
 
 
@@ -91,6 +95,24 @@ def probe_fma(precision):
     out = np.zeros(1)
     _check("mf_probe_fma", _lib.mf_probe_fma(precision, _ptr(out)))
     return float(out[0])
+
+
+def debug_report():
+    """mf_debug_report: (failed bounds checks since the last call, first
+    failure's source line, index, extent); count -1 in a release build."""
+    cnt = ctypes.c_longlong(0)
+    line = ctypes.c_int(0)
+    idx = ctypes.c_longlong(0)
+    ext = ctypes.c_longlong(0)
+    _check("mf_debug_report", _lib.mf_debug_report(ctypes.byref(cnt), ctypes.byref(line), ctypes.byref(idx),
+                                                   ctypes.byref(ext)))
+    return cnt.value, line.value, idx.value, ext.value
+
+
+def debug_selftest():
+    """mf_debug_selftest: status (MF_OK in a debug build, MF_INVALID_ARG in a
+    release build)."""
+    return int(_lib.mf_debug_selftest())
 
 
 def kernel_launches():
