@@ -243,8 +243,9 @@ int mf_time_kernels(mf_ctx* ctx, const uint8_t* mask, int reps, int graph, float
 int mf_probe_fma(int precision, double* tflops_out);
 
 /* Bounds checks of the debug build (the library compiled with MF_DEBUG, see
- * the package's build script): the transform, tangent and pointwise kernels
- * check every shared- and global-memory index against its buffer; an index
+ * the package's build script): the generic and fixed-size transform kernels
+ * and the tangent pass check every shared- and global-memory index against
+ * its buffer (the split 256^2-plane kernels are not instrumented); an index
  * outside is counted and recorded (source line, index, extent) and the
  * access is redirected to element 0 of that buffer, so nothing faults.  This
  * call synchronises the device, returns the number of failed checks since the

@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmixfft.so")
-# debug build: every shared- and global-memory index of the transform,
-# tangent and pointwise kernels checked (MF_DEBUG, see common.cuh)
+# debug build: every shared- and global-memory index of the generic and
+# fixed-size transform kernels and the tangent pass checked (MF_DEBUG, see
+# common.cuh)
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libmixfft_debug.so")
 SOURCES = ["transform.cu", "transform2_f32.cu", "transform2_f64.cu", "pointwise.cu", "cg.cu", "history.cu",

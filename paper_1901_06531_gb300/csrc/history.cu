@@ -270,10 +270,20 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
   }
   hs->defl.m = 0;
   if (hs->f32) null_rotations_dev(sc->meanF, hs->mask, sc->T, sc->S, hs->kappa, 1e-6, &hs->defl);
-  // the first iteration of an extrapolated step is solved to cg_rel: it is
-  // expected to be followed by one more (the test below) only
+  // the first iteration of an extrapolated step is expected to be followed
+  // by one more only: its solve need only leave the next correction below
+  // the Newton tolerance.  Its correction is about the larger of the last two
+  // steps' first ones (r; two, because the step across a load reversal
+  // starts exact and its first correction says nothing about the next), and
+  // the next about eta r, so eta = 0.1 tol_newton / r, kept within
+  // [cg_rel, sqrt(cg_rel)] (the choice of forcing terms of inexact Newton
+  // methods from the expected convergence).
   const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
-  hs->cg_rel_cur = hs->forcing ? (loose ? sqrt(hs->cg_rel) : hs->cg_rel) : 0.0;
+  double eta = loose ? sqrt(hs->cg_rel) : hs->cg_rel;
+  const double r = fmax(hs->first_ratio, hs->first_ratio2);
+  if (first && hs->extrapolated && r > 0.0 && isfinite(r))
+    eta = fmin(sqrt(hs->cg_rel), fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
+  hs->cg_rel_cur = hs->forcing ? eta : 0.0;
   cudaGraphSetConditional(h_go, 1u);
 }
 
@@ -319,7 +329,10 @@ __global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHa
   const double ratio = sqrt(sc->dF2max) / sqrt(fn);
   hs->ratio = ratio;
   hs->nn += 1;
-  if (hs->nn == 1) hs->first_ratio = ratio;
+  if (hs->nn == 1) {
+    hs->first_ratio2 = hs->first_ratio;
+    hs->first_ratio = ratio;
+  }
   if (st && !hs->status) hs->status = st;
   const int last = (ratio < hs->tol_newton && !hs->res32) ? 1 : 0;
   const int kind = last ? 0 : 1;

@@ -217,6 +217,7 @@ struct HistState {
   int proj_arith;          // MF_PROJ_* of the FP32 corrections
   double tol_newton, tol_cg, cg_rel, kappa;
   double first_ratio;      // size of the last step's first correction (persists across launches)
+  double first_ratio2;     // the same of the step before (persists across launches)
   int extrap;              // the predictor extrapolates from the last two converged steps
   // persists across launches (the host keeps it between calls): the last two
   // converged steps behind F, for the extrapolating predictor

@@ -1077,6 +1077,7 @@ cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target,
   hh->cg_rel = cg_rel;
   hh->kappa = c->kappa;
   hh->first_ratio = c->first_ratio;
+  hh->first_ratio2 = c->keep.first_ratio2;
   hh->ratio = INFINITY;
   hh->extrap = c->predictor == MF_PRED_EXTRAPOLATE ? 1 : 0;
   hh->nprev = c->keep.nprev;
@@ -1419,6 +1420,7 @@ int mf_set_F(mf_ctx* c, const double* F_host) {
   if (!c) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
+  c->keep.first_ratio2 = INFINITY;
   c->keep.nprev = 0;   // the extrapolating predictor starts over
   const long long N = c->N;
   double* F = c->at<double>(c->oF);
@@ -1449,6 +1451,7 @@ int mf_load_F(mf_ctx* c, const double* F_dev) {
   if (!c || !F_dev) return MF_INVALID_ARG;
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
+  c->keep.first_ratio2 = INFINITY;
   c->keep.nprev = 0;   // the extrapolating predictor starts over
   const char* p = (const char*)F_dev;
   if (p + 9 * c->N * sizeof(double) > c->ws && p < c->ws + c->ws_need) return MF_INVALID_ARG;

@@ -336,10 +336,12 @@ def test_extrapolating_predictor_reaches_the_oracle(prec):
 
 def test_extrapolating_predictor_across_calls():
     """The predictor's two converged steps carry over between mf_solve calls:
-    a history solved one step per call gives the same iterations and the
-    same result, to rounding (a launch recomputes <F> from the field, in
-    another summation order than the constitutive pass), as the same history
-    in one call."""
+    a history solved one step per call takes the same Newton iterations and
+    reaches the same states as the same history in one call.  Not bit for
+    bit: a launch recomputes <F> from the field (another summation order than
+    the constitutive pass), and the forcing of a step's first inner solve
+    follows the size of earlier corrections; the converged states agree to
+    their accuracy (about the last correction times its forcing, 1e-11)."""
     mf = lib()
     n = 16
     g, params, R = polycrystal((n, n, n), 12, 41)
@@ -352,7 +354,7 @@ def test_extrapolating_predictor_across_calls():
     ctx.set_F(None)
     for k in range(mask.shape[0]):
         o = ctx.solve(mask[k:k + 1], target[k:k + 1], 1e-8, 1e-10, cg_rel=1e-4)
-        assert rel(o["Fbar"][0], one["Fbar"][k]) < 1e-14
+        assert rel(o["Fbar"][0], one["Fbar"][k]) < 1e-10
         np.testing.assert_array_equal(o["newton"][0], one["newton"][k])
     F2, _ = ctx.get_fields()
     # the FP32 inner solves carry the last-bit differences of their inputs
