@@ -78,11 +78,13 @@ def measured_peaks():
 # source files each timed kernel is compiled from
 KERNEL_SOURCES = {
     "tangent_cg": ("cg.cu", "common.cuh", "launch.h"),
-    "xy_forward": ("transform2.cuh", "transform2_impl.cuh", "fft2.cuh", "common.cuh", "dw.cuh", "launch.h"),
+    "xy_forward": ("transform2.cuh", "transform2c.cuh", "transform2_impl.cuh", "fft2.cuh", "common.cuh", "dw.cuh",
+                   "launch.h"),
     "zpass_projection": ("transform2.cuh", "transform2_impl.cuh", "fft2.cuh", "common.cuh", "dw.cuh", "launch.h"),
-    "xy_inverse_residual": ("transform2.cuh", "transform2_impl.cuh", "fft2.cuh", "common.cuh", "dw.cuh",
-                            "launch.h"),
+    "xy_inverse_residual": ("transform2.cuh", "transform2c.cuh", "transform2_impl.cuh", "fft2.cuh", "common.cuh",
+                            "dw.cuh", "launch.h"),
 }
+XY_SCHEDULES = {0: "one block per plane", 1: "persistent bulk-copy", 2: "two-CTA cluster"}
 
 
 def src_hash(kernel):
@@ -354,9 +356,14 @@ def run_matvec_only(args):
     prec = mf.MF_FP64 if args.fp64 else mf.MF_FP32_INNER
     ctx = mf.Context(n, n, n, prec)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    if args.fp64 or args.xy_cluster < 0:
+        ctx.autotune()
+    else:
+        ctx.set_xy_cluster(args.xy_cluster)
     ctx.constitutive()
     if args.kernels_only:
         ms = ctx.time_kernels(mask[0], reps=args.kernels_only)
+        ms_graph = ctx.time_kernels(mask[0], reps=args.kernels_only, graph=True)
         b = torch.empty(9 * n ** 3, dtype=torch.float64, device="cuda")
         res_ms = time_residual(ctx, mask[0], target[0] * mask[0], b, args.kernels_only)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -364,8 +371,15 @@ def run_matvec_only(args):
         ctx.stress()
         ev[1].record()
         torch.cuda.synchronize()
+        fwd, inv, _ = ctx.xy_schedule()
         print(json.dumps({"kernels_only": args.kernels_only, "fp64": bool(args.fp64),
-                          "ms": dict(zip(KERNELS, [float(m) for m in ms])), "residual_ms": res_ms,
+                          "xy_schedule": {"forward": XY_SCHEDULES[fwd], "inverse": XY_SCHEDULES[inv]},
+                          "ms": dict(zip(KERNELS, [float(m) for m in ms])),
+                          "ms_graph": dict(zip(KERNELS, [float(m) for m in ms_graph])),
+                          "frac_graph": {k: b * n ** 3 / (m * 1e-3) / 1e9 / measured_peaks()[0]
+                                         for k, m, b in zip(KERNELS, ms_graph, ALGO_BYTES_F64 if args.fp64
+                                                            else ALGO_BYTES_F32)},
+                          "residual_ms": res_ms,
                           "stress_ms": ev[0].elapsed_time(ev[1])}))
         return
     x = torch.randn(9 * n ** 3, dtype=ctx.inner_dtype, device="cuda")
@@ -671,7 +685,8 @@ def run_ours(args):
     # last load increment (mf_set_predictor); the paper's uniform start is
     # timed beside it below
     ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
-    ztile, ztile_ms, xy_persist, xy_ms = ctx.autotune()
+    ztile, ztile_ms, _, _ = ctx.autotune()
+    xy_fwd, xy_inv, xy_ms = ctx.xy_schedule()
 
     def steps(c, k0, k1):
         idx = [k % nsteps_hist for k in range(k0, k1)]
@@ -923,8 +938,11 @@ def run_ours(args):
                          for k, t, b in zip(KERNELS, kms64, ALGO_BYTES_F64)},
         "autotune": {"zpass_tile_columns": ztile,
                      "zpass_ms_by_tile": {str(w): float(m) for w, m in zip((4, 8, 16), ztile_ms)},
-                     "xy_forward_schedule": "persistent bulk-copy" if xy_persist else "one block per plane",
-                     "xy_forward_ms_by_schedule": {"per_plane": float(xy_ms[0]), "persistent": float(xy_ms[1])}},
+                     "xy_forward_schedule": XY_SCHEDULES[xy_fwd],
+                     "xy_inverse_schedule": XY_SCHEDULES[xy_inv],
+                     "xy_forward_ms_by_schedule": {"per_plane": float(xy_ms[0]), "persistent": float(xy_ms[1]),
+                                                   "cluster": float(xy_ms[2])},
+                     "xy_inverse_ms_by_schedule": {"per_plane": float(xy_ms[3]), "cluster": float(xy_ms[4])}},
         "matvec_gvoxel_s": {"fp32": N / (mv32_ms * 1e-3) / 1e9, "fp64": N / (mv64_ms * 1e-3) / 1e9,
                             "reps": "median of 100 (FP32) and 10 (FP64) warm applications, events per application"},
         "fp64_roofline": {"bound": "fp64 FMA", "flop_per_voxel": MATVEC_FLOP_F64,
@@ -1018,6 +1036,9 @@ def main():
     ap.add_argument("--kernels-only", type=int, default=0,
                     help="profiling driver: time the four CG-iteration kernels this many times each")
     ap.add_argument("--fp64", action="store_true", help="with --matvec-only / --kernels-only: FP64")
+    ap.add_argument("--xy-cluster", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help=("with --matvec-only / --kernels-only (FP32): x-y passes as two-CTA cluster kernels "
+                          "(bit 0 forward, bit 1 inverse); -1: the autotuner's choice"))
     ap.add_argument("--oracle-full", action="store_true",
                     help="time whole oracle runs of the 16^3 and 64^3 workloads (1 and all threads)")
     args = ap.parse_args()

@@ -295,16 +295,20 @@ int mf_selftest_wait_timeout(int max_polls);
  * the fixed-size transform kernels for this context's size and precision and
  * keep the fastest (CUDA events on the context's stream, L2 flushed before
  * every launch); also the residual's z-pass tile (4, 8) and, for FP32-inner
- * contexts whose planes have the persistent x-y kernel, the schedule of the
- * x-y forward pass (one block per plane, or the persistent bulk-copy kernel;
- * an explicit mf_set_xy_persistent takes precedence).  The choices are
+ * contexts whose planes have the persistent or the cluster x-y kernels, the
+ * schedules of the x-y passes (forward: one block per plane, the persistent
+ * bulk-copy kernel or the two-CTA cluster kernel; inverse: one block per
+ * plane or the cluster kernel; mf_set_xy_persistent and mf_set_xy_cluster
+ * take precedence).  The choices are
  * cached per (nx, ny, nz, precision, outer arithmetic) for the process;
  * mf_solve and mf_solve_batch run the tuner on a context's first solve if
  * nothing is cached.  This call re-times and replaces the cached choices.
  * zs_out: host int32 or NULL, the chosen width; ms_out: host 3 floats or
  * NULL, mean ms per width (-1 when not applicable); xy_out: host int32 or
- * NULL, the context's x-y forward schedule after the call (1 persistent);
- * xy_ms_out: host 2 floats or NULL, mean ms per schedule (-1 when not timed).
+ * NULL, the context's x-y forward schedule after the call (0 one block per
+ * plane, 1 persistent, 2 cluster); xy_ms_out: host 2 floats or NULL, mean ms
+ * of the forward pass per plane and persistent (-1 when not timed; all five
+ * timings through mf_xy_schedule).
  * Contexts served by the generic kernels keep their fixed tile. */
 int mf_autotune(mf_ctx* ctx, int32_t* zs_out, float* ms_out, int32_t* xy_out, float* xy_ms_out);
 
@@ -354,6 +358,29 @@ int mf_set_xy_split(mf_ctx* ctx, int split);
  * waits are bounded; a wait that gives up makes the solve return
  * MF_DEVICE_TIMEOUT. */
 int mf_set_xy_persistent(mf_ctx* ctx, int on);
+
+/* The FP32 x-y passes of an FP32-inner context with 128 x 128 planes as
+ * kernels of two-CTA clusters, one cluster per (component, z) plane: bit 0
+ * the forward pass, bit 1 the inverse pass (with the CG update), 0 neither.
+ * The y transform's first radix-2 stage (rows j and j + 64, Eq.
+ * eql_discrete2's DFT along y) is applied to the real rows before the x
+ * transform; each CTA then keeps one 64-row half of the plane's spectrum in
+ * its shared memory (32 KB instead of 66 KB) and the two exchange rows
+ * through distributed shared memory.  Same spectrum layout as the per-plane
+ * kernels; results agree with theirs to FP32 rounding.  The cluster forward
+ * pass takes precedence over the persistent one.  Without this call the
+ * autotuner chooses (mf_autotune); with it the choice is fixed for the
+ * context.  MF_INVALID_ARG for other sizes, precisions, the split kernels, or
+ * `which` outside 0..3. */
+int mf_set_xy_cluster(mf_ctx* ctx, int which);
+
+/* The x-y schedules of a context: fwd_out (host int32 or NULL) 0 one block
+ * per plane, 1 persistent, 2 cluster; inv_out (host int32 or NULL) 0 one
+ * block per plane, 2 cluster; ms_out (host 5 floats or NULL) the
+ * autotuner's mean ms per launch of the forward pass per plane, persistent
+ * and cluster, and of the inverse pass per plane and cluster (-1 when not
+ * timed).  No device work. */
+int mf_xy_schedule(mf_ctx* ctx, int32_t* fwd_out, int32_t* inv_out, float* ms_out);
 
 /* FP32-inner contexts: arithmetic of the projection x <- G*(x) applied to
  * the FP32 corrections before the Newton update (FP32 rounding leaves in

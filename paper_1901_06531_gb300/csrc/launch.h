@@ -35,6 +35,8 @@ struct XYArgs {
   int fin;         // fused (v2, not split) inverse pass with the CG update: finish beta in its last block
   int pdl;         // v2 fused kernels: launch with programmatic dependent launch (see launch_k)
   int persist;     // FP32 v2 forward pass as the persistent bulk-copy kernel (k_xyf_p)
+  int cluster_f;   // FP32 v2 forward pass (nx = 128) as the two-CTA cluster kernel (k_xyf_c)
+  int cluster_i;   // FP32 v2 inverse pass (nx = 128) as the two-CTA cluster kernel (k_xyi_c)
   int* flags;      // device flags word (MF_FLAG_TIMEOUT from bounded waits), or null
   int nx, ny, nz;
   long long N;
@@ -77,6 +79,8 @@ bool mf_v2_supported(int nx, int ny, int nz);
 bool mf_split_supported(int nx);
 // the persistent FP32 forward kernel exists for these plane sizes (nx = ny)
 bool mf_persist_supported(int nx);
+// the two-CTA cluster FP32 x-y kernels exist for these plane sizes (nx = ny)
+bool mf_cluster_supported(int nx);
 // x-y kernel blocks of one pass, i.e. the block partials the inverse pass
 // writes (one per (c, z) plane fused, one per row block split)
 int mf_xy_blocks(int ny, int nz, bool split);

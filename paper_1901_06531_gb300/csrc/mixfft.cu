@@ -264,6 +264,8 @@ struct mf_ctx {
   int pw_blocks = 1;            // blocks of the grid-stride pointwise passes (one voxel per thread at most)
   int xy_persist = 0;           // FP32 x-y forward pass as the persistent bulk-copy kernel
   int xy_persist_user = 0;      // set by mf_set_xy_persistent: the autotuner keeps it
+  int xy_cluster = 0;           // FP32 x-y passes as two-CTA cluster kernels: bit 0 forward, bit 1 inverse
+  int xy_cluster_user = 0;      // set by mf_set_xy_cluster: the autotuner keeps it
   int proj_arith = MF_PROJ_AUTO;   // arithmetic of the projection of each FP32 correction
   double first_ratio = INFINITY;   // max_v abs(dF_v)/abs(<F>) of the last step's first correction
   cudaGraphExec_t cg_exec = nullptr;
@@ -299,7 +301,7 @@ size_t tw_offset(const mf_ctx* c, bool f32, bool dw, size_t* esz) {
 }
 
 XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
-  XYArgs a;
+  XYArgs a{};
   a.v2 = c->v2;
   a.split = c->xy_split;
   a.skip = nullptr;
@@ -308,6 +310,9 @@ XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
   // (pdl_wait): launch them with programmatic dependent launch everywhere
   a.pdl = (c->v2 && !c->xy_split) ? 1 : 0;
   a.persist = (f32 && !dw && c->xy_persist && c->v2 && !c->xy_split) ? 1 : 0;
+  const bool clu = f32 && !dw && c->v2 && !c->xy_split && mf_cluster_supported(c->nx);
+  a.cluster_f = (clu && (c->xy_cluster & 1)) ? 1 : 0;
+  a.cluster_i = (clu && (c->xy_cluster & 2)) ? 1 : 0;
   a.flags = &c->at<Scalars>(c->osc)->flags;
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.N = c->N;
   a.px = c->px; a.pyh = c->pyh;
@@ -574,7 +579,7 @@ int build_cg_graph(mf_ctx* c, const uint8_t* mask) {
 // candidate is timed with CUDA events on the context's stream (L2 flushed
 // before every launch, one untimed launch first) and the fastest kept; the
 // choice is cached for the process per (nx, ny, nz, precision).
-struct TuneEntry { int nx, ny, nz, prec, dw, S, Sr, xyp; float ms[3], msr[2], msxy[2]; };
+struct TuneEntry { int nx, ny, nz, prec, dw, S, Sr, xyp, xyc; float ms[3], msr[2], msxy[3], msxi[2]; };
 std::vector<TuneEntry> g_tune_cache;
 std::mutex g_tune_mutex;
 
@@ -591,6 +596,10 @@ int autotune(mf_ctx* c, int reps) {
           c->xy_persist = t.xyp;
           free_cg_graph(c);
         }
+        if (!c->xy_cluster_user && c->xy_cluster != t.xyc) {
+          c->xy_cluster = t.xyc;
+          free_cg_graph(c);
+        }
         c->tuned = true;
         return MF_OK;
       }
@@ -603,7 +612,8 @@ int autotune(mf_ctx* c, int reps) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return MF_CUDA_ERROR;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MF_CUDA_ERROR; }
-  TuneEntry te{c->nx, c->ny, c->nz, c->prec, dwr, c->zS, c->zSr, c->xy_persist, {0, 0, 0}, {0, 0}, {-1, -1}};
+  TuneEntry te{c->nx,        c->ny,        c->nz,   c->prec,          dwr,     c->zS, c->zSr, c->xy_persist,
+               c->xy_cluster, {0, 0, 0},    {0, 0},  {-1, -1, -1},     {-1, -1}};
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
@@ -644,30 +654,58 @@ int autotune(mf_ctx* c, int reps) {
     te.msr[i] = (float)(tot / reps);
     if (e == cudaSuccess && te.msr[i] < bestr) { bestr = te.msr[i]; te.Sr = rcands[i]; }
   }
-  // the schedule of the FP32 x-y forward pass: one block per plane, or the
-  // persistent bulk-copy kernel (same results); the persistent one is taken
-  // only when it is faster by more than 3% (single timed launches: a tie
-  // keeps the per-plane default), unless mf_set_xy_persistent chose
-  if (e == cudaSuccess && f32 && !c->xy_split && mf_persist_supported(c->nx)) {
-    for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
-      XYArgs xf = xa;
-      xf.persist = form;
-      double tot = 0.0;
-      for (int r = -1; r < reps && e == cudaSuccess; ++r) {
-        e = cudaMemsetAsync(c->ws + c->ob, 0, 9 * c->N * sizeof(double), c->st);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
-        if (e == cudaSuccess)
-          e = mf_launch_project_part(0, f32, c->ws + c->oAp, c->ws + c->ospec, nullptr, nullptr, xf, za, nullptr,
-                                     c->st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (r >= 0) tot += ms;
-      }
-      te.msxy[form] = (float)(tot / reps);
+  // the schedules of the FP32 x-y passes: forward one block per plane, the
+  // persistent bulk-copy kernel or the two-CTA cluster kernel; inverse (with
+  // the CG update) one block per plane or the cluster kernel.  Another form
+  // than one block per plane is taken only when it is faster by more than 3%
+  // (single timed launches: a tie keeps the per-plane default), unless
+  // mf_set_xy_persistent / mf_set_xy_cluster chose
+  auto time_pass = [&](int which, const XYArgs& xf, float* out) {
+    double tot = 0.0;
+    for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+      e = cudaMemsetAsync(c->ws + c->ob, 0, 9 * c->N * sizeof(double), c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+      if (e == cudaSuccess)
+        e = which == 0 ? mf_launch_project_part(0, f32, c->ws + c->oAp, c->ws + c->ospec, nullptr, nullptr, xf, za,
+                                                nullptr, c->st)
+                       : mf_launch_project_part(2, f32, nullptr, c->ws + c->ospec, c->ws + c->or_,
+                                                c->at<double>(c->opart), xf, za, c->at<Scalars>(c->osc), c->st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (r >= 0) tot += ms;
     }
-    if (e == cudaSuccess) te.xyp = (te.msxy[1] < 0.97f * te.msxy[0]) ? 1 : 0;
+    *out = (float)(tot / reps);
+  };
+  const bool xyp_ok = f32 && !c->xy_split && mf_persist_supported(c->nx);
+  const bool xyc_ok = f32 && !c->xy_split && mf_cluster_supported(c->nx);
+  if (e == cudaSuccess && (xyp_ok || xyc_ok)) {
+    XYArgs xf = xa;
+    xf.persist = 0;
+    xf.cluster_f = 0;
+    xf.cluster_i = 0;
+    time_pass(0, xf, &te.msxy[0]);
+    if (xyp_ok) {
+      xf.persist = 1;
+      time_pass(0, xf, &te.msxy[1]);
+      xf.persist = 0;
+    }
+    if (xyc_ok) {
+      xf.cluster_f = 1;
+      time_pass(0, xf, &te.msxy[2]);
+      xf.cluster_f = 0;
+      time_pass(1, xf, &te.msxi[0]);
+      xf.cluster_i = 1;
+      time_pass(1, xf, &te.msxi[1]);
+    }
+    if (e == cudaSuccess) {
+      int best_f = 0;
+      for (int f = 1; f < 3; ++f)
+        if (te.msxy[f] > 0 && te.msxy[f] < 0.97f * te.msxy[0] && te.msxy[f] < te.msxy[best_f]) best_f = f;
+      te.xyp = best_f == 1 ? 1 : 0;
+      te.xyc = (best_f == 2 ? 1 : 0) | ((te.msxi[1] > 0 && te.msxi[1] < 0.97f * te.msxi[0]) ? 2 : 0);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -675,6 +713,7 @@ int autotune(mf_ctx* c, int reps) {
   c->zS = te.S;
   c->zSr = te.Sr;
   if (!c->xy_persist_user) c->xy_persist = te.xyp;
+  if (!c->xy_cluster_user) c->xy_cluster = te.xyc;
   c->tuned = true;
   free_cg_graph(c);   // a captured loop holds the old tile
   std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -1848,6 +1887,34 @@ int mf_set_xy_persistent(mf_ctx* c, int on) {
   return MF_OK;
 }
 
+int mf_set_xy_cluster(mf_ctx* c, int which) {
+  if (!c || which < 0 || which > 3) return MF_INVALID_ARG;
+  if (which && !(c->prec == MF_FP32_INNER && c->v2 && !c->xy_split && mf_cluster_supported(c->nx)))
+    return MF_INVALID_ARG;
+  if (c->xy_cluster != which) free_cg_graph(c);   // the captured loop holds the old kernels
+  c->xy_cluster = which;
+  c->xy_cluster_user = 1;
+  return MF_OK;
+}
+
+int mf_xy_schedule(mf_ctx* c, int32_t* fwd_out, int32_t* inv_out, float* ms_out) {
+  if (!c) return MF_INVALID_ARG;
+  const bool clu = c->prec == MF_FP32_INNER && c->v2 && !c->xy_split && mf_cluster_supported(c->nx);
+  if (fwd_out) *fwd_out = (clu && (c->xy_cluster & 1)) ? 2 : c->xy_persist;
+  if (inv_out) *inv_out = (clu && (c->xy_cluster & 2)) ? 2 : 0;
+  if (ms_out) {
+    for (int i = 0; i < 5; ++i) ms_out[i] = -1.f;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (const TuneEntry& t : g_tune_cache)
+      if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.prec == c->prec &&
+          t.dw == (c->dw_residual() ? 1 : 0)) {
+        for (int i = 0; i < 3; ++i) ms_out[i] = t.msxy[i];
+        for (int i = 0; i < 2; ++i) ms_out[3 + i] = t.msxi[i];
+      }
+  }
+  return MF_OK;
+}
+
 int mf_set_projection_arith(mf_ctx* c, int arith) {
   if (!c || (arith != MF_PROJ_FP32 && arith != MF_PROJ_OUTER && arith != MF_PROJ_AUTO)) return MF_INVALID_ARG;
   if (arith != MF_PROJ_FP32 && c->prec != MF_FP32_INNER) return MF_INVALID_ARG;
@@ -1961,7 +2028,7 @@ int mf_autotune(mf_ctx* c, int32_t* zs_out, float* ms_out, int32_t* xy_out, floa
           t.dw == (c->dw_residual() ? 1 : 0))
         for (int i = 0; i < 3; ++i) ms_out[i] = t.ms[i];
   }
-  if (xy_out) *xy_out = c->xy_persist;
+  if (xy_out) *xy_out = (c->xy_cluster & 1) && mf_cluster_supported(c->nx) ? 2 : c->xy_persist;
   if (xy_ms_out) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     for (const TuneEntry& t : g_tune_cache)

@@ -25,17 +25,14 @@ constexpr size_t kTableBytes = 64 * 1024;
 constexpr size_t kPartialBytes = (size_t)9 * 256 * sizeof(double);
 constexpr size_t kMeanBytes = 256;
 constexpr size_t kNoallocScratchBytes = kSpecBytes + kTableBytes + kPartialBytes + kMeanBytes;
-constexpr int kMaxDevices = 64;
 
 }  // namespace
 
 // The scratch array.  Host code must not use this name as an address: the
-// device address comes from cudaGetSymbolAddress, once per device.
+// device address comes from cudaGetSymbolAddress, on every call.
 static __device__ __align__(256) unsigned char g_mf_noalloc_scratch[kNoallocScratchBytes];
 
 namespace {
-
-unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 bool na_plan(int n, AxisPlan* p) {
   p->n = n;
@@ -86,21 +83,19 @@ extern "C" int mf_residual_noalloc(int nx, int ny, int nz, const double* P_dev, 
   if (!na_plan(nx, &px) || !na_plan(ny / 2, &pyh) || !na_plan(nz, &pz)) return MF_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // once per device: the device address of the scratch array.  The address
-  // is looked up with the current device, so the stream must belong to it.
+  // the device address of the scratch array, looked up on every call (a
+  // device or primary-context reset may reload the module elsewhere) with
+  // the current device, so the stream must belong to it
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MF_CUDA_ERROR;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MF_CUDA_ERROR;
   if (st) {
     int sdev = -1;
     if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return MF_CUDA_ERROR;
     if (sdev != dev) return MF_INVALID_ARG;
   }
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_mf_noalloc_scratch) != cudaSuccess || !p) return MF_CUDA_ERROR;
-    g_scratch_ptr[dev] = (unsigned char*)p;
-  }
-  unsigned char* base = g_scratch_ptr[dev];
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_mf_noalloc_scratch) != cudaSuccess || !sym) return MF_CUDA_ERROR;
+  unsigned char* base = (unsigned char*)sym;
   void* spec = base;
   unsigned char* tab = base + kSpecBytes;
   double* partials = (double*)(base + kSpecBytes + kTableBytes);

@@ -434,5 +434,6 @@ bool mf_v2_supported(int nx, int ny, int nz) {
 
 bool mf_split_supported(int nx) { return nx == 32 || nx == 256; }
 bool mf_persist_supported(int nx) { return nx == 48 || nx == 64 || nx == 96 || nx == 128; }
+bool mf_cluster_supported(int nx) { return nx == 128; }
 
 int mf_xy_blocks(int ny, int nz, bool split) { return split ? 9 * nz * (ny / 16) : 9 * nz; }

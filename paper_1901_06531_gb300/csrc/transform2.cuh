@@ -38,15 +38,29 @@ __device__ __forceinline__ double2 io_out(dwc v) { return to_double2(v); }
 
 constexpr int kThreads = 256;
 // x-y kernels: 16-byte elements (FP64, double word) hold one 128 x 128 plane
-// in 133 KB of shared memory, one block per SM, so they run twice the threads
-// (for FP32 planes, three blocks of 256 measured faster than two of 512)
-template <typename T> __host__ __device__ constexpr int xy_threads() {
-  return sizeof(typename CT<T>::t) == 16 ? 512 : 256;
+// in 133 KB of shared memory, one block per SM, so they run twice the
+// threads; FP32 128 x 128 planes (66 KB) run two blocks of 512 threads per
+// SM at 64 registers a thread (about 1% faster than three blocks of 256 on
+// the GB300), other FP32 planes blocks of 256
+constexpr int kXY128Threads = 512;
+template <typename T, int NX> __host__ __device__ constexpr int xy_threads() {
+  return sizeof(typename CT<T>::t) == 16 ? 512 : (NX == 128 ? kXY128Threads : 256);
+}
+// resident blocks per SM the register allocation of an FP32 128 x 128 x-y
+// kernel is held to when it runs 512 threads: two (64 registers a thread)
+template <typename T, int NX> __host__ __device__ constexpr int xy_min_blocks() {
+  return (sizeof(typename CT<T>::t) == 8 && NX == 128 && kXY128Threads == 512) ? 2 : 1;
 }
 // z-pass threads per block for a tile of S columns of one row group (three
 // components): 24 S, one butterfly per thread in a radix-16 stage of the
 // 128-point transform and two in its radix-8 stage (3 x S x 128/R)
 __host__ __device__ constexpr int z_threads(int S) { return 24 * S; }
+// resident z-pass blocks per SM the register allocation is held to: five
+// blocks of 192 threads for the FP32 operator pass (S = 8, MODE 0), else what
+// the compiler chooses
+template <typename T> __host__ __device__ constexpr int z_min_blocks(int S, int mode) {
+  return (sizeof(typename CT<T>::t) == 8 && S == 8 && mode == 0) ? 5 : 1;
+}
 
 // Asynchronous global -> shared copies of one complex element (8 or 16
 // bytes); many in flight per thread without holding registers.
@@ -66,17 +80,57 @@ struct XYShape {
   static constexpr int H = NX / 2;
   static constexpr int PX = H + 1;            // odd pitch: rows fall in different banks
   static constexpr int NY = NX;
+  // tables after the plane: twx (NX), twy (NY), tw0 (64, see x_stage0_128), posx (H ints)
   static constexpr size_t smem() {
-    return (size_t)NY * PX * sizeof(C) + (size_t)(NX + NY) * sizeof(C) + (size_t)H * sizeof(int);
+    return (size_t)NY * PX * sizeof(C) + (size_t)(NX + NY + 64) * sizeof(C) + (size_t)H * sizeof(int);
   }
 };
 
 template <typename C>
 __device__ __forceinline__ void load_tables(C* twx, C* twy, int* posx, const C* gtw, const int* gpos,
-                                            int nx, int ny, int h) {
+                                            int nx, int ny, int h, C* tw0 = nullptr) {
   for (int i = threadIdx.x; i < nx; i += blockDim.x) twx[i] = gtw[i];
   for (int i = threadIdx.x; i < ny; i += blockDim.x) twy[i] = gtw[nx + i];
   for (int i = threadIdx.x; i < h; i += blockDim.x) posx[i] = gpos[i];
+  if (tw0)   // tw0[8k + b] = W_64^(b k) = W_128^(2 b k) (nx = 128)
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) tw0[i] = gtw[2 * (i & 7) * (i >> 3)];
+}
+
+// First x stage of an FP32 128 x 128 plane (half-length transform of 64
+// points: radix 8, M = 8, eight butterflies per row; forward DIF, or with
+// INV its adjoint as the last inverse stage), TPB threads (a multiple of
+// 256).  Lanes are (row, butterfly b) with the four rows of a warp 8 apart
+// (row (w mod 8) + 8i + 32 (w / 8) + pass offset): with the row pitch PX =
+// 65 (1 mod 16) rows 8 apart start 8 elements apart modulo the 16
+// eight-byte bank pairs, so each half-warp's 16 accesses of positions b + 8k
+// (two rows of 8 consecutive) hit distinct banks; the twiddles W_64^(bk) come
+// from the [k][b] table tw0 for the same reason.  ld(row, pos) gives an
+// input, st(row, pos, value) takes an output.
+template <bool INV, int TPB, typename LD, typename ST>
+__device__ __forceinline__ void x_stage0_128(const float2* tw0, LD ld, ST st) {
+  typedef float2 C;
+  static_assert(TPB % 256 == 0 && TPB <= 1024, "whole groups of eight warps");
+  constexpr int kRowsPerPass = TPB / 8;   // eight lanes per row
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, b = l & 7, i = l >> 3;
+  const int row0 = (w & 7) + 8 * i + 32 * (w >> 3);
+#pragma unroll 1
+  for (int P = 0; P < 128 / kRowsPerPass; ++P) {
+    const int row = kRowsPerPass * P + row0;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = ld(row, b + 8 * r);
+    if (!INV) {
+      fft2::Dft<8, false, C>::run(v);
+#pragma unroll
+      for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], tw0[8 * k + b]);
+    } else {
+#pragma unroll
+      for (int k = 1; k < 8; ++k) v[k] = cmulc(v[k], tw0[8 * k + b]);
+      fft2::Dft<8, true, C>::run(v);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) st(row, b + 8 * k, v[k]);
+  }
 }
 
 // ------------------------------------------------------------- row spectra
@@ -221,12 +275,12 @@ __device__ __forceinline__ void x_merge_first(typename CT<T>::t* buf, const type
 
 // ------------------------------------------------------------------ forward
 template <typename T, int NX>
-__global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(xy_threads<T, NX>(), xy_min_blocks<T, NX>()) k_xyf(const typename IOT<T>::t* __restrict__ in,
                                                   typename CT<T>::t* __restrict__ spec, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
                                                   const int* __restrict__ gpos, const int* skip) {
   typedef XYShape<T, NX> Sh;
-  constexpr int TPB = xy_threads<T>();
+  constexpr int TPB = xy_threads<T, NX>();
   typedef typename CT<T>::t C;
   typedef typename CT<typename IOT<T>::t>::t CI;
   constexpr int H = Sh::H, PX = Sh::PX, NY = Sh::NY;
@@ -234,8 +288,10 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* twx = buf + NY * PX;
   C* twy = twx + NX;
-  int* posx = reinterpret_cast<int*>(twy + NY);
-  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);   // constant: loaded before the wait for the predecessor
+  C* tw0 = twy + NY;
+  int* posx = reinterpret_cast<int*>(tw0 + 64);
+  // constant: loaded before the wait for the predecessor
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H, (sizeof(C) == 8 && NX == 128) ? tw0 : nullptr);
   pdl_wait();
   if (skip && *(volatile const int*)skip) return;
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
@@ -252,8 +308,12 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyf(const typename IOT<T>::
     if constexpr (RowPlan<H>::NST == 2) {
       // first x stage straight from global memory (consecutive threads take
       // consecutive butterflies of a row: 64-byte row segments per warp access)
-      fft2::stage_io<C, H, NX, 0, false, NY, 1, PX, 0, 1, false>(
-          twx, [&](int q, int, int e) { return gload(q, e); }, [&](int, int i, int, C v) { buf[MF_AT(i, NY * PX)] = v; });
+      if constexpr (NX == 128)
+        x_stage0_128<false, TPB>(tw0, gload, [&](int q, int e, C v) { buf[MF_AT(q * PX + e, NY * PX)] = v; });
+      else
+        fft2::stage_io<C, H, NX, 0, false, NY, 1, PX, 0, 1, false>(
+            twx, [&](int q, int, int e) { return gload(q, e); },
+            [&](int, int i, int, C v) { buf[MF_AT(i, NY * PX)] = v; });
       __syncthreads();
       x_last_split<T, NX, TPB>(buf, twx, [&](int y, int pos) { return buf[MF_AT(y * PX + pos, NY * PX)]; });
     } else {
@@ -327,7 +387,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
   C* buf = stg + 2 * PLANE;
   C* twx = buf + NY * PX;
   C* twy = twx + NX;
-  int* posx = reinterpret_cast<int*>(twy + NY);
+  int* posx = reinterpret_cast<int*>(twy + NY + 64);
   __shared__ __align__(8) uint64_t bar[2];
   const int nplanes = 9 * nz;
   if (threadIdx.x == 0) {
@@ -390,14 +450,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 // finish also sums the partials and updates beta, r.r and the stop flag (the
 // work of k_fin_beta, without its launch).
 template <typename T, int NX, int MODE>
-__global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t* __restrict__ spec,
+__global__ void __launch_bounds__(xy_threads<T, NX>(), xy_min_blocks<T, NX>()) k_xyi(const typename CT<T>::t* __restrict__ spec,
                                                   typename IOT<T>::t* __restrict__ out,
                                                   double* __restrict__ partials, int nz, long long N,
                                                   const typename CT<T>::t* __restrict__ gtw,
                                                   const int* __restrict__ gpos, Scalars* sc,
                                                   const int* skip, int fin) {
   typedef XYShape<T, NX> Sh;
-  constexpr int TPB = xy_threads<T>();
+  constexpr int TPB = xy_threads<T, NX>();
   typedef typename CT<T>::t C;
   typedef typename IOT<T>::t TI;
   typedef typename CT<TI>::t CI;
@@ -408,8 +468,10 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* twx = buf + NY * PX;
   C* twy = twx + NX;
-  int* posx = reinterpret_cast<int*>(twy + NY);
-  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H);   // constant: loaded before the wait for the predecessor
+  C* tw0 = twy + NY;
+  int* posx = reinterpret_cast<int*>(tw0 + 64);
+  // constant: loaded before the wait for the predecessor
+  load_tables(twx, twy, posx, gtw, gpos, NX, NY, H, (sizeof(C) == 8 && NX == 128) ? tw0 : nullptr);
   pdl_wait();
   if (skip && *(volatile const int*)skip) return;
   const int c = blockIdx.x % 9, z = blockIdx.x / 9;
@@ -492,7 +554,10 @@ __global__ void __launch_bounds__(xy_threads<T>()) k_xyi(const typename CT<T>::t
   // stage then runs in shared memory and a coalesced loop does the update.
   constexpr int M0 = H / fft2::rad(H, 0);
   constexpr bool kDirect = sizeof(C) == 8 && RowPlan<H>::NST == 2 && (MODE != 3 || (M0 * 8) % 32 == 0);
-  if constexpr (kDirect) {
+  if constexpr (kDirect && NX == 128) {
+    x_stage0_128<true, TPB>(tw0, [&](int q, int e) { return buf[MF_AT(q * PX + e, NY * PX)]; },
+                       [&](int q, int e, C v) { emit((long long)q * H + e, v); });
+  } else if constexpr (kDirect) {
     // consecutive threads take consecutive butterflies of a row
     fft2::stage_io<C, H, NX, 0, true, NY, 1, PX, 0, 1, false>(
         twx, [&](int, int i, int) { return buf[MF_AT(i, NY * PX)]; },
@@ -547,8 +612,10 @@ struct ZShape {
   static constexpr bool E8 = sizeof(C) == 8;
   static constexpr int ZS = S + ((E8 && S < 16) ? 1 : 0);
   static constexpr int CP = NZ * ZS + (E8 ? (S == 8 ? 1 : 0) : (S == 4 ? 4 : 0));
+  // after the three components: twz (NZ), zk (NZ ints), xiz (NZ reals)
   static constexpr size_t smem() {
-    return (size_t)3 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int);
+    return (size_t)3 * CP * sizeof(C) + (size_t)NZ * sizeof(C) + (size_t)NZ * sizeof(int) +
+           (size_t)NZ * sizeof(typename std::conditional<sizeof(C) == 8, float, double>::type);
   }
 };
 
@@ -556,7 +623,7 @@ struct ZShape {
 // frequency, records the null-frequency coefficient / N in a.mean_out).
 // Grid: 3 row groups x (ncol / S) column tiles.
 template <typename T, int NZ, int MODE, int S_>
-__global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
+__global__ void __launch_bounds__(z_threads(S_), z_min_blocks<T>(S_, MODE)) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
   typedef ZShape<T, NZ, S_> Sh;
   constexpr int kZThreads = z_threads(S_);
   typedef typename CT<T>::t C;
@@ -567,9 +634,18 @@ __global__ void __launch_bounds__(z_threads(S_)) k_zp(typename CT<T>::t* __restr
   C* buf = reinterpret_cast<C*>(smem_raw);   // [3][CP]
   C* twz = buf + 3 * CP;
   int* zk = reinterpret_cast<int*>(twz + NZ);
+  // xi_z of each position (k_z / NZ, signed), NaN at the z-Nyquist frequency
+  typedef typename std::conditional<sizeof(C) == 8, float, double>::type TX;
+  TX* xiz = reinterpret_cast<TX*>(zk + NZ);
   const C* gtwz = reinterpret_cast<const C*>(a.twz);
   // constant tables: loaded before the wait for the predecessor
-  for (int i = threadIdx.x; i < NZ; i += kZThreads) { twz[i] = gtwz[i]; zk[i] = a.zk[i]; }
+  for (int i = threadIdx.x; i < NZ; i += kZThreads) {
+    twz[i] = gtwz[i];
+    const int kz = a.zk[i];
+    zk[i] = kz;
+    const int kzs = (2 * kz < NZ) ? kz : kz - NZ;
+    xiz[i] = ((NZ % 2 == 0) && (2 * kz == NZ)) ? (TX)NAN : (TX)kzs * ((TX)1 / (TX)NZ);
+  }
   pdl_wait();
   if (a.skip && *(volatile const int*)a.skip) return;
   const int H = a.nx / 2;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "transform2.cuh"
+#include "transform2c.cuh"
 #include "transform3.cuh"
 
 namespace tr2 {
@@ -42,9 +43,35 @@ cudaError_t launch_xyf_p(const float* in, void* spec, const XYArgs& a, cudaStrea
                   a.N, (const float2*)a.twx, a.xpos, a.skip, a.flags);
 }
 
+// the two-CTA cluster kernels (FP32, 128 x 128 planes): grid of 2 x 9 nz
+// CTAs, consecutive pairs forming a cluster
+inline cudaError_t launch_xyf_c(const float* in, void* spec, const XYArgs& a, cudaStream_t st) {
+  const size_t sm = clu::smem();
+  cudaError_t e = smem_once<k_xyf_c<clu::NX>>(sm);
+  if (e != cudaSuccess) return e;
+  ++g_mf_launches;
+  return launch_k(a.pdl != 0, k_xyf_c<clu::NX>, dim3(18 * a.nz), dim3(clu::kCThreads), sm, st, in, (float2*)spec, a.nz, a.N,
+                  (const float2*)a.twx, a.skip);
+}
+
+template <int MODE>
+cudaError_t launch_xyi_c(const void* spec, float* out, double* partials, const XYArgs& a, const Scalars* sc,
+                         cudaStream_t st) {
+  const size_t sm = clu::smem();
+  cudaError_t e = smem_once<k_xyi_c<MODE>>(sm);
+  if (e != cudaSuccess) return e;
+  ++g_mf_launches;
+  return launch_k(a.pdl != 0, k_xyi_c<MODE>, dim3(18 * a.nz), dim3(clu::kCThreads), sm, st, (const float2*)spec,
+                  out, partials, a.nz, a.N, (const float2*)a.twx, const_cast<Scalars*>(sc), a.skip,
+                  MODE == 3 ? a.fin : 0);
+}
+
 template <typename T, int NX>
 cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a, cudaStream_t st) {
   typedef typename CT<T>::t C;
+  if constexpr (std::is_same<T, float>::value && NX == clu::NX) {
+    if (a.cluster_f) return launch_xyf_c(in, spec, a, st);
+  }
   if constexpr (std::is_same<T, float>::value && RowPlan<NX / 2>::NST == 2) {
     if (a.persist) return launch_xyf_p<NX>(in, spec, a, st);
   }
@@ -52,7 +79,7 @@ cudaError_t launch_xyf(const typename IOT<T>::t* in, void* spec, const XYArgs& a
   cudaError_t e = smem_once<k_xyf<T, NX>>(sm);
   if (e != cudaSuccess) return e;
   ++g_mf_launches;
-  return launch_k(a.pdl != 0, k_xyf<T, NX>, dim3(9 * a.nz), dim3(xy_threads<T>()), sm, st, in, (C*)spec, a.nz, a.N,
+  return launch_k(a.pdl != 0, k_xyf<T, NX>, dim3(9 * a.nz), dim3(xy_threads<T, NX>()), sm, st, in, (C*)spec, a.nz, a.N,
                   (const C*)a.twx, a.xpos, a.skip);
 }
 
@@ -60,12 +87,15 @@ template <typename T, int NX, int MODE>
 cudaError_t launch_xyi(const void* spec, typename IOT<T>::t* out, double* partials, const XYArgs& a,
                        const Scalars* sc, cudaStream_t st) {
   typedef typename CT<T>::t C;
+  if constexpr (std::is_same<T, float>::value && NX == clu::NX) {
+    if (a.cluster_i) return launch_xyi_c<MODE>(spec, out, partials, a, sc, st);
+  }
   const size_t sm = XYShape<T, NX>::smem();
   cudaError_t e = smem_once<k_xyi<T, NX, MODE>>(sm);
   if (e != cudaSuccess) return e;
   // the scalar block is written only by the fused finish (a.fin, MODE 3)
   ++g_mf_launches;
-  return launch_k(a.pdl != 0, k_xyi<T, NX, MODE>, dim3(9 * a.nz), dim3(xy_threads<T>()), sm, st, (const C*)spec,
+  return launch_k(a.pdl != 0, k_xyi<T, NX, MODE>, dim3(9 * a.nz), dim3(xy_threads<T, NX>()), sm, st, (const C*)spec,
                   out, partials, a.nz, a.N, (const C*)a.twx, a.xpos, const_cast<Scalars*>(sc), a.skip,
                   MODE == 3 ? a.fin : 0);
 }

@@ -70,6 +70,8 @@ _lib.mf_debug_report.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_debug_selftest.argtypes = []
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
+_lib.mf_set_xy_cluster.argtypes = [_vp, _i]
+_lib.mf_xy_schedule.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_set_projection_arith.argtypes = [_vp, _i]
 _lib.mf_selftest_wait_timeout.argtypes = [_i]
 _lib.mf_adjoint.argtypes = [_vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp, _vp]
@@ -85,7 +87,7 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_stress", "mf_get_tangent", "mf_matvec", "mf_residual", "mf_residual_noalloc",
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
-            "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_projection_arith",
+            "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_xy_cluster", "mf_xy_schedule", "mf_set_projection_arith",
             "mf_set_inexact_newton", "mf_set_predictor", "mf_probe_fma", "mf_debug_report", "mf_debug_selftest", "mf_selftest_wait_timeout", "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
 
@@ -329,7 +331,8 @@ class Context:
 
     def autotune(self):
         """mf_autotune: returns (chosen z-pass tile width, ms per width 4/8/16,
-        x-y forward schedule (1 persistent), ms per schedule)."""
+        x-y forward schedule (0 one block per plane, 1 persistent, 2 cluster), ms of
+        the forward pass per plane and persistent; mf_xy_schedule has all timings)."""
         zs = np.zeros(1, dtype=np.int32)
         ms = np.zeros(3, dtype=np.float32)
         xy = np.zeros(1, dtype=np.int32)
@@ -367,6 +370,19 @@ class Context:
     def set_xy_persistent(self, on):
         """mf_set_xy_persistent: 1 persistent bulk-copy FP32 x-y forward kernel, 0 one block per plane."""
         _check("mf_set_xy_persistent", _lib.mf_set_xy_persistent(self.h, int(on)))
+
+    def set_xy_cluster(self, which):
+        """mf_set_xy_cluster: two-CTA cluster FP32 x-y kernels, bit 0 forward, bit 1 inverse."""
+        _check("mf_set_xy_cluster", _lib.mf_set_xy_cluster(self.h, int(which)))
+
+    def xy_schedule(self):
+        """mf_xy_schedule: (forward schedule 0/1/2, inverse schedule 0/2, the autotuner's
+        ms for forward per plane / persistent / cluster and inverse per plane / cluster)."""
+        f = np.zeros(1, np.int32)
+        i = np.zeros(1, np.int32)
+        ms = np.zeros(5, np.float32)
+        _check("mf_xy_schedule", _lib.mf_xy_schedule(self.h, _ptr(f), _ptr(i), _ptr(ms)))
+        return int(f[0]), int(i[0]), ms
 
     def set_outer_arith(self, arith):
         """mf_set_outer_arith: MF_OUTER_DOUBLE_WORD or MF_OUTER_FP64."""

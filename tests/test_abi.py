@@ -84,7 +84,7 @@ def test_option_setters_validate_without_gpu(lib):
     lib.mf_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     for name in ("mf_set_projection_arith", "mf_set_xy_persistent", "mf_set_xy_split", "mf_set_outer_arith",
-                 "mf_set_inexact_newton", "mf_set_predictor"):
+                 "mf_set_inexact_newton", "mf_set_predictor", "mf_set_xy_cluster"):
         getattr(lib, name).argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.mf_destroy.argtypes = [ctypes.c_void_p]
     assert lib.mf_create(ctypes.byref(h), 16, 16, 16, mixfft.MF_FP64, None) == 0
@@ -92,6 +92,7 @@ def test_option_setters_validate_without_gpu(lib):
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_FP32) == mixfft.MF_OK
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_AUTO) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_xy_cluster(h, 1) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_inexact_newton(h, 1) == mixfft.MF_OK
     assert lib.mf_set_inexact_newton(h, 0) == mixfft.MF_OK
     assert lib.mf_set_inexact_newton(h, 2) == mixfft.MF_INVALID_ARG
@@ -106,12 +107,24 @@ def test_option_setters_validate_without_gpu(lib):
     assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_OK
     assert lib.mf_set_xy_persistent(h, 0) == mixfft.MF_OK
     assert lib.mf_set_xy_persistent(h, 3) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_xy_cluster(h, 3) == mixfft.MF_INVALID_ARG      # cluster kernels: 128^2 planes only
     assert lib.mf_set_outer_arith(h, 5) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_inexact_newton(h, 1) == mixfft.MF_OK
     assert lib.mf_set_inexact_newton(h, 0) == mixfft.MF_INVALID_ARG
     lib.mf_destroy(h)
     assert lib.mf_create(ctypes.byref(h), 32, 32, 32, mixfft.MF_FP32_INNER, None) == 0
     assert lib.mf_set_xy_persistent(h, 1) == mixfft.MF_INVALID_ARG   # no persistent kernel for 32^2 planes
+    lib.mf_destroy(h)
+    assert lib.mf_create(ctypes.byref(h), 128, 128, 16, mixfft.MF_FP32_INNER, None) == 0
+    lib.mf_xy_schedule.argtypes = [ctypes.c_void_p] * 4
+    fwd, inv = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    ms = (ctypes.c_float * 5)()
+    assert lib.mf_xy_schedule(h, ctypes.byref(fwd), ctypes.byref(inv), ms) == mixfft.MF_OK
+    assert (fwd.value, inv.value) == (0, 0) and list(ms) == [-1.0] * 5   # untuned: per plane, nothing timed
+    assert lib.mf_set_xy_cluster(h, 4) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_xy_cluster(h, 3) == mixfft.MF_OK
+    assert lib.mf_xy_schedule(h, ctypes.byref(fwd), ctypes.byref(inv), None) == mixfft.MF_OK
+    assert (fwd.value, inv.value) == (2, 2)
     lib.mf_destroy(h)
 
 

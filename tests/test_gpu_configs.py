@@ -167,21 +167,24 @@ def test_spheres64_mixed_control_against_oracle(prec, pred):
     print("spheres64", prec, pred, errs)
 
 
-@pytest.mark.parametrize("prec,pred", [(1, 1), (1, 0), (0, 0)])
-def test_polycrystal128_cyclic_stress_against_oracle(prec, pred):
+@pytest.mark.parametrize("prec,pred,xy", [(1, 1, None), (1, 1, 0), (1, 1, 3), (1, 0, None), (0, 0, None)])
+def test_polycrystal128_cyclic_stress_against_oracle(prec, pred, xy):
     """The bench's workload (128^3 polycrystal, cyclic P11 with the rotation
     fixed), in the bench's launch configuration (FP32 inner, double-word
-    outer level, extrapolating predictor, autotuned kernels), with the
-    uniform predictor, and in plain FP64: the load steps the golden file
-    holds, against the oracle."""
+    outer level, extrapolating predictor, autotuned kernels), with each FP32
+    x-y schedule forced (xy: 0 one block per plane, 3 the two-CTA cluster
+    kernels for both passes), with the uniform predictor, and in plain FP64:
+    the load steps the golden file holds, against the oracle."""
     import torch
     mf = lib()
     g = golden("c3_poly128")
     ctx = poly128(mf, prec)
     ctx.set_predictor(pred)
+    if xy is not None:
+        ctx.set_xy_cluster(xy)
     tol_mean, tol_field = (1e-10, 1e-8) if prec == mf.MF_FP64 else (1e-9, 1e-8)
     errs = run_steps(mf, ctx, g, tol_mean, tol_field, kappa=168.0, rotation_free=False)
-    print("poly128", prec, pred, g["steps_done"], errs)
+    print("poly128", prec, pred, xy, ctx.xy_schedule()[:2], g["steps_done"], errs)
     del ctx
     torch.cuda.empty_cache()
 

@@ -384,6 +384,52 @@ def test_persistent_xy_forward_is_identical(shape):
     np.testing.assert_array_equal(ys[0], ys[1])
 
 
+@pytest.mark.parametrize("which,nz", [(1, 16), (2, 16), (3, 16), (3, 128)])
+def test_cluster_xy_kernels_match_oracle(which, nz):
+    """The two-CTA cluster x-y kernels (bit 0 the forward pass, bit 1 the
+    inverse) in the FP32 operator on 128 x 128 planes: element-wise against
+    the FP64 oracle within the FP32 operator bound, and against the
+    per-plane kernels to FP32 rounding (the radix-2 y stage moved before the
+    x transform changes only the order of the roundings)."""
+    import torch
+    mf = lib()
+    shape = (128, 128, nz)
+    ctx, om, F = make(mf, shape, mf.MF_FP32_INNER, "svk", seed=23)
+    ctx.constitutive()
+    x = inputs.random_field((nz, 128, 128), 24)
+    xt = torch_field(x, torch.float32)
+    ys = {}
+    for w in (0, which):
+        ctx.set_xy_cluster(w)
+        assert ctx.xy_schedule()[:2] == (2 if w & 1 else 0, 2 if w & 2 else 0)
+        y = torch.full_like(xt, float("nan"))
+        ctx.matvec(xt, y, MASKS[2])
+        ys[w] = y.cpu().numpy().astype(np.float64)
+    _, K = om.PK(F)
+    ref = osolver.matvec(K, x.astype(np.float32).astype(np.float64), MASKS[2])
+    c_cl = fp32_operator_error(ys[which].reshape(ref.shape), ref)
+    c_pp = fp32_operator_error(ys[0].reshape(ref.shape), ref)
+    d = rel(ys[which], ys[0])
+    print("cluster x-y", which, shape, "c", c_cl, "per-plane c", c_pp, "cluster vs per-plane", d)
+    assert d < 1e-5
+
+
+def test_cluster_xy_choice_is_validated():
+    mf = lib()
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(128, 128, 16, mf.MF_FP64).set_xy_cluster(1)          # FP32 inner only
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(64, 64, 64, mf.MF_FP32_INNER).set_xy_cluster(1)      # 128 x 128 planes only
+    with pytest.raises(mf.MixFFTError):
+        mf.Context(128, 128, 16, mf.MF_FP32_INNER).set_xy_cluster(4)
+    ctx = mf.Context(128, 128, 16, mf.MF_FP32_INNER)
+    ctx.set_xy_cluster(2)
+    assert ctx.xy_schedule()[:2] == (0, 2)
+    ctx.set_xy_persistent(1)
+    ctx.set_xy_cluster(3)
+    assert ctx.xy_schedule()[:2] == (2, 2)   # the cluster forward pass takes precedence
+
+
 def test_persistent_xy_forward_solve_and_validation():
     """A load step with the persistent kernel in the CG loop gives the same
     fields as with the per-plane kernel; the choice is validated."""
