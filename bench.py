@@ -36,7 +36,8 @@ SEED = 1003
 TOL_NEWTON, TOL_CG, CG_REL = 1e-8, 1e-10, 1e-4
 WORKLOAD = ("polycrystal 128^3, 200-grain Voronoi, SVK cubic (168/121/75 GPa) rotated per grain, "
             "cyclic stress P11 +-0.2 GPa in 20 steps (F12=F13=F23=0), FP32 inner CG / double-word outer "
-            "(averages, control and Newton update in FP64), extrapolated Newton start")
+            "(averages, control and Newton update in FP64), Newton start interpolated quadratically from the "
+            "last three converged states")
 METRIC = ("Newton load steps/s at 128^3 (FP32-inner CG / double-word outer), polycrystal cyclic stress "
           "control")
 # algorithmic bytes per voxel of each kernel of one CG iteration.  FP32 (matrix-
@@ -408,7 +409,7 @@ def run_batched(args):
         n = cell["n"]
         c = mf.Context(n, n, n, mf.MF_FP32_INNER, stream=torch.cuda.Stream())
         c.set_material(mf.MF_NEOHOOKE, cell["params"], cell["phase"])
-        c.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+        c.set_predictor(mf.MF_PRED_QUADRATIC)
         ctxs.append(c)
     masks = np.stack([cell["mask"] for cell in cells])
     targets = np.stack([cell["target"] for cell in cells])
@@ -435,7 +436,7 @@ def run_batched(args):
         sizes[str(cell["n"])] = sizes.get(str(cell["n"]), 0) + 1
     res = {"workload": (f"{BATCH_CELLS} sphere-particle neo-Hookean cells, sizes from {{32,48,64,96}}^3 "
                         f"(seed {BATCH_SEED}), vf U(0.1,0.3), contrast U(5,50), random mixed control, "
-                        f"{BATCH_STEPS} load steps, FP32 inner / double-word outer, extrapolated Newton starts; "
+                        f"{BATCH_STEPS} load steps, FP32 inner / double-word outer, extrapolated (quadratic) Newton starts; "
                         "all cells one graph launch (mf_solve_batch)"),
            "cells_by_size": sizes, "voxels_total": voxels,
            "batch_s": t_batch, "sequential_s": t_seq,
@@ -546,10 +547,10 @@ def run_paper_cases(args):
     mask, target = inputs.history_mixed_strain11(10, 1.05)
     c2 = {"workload": f"{n}^3 RSA spheres r=4 vf 0.25 (seed 1002), neo-Hookean contrast 10, "
                       "F11 -> 1.05 in 10 steps, other components stress free"}
-    for name, prec, forcing, pred in (("fp32_inner", mf.MF_FP32_INNER, None, mf.MF_PRED_EXTRAPOLATE),
+    for name, prec, forcing, pred in (("fp32_inner", mf.MF_FP32_INNER, None, mf.MF_PRED_QUADRATIC),
                                       ("fp32_inner_uniform_predictor", mf.MF_FP32_INNER, None, mf.MF_PRED_UNIFORM),
                                       ("fp64", mf.MF_FP64, 0, mf.MF_PRED_UNIFORM),
-                                      ("fp64_forcing", mf.MF_FP64, 1, mf.MF_PRED_EXTRAPOLATE)):
+                                      ("fp64_forcing", mf.MF_FP64, 1, mf.MF_PRED_QUADRATIC)):
         ctx = mf.Context(n, n, n, prec)
         ctx.set_material(mf.MF_NEOHOOKE, params, phs)
         ctx.set_predictor(pred)
@@ -681,10 +682,10 @@ def run_ours(args):
 
     ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
-    # each step starts from the last converged state extrapolated along the
-    # last load increment (mf_set_predictor); the paper's uniform start is
-    # timed beside it below
-    ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+    # each step starts from the quadratic through the last three converged
+    # states (mf_set_predictor); the linear extrapolation and the paper's
+    # uniform start are timed beside it below
+    ctx.set_predictor(mf.MF_PRED_QUADRATIC)
     ztile, ztile_ms, _, _ = ctx.autotune()
     xy_fwd, xy_inv, xy_ms = ctx.xy_schedule()
 
@@ -739,7 +740,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     uniform_ms = a.elapsed_time(b) / args.steps
     its_uniform = [(int(x), int(y)) for x, y in zip(o_uni["newton"], o_uni["cg"])]
+    # linear extrapolation along the last load increment, whole history
     ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+    steps(ctx, 0, 1)
+    ctx.set_F(None)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    o_lin = steps(ctx, 0, args.steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    linear_ms = a.elapsed_time(b) / args.steps
+    its_linear = [(int(x), int(y)) for x, y in zip(o_lin["newton"], o_lin["cg"])]
+    ctx.set_predictor(mf.MF_PRED_QUADRATIC)
     steps(ctx, 0, 1)
 
     # end to end through the C ABI with host buffers: step inputs go in as
@@ -838,8 +852,8 @@ def run_ours(args):
     ctx64.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
     steps(ctx64, 0, 1)
     fp64 = {}
-    for name, forcing, pred in (("plain", 0, mf.MF_PRED_UNIFORM), ("plain_extrapolated", 0, mf.MF_PRED_EXTRAPOLATE),
-                                ("forcing", 1, mf.MF_PRED_EXTRAPOLATE)):
+    for name, forcing, pred in (("plain", 0, mf.MF_PRED_UNIFORM), ("plain_extrapolated", 0, mf.MF_PRED_QUADRATIC),
+                                ("forcing", 1, mf.MF_PRED_QUADRATIC)):
         ctx64.set_inexact_newton(forcing)
         ctx64.set_predictor(pred)
         steps(ctx64, 0, 1)
@@ -854,7 +868,7 @@ def run_ours(args):
         fp64[name] = {
             "ms_per_step": a.elapsed_time(b) / nacc,
             "newton_cg_per_step": [(int(x), int(y)) for x, y in zip(o["newton"], o["cg"])], "steps": nacc}
-    # accuracy, lockstep: FP32 inner (double-word outer, extrapolated
+    # accuracy, lockstep: FP32 inner (double-word outer, quadratic
     # starts) against plain FP64 with the paper's uniform start
     ctx64.set_inexact_newton(0)
     ctx64.set_predictor(mf.MF_PRED_UNIFORM)
@@ -874,14 +888,14 @@ def run_ours(args):
                 "Fbar_max_rel": max(acc["Fbar"]), "Pbar_max_abs_over_C11": max(acc["Pbar"]),
                 "F_field_max_rel": max(acc["F_field"]),
                 "per_step": {k: [float("%.3g" % v) for v in acc[k]] for k in ("Fbar", "Pbar", "F_field")},
-                "note": ("FP32 inner with double-word outer arithmetic and extrapolated starts (the timed "
+                "note": ("FP32 inner with double-word outer arithmetic and quadratic starts (the timed "
                          "configuration) against the plain FP64 path with uniform starts, every step of the "
                          "history, same tolerances; <P> error over C11 = 168")}
-    # the FP64 path with forcing (and extrapolated starts) against plain FP64
+    # the FP64 path with forcing (and quadratic starts) against plain FP64
     # at the end of the history
     F64p = ctx64.get_fields()[0]
     ctx64.set_inexact_newton(1)
-    ctx64.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+    ctx64.set_predictor(mf.MF_PRED_QUADRATIC)
     ctx64.set_F(None)
     of = steps(ctx64, 0, nacc)
     F64f = ctx64.get_fields()[0]
@@ -968,6 +982,7 @@ def run_ours(args):
             "fp32_inner_dw_outer_per_call_median": float(np.median(step_ms)),
             "fp32_inner_fp64_outer": fp64_outer_ms,
             "fp32_inner_dw_outer_uniform_predictor": uniform_ms,
+            "fp32_inner_dw_outer_linear_predictor": linear_ms,
             "fp64_plain": fp64["plain"]["ms_per_step"],
             "fp64_plain_extrapolated": fp64["plain_extrapolated"]["ms_per_step"],
             "fp64_forcing": fp64["forcing"]["ms_per_step"],
@@ -976,21 +991,24 @@ def run_ours(args):
                 "fp32_inner_dw_outer": ("the timed configuration: FP32 inner CG; outer level (P, residual "
                                         "transforms) in double-word FP32 (about 48 bits), FP32 first residual "
                                         "of a step that did not start extrapolated; averages, control and "
-                                        "Newton update in FP64; each step starts from the last converged state "
-                                        "extrapolated along the last load increment"),
+                                        "Newton update in FP64; each step starts from the quadratic through the "
+                                        "last three converged states (distinct loads) at the new load"),
+                "fp32_inner_dw_outer_linear_predictor": ("the same with the start extrapolated linearly along the "
+                                                         "last load increment"),
                 "fp32_inner_dw_outer_uniform_predictor": ("the same with the paper's uniform start (last "
                                                           "converged state, strain-controlled components "
                                                           "shifted to the new F-bar)"),
-                "fp64_plain_extrapolated": "plain FP64, CG to the absolute tolerance, extrapolated starts",
+                "fp64_plain_extrapolated": "plain FP64, CG to the absolute tolerance, quadratic starts",
                 "fp32_inner_fp64_outer": "FP32 inner CG, outer level (P and every residual) in strict FP64",
                 "fp64_plain": "every step in FP64, CG to the absolute tolerance (Sec. 4's rule), uniform starts",
-                "fp64_forcing": ("every step in FP64 with the same inexact-Newton forcing and extrapolated starts "
+                "fp64_forcing": ("every step in FP64 with the same inexact-Newton forcing and quadratic starts "
                                  "as the FP32-inner path (mf_set_inexact_newton): same stopping rule")},
             "ratio_fp64_plain_over_fp32_inner": fp64["plain"]["ms_per_step"] / (total_ms / args.steps),
             "ratio_fp64_forcing_over_fp32_inner": fp64["forcing"]["ms_per_step"] / (total_ms / args.steps)},
         "accuracy_fp32_inner_vs_fp64": accuracy,
         "iterations": {"fp32_inner_newton_cg_per_step": its,
                        "fp32_inner_uniform_predictor_newton_cg_per_step": its_uniform,
+                       "fp32_inner_linear_predictor_newton_cg_per_step": its_linear,
                        "fp64_plain_extrapolated_newton_cg_per_step": fp64["plain_extrapolated"]["newton_cg_per_step"],
                        "fp64_plain_newton_cg_per_step": fp64["plain"]["newton_cg_per_step"],
                        "fp64_forcing_newton_cg_per_step": fp64["forcing"]["newton_cg_per_step"]},

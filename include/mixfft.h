@@ -54,7 +54,7 @@ typedef enum { MF_FP64 = 0, MF_FP32_INNER = 1 } mf_precision;
 typedef enum { MF_NEOHOOKE = 0, MF_SVK_CUBIC = 1 } mf_model;
 typedef enum { MF_OUTER_DOUBLE_WORD = 0, MF_OUTER_FP64 = 1 } mf_outer_arith;
 typedef enum { MF_PROJ_FP32 = 0, MF_PROJ_OUTER = 1, MF_PROJ_AUTO = 2 } mf_projection_arith;
-typedef enum { MF_PRED_UNIFORM = 0, MF_PRED_EXTRAPOLATE = 1 } mf_predictor;
+typedef enum { MF_PRED_UNIFORM = 0, MF_PRED_EXTRAPOLATE = 1, MF_PRED_QUADRATIC = 2 } mf_predictor;
 
 typedef struct mf_ctx mf_ctx;
 
@@ -413,10 +413,18 @@ int mf_set_projection_arith(mf_ctx* ctx, int arith);
  * F + alpha (F - F_prev), alpha the projection of this step's increment of the
  * prescribed values on the last one (1 along a ramp, -1 back across a
  * reversal), then shifted as above; the first residual of such a step runs
- * in the outer arithmetic and its inner solve to cg_rel.  The converged state
- * is the same to the Newton tolerance; the iteration counts drop along
- * smooth load paths.  The two converged steps are remembered across mf_solve
- * calls (not across mf_set_F, mf_set_material, mf_load_F or a failed step).
+ * in the outer arithmetic, and its inner solve is forced to 0.1 tol_newton
+ * over the expected size of its first correction (the larger of the last
+ * two steps' first corrections relative to F), within [cg_rel,
+ * sqrt(cg_rel)].  MF_PRED_QUADRATIC: with three converged steps of the same
+ * mask whose prescribed values lie on one line at distinct positions, F is
+ * the quadratic through the three states (Lagrange weights in the position
+ * along that line; the converged state of a hyperelastic law is a function
+ * of the load), else as MF_PRED_EXTRAPOLATE; one more field of 9 N doubles
+ * in the workspace holds the third state.  The converged state is the same
+ * to the Newton tolerance; the iteration counts drop along smooth load
+ * paths.  The converged steps are remembered across mf_solve calls (not
+ * across mf_set_F, mf_set_material, mf_load_F or a failed step).
  * MF_INVALID_ARG for another value. */
 int mf_set_predictor(mf_ctx* ctx, int kind);
 

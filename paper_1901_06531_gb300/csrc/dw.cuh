@@ -85,6 +85,52 @@ __device__ __forceinline__ dw& operator-=(dw& a, dw b) { a = a - b; return a; }
 
 __device__ __forceinline__ dwc cmake(dw a, dw b) { dwc r; r.x = a; r.y = b; return r; }
 
+#ifndef MF_NO_F32X2
+// Complex double-word add and subtract with the real and imaginary parts in
+// the two lanes of packed FP32 instructions (add.f32x2, sub.f32x2): the same
+// operations in the same order as dwops::add on each part, so the results
+// are those of the scalar form bit for bit.
+namespace dwpk {
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(u64 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ u64 add(u64 a, u64 b) {
+  u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 sub(u64 a, u64 b) {
+  u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// (a + b) or (a - b) per part; NEG: subtract
+template <bool NEG>
+__device__ __forceinline__ dwc addsub(dwc a, dwc b) {
+  const u64 A = pk(a.x.hi, a.y.hi), B = pk(b.x.hi, b.y.hi);
+  const u64 s = NEG ? sub(A, B) : add(A, B);
+  const u64 bb = sub(s, A);
+  // TwoSum error: (a.hi - (s - bb)) + (b.hi - bb), with b.hi negated for NEG
+  const u64 e0 = sub(A, sub(s, bb));
+  const u64 e = NEG ? sub(e0, add(B, bb)) : add(e0, sub(B, bb));
+  const u64 L = NEG ? sub(pk(a.x.lo, a.y.lo), pk(b.x.lo, b.y.lo)) : add(pk(a.x.lo, a.y.lo), pk(b.x.lo, b.y.lo));
+  const u64 t = add(e, L);
+  const u64 s2 = add(s, t);
+  const u64 e2 = sub(t, sub(s2, s));
+  dwc r;
+  upk(s2, r.x.hi, r.y.hi);
+  upk(e2, r.x.lo, r.y.lo);
+  return r;
+}
+}  // namespace dwpk
+__device__ __forceinline__ dwc cadd(dwc a, dwc b) { return dwpk::addsub<false>(a, b); }
+__device__ __forceinline__ dwc csub(dwc a, dwc b) { return dwpk::addsub<true>(a, b); }
+#endif
+
 // Complex products with the TwoProd errors of both real products gathered
 // before one TwoSum (fewer operations than four double-word products and
 // two double-word sums).  a b (SIGN = -1) or a conj(b) pieces are formed by

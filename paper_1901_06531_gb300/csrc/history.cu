@@ -186,6 +186,105 @@ __global__ void k_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, in
 // start is close to the solution: its first residual runs in the outer
 // arithmetic (FP32 rounding, relative to abs(P), would no longer be small
 // against it).
+// The quadratic predictor's start of a step (MF_PRED_QUADRATIC).  The
+// converged state of a hyperelastic law is a function of the load, so F at
+// the new target is interpolated from the kept states with this step's
+// mask: the last converged one (in F, target t1) and those in slots A and B
+// (targets t2, t3).  With A and B usable and the three targets on one line
+// at distinct positions: Lagrange weights in the position s along that line
+// (s = 0 at t1); with one of them: linear along the line through it; else no
+// extrapolation.  A target at a kept one gets that state exactly.  Then the
+// last converged state takes a slot: the one holding its own target (a
+// repeated load), else the one holding this step's target (the step
+// reconverges that state), else the older one; so the slots keep distinct
+// loads and a reversal returns to a kept state.  Returns 1 when F is
+// extrapolated.
+__device__ bool same_target(const double* a, const double* b) {
+  double d = 0.0, m = 0.0;
+  for (int c = 0; c < 9; ++c) {
+    d += (a[c] - b[c]) * (a[c] - b[c]);
+    m += a[c] * a[c] + b[c] * b[c];
+  }
+  return d <= 1e-24 * m;
+}
+
+__device__ int quadratic_start(HistState* hs, const StepIn& row) {
+  bool okF = hs->nprev >= 1, okA = hs->nprev >= 2, okB = hs->nprev >= 3;
+  for (int c = 0; c < 9; ++c) {
+    if (row.mask[c] != hs->mprev[c]) okF = false;
+    if (row.mask[c] != hs->mprev2[c]) okA = false;
+    if (row.mask[c] != hs->mprev3[c]) okB = false;
+  }
+  okA = okA && okF && !same_target(hs->t2, hs->t1);
+  okB = okB && okF && !same_target(hs->t3, hs->t1);
+  double w1 = 0.0, w2 = 0.0;
+  int ex = 0;
+  if (okA || okB) {
+    const double* tn = okA ? hs->t2 : hs->t3;
+    double nd = 0.0;
+    for (int c = 0; c < 9; ++c) nd += (tn[c] - hs->t1[c]) * (tn[c] - hs->t1[c]);
+    nd = sqrt(nd);
+    double st = 0.0;
+    for (int c = 0; c < 9; ++c) st += (row.target[c] - hs->t1[c]) * (tn[c] - hs->t1[c]) / nd;
+    if (okA && okB) {
+      double sB = 0.0, q3 = 0.0;
+      for (int c = 0; c < 9; ++c) sB += (hs->t3[c] - hs->t1[c]) * (hs->t2[c] - hs->t1[c]) / nd;
+      for (int c = 0; c < 9; ++c) {
+        const double off = (hs->t3[c] - hs->t1[c]) - sB * (hs->t2[c] - hs->t1[c]) / nd;
+        q3 += off * off;
+      }
+      const double sA = nd;
+      const bool on_line = q3 <= 1e-20 * (sB * sB + sA * sA);
+      const bool distinct = fabs(sB) > 1e-6 * sA && fabs(sB - sA) > 1e-6 * sA;
+      if (on_line && distinct) {
+        const double a1 = st * (st - sB) / (sA * (sA - sB));
+        const double a2 = st * (st - sA) / (sB * (sB - sA));
+        // far outside the three states the weights amplify their rounding
+        if (fabs(1.0 - a1 - a2) + fabs(a1) + fabs(a2) <= 20.0) {
+          w1 = a1;
+          w2 = a2;
+          ex = 1;
+        }
+      }
+    }
+    if (!ex) {
+      // linear along the line through the usable slot
+      if (okA) w1 = st / nd;
+      else w2 = st / nd;
+      ex = 1;
+    }
+  }
+  hs->quad = ex;
+  hs->w[1] = w1;
+  hs->w[2] = w2;
+  hs->w[0] = 1.0 - w1 - w2;
+  for (int c = 0; c < 9; ++c)
+    hs->pmean[c] = hs->fmean1[c] + w1 * (hs->fmean2[c] - hs->fmean1[c]) + w2 * (hs->fmean3[c] - hs->fmean1[c]);
+  // the slot for the last converged state (none before the first one)
+  if (hs->nprev >= 1) {
+    int dst;
+    if (hs->nprev < 2) dst = 0;
+    else if (same_target(hs->t1, hs->t2)) dst = 0;
+    else if (hs->nprev < 3) dst = 1;
+    else if (same_target(hs->t1, hs->t3)) dst = 1;
+    else if (same_target(row.target, hs->t2)) dst = 0;   // this step reconverges that state
+    else if (same_target(row.target, hs->t3)) dst = 1;
+    else dst = hs->age2 <= hs->age3 ? 0 : 1;
+    hs->dst = dst;
+    double* tt = dst == 0 ? hs->t2 : hs->t3;
+    double* fm = dst == 0 ? hs->fmean2 : hs->fmean3;
+    unsigned char* mm = dst == 0 ? hs->mprev2 : hs->mprev3;
+    for (int c = 0; c < 9; ++c) {
+      tt[c] = hs->t1[c];
+      fm[c] = hs->fmean1[c];
+      mm[c] = hs->mprev[c];
+    }
+    if (dst == 0) hs->age2 = hs->nseen;
+    else hs->age3 = hs->nseen;
+  }
+  return ex;
+}
+
 __global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle h_first, int set_first) {
   const StepIn& row = t.in[hs->k];
   bool same = hs->nprev >= 2;
@@ -203,9 +302,12 @@ __global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHa
     num += d1 * d0;
     den += d0 * d0;
   }
-  const int ex = (hs->extrap && same && den > 0.0) ? 1 : 0;
-  hs->extrapolated = ex;
+  int ex = (hs->extrap == 1 && same && den > 0.0) ? 1 : 0;
   hs->alpha = ex ? num / den : 0.0;
+  hs->quad = 0;
+  hs->dst = -1;
+  if (hs->extrap == 2) ex = quadratic_start(hs, row);
+  hs->extrapolated = ex;
   hs->nn = 0;
   hs->ncg = 0;
   hs->ratio = INFINITY;
@@ -217,12 +319,14 @@ __global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHa
 }
 
 // Predictor of a load step (Sec. 2.1, 2.3): with the extrapolating
-// predictor, F <- F + alpha (F - Fprev) (and Fprev <- F, the state the next
-// step extrapolates from); then every strain-controlled component shifted
-// uniformly so that its average is the prescribed F-bar.  After an FP32
-// update (after_update) only the shift, to the averages of that update.
-__global__ void k_predictor_hist(double* __restrict__ F, double* __restrict__ Fprev, long long N,
-                                 const HistState* hs, const Scalars* sc, bool after_update) {
+// predictor, F <- F + alpha (F - Fprev) and Fprev <- F, the state the next
+// step extrapolates from; with the quadratic one (Fprev2 given: the slots A
+// = Fprev, B = Fprev2) the weights and the slot of quadratic_start; then
+// every strain-controlled component shifted uniformly so that its average
+// is the prescribed F-bar.  After an FP32 update (after_update) only the
+// shift, to the averages of that update.
+__global__ void k_predictor_hist(double* __restrict__ F, double* __restrict__ Fprev, double* __restrict__ Fprev2,
+                                 long long N, const HistState* hs, const Scalars* sc, bool after_update) {
   double shift[9];
   const double a = (!after_update && hs->extrapolated) ? hs->alpha : 0.0;
   for (int c = 0; c < 9; ++c) {
@@ -231,8 +335,31 @@ __global__ void k_predictor_hist(double* __restrict__ F, double* __restrict__ Fp
     else mean = sc->meanF[c] + a * (sc->meanF[c] - hs->fmean2[c]);
     shift[c] = hs->mask[c] ? 0.0 : hs->target[c] - mean;
   }
+  if (!after_update && Fprev2 != nullptr) {
+    // quadratic predictor: F <- F + w1 (A - F) + w2 (B - F) + shift, and the
+    // last converged F into its slot (quadratic_start chose both)
+    const bool qx = hs->extrapolated && hs->quad;
+    const double v1 = qx ? hs->w[1] : 0.0, v2 = qx ? hs->w[2] : 0.0;
+    const int dst = hs->dst;
+    double qshift[9];
+    for (int c = 0; c < 9; ++c) qshift[c] = hs->mask[c] ? 0.0 : hs->target[c] - (qx ? hs->pmean[c] : sc->meanF[c]);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const double f = F[c * N + v];
+        double fn = f;
+        if (v1 != 0.0) fn += v1 * (Fprev[c * N + v] - f);
+        if (v2 != 0.0) fn += v2 * (Fprev2[c * N + v] - f);
+        if (dst == 0) Fprev[c * N + v] = f;
+        else if (dst == 1) Fprev2[c * N + v] = f;
+        F[c * N + v] = fn + qshift[c];
+      }
+    }
+    return;
+  }
   if (!after_update && Fprev != nullptr) {
-    // every component: Fprev <- F, F <- F + alpha (F - Fprev) + shift
+    // every component: the kept state shifted back by one step, F predicted
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -361,15 +488,19 @@ __global__ void k_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaG
   hs->launches += hs->extrapolated ? kernels_ex : kernels;
   if (!hs->status) {
     const int k = hs->k;
-    // the converged step joins the two the predictor extrapolates from
+    // the converged step joins the states the predictor extrapolates from
+    // (the quadratic predictor's slots were filled at the step's start)
     for (int c = 0; c < 9; ++c) {
-      hs->t2[c] = hs->t1[c];
+      if (hs->extrap != 2) {
+        hs->t2[c] = hs->t1[c];
+        hs->fmean2[c] = hs->fmean1[c];
+      }
       hs->t1[c] = hs->target[c];
-      hs->fmean2[c] = hs->fmean1[c];
       hs->fmean1[c] = sc->meanF[c];
       hs->mprev[c] = hs->mask[c];
     }
-    hs->nprev = hs->nprev < 2 ? hs->nprev + 1 : 2;
+    hs->nprev = hs->nprev < 3 ? hs->nprev + 1 : 3;
+    hs->nseen += 1;
     StepOut& row = t.out[k];
     for (int c = 0; c < 9; ++c) {
       row.Fbar[c] = sc->meanF[c];
@@ -670,9 +801,9 @@ cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphCondition
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, long long N, const HistState* hs, const Scalars* sc,
-                                     bool after_update, cudaStream_t st) {
-  k_predictor_hist<<<grid_for(N), kThreads, 0, st>>>(F, Fprev, N, hs, sc, after_update);
+cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, double* Fprev2, long long N, const HistState* hs,
+                                     const Scalars* sc, bool after_update, cudaStream_t st) {
+  k_predictor_hist<<<grid_for(N), kThreads, 0, st>>>(F, Fprev, Fprev2, N, hs, sc, after_update);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

@@ -222,13 +222,20 @@ struct HistState {
   double tol_newton, tol_cg, cg_rel, kappa;
   double first_ratio;      // size of the last step's first correction (persists across launches)
   double first_ratio2;     // the same of the step before (persists across launches)
-  int extrap;              // the predictor extrapolates from the last two converged steps
-  // persists across launches (the host keeps it between calls): the last two
-  // converged steps behind F, for the extrapolating predictor
-  int nprev;               // consecutive converged steps recorded (0, 1, 2)
-  double t1[9], t2[9];     // their targets (t1 the latest)
-  double fmean1[9], fmean2[9];   // their <F>
-  unsigned char mprev[9];  // their control mask
+  int extrap;              // predictor: 0 uniform, 1 linear from the last two converged
+                           // steps, 2 quadratic from the last three (MF_PRED_*)
+  // persists across launches (the host keeps it between calls): the last
+  // three converged steps behind F, for the extrapolating predictors
+  // linear (extrap 1): t1, t2 the last two steps' targets.  Quadratic
+  // (extrap 2): t1 the last step's (the state in F), t2 and t3 those of the
+  // states kept in the two extra fields (slots A and B, distinct targets;
+  // a new state replaces a slot with its target, else the older slot)
+  int nprev;               // converged states recorded (0 .. 3)
+  double t1[9], t2[9], t3[9];             // their targets
+  double fmean1[9], fmean2[9], fmean3[9]; // their <F>
+  unsigned char mprev[9], mprev2[9], mprev3[9];   // their control masks
+  int nseen;               // converged steps so far (the slots' ages)
+  int age2, age3;          // when slots A and B were written
   // state
   int k;                   // step of the table being solved
   int nn, ncg;             // Newton and CG iterations of the step so far
@@ -241,7 +248,11 @@ struct HistState {
   double ratio;            // max_v abs(dF_v) / abs(<F>) of the last correction
   double cg_rel_cur;       // forcing of the current CG solve (0: tol_cg alone)
   int extrapolated;        // this step started from an extrapolated F
-  double alpha;            // its extrapolation factor
+  double alpha;            // its linear extrapolation factor
+  int quad;                // quadratic predictor: the weights below apply
+  double w[3];             // F <- F + w1 (A - F) + w2 (B - F); w0 = 1 - w1 - w2
+  double pmean[9];         // the predicted <F> (quadratic predictor)
+  int dst;                 // slot the last converged F is copied to: 0 A, 1 B, -1 none
   double target[9], pbar[9];
   unsigned char mask[9];
   Defl defl;               // null rotations of the current Newton iteration
@@ -275,8 +286,8 @@ cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphCondition
 // Fprev (9N, may be null when the predictor does not extrapolate): the
 // converged F before the current one; the step's predictor replaces it by
 // the current F and extrapolates F along the last increment
-cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, long long N, const HistState* hs, const Scalars* sc,
-                                     bool after_update, cudaStream_t st);
+cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, double* Fprev2, long long N, const HistState* hs,
+                                     const Scalars* sc, bool after_update, cudaStream_t st);
 cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
                                  cudaGraphConditionalHandle h_newton, bool first, cudaStream_t st);
 cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, bool first, cudaStream_t st);

@@ -241,7 +241,7 @@ struct mf_ctx {
   size_t oF, oP, ob, oK, ox, or_, op, op2, oAp, oH, ospec, ophase, oscale, oscale32, otable,
       otable32, otabledw, opart, osc, ores, oxpos, oxk, oxe, oyk, ozk, otw64, otw32, otwdw;
   // load-history state and tables (history.cu)
-  size_t ohist, othout, othin, oFprev;
+  size_t ohist, othout, othin, oFprev, oFprev2;
   int predictor = MF_PRED_UNIFORM;  // mf_set_predictor
   HistState keep;                   // the history fields that persist between calls (nprev, t1, ...)
   char* pin = nullptr;              // pinned staging of the history block (cudaMallocHost)
@@ -948,7 +948,7 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
     }
     // FP32 corrections carry a rounding-level average on the strain-controlled
     // components; the FP64 outer level re-imposes F-bar there
-    if (e == cudaSuccess) e = mf_launch_predictor_hist(F, nullptr, N, hs, sc, true, s1);
+    if (e == cudaSuccess) e = mf_launch_predictor_hist(F, nullptr, nullptr, N, hs, sc, true, s1);
   } else if (e == cudaSuccess) {
     e = mf_launch_newton_update_hist(F, c->ws + c->ox, false, N, part, c->pw_blocks, hs, sc, s1);
   }
@@ -1009,7 +1009,8 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
     e = cap_begin(caps[1], B1);
     if (e == cudaSuccess) {
       const long long ls = g_mf_launches;
-      const bool extrap = c->predictor == MF_PRED_EXTRAPOLATE;
+      const bool extrap = c->predictor != MF_PRED_UNIFORM;
+      double* Fprev2 = c->predictor == MF_PRED_QUADRATIC ? c->at<double>(c->oFprev2) : nullptr;
       const bool dwr = c->dw_residual();
       // with the extrapolating predictor on a double-word context, the first
       // residual's arithmetic follows the start (IF: extrapolated -> outer)
@@ -1018,7 +1019,8 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
       if (choose) e = cap_handle(caps[1], &h_first);
       if (e == cudaSuccess) e = mf_launch_step_begin(hs, t, choose ? &h_first : nullptr, caps[1]);
       if (e == cudaSuccess)
-        e = mf_launch_predictor_hist(F, extrap ? c->at<double>(c->oFprev) : nullptr, N, hs, sc, false, caps[1]);
+        e = mf_launch_predictor_hist(F, extrap ? c->at<double>(c->oFprev) : nullptr, Fprev2, N, hs, sc, false,
+                                     caps[1]);
       // the pass after the predictor: FP64 P and K, or (FP32 inner) H and the
       // rotation moments, with P itself in FP32 for an FP32 first residual;
       // then the first residual
@@ -1118,13 +1120,20 @@ cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target,
   hh->first_ratio = c->first_ratio;
   hh->first_ratio2 = c->keep.first_ratio2;
   hh->ratio = INFINITY;
-  hh->extrap = c->predictor == MF_PRED_EXTRAPOLATE ? 1 : 0;
+  hh->extrap = c->predictor;
   hh->nprev = c->keep.nprev;
   memcpy(hh->t1, c->keep.t1, sizeof(hh->t1));
   memcpy(hh->t2, c->keep.t2, sizeof(hh->t2));
+  memcpy(hh->t3, c->keep.t3, sizeof(hh->t3));
   memcpy(hh->fmean1, c->keep.fmean1, sizeof(hh->fmean1));
   memcpy(hh->fmean2, c->keep.fmean2, sizeof(hh->fmean2));
+  memcpy(hh->fmean3, c->keep.fmean3, sizeof(hh->fmean3));
   memcpy(hh->mprev, c->keep.mprev, sizeof(hh->mprev));
+  memcpy(hh->mprev2, c->keep.mprev2, sizeof(hh->mprev2));
+  memcpy(hh->mprev3, c->keep.mprev3, sizeof(hh->mprev3));
+  hh->nseen = c->keep.nseen;
+  hh->age2 = c->keep.age2;
+  hh->age3 = c->keep.age3;
   StepIn* in = pin_in(c);
   for (int k = k0; k < k1; ++k) {
     StepIn& r = in[k - k0];
@@ -1280,6 +1289,7 @@ int mf_create(mf_ctx** out, int nx, int ny, int nz, int precision, void* stream)
   c->othout = c->ohist + hist_state_bytes();
   c->othin = take((size_t)kHistSteps * sizeof(StepIn));
   c->oFprev = take(9 * N * sizeof(double));
+  c->oFprev2 = take(9 * N * sizeof(double));
   c->ores = take(9 * sizeof(double));
   c->oxpos = take(nx * sizeof(int));
   c->oxk = take(nx * sizeof(int));
@@ -1923,7 +1933,8 @@ int mf_set_projection_arith(mf_ctx* c, int arith) {
 }
 
 int mf_set_predictor(mf_ctx* c, int kind) {
-  if (!c || (kind != MF_PRED_UNIFORM && kind != MF_PRED_EXTRAPOLATE)) return MF_INVALID_ARG;
+  if (!c || (kind != MF_PRED_UNIFORM && kind != MF_PRED_EXTRAPOLATE && kind != MF_PRED_QUADRATIC))
+    return MF_INVALID_ARG;
   if (c->predictor != kind) free_cg_graph(c);   // the captured histories hold the predictor's passes
   c->predictor = kind;
   return MF_OK;

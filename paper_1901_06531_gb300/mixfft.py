@@ -24,7 +24,7 @@ MF_FP64, MF_FP32_INNER = 0, 1
 MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
 MF_OUTER_DOUBLE_WORD, MF_OUTER_FP64 = 0, 1
 MF_PROJ_FP32, MF_PROJ_OUTER, MF_PROJ_AUTO = 0, 1, 2
-MF_PRED_UNIFORM, MF_PRED_EXTRAPOLATE = 0, 1
+MF_PRED_UNIFORM, MF_PRED_EXTRAPOLATE, MF_PRED_QUADRATIC = 0, 1, 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
@@ -389,7 +389,7 @@ class Context:
         _check("mf_set_outer_arith", _lib.mf_set_outer_arith(self.h, arith))
 
     def set_predictor(self, kind):
-        """mf_set_predictor: MF_PRED_UNIFORM (default) or MF_PRED_EXTRAPOLATE."""
+        """mf_set_predictor: MF_PRED_UNIFORM (default), MF_PRED_EXTRAPOLATE or MF_PRED_QUADRATIC."""
         _check("mf_set_predictor", _lib.mf_set_predictor(self.h, int(kind)))
 
     def set_inexact_newton(self, on):

@@ -98,7 +98,8 @@ def test_option_setters_validate_without_gpu(lib):
     assert lib.mf_set_inexact_newton(h, 2) == mixfft.MF_INVALID_ARG
     assert lib.mf_set_predictor(h, mixfft.MF_PRED_EXTRAPOLATE) == mixfft.MF_OK
     assert lib.mf_set_predictor(h, mixfft.MF_PRED_UNIFORM) == mixfft.MF_OK
-    assert lib.mf_set_predictor(h, 2) == mixfft.MF_INVALID_ARG
+    assert lib.mf_set_predictor(h, mixfft.MF_PRED_QUADRATIC) == mixfft.MF_OK
+    assert lib.mf_set_predictor(h, 3) == mixfft.MF_INVALID_ARG
     lib.mf_destroy(h)
     assert lib.mf_create(ctypes.byref(h), 64, 64, 32, mixfft.MF_FP32_INNER, None) == 0
     assert lib.mf_set_projection_arith(h, mixfft.MF_PROJ_OUTER) == mixfft.MF_OK

@@ -152,7 +152,7 @@ def poly128(mf, prec):
     return ctx
 
 
-@pytest.mark.parametrize("prec,pred", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("prec,pred", [(0, 0), (1, 0), (1, 1), (1, 2)])
 def test_spheres64_mixed_control_against_oracle(prec, pred):
     """64^3 random spheres (r = 4, 25 %), neo-Hookean contrast 10, F11 -> 1.05
     in 10 steps with the other eight components stress free: every step
@@ -167,14 +167,16 @@ def test_spheres64_mixed_control_against_oracle(prec, pred):
     print("spheres64", prec, pred, errs)
 
 
-@pytest.mark.parametrize("prec,pred,xy", [(1, 1, None), (1, 1, 0), (1, 1, 3), (1, 0, None), (0, 0, None)])
+@pytest.mark.parametrize("prec,pred,xy", [(1, 2, None), (1, 1, None), (1, 1, 0), (1, 1, 3), (1, 0, None),
+                                          (0, 0, None), (0, 2, None)])
 def test_polycrystal128_cyclic_stress_against_oracle(prec, pred, xy):
     """The bench's workload (128^3 polycrystal, cyclic P11 with the rotation
     fixed), in the bench's launch configuration (FP32 inner, double-word
     outer level, extrapolating predictor, autotuned kernels), with each FP32
     x-y schedule forced (xy: 0 one block per plane, 3 the two-CTA cluster
     kernels for both passes), with the uniform predictor, and in plain FP64:
-    the load steps the golden file holds, against the oracle."""
+    the load steps the golden file holds, against the oracle; pred 2 is the
+    quadratic predictor."""
     import torch
     mf = lib()
     g = golden("c3_poly128")

@@ -317,7 +317,7 @@ def test_extrapolating_predictor_reaches_the_oracle(prec):
     mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(12, 0.2))
     ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
     outs = {}
-    for pred in (mf.MF_PRED_UNIFORM, mf.MF_PRED_EXTRAPOLATE):
+    for pred in (mf.MF_PRED_UNIFORM, mf.MF_PRED_EXTRAPOLATE, mf.MF_PRED_QUADRATIC):
         ctx = mf.Context(n, n, n, prec)
         ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
         ctx.set_predictor(pred)
@@ -328,14 +328,18 @@ def test_extrapolating_predictor_reaches_the_oracle(prec):
         assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) / 168.0 < tol_mean
         assert rel(F, ref["F"]) < 1e-8
         outs[pred] = out
-    u, x = outs[mf.MF_PRED_UNIFORM], outs[mf.MF_PRED_EXTRAPOLATE]
-    print("predictor", prec, u["newton"].tolist(), x["newton"].tolist(), u["cg"].sum(), x["cg"].sum())
+    u, x, q = outs[mf.MF_PRED_UNIFORM], outs[mf.MF_PRED_EXTRAPOLATE], outs[mf.MF_PRED_QUADRATIC]
+    print("predictor", prec, u["newton"].tolist(), x["newton"].tolist(), q["newton"].tolist(),
+          u["cg"].sum(), x["cg"].sum(), q["cg"].sum())
     assert x["newton"].sum() < u["newton"].sum()
     assert x["cg"].sum() <= u["cg"].sum()
+    assert q["newton"].sum() <= x["newton"].sum()
 
 
-def test_extrapolating_predictor_across_calls():
-    """The predictor's two converged steps carry over between mf_solve calls:
+@pytest.mark.parametrize("pred", [1, 2])
+def test_extrapolating_predictor_across_calls(pred):
+    """The predictor's converged steps carry over between mf_solve calls
+    (two for the linear, three for the quadratic extrapolation):
     a history solved one step per call takes the same Newton iterations and
     reaches the same states as the same history in one call.  Not bit for
     bit: a launch recomputes <F> from the field (another summation order than
@@ -348,7 +352,7 @@ def test_extrapolating_predictor_across_calls():
     mask, target = inputs.fix_rotation(*inputs.history_cyclic_stress(8, 0.2))
     ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
     ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
-    ctx.set_predictor(mf.MF_PRED_EXTRAPOLATE)
+    ctx.set_predictor(pred)
     one = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
     F1, _ = ctx.get_fields()
     ctx.set_F(None)
