@@ -178,14 +178,6 @@ __global__ void k_hist_init(HistState* hs, cudaGraphConditionalHandle h_step, in
   cudaGraphSetConditional(h_step, hs->nsteps > 0 ? 1u : 0u);
 }
 
-// Load step k of the table: control mask, targets, P-bar (Sec. 2.3).  With
-// the extrapolating predictor and the last two converged steps at hand (same
-// mask), the factor alpha of the increment: the projection of this step's
-// target increment on the last one, alpha = dT_k . dT_(k-1) / abs(dT_(k-1))^2
-// (1 along a ramp, -1 back across a reversal of the load).  An extrapolated
-// start is close to the solution: its first residual runs in the outer
-// arithmetic (FP32 rounding, relative to abs(P), would no longer be small
-// against it).
 // The quadratic predictor's start of a step (MF_PRED_QUADRATIC).  The
 // converged state of a hyperelastic law is a function of the load, so F at
 // the new target is interpolated from the kept states with this step's
@@ -285,6 +277,14 @@ __device__ int quadratic_start(HistState* hs, const StepIn& row) {
   return ex;
 }
 
+// Load step k of the table: control mask, targets, P-bar (Sec. 2.3).  With
+// the extrapolating predictor and the last two converged steps at hand (same
+// mask), the factor alpha of the increment: the projection of this step's
+// target increment on the last one, alpha = dT_k . dT_(k-1) / abs(dT_(k-1))^2
+// (1 along a ramp, -1 back across a reversal of the load); with the
+// quadratic predictor, quadratic_start.  An extrapolated start is close to
+// the solution: its first residual runs in the outer arithmetic (FP32
+// rounding, relative to abs(P), would no longer be small against it).
 __global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle h_first, int set_first) {
   const StepIn& row = t.in[hs->k];
   bool same = hs->nprev >= 2;
@@ -404,7 +404,13 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
   // starts exact and its first correction says nothing about the next), and
   // the next about eta r, so eta = 0.1 tol_newton / r, kept within
   // [cg_rel, sqrt(cg_rel)] (the choice of forcing terms of inexact Newton
-  // methods from the expected convergence).
+  // methods from the expected convergence).  The upper bound matters when r
+  // is below tol_newton and the step ends on this correction: its error,
+  // about eta r, is carried into the next step's start by the extrapolating
+  // predictors with a gain of about eta sum abs(w) (7 for the quadratic one
+  // along a ramp); sqrt(cg_rel) keeps that gain far below one (0.1 would
+  // save three of seven CG iterations on the 128^3 polycrystal but leave the
+  // states 3-10 times farther from the FP64 solution).
   const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
   double eta = loose ? sqrt(hs->cg_rel) : hs->cg_rel;
   const double r = fmax(hs->first_ratio, hs->first_ratio2);
