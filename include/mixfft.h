@@ -424,7 +424,10 @@ int mf_set_projection_arith(mf_ctx* ctx, int arith);
  * in the workspace holds the third state.  The converged state is the same
  * to the Newton tolerance; the iteration counts drop along smooth load
  * paths.  The converged steps are remembered across mf_solve calls (not
- * across mf_set_F, mf_set_material, mf_load_F or a failed step).
+ * across mf_set_F, mf_set_material, mf_load_F or a failed step); after
+ * mf_set_F(NULL) (and at creation) F = I counts as the first one, the
+ * equilibrium at zero load (P-bar = 0, F-bar = I) under the first step's
+ * mask, since both laws give P(I) = 0.
  * MF_INVALID_ARG for another value. */
 int mf_set_predictor(mf_ctx* ctx, int kind);
 

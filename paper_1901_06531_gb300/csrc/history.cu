@@ -287,6 +287,18 @@ __device__ int quadratic_start(HistState* hs, const StepIn& row) {
 // rounding, relative to abs(P), would no longer be small against it).
 __global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle h_first, int set_first) {
   const StepIn& row = t.in[hs->k];
+  if (hs->ident) {
+    // the reference state as the last converged one, at this mask's zero
+    // load: P-bar = 0 on the stress-controlled components, F-bar = I on the
+    // strain-controlled ones (both laws give P(I) = 0)
+    for (int c = 0; c < 9; ++c) {
+      const double id = (c % 4 == 0) ? 1.0 : 0.0;
+      hs->t1[c] = row.mask[c] ? 0.0 : id;
+      hs->fmean1[c] = id;
+      hs->mprev[c] = row.mask[c];
+    }
+    hs->ident = 0;
+  }
   bool same = hs->nprev >= 2;
   for (int c = 0; c < 9; ++c) {
     const unsigned char m = row.mask[c];

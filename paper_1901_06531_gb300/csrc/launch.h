@@ -235,6 +235,9 @@ struct HistState {
   double fmean1[9], fmean2[9], fmean3[9]; // their <F>
   unsigned char mprev[9], mprev2[9], mprev3[9];   // their control masks
   int nseen;               // converged steps so far (the slots' ages)
+  int ident;               // F is the reference state F = I, in equilibrium at zero
+                           // load (P(I) = 0): a converged state whose target the
+                           // next step's mask gives (P-bar 0, F-bar = I)
   int age2, age3;          // when slots A and B were written
   // state
   int k;                   // step of the table being solved

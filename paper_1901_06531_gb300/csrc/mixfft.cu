@@ -1132,6 +1132,7 @@ cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target,
   memcpy(hh->mprev2, c->keep.mprev2, sizeof(hh->mprev2));
   memcpy(hh->mprev3, c->keep.mprev3, sizeof(hh->mprev3));
   hh->nseen = c->keep.nseen;
+  hh->ident = c->keep.ident;
   hh->age2 = c->keep.age2;
   hh->age3 = c->keep.age3;
   StepIn* in = pin_in(c);
@@ -1165,7 +1166,10 @@ int finish_history(mf_ctx* c, int k0, int k1, double* Fbar_out, double* Pbar_out
   }
   c->first_ratio = hs.first_ratio;
   c->keep = hs;
-  if (hs.status) c->keep.nprev = 0;
+  if (hs.status) {
+    c->keep.nprev = 0;
+    c->keep.ident = 0;
+  }
   c->have_K = false;
   c->have_H = false;
   g_mf_launches += hs.launches;
@@ -1470,7 +1474,10 @@ int mf_set_F(mf_ctx* c, const double* F_host) {
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
   c->keep.first_ratio2 = INFINITY;
-  c->keep.nprev = 0;   // the extrapolating predictor starts over
+  // the extrapolating predictors start over; F = I is itself a converged
+  // state (zero load), the first one they extrapolate from
+  c->keep.nprev = F_host ? 0 : 1;
+  c->keep.ident = F_host ? 0 : 1;
   const long long N = c->N;
   double* F = c->at<double>(c->oF);
   cudaError_t e;
@@ -1501,7 +1508,8 @@ int mf_load_F(mf_ctx* c, const double* F_dev) {
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
   c->keep.first_ratio2 = INFINITY;
-  c->keep.nprev = 0;   // the extrapolating predictor starts over
+  c->keep.nprev = 0;   // the extrapolating predictors start over
+  c->keep.ident = 0;
   const char* p = (const char*)F_dev;
   if (p + 9 * c->N * sizeof(double) > c->ws && p < c->ws + c->ws_need) return MF_INVALID_ARG;
   cudaError_t e = cudaMemcpyAsync(c->ws + c->oF, F_dev, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice,
