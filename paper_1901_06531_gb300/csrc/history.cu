@@ -433,9 +433,13 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
 }
 
 // Projection of the FP32 correction onto the range of G* before the update:
-// 0 none (a late correction below 1e-6 of F, after one that small), 1 FP32
-// transforms, 2 outer arithmetic (MF_PROJ_OUTER, or MF_PROJ_AUTO for a
-// correction expected to be at least kProjOuterAbove of F).
+// 0 none (a late correction below 1e-6 of F, after one that small; or the
+// first correction of an extrapolated step expected below kProjSkipBelow of
+// F: the FP32 rounding outside range(G*), about 1e-5 of a correction, is
+// then below 1e-13 of F), 1 FP32 transforms, 2 outer arithmetic
+// (MF_PROJ_OUTER, or MF_PROJ_AUTO for a correction expected to be at least
+// kProjOuterAbove of F).
+constexpr double kProjSkipBelow = 1e-8;
 __global__ void k_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, int first) {
   const int nn = hs->nn;
   const double ratio = hs->ratio;
@@ -443,7 +447,9 @@ __global__ void k_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, 
       hs->proj_arith == MF_PROJ_OUTER ||
       (hs->proj_arith == MF_PROJ_AUTO &&
        (first ? !(hs->first_ratio < kProjOuterAbove) : !(ratio < 10.0 * kProjOuterAbove)));
-  const bool project = outer || nn < 2 || !(ratio < 1e-6);
+  const bool tiny_first = first && hs->extrapolated && hs->proj_arith != MF_PROJ_OUTER &&
+                          fmax(hs->first_ratio, hs->first_ratio2) < kProjSkipBelow;
+  const bool project = !tiny_first && (outer || nn < 2 || !(ratio < 1e-6));
   const int kind = !project ? 0 : (outer ? 2 : 1);
   hs->proj_kind = kind;
   cudaGraphSetConditional(h_proj, (unsigned)kind);
