@@ -486,11 +486,66 @@ __global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHa
   }
   if (st && !hs->status) hs->status = st;
   const int last = (ratio < hs->tol_newton && !hs->res32) ? 1 : 0;
-  const int kind = last ? 0 : 1;
+  // a step that ends on an FP32 correction applied as computed (no
+  // projection, no deflation), with more steps to come in this launch:
+  // <P> at the final F from the linearisation, <P(F)> + <K:dF>; the error,
+  // of the order of abs(K') abs(dF)^2 with abs(dF) < tol_newton abs(F), is
+  // far below the averages' accuracy.  The last step of a launch evaluates
+  // P, so the fields a caller reads are exact.
+  const bool lin = last && hs->f32 && hs->proj_kind == 0 && hs->defl.m == 0 && hs->k + 1 < hs->nsteps;
+  const int kind = last ? (lin ? 2 : 0) : 1;
   hs->last = last;
   hs->res32 = 0;
   hs->cons_kind = kind;
   cudaGraphSetConditional(h_cons, (unsigned)kind);
+}
+
+// Column sums of the 9 components of t (one partial per block and column)
+// and their finish: the linearised end-of-step averages (cons kind 2).
+__global__ void __launch_bounds__(kThreads) k_lin_sums(const float* __restrict__ t, long long N,
+                                                       double* __restrict__ partials) {
+  __shared__ double red[9][kThreads / 32];
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] += (double)t[c * N + v];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    double s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[c][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[threadIdx.x][w];
+    partials[blockIdx.x * 9 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_lin_fin(const double* __restrict__ partials, int nblk, long long N, const HistState* hs,
+                          Scalars* sc) {
+  __shared__ double red[kThreads / 32];
+  for (int c = 0; c < 9; ++c) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[b * 9 + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+      sc->meanP[c] += tot / (double)N;
+      // the update's averages, with F-bar re-imposed on the strain-controlled components
+      sc->meanF[c] = hs->mask[c] ? sc->meanF_new[c] : hs->target[c];
+    }
+    __syncthreads();
+  }
 }
 
 // After the constitutive pass that follows an update: its failures, the
@@ -822,6 +877,14 @@ cudaError_t mf_launch_hist_init(HistState* hs, cudaGraphConditionalHandle h_step
 cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle* h_first, cudaStream_t st) {
   k_step_begin<<<1, 1, 0, st>>>(hs, t, h_first ? *h_first : cudaGraphConditionalHandle(), h_first ? 1 : 0);
   g_mf_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_lin_means(const float* t, long long N, double* partials, int nblk, const HistState* hs,
+                                Scalars* sc, cudaStream_t st) {
+  k_lin_sums<<<nblk, kThreads, 0, st>>>(t, N, partials);
+  k_lin_fin<<<1, kThreads, 0, st>>>(partials, nblk, N, hs, sc);
+  g_mf_launches += 2;
   return cudaGetLastError();
 }
 

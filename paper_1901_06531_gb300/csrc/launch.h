@@ -264,7 +264,7 @@ struct HistState {
 // Kernel counts of the captured pieces of one Newton iteration, for the
 // launch counter: fixed part, per projection kind, per final/next pass.
 struct IterCounts {
-  int fixed, proj[3], cons[2], cg_body;
+  int fixed, proj[3], cons[3], cg_body;
 };
 // One row of the step table (in) and of the result table (out).
 struct StepIn {
@@ -289,6 +289,11 @@ cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphCondition
 // Fprev (9N, may be null when the predictor does not extrapolate): the
 // converged F before the current one; the step's predictor replaces it by
 // the current F and extrapolates F along the last increment
+// <P> and <F> at the end of a step from the linearisation at the iteration's
+// start (FP32 inner, cons kind 2): t = K(H):x applied by the tangent pass
+// beforehand; <P> += <t>, <F> <- the post-update averages.
+cudaError_t mf_launch_lin_means(const float* t, long long N, double* partials, int nblk, const HistState* hs,
+                                Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, double* Fprev2, long long N, const HistState* hs,
                                      const Scalars* sc, bool after_update, cudaStream_t st);
 cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,

@@ -958,16 +958,27 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   cudaGraphConditionalHandle h_cons;
   if (e == cudaSuccess) e = cap_handle(s1, &h_cons);
   if (e == cudaSuccess) e = mf_launch_newton_post(hs, sc, h_cons, s1);
-  constexpr int nkind = 2;
-  cudaGraph_t cb[nkind] = {nullptr, nullptr};
+  // (FP32 inner) 2: the step ends, its averages from the linearisation:
+  // t = K(H):x with the tangent pass, <P> += <t>
+  const int nkind = f32 ? 3 : 2;
+  cudaGraph_t cb[3] = {nullptr, nullptr, nullptr};
   if (e == cudaSuccess) e = cap_conditional(s1, h_cons, cudaGraphCondTypeSwitch, nkind, cb);
   for (int kind = 0; kind < nkind && e == cudaSuccess; ++kind) {
     const long long lb = g_mf_launches;
     e = cap_begin(s2, cb[kind]);
     if (e != cudaSuccess) break;
-    const bool more = kind != 0;
-    int st = run_constitutive(c, more && !f32, more && f32, more && f32, false, s2);
-    if (!st && more && capture_residual(c, mask, false, s2) != cudaSuccess) st = MF_CUDA_ERROR;
+    int st = 0;
+    if (kind == 2) {
+      cudaError_t el = mf_launch_tangent(c->ws + c->ox, nullptr, nullptr, nullptr, true, tangent_kind(c), false,
+                                         tangent_args(c), c->ws + c->oAp, N, nullptr, c->pw_blocks, sc, s2);
+      if (el == cudaSuccess)
+        el = mf_launch_lin_means(c->at<float>(c->oAp), N, part, c->pw_blocks, hs, sc, s2);
+      if (el != cudaSuccess) st = MF_CUDA_ERROR;
+    } else {
+      const bool more = kind != 0;
+      st = run_constitutive(c, more && !f32, more && f32, more && f32, false, s2);
+      if (!st && more && capture_residual(c, mask, false, s2) != cudaSuccess) st = MF_CUDA_ERROR;
+    }
     e = cap_end(s2, st ? cudaErrorUnknown : cudaSuccess);
     cnt.cons[kind] = (int)(g_mf_launches - lb);
     in_bodies += g_mf_launches - lb;

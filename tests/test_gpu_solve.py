@@ -359,6 +359,10 @@ def test_extrapolating_predictor_across_calls(pred):
     for k in range(mask.shape[0]):
         o = ctx.solve(mask[k:k + 1], target[k:k + 1], 1e-8, 1e-10, cg_rel=1e-4)
         assert rel(o["Fbar"][0], one["Fbar"][k]) < 1e-10
+        # within one call a step that ends on an unprojected FP32 correction
+        # takes <P> from the linearisation <P> + <K:dF>; one step per call
+        # always evaluates P at the final F
+        assert np.max(np.abs(o["Pbar"][0] - one["Pbar"][k])) / 168.0 < 1e-10
         np.testing.assert_array_equal(o["newton"][0], one["newton"][k])
     F2, _ = ctx.get_fields()
     # the FP32 inner solves carry the last-bit differences of their inputs
