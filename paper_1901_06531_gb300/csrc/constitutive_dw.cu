@@ -23,32 +23,34 @@ __device__ __forceinline__ constexpr int vgt(int i, int j) {
   return i == j ? i : (i + j == 3 ? 3 : (i + j == 2 ? 4 : 5));
 }
 
+// Every sum of products below is one compensated accumulation (DwAcc).
 __device__ __forceinline__ void svk_dw(const dw (&h)[9], const dw* __restrict__ cv, dw (&P)[9]) {
   dw e6[6];
   auto E = [&](int a, int b) {
-    dw s = h[3 * a + b] + h[3 * b + a];
+    DwAcc s(h[3 * a + b]);
+    s.add(h[3 * b + a]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) s = s + h[3 * k + a] * h[3 * k + b];
-    return half(s);
+    for (int k = 0; k < 3; ++k) s.fma(h[3 * k + a], h[3 * k + b]);
+    return half(s.value());
   };
   e6[0] = E(0, 0); e6[1] = E(1, 1); e6[2] = E(2, 2);
   e6[3] = twice(E(1, 2)); e6[4] = twice(E(0, 2)); e6[5] = twice(E(0, 1));
   dw sv[6];
 #pragma unroll
   for (int I = 0; I < 6; ++I) {
-    dw acc = cv[6 * I] * e6[0];
+    DwAcc acc(cv[6 * I] * e6[0]);
 #pragma unroll
-    for (int J = 1; J < 6; ++J) acc = acc + cv[6 * I + J] * e6[J];
-    sv[I] = acc;
+    for (int J = 1; J < 6; ++J) acc.fma(cv[6 * I + J], e6[J]);
+    sv[I] = acc.value();
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      dw acc = sv[vgt(i, j)];
+      DwAcc acc(sv[vgt(i, j)]);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) acc = acc + h[3 * i + k] * sv[vgt(k, j)];
-      P[3 * i + j] = acc;
+      for (int k = 0; k < 3; ++k) acc.fma(h[3 * i + k], sv[vgt(k, j)]);
+      P[3 * i + j] = acc.value();
     }
 }
 
@@ -175,9 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
                                                               double* __restrict__ partials, Scalars* sc) {
   constexpr int NC = MOM ? 36 : 18;
   __shared__ double tot[NC];
-  dw acc[18];
-#pragma unroll
-  for (int c = 0; c < 18; ++c) acc[c] = dw(0.0f, 0.0f);
+  DwAcc acc[18];   // per-thread sums of F and P, normalised once at the end
   float mom[18];
 #pragma unroll
   for (int c = 0; c < 18; ++c) mom[c] = 0.f;
@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
       if constexpr (P32) Pf[c * N + v] = p[c].hi;
       else P[c * N + v] = dw_join(p[c]);
       if (WH) H[c * N + v] = h[c].hi;
-      acc[c] = acc[c] + f[c];
-      acc[9 + c] = acc[9 + c] + p[c];
+      acc[c].add(f[c]);
+      acc[9 + c].add(p[c]);
     }
     if (MOM) {
 #pragma unroll
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
   if (bad) atomicOr(&sc->flags, MF_FLAG_NONPOS_J);
   double a[NC];
 #pragma unroll
-  for (int c = 0; c < 18; ++c) a[c] = dw_join(acc[c]);
+  for (int c = 0; c < 18; ++c) a[c] = dw_join(acc[c].value());
   if constexpr (MOM) {
 #pragma unroll
     for (int c = 0; c < 18; ++c) a[18 + c] = (double)mom[c];

@@ -83,6 +83,38 @@ __device__ __forceinline__ dw operator/(dw a, dw b) { return dwops::div(a, b); }
 __device__ __forceinline__ dw& operator+=(dw& a, dw b) { a = a + b; return a; }
 __device__ __forceinline__ dw& operator-=(dw& a, dw b) { a = a - b; return a; }
 
+// Compensated sum of double-word terms and products with one normalisation
+// at the end (Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J.
+// Sci. Comput. 2005, algorithm Dot2, on the high parts): the running head s
+// is updated by TwoSum, so the head is exact up to the error e, which
+// gathers the TwoSum and TwoProd errors and the low-part terms in one FP32
+// word.  Each error added to e is of order 2^-24 of the term, so its own
+// rounding is of order 2^-48: the accuracy of a chain of double-word
+// operations, in about 12 FP32 operations per product term instead of 20.
+struct DwAcc {
+  float s, e;
+  __device__ __forceinline__ DwAcc() : s(0.0f), e(0.0f) {}
+  __device__ __forceinline__ explicit DwAcc(dw a) : s(a.hi), e(a.lo) {}
+  __device__ __forceinline__ void head(float p, float pe) {   // s += p (TwoSum), pe joins the error
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(err, pe));
+  }
+  __device__ __forceinline__ void add(dw a) { head(a.hi, a.lo); }
+  // += a b
+  __device__ __forceinline__ void fma(dw a, dw b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);   // TwoProd error
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    pe = __fmaf_rn(a.lo, b.lo, pe);          // kept: one sign for squares, as in mul
+    head(p, pe);
+  }
+  __device__ __forceinline__ dw value() const { return dwops::fast_two_sum(s, e); }
+};
+
 __device__ __forceinline__ dwc cmake(dw a, dw b) { dwc r; r.x = a; r.y = b; return r; }
 
 #ifndef MF_NO_F32X2

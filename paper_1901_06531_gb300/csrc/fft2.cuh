@@ -10,6 +10,8 @@
 // the inverse is its adjoint (digit-reversed input).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace fft2 {
@@ -70,10 +72,19 @@ __device__ __forceinline__ C twc(C v) {
     typedef decltype(v.x) T;
     const T c = (T)c16(e16);
     const T s = INV ? (T)s16(e16) : (T)-s16(e16);       // W^e = cos - i sin
-    C r;
-    r.x = v.x * c - v.y * s;
-    r.y = v.x * s + v.y * c;
-    return r;
+    if constexpr (!std::is_floating_point<T>::value) {
+      // double word: the fused complex product (its TwoProd errors gathered
+      // before one TwoSum per part) instead of four products and two sums
+      C w;
+      w.x = c;
+      w.y = s;
+      return cmul(v, w);
+    } else {
+      C r;
+      r.x = v.x * c - v.y * s;
+      r.y = v.x * s + v.y * c;
+      return r;
+    }
   }
 }
 
