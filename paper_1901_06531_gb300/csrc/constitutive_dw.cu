@@ -57,12 +57,36 @@ __device__ __forceinline__ void svk_dw(const dw (&h)[9], const dw* __restrict__ 
 // Returns false when J <= 0 (P is then zero).
 __device__ __forceinline__ bool neohooke_dw(const dw (&h)[9], const dw (&f)[9], dw mu, dw lam, dw (&P)[9]) {
   const dw one(1.0f, 0.0f);
-  const dw trH = h[0] + h[4] + h[8];
-  dw trH2 = h[0] * h[0] + h[4] * h[4] + h[8] * h[8];
-  trH2 = trH2 + twice(h[1] * h[3] + h[2] * h[6] + h[5] * h[7]);
-  const dw detH = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
-                  h[2] * (h[3] * h[7] - h[4] * h[6]);
-  const dw Jm1 = trH + half(trH * trH - trH2) + detH;
+  // a b - c d
+  auto det2 = [](dw a, dw b, dw c, dw d) {
+    DwAcc s;
+    s.fma(a, b);
+    s.fma(-c, d);
+    return s.value();
+  };
+  DwAcc tr(h[0]);
+  tr.add(h[4]);
+  tr.add(h[8]);
+  const dw trH = tr.value();
+  DwAcc t2;   // tr(H H) = sum_i h_ii^2 + 2 sum_(i<j) h_ij h_ji
+  t2.fma(h[0], h[0]);
+  t2.fma(h[4], h[4]);
+  t2.fma(h[8], h[8]);
+  t2.fma(twice(h[1]), h[3]);
+  t2.fma(twice(h[2]), h[6]);
+  t2.fma(twice(h[5]), h[7]);
+  const dw trH2 = t2.value();
+  DwAcc dh;   // det H by the first row
+  dh.fma(h[0], det2(h[4], h[8], h[5], h[7]));
+  dh.fma(-h[1], det2(h[3], h[8], h[5], h[6]));
+  dh.fma(h[2], det2(h[3], h[7], h[4], h[6]));
+  DwAcc q;    // (tr^2 H - tr H^2) / 2
+  q.fma(trH, trH);
+  q.add(-trH2);
+  DwAcc jm(trH);
+  jm.add(half(q.value()));
+  jm.add(dh.value());
+  const dw Jm1 = jm.value();
   const dw J = Jm1 + one;
   if (!(J.hi > 0.0f)) {
 #pragma unroll
@@ -71,19 +95,24 @@ __device__ __forceinline__ bool neohooke_dw(const dw (&h)[9], const dw (&f)[9], 
   }
   const dw iJ = one / J;
   dw G[9];   // F^-T = cof(F) / J
-  G[0] = (f[4] * f[8] - f[5] * f[7]) * iJ;
-  G[1] = (f[5] * f[6] - f[3] * f[8]) * iJ;
-  G[2] = (f[3] * f[7] - f[4] * f[6]) * iJ;
-  G[3] = (f[2] * f[7] - f[1] * f[8]) * iJ;
-  G[4] = (f[0] * f[8] - f[2] * f[6]) * iJ;
-  G[5] = (f[1] * f[6] - f[0] * f[7]) * iJ;
-  G[6] = (f[1] * f[5] - f[2] * f[4]) * iJ;
-  G[7] = (f[2] * f[3] - f[0] * f[5]) * iJ;
-  G[8] = (f[0] * f[4] - f[1] * f[3]) * iJ;
+  G[0] = det2(f[4], f[8], f[5], f[7]) * iJ;
+  G[1] = det2(f[5], f[6], f[3], f[8]) * iJ;
+  G[2] = det2(f[3], f[7], f[4], f[6]) * iJ;
+  G[3] = det2(f[2], f[7], f[1], f[8]) * iJ;
+  G[4] = det2(f[0], f[8], f[2], f[6]) * iJ;
+  G[5] = det2(f[1], f[6], f[0], f[7]) * iJ;
+  G[6] = det2(f[1], f[5], f[2], f[4]) * iJ;
+  G[7] = det2(f[2], f[3], f[0], f[5]) * iJ;
+  G[8] = det2(f[0], f[4], f[1], f[3]) * iJ;
   const dw lnJ = dw_split(log1p(dw_join(Jm1)));
   const dw cg = lam * lnJ - mu;
 #pragma unroll
-  for (int c = 0; c < 9; ++c) P[c] = mu * f[c] + cg * G[c];
+  for (int c = 0; c < 9; ++c) {
+    DwAcc pc;
+    pc.fma(mu, f[c]);
+    pc.fma(cg, G[c]);
+    P[c] = pc.value();
+  }
   return true;
 }
 
