@@ -368,3 +368,39 @@ def test_extrapolating_predictor_across_calls(pred):
     # the FP32 inner solves carry the last-bit differences of their inputs
     # into the fields at FP32-solve level (measured 8e-13)
     assert rel(F2, F1) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_quadratic_predictor_on_a_bent_path_with_a_mask_change(prec):
+    """MF_PRED_QUADRATIC where its conditions fail part of the time: the
+    prescribed values turn a corner (the three kept targets are not on one
+    line: linear start along the last leg, or none) and the control mask
+    changes halfway (kept states of the other mask are not used).  Every
+    step reaches the oracle's converged state (uniform start) to the
+    precision's tolerance."""
+    mf = lib()
+    n = 16
+    g, params, R = polycrystal((n, n, n), 12, 53)
+    om = omat.Material(g, omat.SVK_CUBIC, params, R)
+    m1 = np.array([1, 0, 0, 1, 1, 0, 1, 1, 1], np.uint8)   # P11 ramp, F12 = F13 = F23 = 0
+    m2 = np.array([1, 0, 0, 0, 1, 0, 0, 1, 1], np.uint8)   # F21, F31 prescribed as well
+    mask = np.array([m1] * 5 + [m2] * 5)
+    target = np.zeros((10, 9))
+    p11 = [0.03, 0.06, 0.09, 0.09, 0.09, 0.12, 0.15, 0.15, 0.12, 0.09]
+    p22 = [0.0, 0.0, 0.0, 0.03, 0.06, 0.06, 0.06, 0.09, 0.12, 0.12]
+    for k in range(10):
+        target[k, 0] = p11[k]
+        target[k, 4] = p22[k]
+    ref = osolver.solve(om, mask, target, 1e-10, 1e-12)
+    ctx = mf.Context(n, n, n, prec)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    ctx.set_predictor(mf.MF_PRED_QUADRATIC)
+    out = ctx.solve(mask, target, 1e-8, 1e-10, cg_rel=1e-4)
+    F, _ = ctx.get_fields()
+    tol_mean = 1e-10 if prec == mf.MF_FP64 else 1e-9
+    print("bent path", prec, out["newton"].tolist(), out["cg"].tolist())
+    assert rel(out["Fbar"], ref["Fbar"]) < tol_mean
+    assert np.max(np.abs(out["Pbar"] - ref["Pbar"])) / 168.0 < tol_mean
+    assert rel(F, ref["F"]) < 1e-8
+    check_control(out, mask, target, tol_mean * 168.0, 1e-14)
+
