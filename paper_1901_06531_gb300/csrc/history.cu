@@ -414,20 +414,27 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
   // the Newton tolerance.  Its correction is about the larger of the last two
   // steps' first ones (r; two, because the step across a load reversal
   // starts exact and its first correction says nothing about the next), and
-  // the next about eta r, so eta = 0.1 tol_newton / r, kept within
-  // [cg_rel, sqrt(cg_rel)] (the choice of forcing terms of inexact Newton
-  // methods from the expected convergence).  The upper bound matters when r
-  // is below tol_newton and the step ends on this correction: its error,
-  // about eta r, is carried into the next step's start by the extrapolating
-  // predictors with a gain of about eta sum abs(w) (7 for the quadratic one
-  // along a ramp); sqrt(cg_rel) keeps that gain far below one (0.1 would
-  // save three of seven CG iterations on the 128^3 polycrystal but leave the
-  // states 3-10 times farther from the FP64 solution).
+  // the next about eta r, so eta = 0.1 tol_newton / r (the choice of
+  // forcing terms of inexact Newton methods from the expected convergence),
+  // at least cg_rel.  Its upper bound matters when r is below tol_newton and
+  // the step ends on this correction: the step leaves an error of about eta
+  // times its start's error, and the start carries the kept states' errors
+  // with the gain sum abs(w) of the extrapolation (7 for the quadratic one
+  // along a ramp: w = 3, -3, 1), so the states' errors evolve as e' = eta
+  // (tau + sum abs(w) e), tau the extrapolation's own error.  The bound
+  // 0.25 / sum abs(w) holds that gain to 1/4 (errors from earlier steps
+  // shrink fourfold per step, and e settles near 1.3 eta tau); it is kept
+  // within [sqrt(cg_rel), 0.1], 0.1 keeping the computed correction, whose
+  // size the Newton test reads, within about 10 %.
   const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
   double eta = loose ? sqrt(hs->cg_rel) : hs->cg_rel;
   const double r = fmax(hs->first_ratio, hs->first_ratio2);
-  if (first && hs->extrapolated && r > 0.0 && isfinite(r))
-    eta = fmin(sqrt(hs->cg_rel), fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
+  if (first && hs->extrapolated && r > 0.0 && isfinite(r)) {
+    const double gain = hs->quad ? fabs(hs->w[0]) + fabs(hs->w[1]) + fabs(hs->w[2])
+                                 : 1.0 + 2.0 * fabs(hs->alpha);
+    const double hi = fmax(sqrt(hs->cg_rel), fmin(0.1, 0.25 / fmax(gain, 1.0)));
+    eta = fmin(hi, fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
+  }
   hs->cg_rel_cur = hs->forcing ? eta : 0.0;
   cudaGraphSetConditional(h_go, 1u);
 }
