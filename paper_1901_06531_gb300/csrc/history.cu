@@ -429,11 +429,14 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
   const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
   double eta = loose ? sqrt(hs->cg_rel) : hs->cg_rel;
   const double r = fmax(hs->first_ratio, hs->first_ratio2);
+  hs->eta_hi = 0.0;
   if (first && hs->extrapolated && r > 0.0 && isfinite(r)) {
     const double gain = hs->quad ? fabs(hs->w[0]) + fabs(hs->w[1]) + fabs(hs->w[2])
                                  : 1.0 + 2.0 * fabs(hs->alpha);
     const double hi = fmax(sqrt(hs->cg_rel), fmin(0.1, 0.25 / fmax(gain, 1.0)));
     eta = fmin(hi, fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
+    // refined at the CG start from this step's own first residual (k_fin_cg_init_h)
+    hs->eta_hi = hi;
   }
   hs->cg_rel_cur = hs->forcing ? eta : 0.0;
   cudaGraphSetConditional(h_go, 1u);
@@ -490,6 +493,10 @@ __global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHa
   if (hs->nn == 1) {
     hs->first_ratio2 = hs->first_ratio;
     hs->first_ratio = ratio;
+    if (hs->rms0 > 0.0 && isfinite(ratio)) {
+      hs->kr2 = hs->kr1;
+      hs->kr1 = ratio / hs->rms0;
+    }
   }
   if (st && !hs->status) hs->status = st;
   const int last = (ratio < hs->tol_newton && !hs->res32) ? 1 : 0;
@@ -651,8 +658,20 @@ __global__ void __launch_bounds__(kThreads) k_cg_init_h(const double* __restrict
   }
 }
 
+// CG start: r.r, the stop threshold rms(r) <= max(tol_cg, eta rms(r0)).  At
+// a step's first Newton iteration rms(r0) is recorded; for an extrapolated
+// step's first solve eta is refined from it: the first correction relative
+// to F has been close to k rms(r0) with the same k from step to step (k
+// reflects the operator's stiffness, not the quality of the start), so the
+// expected correction is r = 2 max(k of the last two steps) rms(r0) (2 a
+// margin) and eta = 0.1 tol_newton / r within the bounds of k_newton_pre.
+// This follows a change of the predictor's order (uniform, then linear,
+// then quadratic on a history's first steps), which the last steps' first
+// corrections alone do not see.  Too loose an eta costs at most one more
+// Newton iteration: a step ends only on a correction below tol_newton, and
+// the error it leaves is below eta tol_newton.
 __global__ void __launch_bounds__(kThreads) k_fin_cg_init_h(const double* __restrict__ partials, int npart,
-                                                            long long N, const HistState* hs, Scalars* sc) {
+                                                            long long N, HistState* hs, Scalars* sc) {
   __shared__ double shm[kThreads];
   double s = 0.0;
   for (int b = threadIdx.x; b < npart; b += kThreads) s += partials[b];
@@ -668,8 +687,17 @@ __global__ void __launch_bounds__(kThreads) k_fin_cg_init_h(const double* __rest
     sc->rr0 = rr;
     sc->alpha = 0.0;
     sc->beta = 0.0;
+    const double rms = sqrt(rr / (double)N);
+    if (hs->nn == 0) hs->rms0 = rms;
+    if (hs->eta_hi > 0.0 && hs->cg_rel_cur > 0.0) {
+      const double k = fmax(hs->kr1, hs->kr2);
+      if (k > 0.0 && isfinite(k) && rms > 0.0) {
+        const double r = 2.0 * k * rms;
+        hs->cg_rel_cur = fmin(hs->eta_hi, fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
+      }
+    }
     double thr = hs->tol_cg;
-    if (hs->cg_rel_cur > 0.0) thr = fmax(hs->tol_cg, hs->cg_rel_cur * sqrt(rr / (double)N));
+    if (hs->cg_rel_cur > 0.0) thr = fmax(hs->tol_cg, hs->cg_rel_cur * rms);
     sc->thr2N = thr * thr * (double)N;
     sc->done = (rr <= sc->thr2N) ? 1 : 0;
   }
@@ -936,7 +964,7 @@ cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, c
 }
 
 cudaError_t mf_launch_cg_init_hist(const double* b, void* r, bool f32, long long n9, double* partials, int nblk,
-                                   long long N, const HistState* hs, Scalars* sc, cudaStream_t st) {
+                                   long long N, HistState* hs, Scalars* sc, cudaStream_t st) {
   if (f32) k_cg_init_h<float><<<nblk, kThreads, 0, st>>>(b, (float*)r, n9, partials);
   else k_cg_init_h<double><<<nblk, kThreads, 0, st>>>(b, (double*)r, n9, partials);
   k_fin_cg_init_h<<<1, kThreads, 0, st>>>(partials, nblk, N, hs, sc);

@@ -222,6 +222,9 @@ struct HistState {
   double tol_newton, tol_cg, cg_rel, kappa;
   double first_ratio;      // size of the last step's first correction (persists across launches)
   double first_ratio2;     // the same of the step before (persists across launches)
+  double kr1, kr2;         // first correction / first rms(r0) of the last two steps (persist)
+  double rms0;             // rms of the current step's first residual
+  double eta_hi;           // upper bound of the current forcing (0: no refinement at the CG start)
   int extrap;              // predictor: 0 uniform, 1 linear from the last two converged
                            // steps, 2 quadratic from the last three (MF_PRED_*)
   // persists across launches (the host keeps it between calls): the last
@@ -309,7 +312,7 @@ cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, c
 // CG start with the tolerance and forcing of the current Newton iteration read
 // from the history state
 cudaError_t mf_launch_cg_init_hist(const double* b, void* r, bool f32, long long n9, double* partials, int nblk,
-                                   long long N, const HistState* hs, Scalars* sc, cudaStream_t st);
+                                   long long N, HistState* hs, Scalars* sc, cudaStream_t st);
 // CG counters reset for a loop inside a history graph; sets the loop's
 // condition (0 when the start already stopped it)
 cudaError_t mf_launch_cg_start_hist(Scalars* sc, int max_its, cudaGraphConditionalHandle h_cg, cudaStream_t st);

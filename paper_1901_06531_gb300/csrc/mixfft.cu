@@ -1130,6 +1130,10 @@ cudaError_t upload_history(mf_ctx* c, const uint8_t* mask, const double* target,
   hh->kappa = c->kappa;
   hh->first_ratio = c->first_ratio;
   hh->first_ratio2 = c->keep.first_ratio2;
+  hh->kr1 = c->keep.kr1;
+  hh->kr2 = c->keep.kr2;
+  hh->rms0 = 0.0;
+  hh->eta_hi = 0.0;
   hh->ratio = INFINITY;
   hh->extrap = c->predictor;
   hh->nprev = c->keep.nprev;
@@ -1485,6 +1489,7 @@ int mf_set_F(mf_ctx* c, const double* F_host) {
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
   c->keep.first_ratio2 = INFINITY;
+  c->keep.kr1 = c->keep.kr2 = 0.0;
   // the extrapolating predictors start over; F = I is itself a converged
   // state (zero load), the first one they extrapolate from
   c->keep.nprev = F_host ? 0 : 1;
@@ -1519,6 +1524,7 @@ int mf_load_F(mf_ctx* c, const double* F_dev) {
   if (!c->ws) return MF_NO_WORKSPACE;
   c->first_ratio = INFINITY;
   c->keep.first_ratio2 = INFINITY;
+  c->keep.kr1 = c->keep.kr2 = 0.0;
   c->keep.nprev = 0;   // the extrapolating predictors start over
   c->keep.ident = 0;
   const char* p = (const char*)F_dev;
