@@ -249,6 +249,7 @@ struct Scalars {
   double T[9];        // sum_v P_v F_v^T   (rotation moments, row-major)
   double S[9];        // sum_v F_v F_v^T
   double What[9];     // skew matrix of the last null-rotation projection
+  double lin[9];      // FP32 inner solve: sum over its iterations of alpha_k <t_k> (= <K:x>, x = sum alpha_k p_k)
   int flags;          // bit 0: breakdown, bit 1: nonpositive J, bit 2: non-finite
   int done;           // CG converged
   int its;            // CG iterations completed

@@ -12,6 +12,7 @@
 // from FP64 log1p of J - 1.  F is read and P written in FP64.
 #include "dw.cuh"
 #include "launch.h"
+#include "predict.cuh"
 
 namespace {
 
@@ -197,13 +198,17 @@ __device__ __forceinline__ void block_sum_dw(double (&v)[NC], double* out) {
 // Columns of the block partials: F 0-8, P 9-17, and with MOM T = sum P F^T
 // 18-26, S = sum F F^T 27-35 (FP32 products of the high parts: only used to
 // detect null rotations).  P32: P evaluated in FP32 from H and written, in
-// FP32, to Pf instead of P (the averages of F stay double word).
-template <int MODEL, bool WH, bool MOM, bool P32>
-__global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __restrict__ F, double* __restrict__ P,
+// FP32, to Pf instead of P (the averages of F stay double word).  PRED: the
+// load step's predictor (pred_coef) applied to F first, the predicted F
+// stored and evaluated (the pass is compute bound, so the predictor's loads
+// and stores cost little here against a pass of their own).
+template <int MODEL, bool WH, bool MOM, bool P32, bool PRED>
+__global__ void __launch_bounds__(kThreads) k_constitutive_dw(double* __restrict__ F, double* __restrict__ P,
                                                               float* __restrict__ Pf, float* __restrict__ H,
                                                               MatArgs m, const dw* __restrict__ table,
                                                               const float* __restrict__ table32, long long N,
-                                                              double* __restrict__ partials, Scalars* sc) {
+                                                              double* __restrict__ partials, Scalars* sc,
+                                                              PredArgs pa) {
   constexpr int NC = MOM ? 36 : 18;
   __shared__ double tot[NC];
   DwAcc acc[18];   // per-thread sums of F and P, normalised once at the end
@@ -211,11 +216,24 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
 #pragma unroll
   for (int c = 0; c < 18; ++c) mom[c] = 0.f;
   bool bad = false;
+  __shared__ PredCoef pk_s;   // the predictor's coefficients (PRED), read from shared memory at each use
+  if constexpr (PRED) {
+    if (threadIdx.x == 0) pk_s = pred_coef(pa, sc);
+    __syncthreads();
+  }
+  volatile PredCoef& pk = pk_s;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
        v += (long long)gridDim.x * blockDim.x) {
     double fd[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) fd[c] = F[c * N + v];
+    if constexpr (PRED) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        fd[c] = pred_apply(pa, pk, c, N, v, fd[c]);
+        F[c * N + v] = fd[c];
+      }
+    }
     const int ph = m.phase[v];
     dw h[9], f[9];
 #pragma unroll
@@ -282,17 +300,21 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(const double* __re
 }
 
 template <int MODEL>
-cudaError_t launch_model(const double* F, double* P, float* Pf, float* H, bool moments, const MatArgs& m,
-                         const dw* table, const float* table32, long long N, double* partials, int nblk,
-                         Scalars* sc, cudaStream_t st) {
-#define MF_CDW(WH, MOM, P32)                                                                               \
-  k_constitutive_dw<MODEL, WH, MOM, P32><<<nblk, kThreads, 0, st>>>(F, P, Pf, H, m, table, table32, N, \
-                                                                    partials, sc)
-  if (Pf && H && moments) MF_CDW(true, true, true);
-  else if (H && moments) MF_CDW(true, true, false);
-  else if (H) MF_CDW(true, false, false);
-  else if (moments) MF_CDW(false, true, false);
-  else MF_CDW(false, false, false);
+cudaError_t launch_model(double* F, double* P, float* Pf, float* H, bool moments, const MatArgs& m, const dw* table,
+                         const float* table32, long long N, double* partials, int nblk, Scalars* sc,
+                         const PredArgs* pred, cudaStream_t st) {
+  const PredArgs pa = pred ? *pred : PredArgs{nullptr, nullptr, nullptr, 0};
+#define MF_CDW(WH, MOM, P32, PR)                                                                               \
+  k_constitutive_dw<MODEL, WH, MOM, P32, PR><<<nblk, kThreads, 0, st>>>(F, P, Pf, H, m, table, table32, N, \
+                                                                        partials, sc, pa)
+  if (pred && Pf && H && moments) MF_CDW(true, true, true, true);
+  else if (pred && H && moments && !Pf) MF_CDW(true, true, false, true);
+  else if (pred) return cudaErrorInvalidValue;   // the predictor rides on the full passes only
+  else if (Pf && H && moments) MF_CDW(true, true, true, false);
+  else if (H && moments) MF_CDW(true, true, false, false);
+  else if (H) MF_CDW(true, false, false, false);
+  else if (moments) MF_CDW(false, true, false, false);
+  else MF_CDW(false, false, false, false);
 #undef MF_CDW
   return cudaGetLastError();
 }
@@ -301,12 +323,15 @@ cudaError_t launch_model(const double* F, double* P, float* Pf, float* H, bool m
 
 cudaError_t mf_launch_constitutive_dw(const double* F, double* P, float* H, bool moments, const MatArgs& m,
                                       const void* table_dw, long long N, double* partials, int nblk,
-                                      Scalars* sc, cudaStream_t st, float* Pf, const float* table32) {
+                                      Scalars* sc, cudaStream_t st, float* Pf, const float* table32,
+                                      const PredArgs* pred) {
   const dw* table = (const dw*)table_dw;
   if (Pf && !(H && moments && table32)) return cudaErrorInvalidValue;   // the FP32-P pass is the full one
+  // F is written only by the predictor (pred non-null)
+  double* Fw = const_cast<double*>(F);
   cudaError_t e = m.model == 0
-                      ? launch_model<0>(F, P, Pf, H, moments, m, table, table32, N, partials, nblk, sc, st)
-                      : launch_model<1>(F, P, Pf, H, moments, m, table, table32, N, partials, nblk, sc, st);
+                      ? launch_model<0>(Fw, P, Pf, H, moments, m, table, table32, N, partials, nblk, sc, pred, st)
+                      : launch_model<1>(Fw, P, Pf, H, moments, m, table, table32, N, partials, nblk, sc, pred, st);
   g_mf_launches += 1;
   if (e != cudaSuccess) return e;
   return mf_launch_fin_means(partials, nblk, moments ? 36 : 18, N, sc, st);

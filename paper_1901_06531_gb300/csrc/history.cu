@@ -12,6 +12,7 @@
 #include "../../include/mixfft.h"
 #include "dw.cuh"
 #include "launch.h"
+#include "predict.cuh"
 
 namespace {
 
@@ -330,65 +331,33 @@ __global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHa
   if (set_first) cudaGraphSetConditional(h_first, ex ? 1u : 0u);
 }
 
-// Predictor of a load step (Sec. 2.1, 2.3): with the extrapolating
-// predictor, F <- F + alpha (F - Fprev) and Fprev <- F, the state the next
-// step extrapolates from; with the quadratic one (Fprev2 given: the slots A
-// = Fprev, B = Fprev2) the weights and the slot of quadratic_start; then
-// every strain-controlled component shifted uniformly so that its average
-// is the prescribed F-bar.  After an FP32 update (after_update) only the
-// shift, to the averages of that update.
-__global__ void k_predictor_hist(double* __restrict__ F, double* __restrict__ Fprev, double* __restrict__ Fprev2,
-                                 long long N, const HistState* hs, const Scalars* sc, bool after_update) {
-  double shift[9];
-  const double a = (!after_update && hs->extrapolated) ? hs->alpha : 0.0;
-  for (int c = 0; c < 9; ++c) {
-    double mean;
-    if (after_update) mean = sc->meanF_new[c];
-    else mean = sc->meanF[c] + a * (sc->meanF[c] - hs->fmean2[c]);
-    shift[c] = hs->mask[c] ? 0.0 : hs->target[c] - mean;
-  }
-  if (!after_update && Fprev2 != nullptr) {
-    // quadratic predictor: F <- F + w1 (A - F) + w2 (B - F) + shift, and the
-    // last converged F into its slot (quadratic_start chose both)
-    const bool qx = hs->extrapolated && hs->quad;
-    const double v1 = qx ? hs->w[1] : 0.0, v2 = qx ? hs->w[2] : 0.0;
-    const int dst = hs->dst;
-    double qshift[9];
-    for (int c = 0; c < 9; ++c) qshift[c] = hs->mask[c] ? 0.0 : hs->target[c] - (qx ? hs->pmean[c] : sc->meanF[c]);
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-         v += (long long)gridDim.x * blockDim.x) {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const double f = F[c * N + v];
-        double fn = f;
-        if (v1 != 0.0) fn += v1 * (Fprev[c * N + v] - f);
-        if (v2 != 0.0) fn += v2 * (Fprev2[c * N + v] - f);
-        if (dst == 0) Fprev[c * N + v] = f;
-        else if (dst == 1) Fprev2[c * N + v] = f;
-        F[c * N + v] = fn + qshift[c];
-      }
+// Predictor of a load step (Sec. 2.1, 2.3), the forms of pred_coef: with
+// the extrapolating predictor, F <- F + alpha (F - Fprev) and Fprev <- F,
+// the state the next step extrapolates from; with the quadratic one (Fprev2
+// given: the slots A = Fprev, B = Fprev2) the weights and the slot of
+// quadratic_start; then every strain-controlled component shifted uniformly
+// so that its average is the prescribed F-bar.  After an FP32 update
+// (after_update) only the shift, to the averages of that update.  (A
+// double-word context applies the step's predictor inside its first
+// constitutive pass instead.)
+__global__ void k_predictor_hist(double* __restrict__ F, PredArgs pa, long long N, const Scalars* sc,
+                                 bool after_update) {
+  const HistState* hs = pa.hs;
+  const long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, dv = (long long)gridDim.x * blockDim.x;
+  if (after_update || pa.kind == 0) {
+    // the strain-controlled components only
+    const PredCoef k = pred_coef(pa, sc);
+    for (int c = 0; c < 9; ++c) {
+      if (hs->mask[c]) continue;
+      const double shift = after_update ? hs->target[c] - sc->meanF_new[c] : k.sh[c];
+      for (long long v = v0; v < N; v += dv) F[c * N + v] += shift;
     }
     return;
   }
-  if (!after_update && Fprev != nullptr) {
-    // every component: the kept state shifted back by one step, F predicted
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-         v += (long long)gridDim.x * blockDim.x) {
+  const PredCoef k = pred_coef(pa, sc);
+  for (long long v = v0; v < N; v += dv) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const double f = F[c * N + v], fp = Fprev[c * N + v];
-        Fprev[c * N + v] = f;
-        F[c * N + v] = f + a * (f - fp) + shift[c];
-      }
-    }
-    return;
-  }
-  // the strain-controlled components only
-  for (int c = 0; c < 9; ++c) {
-    if (hs->mask[c]) continue;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-         v += (long long)gridDim.x * blockDim.x)
-      F[c * N + v] += shift[c];
+    for (int c = 0; c < 9; ++c) F[c * N + v] = pred_apply(pa, k, c, N, v, F[c * N + v]);
   }
 }
 
@@ -504,62 +473,27 @@ __global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHa
   // projection, no deflation), with more steps to come in this launch:
   // <P> at the final F from the linearisation, <P(F)> + <K:dF>; the error,
   // of the order of abs(K') abs(dF)^2 with abs(dF) < tol_newton abs(F), is
-  // far below the averages' accuracy.  The last step of a launch evaluates
-  // P, so the fields a caller reads are exact.
+  // far below the averages' accuracy.  <K:dF> = sum_k alpha_k <K:p_k>, the
+  // solve's z-passes having added each iteration's term to sc->lin (the
+  // null-frequency coefficient of K:p_k), so no pass over the fields runs
+  // (kind 2: no body).  The last step of a launch evaluates P, so the
+  // fields a caller reads are exact.
   const bool lin = last && hs->f32 && hs->proj_kind == 0 && hs->defl.m == 0 && hs->k + 1 < hs->nsteps;
   const int kind = last ? (lin ? 2 : 0) : 1;
+  if (lin) {
+    // the update's averages as they are: the strain-controlled ones differ
+    // from F-bar by the rounding of the FP32 correction's average (far below
+    // 1e-14 of F for a correction below tol_newton); the next step's
+    // predictor, which shifts F by F-bar minus these, removes it
+    for (int c = 0; c < 9; ++c) {
+      sc->meanP[c] += sc->lin[c];
+      sc->meanF[c] = sc->meanF_new[c];
+    }
+  }
   hs->last = last;
   hs->res32 = 0;
   hs->cons_kind = kind;
   cudaGraphSetConditional(h_cons, (unsigned)kind);
-}
-
-// Column sums of the 9 components of t (one partial per block and column)
-// and their finish: the linearised end-of-step averages (cons kind 2).
-__global__ void __launch_bounds__(kThreads) k_lin_sums(const float* __restrict__ t, long long N,
-                                                       double* __restrict__ partials) {
-  __shared__ double red[9][kThreads / 32];
-  double acc[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-       v += (long long)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] += (double)t[c * N + v];
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < 9; ++c) {
-    double s = acc[c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[c][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < 9) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += red[threadIdx.x][w];
-    partials[blockIdx.x * 9 + threadIdx.x] = s;
-  }
-}
-
-__global__ void k_lin_fin(const double* __restrict__ partials, int nblk, long long N, const HistState* hs,
-                          Scalars* sc) {
-  __shared__ double red[kThreads / 32];
-  for (int c = 0; c < 9; ++c) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partials[b * 9 + c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-      sc->meanP[c] += tot / (double)N;
-      // the update's averages, with F-bar re-imposed on the strain-controlled components
-      sc->meanF[c] = hs->mask[c] ? sc->meanF_new[c] : hs->target[c];
-    }
-    __syncthreads();
-  }
 }
 
 // After the constitutive pass that follows an update: its failures, the
@@ -687,6 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_fin_cg_init_h(const double* __rest
     sc->rr0 = rr;
     sc->alpha = 0.0;
     sc->beta = 0.0;
+    for (int c = 0; c < 9; ++c) sc->lin[c] = 0.0;
     const double rms = sqrt(rr / (double)N);
     if (hs->nn == 0) hs->rms0 = rms;
     if (hs->eta_hi > 0.0 && hs->cg_rel_cur > 0.0) {
@@ -915,17 +850,10 @@ cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphCondition
   return cudaGetLastError();
 }
 
-cudaError_t mf_launch_lin_means(const float* t, long long N, double* partials, int nblk, const HistState* hs,
-                                Scalars* sc, cudaStream_t st) {
-  k_lin_sums<<<nblk, kThreads, 0, st>>>(t, N, partials);
-  k_lin_fin<<<1, kThreads, 0, st>>>(partials, nblk, N, hs, sc);
-  g_mf_launches += 2;
-  return cudaGetLastError();
-}
-
 cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, double* Fprev2, long long N, const HistState* hs,
                                      const Scalars* sc, bool after_update, cudaStream_t st) {
-  k_predictor_hist<<<grid_for(N), kThreads, 0, st>>>(F, Fprev, Fprev2, N, hs, sc, after_update);
+  const PredArgs pa{Fprev, Fprev2, hs, Fprev2 ? 2 : (Fprev ? 1 : 0)};
+  k_predictor_hist<<<grid_for(N), kThreads, 0, st>>>(F, pa, N, sc, after_update);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

@@ -65,6 +65,8 @@ struct ZArgs {
   double add[9];     // added at the null frequency after scaling (residual: P-bar)
   double* mean_out;  // residual: receives the null-frequency coefficient / N
   const double* add_dev;  // if non-null: the values to add, read on the device (replaces add)
+  double* lin;            // operator in a CG iteration: lin[c] += *lin_alpha * (null-frequency coefficient / N)
+  const double* lin_alpha;
 };
 
 // Process-wide count of kernel launches issued by the library.
@@ -182,10 +184,13 @@ cudaError_t mf_launch_fin_means(const double* partials, int nblk, int ncol, long
 // Pf (with H, moments and table32, the FP32 copy of the material table):
 // P evaluated in FP32 from H and stored to Pf (9N floats) instead of P;
 // the averages of F keep double-word accuracy, those of P are FP32's.
+// pred (predict.cuh; with H and moments only): the load step's predictor
+// applied to F in the same pass, F overwritten by the predicted state.
+struct PredArgs;
 cudaError_t mf_launch_constitutive_dw(const double* F, double* P, float* H, bool moments, const MatArgs& m,
                                       const void* table_dw, long long N, double* partials, int nblk,
                                       Scalars* sc, cudaStream_t st, float* Pf = nullptr,
-                                      const float* table32 = nullptr);
+                                      const float* table32 = nullptr, const PredArgs* pred = nullptr);
 cudaError_t mf_launch_mean_F(const double* F, long long N, double* partials, int nblk, Scalars* sc,
                              cudaStream_t st);
 cudaError_t mf_launch_predictor(double* F, long long N, const uint8_t* mask9, const double* target9,
@@ -292,11 +297,6 @@ cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphCondition
 // Fprev (9N, may be null when the predictor does not extrapolate): the
 // converged F before the current one; the step's predictor replaces it by
 // the current F and extrapolates F along the last increment
-// <P> and <F> at the end of a step from the linearisation at the iteration's
-// start (FP32 inner, cons kind 2): t = K(H):x applied by the tangent pass
-// beforehand; <P> += <t>, <F> <- the post-update averages.
-cudaError_t mf_launch_lin_means(const float* t, long long N, double* partials, int nblk, const HistState* hs,
-                                Scalars* sc, cudaStream_t st);
 cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, double* Fprev2, long long N, const HistState* hs,
                                      const Scalars* sc, bool after_update, cudaStream_t st);
 cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,

@@ -16,6 +16,7 @@
 #include "dw.cuh"
 #include "fft2.cuh"
 #include "launch.h"
+#include "predict.cuh"
 
 namespace {
 
@@ -325,7 +326,7 @@ XYArgs xy_args(const mf_ctx* c, bool f32, bool dw = false) {
 }
 
 ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale, bool dw = false) {
-  ZArgs a;
+  ZArgs a{};
   memset(&a, 0, sizeof(a));
   a.v2 = c->v2;
   a.pdl = c->v2;   // the fixed-size z-pass waits for its predecessor itself
@@ -344,6 +345,8 @@ ZArgs z_args(const mf_ctx* c, bool f32, const uint8_t* mask, double scale, bool 
     if (mask[k]) a.mask |= 1u << k;
   a.scale = scale;
   a.mean_out = nullptr;
+  a.lin = nullptr;
+  a.lin_alpha = nullptr;
   return a;
 }
 
@@ -376,10 +379,12 @@ int flags_status(int flags) {
 // FP32, in the scratch the FP32 residual transforms read (the t vector), P
 // itself untouched.
 int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false, bool p32 = false,
-                     cudaStream_t cap = nullptr) {
+                     cudaStream_t cap = nullptr, const PredArgs* pred = nullptr) {
   // cap: the stream of a graph capture (the passes become graph nodes; the
-  // context's record of what the workspace holds is left alone)
+  // context's record of what the workspace holds is left alone); pred: the
+  // load step's predictor applied in the same pass (double-word pass only)
   cudaStream_t st = cap ? cap : c->st;
+  if (pred && (want_K || !c->dw_outer())) return MF_INVALID_ARG;
   if (!want_K && c->dw_outer()) {
     // P, H and the moments in one double-word pass
     const bool f32p = p32 && want_H && moments;
@@ -388,7 +393,7 @@ int run_constitutive(mf_ctx* c, bool want_K, bool want_H, bool moments = false, 
                                                     c->ws + c->otabledw, c->N, c->at<double>(c->opart),
                                                     c->pw_blocks, c->at<Scalars>(c->osc), st,
                                                     f32p ? c->at<float>(c->oAp) : nullptr,
-                                                    c->at<float>(c->otable32));
+                                                    c->at<float>(c->otable32), pred);
     if (!cap) {
       c->have_K = false;
       c->have_H = want_H && e == cudaSuccess;
@@ -501,6 +506,13 @@ cudaError_t capture_cg_body(mf_ctx* c, cudaStream_t cs, cudaGraph_t body, const 
   XYArgs xa = xy_args(c, f32);
   za.skip = &sc->stop;
   xa.skip = &sc->stop;
+  // FP32: the z-pass adds alpha_k <t_k> (t_k = K:p_k, its null-frequency
+  // coefficient / N) to sc->lin, so that a solve ends with <K:x> at hand
+  // (x = sum_k alpha_k p_k; the linearised end-of-step averages)
+  if (f32) {
+    za.lin = sc->lin;
+    za.lin_alpha = &sc->alpha;
+  }
   // the fused x-y inverse kernel finishes beta itself; the split and generic
   // kernels leave it to k_fin_beta
   xa.fin = (xa.v2 && !xa.split) ? 1 : 0;
@@ -946,9 +958,6 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
       cnt.proj[kind] = (int)(g_mf_launches - lb);
       in_bodies += g_mf_launches - lb;
     }
-    // FP32 corrections carry a rounding-level average on the strain-controlled
-    // components; the FP64 outer level re-imposes F-bar there
-    if (e == cudaSuccess) e = mf_launch_predictor_hist(F, nullptr, nullptr, N, hs, sc, true, s1);
   } else if (e == cudaSuccess) {
     e = mf_launch_newton_update_hist(F, c->ws + c->ox, false, N, part, c->pw_blocks, hs, sc, s1);
   }
@@ -958,27 +967,25 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   cudaGraphConditionalHandle h_cons;
   if (e == cudaSuccess) e = cap_handle(s1, &h_cons);
   if (e == cudaSuccess) e = mf_launch_newton_post(hs, sc, h_cons, s1);
-  // (FP32 inner) 2: the step ends, its averages from the linearisation:
-  // t = K(H):x with the tangent pass, <P> += <t>
-  const int nkind = f32 ? 3 : 2;
-  cudaGraph_t cb[3] = {nullptr, nullptr, nullptr};
+  // (FP32 inner) 2: the step ends, its averages from the linearisation,
+  // which k_newton_post takes from the sums the solve's z-passes kept (no
+  // body: the switch runs none for a value past its last body)
+  const int nkind = 2;
+  cudaGraph_t cb[2] = {nullptr, nullptr};
   if (e == cudaSuccess) e = cap_conditional(s1, h_cons, cudaGraphCondTypeSwitch, nkind, cb);
   for (int kind = 0; kind < nkind && e == cudaSuccess; ++kind) {
     const long long lb = g_mf_launches;
     e = cap_begin(s2, cb[kind]);
     if (e != cudaSuccess) break;
+    const bool more = kind != 0;
+    // FP32 corrections carry a rounding-level average on the strain-controlled
+    // components; the outer level re-imposes F-bar there before the pass over
+    // F (after a kind-2 ending the next step's predictor does, from the
+    // averages k_newton_post records)
     int st = 0;
-    if (kind == 2) {
-      cudaError_t el = mf_launch_tangent(c->ws + c->ox, nullptr, nullptr, nullptr, true, tangent_kind(c), false,
-                                         tangent_args(c), c->ws + c->oAp, N, nullptr, c->pw_blocks, sc, s2);
-      if (el == cudaSuccess)
-        el = mf_launch_lin_means(c->at<float>(c->oAp), N, part, c->pw_blocks, hs, sc, s2);
-      if (el != cudaSuccess) st = MF_CUDA_ERROR;
-    } else {
-      const bool more = kind != 0;
-      st = run_constitutive(c, more && !f32, more && f32, more && f32, false, s2);
-      if (!st && more && capture_residual(c, mask, false, s2) != cudaSuccess) st = MF_CUDA_ERROR;
-    }
+    if (f32 && mf_launch_predictor_hist(F, nullptr, nullptr, N, hs, sc, true, s2) != cudaSuccess) st = MF_CUDA_ERROR;
+    if (!st) st = run_constitutive(c, more && !f32, more && f32, more && f32, false, s2);
+    if (!st && more && capture_residual(c, mask, false, s2) != cudaSuccess) st = MF_CUDA_ERROR;
     e = cap_end(s2, st ? cudaErrorUnknown : cudaSuccess);
     cnt.cons[kind] = (int)(g_mf_launches - lb);
     in_bodies += g_mf_launches - lb;
@@ -1029,15 +1036,18 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
       const bool choose = extrap && dwr;
       if (choose) e = cap_handle(caps[1], &h_first);
       if (e == cudaSuccess) e = mf_launch_step_begin(hs, t, choose ? &h_first : nullptr, caps[1]);
-      if (e == cudaSuccess)
-        e = mf_launch_predictor_hist(F, extrap ? c->at<double>(c->oFprev) : nullptr, Fprev2, N, hs, sc, false,
-                                     caps[1]);
+      // the predictor: in the double-word constitutive pass that follows
+      // (FP32 inner with a double-word outer level), else a pass of its own
+      double* Fprev = extrap ? c->at<double>(c->oFprev) : nullptr;
+      const PredArgs pred{Fprev, Fprev2, hs, Fprev2 ? 2 : (Fprev ? 1 : 0)};
+      const bool fuse_pred = f32 && c->dw_outer();
+      if (e == cudaSuccess && !fuse_pred) e = mf_launch_predictor_hist(F, Fprev, Fprev2, N, hs, sc, false, caps[1]);
       // the pass after the predictor: FP64 P and K, or (FP32 inner) H and the
       // rotation moments, with P itself in FP32 for an FP32 first residual;
       // then the first residual
       int step_kernels = 0, step_kernels_ex = 0;
       auto first_pass = [&](bool res32, cudaStream_t st) {
-        int r = run_constitutive(c, !f32, f32, f32, res32, st);
+        int r = run_constitutive(c, !f32, f32, f32, res32, st, fuse_pred ? &pred : nullptr);
         if (!r && capture_residual(c, mask, res32, st) != cudaSuccess) r = MF_CUDA_ERROR;
         return r ? cudaErrorUnknown : cudaSuccess;
       };

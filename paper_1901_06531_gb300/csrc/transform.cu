@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(512) k_xy_inverse(const typename CT<T>::t* __r
 }
 
 // ---------------------------------------------------------------- z pass
-// MODE 0: projected operator.  MODE 1: residual (adds a.add at the null
-// frequency and records the null-frequency coefficient / N in a.mean_out).
+// MODE 0: projected operator (with a.lin, the null-frequency coefficient / N
+// times *a.lin_alpha added to a.lin).  MODE 1: residual (adds a.add at the
+// null frequency and records the null-frequency coefficient / N in a.mean_out).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_zpass(typename CT<T>::t* __restrict__ spec, ZArgs a) {
   typedef typename CT<T>::t C;
@@ -228,6 +229,7 @@ __global__ void __launch_bounds__(512) k_zpass(typename CT<T>::t* __restrict__ s
       for (int c = 0; c < 9; ++c) {
         const C X = e[c * zstride];
         if (MODE == 1 && a.mean_out) a.mean_out[c] = (double)X.x / (double)a.N;
+        if (MODE == 0 && a.lin) a.lin[c] += *a.lin_alpha * ((double)X.x / (double)a.N);
         if (a.mask & (1u << c)) {
           T add = (MODE == 1) ? (T)(a.add_dev ? a.add_dev[c] : a.add[c]) : (T)0;
           e[c * zstride] = cmake(scale * X.x + add, scale * X.y);

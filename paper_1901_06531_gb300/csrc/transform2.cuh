@@ -619,8 +619,9 @@ struct ZShape {
   }
 };
 
-// MODE 0: operator (scale, mask).  MODE 1: residual (adds a.add at the null
-// frequency, records the null-frequency coefficient / N in a.mean_out).
+// MODE 0: operator (scale, mask; with a.lin, the null-frequency coefficient
+// / N times *a.lin_alpha added to a.lin, read before the transform).  MODE 1: residual (adds a.add at the
+// null frequency, records the null-frequency coefficient / N in a.mean_out).
 // Grid: 3 row groups x (ncol / S) column tiles.
 template <typename T, int NZ, int MODE, int S_>
 __global__ void __launch_bounds__(z_threads(S_), z_min_blocks<T>(S_, MODE)) k_zp(typename CT<T>::t* __restrict__ spec, ZArgs a) {
@@ -660,6 +661,24 @@ __global__ void __launch_bounds__(z_threads(S_), z_min_blocks<T>(S_, MODE)) k_zp
   auto gidx = [&](int q, int z) {
     return MF_AT(goff + ((long long)(q / S) * NZ + z) * ncol + (q % S), 9LL * NZ * ncol) - goff;
   };
+  if (MODE == 0 && a.lin) {
+    // the null-frequency coefficient of each component of the row group is
+    // the sum over z of its planes' (kx, ky) = (0, 0) coefficients: read
+    // here, before the transform overwrites them, by the block holding that
+    // column (one warp per component, summed in FP64)
+    int sdc = -1;
+    for (int s = 0; s < S; ++s) {
+      const int col = col0 + s, row = col / H, slot = col - row * H;
+      if (a.xk[slot] == 0 && a.yk[row] == 0) sdc = s;
+    }
+    if (sdc >= 0 && threadIdx.x < 96) {
+      const int cl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      double sum = 0.0;
+      for (int z = lane; z < NZ; z += 32) sum += (double)gsp[gidx(cl * S + sdc, z)].x;
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) a.lin[3 * g + cl] += *a.lin_alpha * (sum / (double)a.N);
+    }
+  }
   __syncthreads();
   if constexpr (NST > 1) {
     // first forward stage: global -> registers -> shared
