@@ -1036,6 +1036,75 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def phase_composition(t, ids, names, skip_steps=2):
+    """Per-phase durations of a traced history (mf_trace_read marks): each
+    phase lasts from the mark before it to its own; the steps are split at
+    the step-start marks.  Returns the per-step averages (us) over the steps
+    after the first `skip_steps`, and every step's total."""
+    starts = [i for i, x in enumerate(ids) if x == 1]
+    totals, acc = [], {}
+    for si, a in enumerate(starts):
+        b = starts[si + 1] if si + 1 < len(starts) else len(ids)
+        end = t[b] if b < len(ids) else t[b - 1]
+        totals.append(round((int(end) - int(t[a])) / 1e3, 1))
+        if si < skip_steps:
+            continue
+        for i in range(a + 1, b):
+            k = names.get(int(ids[i]), str(int(ids[i])))
+            acc[k] = acc.get(k, 0.0) + (int(t[i]) - int(t[i - 1])) / 1e3
+    n = max(1, len(starts) - skip_steps)
+    return {k: round(v / n, 1) for k, v in sorted(acc.items(), key=lambda kv: -kv[1])}, totals
+
+
+def run_phase_trace(args):
+    """The composition of a load step of the timed workload: the history run
+    on the trace build of the library (phase timestamps from the device),
+    in a child process that loads that build."""
+    import subprocess
+    from paper_1901_06531_gb300 import build
+    build.build(trace=True)
+    env = dict(os.environ, MF_LIBRARY="trace")
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--phase-trace-child", "--steps",
+                          str(args.steps), "--warmup", str(args.warmup)], env=env, capture_output=True, text=True)
+    sys.stdout.write(res.stdout)
+    sys.stderr.write(res.stderr)
+    if res.returncode:
+        raise SystemExit(res.returncode)
+
+
+def phase_trace_child(args):
+    import torch
+    from paper_1901_06531_gb300 import mixfft as mf
+    g, params, R, mask, target = workload()
+    n = N1
+    ctx = mf.Context(n, n, n, mf.MF_FP32_INNER)
+    ctx.set_material(mf.MF_SVK_CUBIC, params, g, rot=R)
+    ctx.set_predictor(mf.MF_PRED_QUADRATIC)
+    ctx.autotune()
+    nst = mask.shape[0]
+
+    def steps(k0, k1):
+        idx = [k % nst for k in range(k0, k1)]
+        return ctx.solve(mask[idx], target[idx], TOL_NEWTON, TOL_CG, CG_REL)
+
+    steps(0, args.warmup)
+    ctx.set_F(None)
+    mf.trace_read()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    o = steps(0, args.steps)
+    b.record()
+    torch.cuda.synchronize()
+    t, ids = mf.trace_read()
+    comp, totals = phase_composition(t, ids, mf.TRACE_PHASES)
+    print(json.dumps({"phase_trace": {
+        "workload": "128^3 polycrystal, the timed history on the trace build (a mark kernel between phases)",
+        "traced_ms_per_step": a.elapsed_time(b) / args.steps, "marks": int(len(t)),
+        "newton_cg_per_step": [[int(x), int(y)] for x, y in zip(o["newton"], o["cg"])],
+        "step_us": totals, "us_per_step_after_step_2": comp}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1059,8 +1128,15 @@ def main():
                           "(bit 0 forward, bit 1 inverse); -1: the autotuner's choice"))
     ap.add_argument("--oracle-full", action="store_true",
                     help="time whole oracle runs of the 16^3 and 64^3 workloads (1 and all threads)")
+    ap.add_argument("--phase-trace", action="store_true",
+                    help="the composition of a load step from the trace build's phase timestamps")
+    ap.add_argument("--phase-trace-child", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.oracle_full:
+    if args.phase_trace_child:
+        phase_trace_child(args)
+    elif args.phase_trace:
+        run_phase_trace(args)
+    elif args.oracle_full:
         run_oracle_full(args)
     elif args.matvec_only or args.kernels_only:
         run_matvec_only(args)

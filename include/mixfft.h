@@ -260,6 +260,41 @@ int mf_debug_report(long long* count_out, int* line_out, long long* index_out, l
  * A release build launches nothing and returns MF_INVALID_ARG. */
 int mf_debug_selftest(void);
 
+/* Phase timestamps of load histories (the library compiled with MF_TRACE,
+ * the package's build script with trace=True, libmixfft_trace.so).  The
+ * graph of a history (mf_solve, mf_solve_batch) records, in one-thread
+ * kernels between its phases, the device's global timer (ns) and a phase id:
+ * MF_TRACE_STEP_START and MF_TRACE_ITER_START where a load step and a Newton
+ * iteration begin, every other id where the phase it names ends, so a
+ * phase's duration is its mark minus the mark before.  The marks add a
+ * launch each (a few us per mark), so traced histories run slower than
+ * release ones; they are for the composition of a step, not its time.  This
+ * call synchronises the device, copies up to `cap` entries (oldest first)
+ * into t_ns and ids, sets *n_out to the number recorded since the last call
+ * (the device keeps at most 65536) and clears them.  A release build
+ * returns MF_INVALID_ARG. */
+typedef enum {
+  MF_TRACE_STEP_START = 1,          /* a load step begins */
+  MF_TRACE_STEP_BEGIN = 2,          /* the step's control kernel (targets, predictor weights) */
+  MF_TRACE_FIRST_CONSTITUTIVE = 3,  /* the predictor and the constitutive pass */
+  MF_TRACE_FIRST_RESIDUAL = 4,      /* the step's first residual */
+  MF_TRACE_ITER_START = 10,         /* a Newton iteration begins */
+  MF_TRACE_NEWTON_PRE = 11,         /* its control kernel and the right-hand side's null rotations */
+  MF_TRACE_CG_INIT = 12,            /* the CG start */
+  MF_TRACE_CG_LOOP = 13,            /* the CG iterations */
+  MF_TRACE_PROJECTION = 14,         /* the projection choice and the projection of the correction */
+  MF_TRACE_DEFLATION = 15,          /* the correction's null rotations */
+  MF_TRACE_UPDATE = 16,             /* the Newton update */
+  MF_TRACE_NEWTON_POST = 17,        /* the Newton test */
+  MF_TRACE_FBAR = 18,               /* F-bar re-imposed on the strain-controlled components */
+  MF_TRACE_CONSTITUTIVE = 19,       /* the constitutive pass after the update */
+  MF_TRACE_RESIDUAL = 20,           /* the next iteration's residual */
+  MF_TRACE_CONS_SWITCH = 21,        /* the end of the pass after the update */
+  MF_TRACE_NEWTON_LOOP = 30,        /* the step's further Newton iterations */
+  MF_TRACE_STEP_END = 31            /* the step's closing control kernel */
+} mf_trace_phase;
+int mf_trace_read(int cap, unsigned long long* t_ns, int* ids, int* n_out);
+
 /* Number of kernel launches the library has issued in this process (all
  * contexts); differences around a region count its launches. */
 long long mf_kernel_launches(void);

@@ -21,6 +21,10 @@ LIB = os.path.join(HERE, "libmixfft.so")
 # common.cuh)
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libmixfft_debug.so")
+# trace build: device timestamps between the phases of a load history's
+# graph (MF_TRACE, read back with mf_trace_read)
+BUILD_TRACE = os.path.join(HERE, "_build_trace")
+LIB_TRACE = os.path.join(HERE, "libmixfft_trace.so")
 SOURCES = ["transform.cu", "transform2_f32.cu", "transform2_f64.cu", "pointwise.cu", "cg.cu", "history.cu",
            "mixfft.cu", "noalloc.cu", "cufft_path.cu", "adjoint.cu", "transform2_dw.cu",
            "constitutive_dw.cu", "probe.cu"]
@@ -36,9 +40,10 @@ def nvcc():
     return exe
 
 
-def _compile(src, verbose, debug=False):
-    obj = os.path.join(BUILD_DEBUG if debug else BUILD, src.replace(".cu", ".o"))
-    cmd = [nvcc(), *ARCH, *FLAGS, *(["-DMF_DEBUG"] if debug else []), "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src, verbose, debug=False, trace=False):
+    obj = os.path.join(BUILD_DEBUG if debug else (BUILD_TRACE if trace else BUILD), src.replace(".cu", ".o"))
+    cmd = [nvcc(), *ARCH, *FLAGS, *(["-DMF_DEBUG"] if debug else []), *(["-DMF_TRACE"] if trace else []), "-c",
+           os.path.join(CSRC, src), "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{res.stderr}")
@@ -47,19 +52,20 @@ def _compile(src, verbose, debug=False):
     return obj
 
 
-def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+def build(verbose: bool = False, force: bool = False, debug: bool = False, trace: bool = False) -> str:
     """Compile libmixfft.so (or, with debug, libmixfft_debug.so: the same
-    library with the bounds checks of MF_DEBUG) unless it is newer than
-    every source; returns its path."""
-    out = LIB_DEBUG if debug else LIB
-    os.makedirs(BUILD_DEBUG if debug else BUILD, exist_ok=True)
+    library with the bounds checks of MF_DEBUG; with trace,
+    libmixfft_trace.so: with the phase timestamps of MF_TRACE) unless it is
+    newer than every source; returns its path."""
+    out = LIB_DEBUG if debug else (LIB_TRACE if trace else LIB)
+    os.makedirs(BUILD_DEBUG if debug else (BUILD_TRACE if trace else BUILD), exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
         os.path.join(os.path.dirname(HERE), "include", "mixfft.h")]
     if (not force and os.path.exists(out)
             and os.path.getmtime(out) >= max(os.path.getmtime(d) for d in deps)):
         return out
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, debug), SOURCES))
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug, trace), SOURCES))
     tmp = out + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"]
     res = subprocess.run(cmd, capture_output=True, text=True)

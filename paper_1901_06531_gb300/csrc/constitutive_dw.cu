@@ -203,7 +203,7 @@ __device__ __forceinline__ void block_sum_dw(double (&v)[NC], double* out) {
 // stored and evaluated (the pass is compute bound, so the predictor's loads
 // and stores cost little here against a pass of their own).
 template <int MODEL, bool WH, bool MOM, bool P32, bool PRED>
-__global__ void __launch_bounds__(kThreads) k_constitutive_dw(double* __restrict__ F, double* __restrict__ P,
+__global__ void __launch_bounds__(kThreads, 2) k_constitutive_dw(double* __restrict__ F, double* __restrict__ P,
                                                               float* __restrict__ Pf, float* __restrict__ H,
                                                               MatArgs m, const dw* __restrict__ table,
                                                               const float* __restrict__ table32, long long N,
@@ -228,9 +228,27 @@ __global__ void __launch_bounds__(kThreads) k_constitutive_dw(double* __restrict
 #pragma unroll
     for (int c = 0; c < 9; ++c) fd[c] = F[c * N + v];
     if constexpr (PRED) {
+      // every load of the voxel issued before any store (the slots and F
+      // are distinct fields)
+      double* __restrict__ A = pa.A;
+      double* __restrict__ B = pa.B;
+      const double v1 = pk.v1, v2 = pk.v2;
+      const int dst = pk.dst;
+      double fa[9], fb[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        fd[c] = pred_apply(pa, pk, c, N, v, fd[c]);
+        fa[c] = v1 != 0.0 ? A[c * N + v] : 0.0;
+        fb[c] = v2 != 0.0 ? B[c * N + v] : 0.0;
+      }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const double f = fd[c];
+        double fn = f;
+        if (v1 != 0.0) fn += v1 * (fa[c] - f);
+        if (v2 != 0.0) fn += v2 * (fb[c] - f);
+        if (dst == 0) A[c * N + v] = f;
+        else if (dst == 1) B[c * N + v] = f;
+        fd[c] = fn + pk.sh[c];
         F[c * N + v] = fd[c];
       }
     }

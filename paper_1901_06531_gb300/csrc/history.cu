@@ -110,6 +110,16 @@ __device__ void null_rotations_dev(const double* meanF, const unsigned char* mas
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) CtC[a][b] += row[a] * row[b];
   }
+  // no admissible rotation when C^T C is clearly nonsingular: its smallest
+  // eigenvalue is at least det / tr^2, and a det above 1e-12 tr^3 (far above
+  // its rounding) with tr above 1e-6 puts it above the 1e-20 of the test
+  // below; the eigen-decomposition, slow in one thread, is skipped then
+  // (the common case of mixed control with strain-controlled shear components)
+  const double tr = CtC[0][0] + CtC[1][1] + CtC[2][2];
+  const double det = CtC[0][0] * (CtC[1][1] * CtC[2][2] - CtC[1][2] * CtC[2][1]) -
+                     CtC[0][1] * (CtC[1][0] * CtC[2][2] - CtC[1][2] * CtC[2][0]) +
+                     CtC[0][2] * (CtC[1][0] * CtC[2][1] - CtC[1][1] * CtC[2][0]);
+  if (tr > 1e-6 && det > 1e-12 * tr * tr * tr) return;
   double V[3][3];
   jacobi3(3, CtC, V);
   double Z[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
@@ -214,16 +224,21 @@ __device__ int quadratic_start(HistState* hs, const StepIn& row) {
   int ex = 0;
   if (okA || okB) {
     const double* tn = okA ? hs->t2 : hs->t3;
+    // (one thread: FP64 divisions are slow here, so each quotient is taken
+    // once, after its sum)
     double nd = 0.0;
     for (int c = 0; c < 9; ++c) nd += (tn[c] - hs->t1[c]) * (tn[c] - hs->t1[c]);
     nd = sqrt(nd);
     double st = 0.0;
-    for (int c = 0; c < 9; ++c) st += (row.target[c] - hs->t1[c]) * (tn[c] - hs->t1[c]) / nd;
+    for (int c = 0; c < 9; ++c) st += (row.target[c] - hs->t1[c]) * (tn[c] - hs->t1[c]);
+    st /= nd;
     if (okA && okB) {
       double sB = 0.0, q3 = 0.0;
-      for (int c = 0; c < 9; ++c) sB += (hs->t3[c] - hs->t1[c]) * (hs->t2[c] - hs->t1[c]) / nd;
+      for (int c = 0; c < 9; ++c) sB += (hs->t3[c] - hs->t1[c]) * (hs->t2[c] - hs->t1[c]);
+      sB /= nd;
+      const double sBn = sB / nd;
       for (int c = 0; c < 9; ++c) {
-        const double off = (hs->t3[c] - hs->t1[c]) - sB * (hs->t2[c] - hs->t1[c]) / nd;
+        const double off = (hs->t3[c] - hs->t1[c]) - sBn * (hs->t2[c] - hs->t1[c]);
         q3 += off * off;
       }
       const double sA = nd;
@@ -278,6 +293,23 @@ __device__ int quadratic_start(HistState* hs, const StepIn& row) {
   return ex;
 }
 
+// The control kernels below run their logic in one thread on a copy of the
+// history state in shared memory, read and written back by a whole warp in
+// parallel: the logic's many dependent accesses to the state then cost
+// shared-memory latency instead of global-memory latency each.
+static_assert(sizeof(HistState) % 8 == 0, "HistState is copied in 8-byte words");
+template <typename Fn>
+__device__ __forceinline__ void on_shared_state(HistState* hs_g, Fn fn) {
+  __shared__ __align__(16) unsigned long long raw[sizeof(HistState) / 8];
+  unsigned long long* g = reinterpret_cast<unsigned long long*>(hs_g);
+  for (int i = threadIdx.x; i < (int)(sizeof(HistState) / 8); i += blockDim.x) raw[i] = g[i];
+  __syncthreads();
+  if (threadIdx.x == 0) fn(reinterpret_cast<HistState*>(raw));
+  __syncthreads();
+  for (int i = threadIdx.x; i < (int)(sizeof(HistState) / 8); i += blockDim.x) g[i] = raw[i];
+}
+constexpr int kCtlThreads = 32;
+
 // Load step k of the table: control mask, targets, P-bar (Sec. 2.3).  With
 // the extrapolating predictor and the last two converged steps at hand (same
 // mask), the factor alpha of the increment: the projection of this step's
@@ -286,49 +318,51 @@ __device__ int quadratic_start(HistState* hs, const StepIn& row) {
 // quadratic predictor, quadratic_start.  An extrapolated start is close to
 // the solution: its first residual runs in the outer arithmetic (FP32
 // rounding, relative to abs(P), would no longer be small against it).
-__global__ void k_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle h_first, int set_first) {
-  const StepIn& row = t.in[hs->k];
-  if (hs->ident) {
-    // the reference state as the last converged one, at this mask's zero
-    // load: P-bar = 0 on the stress-controlled components, F-bar = I on the
-    // strain-controlled ones (both laws give P(I) = 0)
-    for (int c = 0; c < 9; ++c) {
-      const double id = (c % 4 == 0) ? 1.0 : 0.0;
-      hs->t1[c] = row.mask[c] ? 0.0 : id;
-      hs->fmean1[c] = id;
-      hs->mprev[c] = row.mask[c];
+__global__ void k_step_begin(HistState* hs_g, HistTables t, cudaGraphConditionalHandle h_first, int set_first) {
+  on_shared_state(hs_g, [&](HistState* hs) {
+    const StepIn& row = t.in[hs->k];
+    if (hs->ident) {
+      // the reference state as the last converged one, at this mask's zero
+      // load: P-bar = 0 on the stress-controlled components, F-bar = I on the
+      // strain-controlled ones (both laws give P(I) = 0)
+      for (int c = 0; c < 9; ++c) {
+        const double id = (c % 4 == 0) ? 1.0 : 0.0;
+        hs->t1[c] = row.mask[c] ? 0.0 : id;
+        hs->fmean1[c] = id;
+        hs->mprev[c] = row.mask[c];
+      }
+      hs->ident = 0;
     }
-    hs->ident = 0;
-  }
-  bool same = hs->nprev >= 2;
-  for (int c = 0; c < 9; ++c) {
-    const unsigned char m = row.mask[c];
-    const double v = row.target[c];
-    hs->mask[c] = m;
-    hs->target[c] = v;
-    hs->pbar[c] = m ? v : 0.0;
-    if (m != hs->mprev[c]) same = false;
-  }
-  double num = 0.0, den = 0.0;
-  for (int c = 0; c < 9; ++c) {
-    const double d1 = hs->target[c] - hs->t1[c], d0 = hs->t1[c] - hs->t2[c];
-    num += d1 * d0;
-    den += d0 * d0;
-  }
-  int ex = (hs->extrap == 1 && same && den > 0.0) ? 1 : 0;
-  hs->alpha = ex ? num / den : 0.0;
-  hs->quad = 0;
-  hs->dst = -1;
-  if (hs->extrap == 2) ex = quadratic_start(hs, row);
-  hs->extrapolated = ex;
-  hs->nn = 0;
-  hs->ncg = 0;
-  hs->ratio = INFINITY;
-  hs->last = 0;
-  // the first residual of a step uses FP32 transforms where they exist,
-  // unless the start was extrapolated
-  hs->res32 = hs->dw_res && !ex;
-  if (set_first) cudaGraphSetConditional(h_first, ex ? 1u : 0u);
+    bool same = hs->nprev >= 2;
+    for (int c = 0; c < 9; ++c) {
+      const unsigned char m = row.mask[c];
+      const double v = row.target[c];
+      hs->mask[c] = m;
+      hs->target[c] = v;
+      hs->pbar[c] = m ? v : 0.0;
+      if (m != hs->mprev[c]) same = false;
+    }
+    double num = 0.0, den = 0.0;
+    for (int c = 0; c < 9; ++c) {
+      const double d1 = hs->target[c] - hs->t1[c], d0 = hs->t1[c] - hs->t2[c];
+      num += d1 * d0;
+      den += d0 * d0;
+    }
+    int ex = (hs->extrap == 1 && same && den > 0.0) ? 1 : 0;
+    hs->alpha = ex ? num / den : 0.0;
+    hs->quad = 0;
+    hs->dst = -1;
+    if (hs->extrap == 2) ex = quadratic_start(hs, row);
+    hs->extrapolated = ex;
+    hs->nn = 0;
+    hs->ncg = 0;
+    hs->ratio = INFINITY;
+    hs->last = 0;
+    // the first residual of a step uses FP32 transforms where they exist,
+    // unless the start was extrapolated
+    hs->res32 = hs->dw_res && !ex;
+    if (set_first) cudaGraphSetConditional(h_first, ex ? 1u : 0u);
+  });
 }
 
 // Predictor of a load step (Sec. 2.1, 2.3), the forms of pred_coef: with
@@ -355,9 +389,27 @@ __global__ void k_predictor_hist(double* __restrict__ F, PredArgs pa, long long 
     return;
   }
   const PredCoef k = pred_coef(pa, sc);
+  double* __restrict__ A = pa.A;
+  double* __restrict__ B = pa.B;
   for (long long v = v0; v < N; v += dv) {
+    // every load of the voxel issued before any store (F and the slots are
+    // distinct fields), then the form of predict.cuh
+    double f[9], fa[9], fb[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) F[c * N + v] = pred_apply(pa, k, c, N, v, F[c * N + v]);
+    for (int c = 0; c < 9; ++c) {
+      f[c] = F[c * N + v];
+      fa[c] = k.v1 != 0.0 ? A[c * N + v] : 0.0;
+      fb[c] = k.v2 != 0.0 ? B[c * N + v] : 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      double fn = f[c];
+      if (k.v1 != 0.0) fn += k.v1 * (fa[c] - f[c]);
+      if (k.v2 != 0.0) fn += k.v2 * (fb[c] - f[c]);
+      if (k.dst == 0) A[c * N + v] = f[c];
+      else if (k.dst == 1) B[c * N + v] = f[c];
+      F[c * N + v] = fn + k.sh[c];
+    }
   }
 }
 
@@ -366,49 +418,51 @@ __global__ void k_predictor_hist(double* __restrict__ F, PredArgs pa, long long 
 // (from T and S of that pass); the forcing of the inner solve: sqrt(cg_rel)
 // for the first iteration of a step and for one whose predecessor's
 // correction was below sqrt(tol_newton), cg_rel otherwise.
-__global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
+__global__ void k_newton_pre(HistState* hs_g, const Scalars* sc, cudaGraphConditionalHandle h_go,
                              cudaGraphConditionalHandle h_newton, int first) {
-  int st = flags_to_status(sc->flags);
-  if (!st && hs->nn >= hs->max_newton) st = MF_NOT_CONVERGED;
-  if (st) {
-    if (!hs->status) hs->status = st;
-    cudaGraphSetConditional(h_go, 0u);
-    cudaGraphSetConditional(h_newton, 0u);
-    return;
-  }
-  hs->defl.m = 0;
-  if (hs->f32) null_rotations_dev(sc->meanF, hs->mask, sc->T, sc->S, hs->kappa, 1e-6, &hs->defl);
-  // the first iteration of an extrapolated step is expected to be followed
-  // by one more only: its solve need only leave the next correction below
-  // the Newton tolerance.  Its correction is about the larger of the last two
-  // steps' first ones (r; two, because the step across a load reversal
-  // starts exact and its first correction says nothing about the next), and
-  // the next about eta r, so eta = 0.1 tol_newton / r (the choice of
-  // forcing terms of inexact Newton methods from the expected convergence),
-  // at least cg_rel.  Its upper bound matters when r is below tol_newton and
-  // the step ends on this correction: the step leaves an error of about eta
-  // times its start's error, and the start carries the kept states' errors
-  // with the gain sum abs(w) of the extrapolation (7 for the quadratic one
-  // along a ramp: w = 3, -3, 1), so the states' errors evolve as e' = eta
-  // (tau + sum abs(w) e), tau the extrapolation's own error.  The bound
-  // 0.25 / sum abs(w) holds that gain to 1/4 (errors from earlier steps
-  // shrink fourfold per step, and e settles near 1.3 eta tau); it is kept
-  // within [sqrt(cg_rel), 0.1], 0.1 keeping the computed correction, whose
-  // size the Newton test reads, within about 10 %.
-  const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
-  double eta = loose ? sqrt(hs->cg_rel) : hs->cg_rel;
-  const double r = fmax(hs->first_ratio, hs->first_ratio2);
-  hs->eta_hi = 0.0;
-  if (first && hs->extrapolated && r > 0.0 && isfinite(r)) {
-    const double gain = hs->quad ? fabs(hs->w[0]) + fabs(hs->w[1]) + fabs(hs->w[2])
-                                 : 1.0 + 2.0 * fabs(hs->alpha);
-    const double hi = fmax(sqrt(hs->cg_rel), fmin(0.1, 0.25 / fmax(gain, 1.0)));
-    eta = fmin(hi, fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
-    // refined at the CG start from this step's own first residual (k_fin_cg_init_h)
-    hs->eta_hi = hi;
-  }
-  hs->cg_rel_cur = hs->forcing ? eta : 0.0;
-  cudaGraphSetConditional(h_go, 1u);
+  on_shared_state(hs_g, [&](HistState* hs) {
+    int st = flags_to_status(sc->flags);
+    if (!st && hs->nn >= hs->max_newton) st = MF_NOT_CONVERGED;
+    if (st) {
+      if (!hs->status) hs->status = st;
+      cudaGraphSetConditional(h_go, 0u);
+      cudaGraphSetConditional(h_newton, 0u);
+      return;
+    }
+    hs->defl.m = 0;
+    if (hs->f32) null_rotations_dev(sc->meanF, hs->mask, sc->T, sc->S, hs->kappa, 1e-6, &hs->defl);
+    // the first iteration of an extrapolated step is expected to be followed
+    // by one more only: its solve need only leave the next correction below
+    // the Newton tolerance.  Its correction is about the larger of the last two
+    // steps' first ones (r; two, because the step across a load reversal
+    // starts exact and its first correction says nothing about the next), and
+    // the next about eta r, so eta = 0.1 tol_newton / r (the choice of
+    // forcing terms of inexact Newton methods from the expected convergence),
+    // at least cg_rel.  Its upper bound matters when r is below tol_newton and
+    // the step ends on this correction: the step leaves an error of about eta
+    // times its start's error, and the start carries the kept states' errors
+    // with the gain sum abs(w) of the extrapolation (7 for the quadratic one
+    // along a ramp: w = 3, -3, 1), so the states' errors evolve as e' = eta
+    // (tau + sum abs(w) e), tau the extrapolation's own error.  The bound
+    // 0.25 / sum abs(w) holds that gain to 1/4 (errors from earlier steps
+    // shrink fourfold per step, and e settles near 1.3 eta tau); it is kept
+    // within [sqrt(cg_rel), 0.1], 0.1 keeping the computed correction, whose
+    // size the Newton test reads, within about 10 %.
+    const bool loose = (first && !hs->extrapolated) || hs->ratio < sqrt(hs->tol_newton);
+    double eta = loose ? sqrt(hs->cg_rel) : hs->cg_rel;
+    const double r = fmax(hs->first_ratio, hs->first_ratio2);
+    hs->eta_hi = 0.0;
+    if (first && hs->extrapolated && r > 0.0 && isfinite(r)) {
+      const double gain = hs->quad ? fabs(hs->w[0]) + fabs(hs->w[1]) + fabs(hs->w[2])
+                                   : 1.0 + 2.0 * fabs(hs->alpha);
+      const double hi = fmax(sqrt(hs->cg_rel), fmin(0.1, 0.25 / fmax(gain, 1.0)));
+      eta = fmin(hi, fmax(hs->cg_rel, 0.1 * hs->tol_newton / r));
+      // refined at the CG start from this step's own first residual (k_fin_cg_init_h)
+      hs->eta_hi = hi;
+    }
+    hs->cg_rel_cur = hs->forcing ? eta : 0.0;
+    cudaGraphSetConditional(h_go, 1u);
+  });
 }
 
 // Projection of the FP32 correction onto the range of G* before the update:
@@ -419,19 +473,21 @@ __global__ void k_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditio
 // (MF_PROJ_OUTER, or MF_PROJ_AUTO for a correction expected to be at least
 // kProjOuterAbove of F).
 constexpr double kProjSkipBelow = 1e-8;
-__global__ void k_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, int first) {
-  const int nn = hs->nn;
-  const double ratio = hs->ratio;
-  const bool outer =
-      hs->proj_arith == MF_PROJ_OUTER ||
-      (hs->proj_arith == MF_PROJ_AUTO &&
-       (first ? !(hs->first_ratio < kProjOuterAbove) : !(ratio < 10.0 * kProjOuterAbove)));
-  const bool tiny_first = first && hs->extrapolated && hs->proj_arith != MF_PROJ_OUTER &&
-                          fmax(hs->first_ratio, hs->first_ratio2) < kProjSkipBelow;
-  const bool project = !tiny_first && (outer || nn < 2 || !(ratio < 1e-6));
-  const int kind = !project ? 0 : (outer ? 2 : 1);
-  hs->proj_kind = kind;
-  cudaGraphSetConditional(h_proj, (unsigned)kind);
+__global__ void k_proj_decide(HistState* hs_g, cudaGraphConditionalHandle h_proj, int first) {
+  on_shared_state(hs_g, [&](HistState* hs) {
+    const int nn = hs->nn;
+    const double ratio = hs->ratio;
+    const bool outer =
+        hs->proj_arith == MF_PROJ_OUTER ||
+        (hs->proj_arith == MF_PROJ_AUTO &&
+         (first ? !(hs->first_ratio < kProjOuterAbove) : !(ratio < 10.0 * kProjOuterAbove)));
+    const bool tiny_first = first && hs->extrapolated && hs->proj_arith != MF_PROJ_OUTER &&
+                            fmax(hs->first_ratio, hs->first_ratio2) < kProjSkipBelow;
+    const bool project = !tiny_first && (outer || nn < 2 || !(ratio < 1e-6));
+    const int kind = !project ? 0 : (outer ? 2 : 1);
+    hs->proj_kind = kind;
+    cudaGraphSetConditional(h_proj, (unsigned)kind);
+  });
 }
 
 // After the update: the outcome of the inner solve (an FP32 inner solve that
@@ -445,99 +501,105 @@ __global__ void k_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, 
 // rounding, relative to abs(P), is no longer small against the shrinking
 // residual, and the 128^3 polycrystal needed a fourth Newton iteration per
 // step.)
-__global__ void k_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_cons) {
-  int flags = sc->flags;
-  if (hs->f32 && (flags & MF_FLAG_BREAKDOWN) && !(flags & ~MF_FLAG_BREAKDOWN) && sc->its > 1) {
-    sc->flags = 0;
-    flags = 0;
-  }
-  int st = flags_to_status(flags);
-  if (!st && !sc->done) st = MF_NOT_CONVERGED;
-  hs->ncg += sc->its;
-  double fn = 0.0;
-  for (int q = 0; q < 9; ++q) fn += sc->meanF_new[q] * sc->meanF_new[q];
-  const double ratio = sqrt(sc->dF2max) / sqrt(fn);
-  hs->ratio = ratio;
-  hs->nn += 1;
-  if (hs->nn == 1) {
-    hs->first_ratio2 = hs->first_ratio;
-    hs->first_ratio = ratio;
-    if (hs->rms0 > 0.0 && isfinite(ratio)) {
-      hs->kr2 = hs->kr1;
-      hs->kr1 = ratio / hs->rms0;
+__global__ void k_newton_post(HistState* hs_g, Scalars* sc, cudaGraphConditionalHandle h_cons) {
+  on_shared_state(hs_g, [&](HistState* hs) {
+    int flags = sc->flags;
+    if (hs->f32 && (flags & MF_FLAG_BREAKDOWN) && !(flags & ~MF_FLAG_BREAKDOWN) && sc->its > 1) {
+      sc->flags = 0;
+      flags = 0;
     }
-  }
-  if (st && !hs->status) hs->status = st;
-  const int last = (ratio < hs->tol_newton && !hs->res32) ? 1 : 0;
-  // a step that ends on an FP32 correction applied as computed (no
-  // projection, no deflation), with more steps to come in this launch:
-  // <P> at the final F from the linearisation, <P(F)> + <K:dF>; the error,
-  // of the order of abs(K') abs(dF)^2 with abs(dF) < tol_newton abs(F), is
-  // far below the averages' accuracy.  <K:dF> = sum_k alpha_k <K:p_k>, the
-  // solve's z-passes having added each iteration's term to sc->lin (the
-  // null-frequency coefficient of K:p_k), so no pass over the fields runs
-  // (kind 2: no body).  The last step of a launch evaluates P, so the
-  // fields a caller reads are exact.
-  const bool lin = last && hs->f32 && hs->proj_kind == 0 && hs->defl.m == 0 && hs->k + 1 < hs->nsteps;
-  const int kind = last ? (lin ? 2 : 0) : 1;
-  if (lin) {
-    // the update's averages as they are: the strain-controlled ones differ
-    // from F-bar by the rounding of the FP32 correction's average (far below
-    // 1e-14 of F for a correction below tol_newton); the next step's
-    // predictor, which shifts F by F-bar minus these, removes it
-    for (int c = 0; c < 9; ++c) {
-      sc->meanP[c] += sc->lin[c];
-      sc->meanF[c] = sc->meanF_new[c];
+    int st = flags_to_status(flags);
+    if (!st && !sc->done) st = MF_NOT_CONVERGED;
+    hs->ncg += sc->its;
+    double fn = 0.0;
+    for (int q = 0; q < 9; ++q) fn += sc->meanF_new[q] * sc->meanF_new[q];
+    const double ratio = sqrt(sc->dF2max) / sqrt(fn);
+    hs->ratio = ratio;
+    hs->nn += 1;
+    if (hs->nn == 1) {
+      hs->first_ratio2 = hs->first_ratio;
+      hs->first_ratio = ratio;
+      if (hs->rms0 > 0.0 && isfinite(ratio)) {
+        hs->kr2 = hs->kr1;
+        hs->kr1 = ratio / hs->rms0;
+      }
     }
-  }
-  hs->last = last;
-  hs->res32 = 0;
-  hs->cons_kind = kind;
-  cudaGraphSetConditional(h_cons, (unsigned)kind);
+    if (st && !hs->status) hs->status = st;
+    const int last = (ratio < hs->tol_newton && !hs->res32) ? 1 : 0;
+    // a step that ends on an FP32 correction applied as computed (no
+    // projection, no deflation), with more steps to come in this launch:
+    // <P> at the final F from the linearisation, <P(F)> + <K:dF>; the error,
+    // of the order of abs(K') abs(dF)^2 with abs(dF) < tol_newton abs(F), is
+    // far below the averages' accuracy.  <K:dF> = sum_k alpha_k <K:p_k>, the
+    // solve's z-passes having added each iteration's term to sc->lin (the
+    // null-frequency coefficient of K:p_k), so no pass over the fields runs
+    // (kind 2: no body).  The last step of a launch evaluates P, so the
+    // fields a caller reads are exact.
+    const bool lin = last && hs->f32 && hs->proj_kind == 0 && hs->defl.m == 0 && hs->k + 1 < hs->nsteps;
+    const int kind = last ? (lin ? 2 : 0) : 1;
+    if (lin) {
+      // the update's averages as they are: the strain-controlled ones differ
+      // from F-bar by the rounding of the FP32 correction's average (far below
+      // 1e-14 of F for a correction below tol_newton); the next step's
+      // predictor, which shifts F by F-bar minus these, removes it
+      for (int c = 0; c < 9; ++c) {
+        sc->meanP[c] += sc->lin[c];
+        sc->meanF[c] = sc->meanF_new[c];
+      }
+    }
+    hs->last = last;
+    hs->res32 = 0;
+    hs->cons_kind = kind;
+    cudaGraphSetConditional(h_cons, (unsigned)kind);
+  });
 }
 
 // After the constitutive pass that follows an update: its failures, the
 // launch count of the iteration, and whether another Newton iteration runs.
-__global__ void k_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
+__global__ void k_newton_cond(HistState* hs_g, const Scalars* sc, cudaGraphConditionalHandle h_newton,
                               IterCounts cnt) {
-  const int st = flags_to_status(sc->flags);
-  if (st && !hs->status) hs->status = st;
-  const int its = sc->its;
-  hs->launches += cnt.fixed + cnt.proj[hs->proj_kind] + cnt.cons[hs->cons_kind] +
-                  (long long)cnt.cg_body * (its == 0 ? 1 : (its + 1) / 2);
-  cudaGraphSetConditional(h_newton, (!hs->last && !hs->status) ? 1u : 0u);
+  on_shared_state(hs_g, [&](HistState* hs) {
+    const int st = flags_to_status(sc->flags);
+    if (st && !hs->status) hs->status = st;
+    const int its = sc->its;
+    hs->launches += cnt.fixed + cnt.proj[hs->proj_kind] + cnt.cons[hs->cons_kind] +
+                    (long long)cnt.cg_body * (its == 0 ? 1 : (its + 1) / 2);
+    cudaGraphSetConditional(h_newton, (!hs->last && !hs->status) ? 1u : 0u);
+  });
 }
 
 // End of a load step: record <F>, <P> (Sec. 2.2) and the iteration counts;
 // continue with the next step unless the history failed.
-__global__ void k_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
+__global__ void k_step_end(HistState* hs_g, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
                            int kernels, int kernels_ex) {
-  hs->launches += hs->extrapolated ? kernels_ex : kernels;
-  if (!hs->status) {
-    const int k = hs->k;
-    // the converged step joins the states the predictor extrapolates from
-    // (the quadratic predictor's slots were filled at the step's start)
-    for (int c = 0; c < 9; ++c) {
-      if (hs->extrap != 2) {
-        hs->t2[c] = hs->t1[c];
-        hs->fmean2[c] = hs->fmean1[c];
+  on_shared_state(hs_g, [&](HistState* hs) {
+    hs->launches += hs->extrapolated ? kernels_ex : kernels;
+    if (!hs->status) {
+      const int k = hs->k;
+      // the converged step joins the states the predictor extrapolates from
+      // (the quadratic predictor's slots were filled at the step's start)
+      for (int c = 0; c < 9; ++c) {
+        if (hs->extrap != 2) {
+          hs->t2[c] = hs->t1[c];
+          hs->fmean2[c] = hs->fmean1[c];
+        }
+        hs->t1[c] = hs->target[c];
+        hs->fmean1[c] = sc->meanF[c];
+        hs->mprev[c] = hs->mask[c];
       }
-      hs->t1[c] = hs->target[c];
-      hs->fmean1[c] = sc->meanF[c];
-      hs->mprev[c] = hs->mask[c];
+      hs->nprev = hs->nprev < 3 ? hs->nprev + 1 : 3;
+      hs->nseen += 1;
+      StepOut& row = t.out[k];
+      for (int c = 0; c < 9; ++c) {
+        row.Fbar[c] = sc->meanF[c];
+        row.Pbar[c] = sc->meanP[c];
+      }
+      row.newton = hs->nn;
+      row.cg = hs->ncg;
+      hs->k = k + 1;
     }
-    hs->nprev = hs->nprev < 3 ? hs->nprev + 1 : 3;
-    hs->nseen += 1;
-    StepOut& row = t.out[k];
-    for (int c = 0; c < 9; ++c) {
-      row.Fbar[c] = sc->meanF[c];
-      row.Pbar[c] = sc->meanP[c];
-    }
-    row.newton = hs->nn;
-    row.cg = hs->ncg;
-    hs->k = k + 1;
-  }
-  cudaGraphSetConditional(h_step, (!hs->status && hs->k < hs->nsteps) ? 1u : 0u);
+    cudaGraphSetConditional(h_step, (!hs->status && hs->k < hs->nsteps) ? 1u : 0u);
+  });
 }
 
 // Start of a CG loop inside a history graph: counters reset and the loop's
@@ -561,20 +623,46 @@ __global__ void __launch_bounds__(kThreads) k_cg_init_h(const double* __restrict
   __shared__ double red[kThreads / 32];
   double acc = 0.0;
   float fs = 0.f, fc = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n9;
-       i += (long long)gridDim.x * blockDim.x) {
+  // r = b rounded to FP32, r.r as a Neumaier-compensated FP32 sum of the
+  // exact squares (square and its FMA error)
+  auto put = [&](float v) {
+    const float pr = v * v;
+    const float e = fmaf(v, v, -pr);
+    float t = fs + pr;
+    fc += (fabsf(fs) >= fabsf(pr)) ? ((fs - t) + pr) : ((pr - t) + fs);
+    fs = t;
+    t = fs + e;
+    fc += (fabsf(fs) >= fabsf(e)) ? ((fs - t) + e) : ((e - t) + fs);
+    fs = t;
+  };
+  auto rnd = [](double x) {
+    const dw d = dw_split(x);
+    return __fadd_rn(d.hi, d.lo);
+  };
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, di = (long long)gridDim.x * blockDim.x;
+  long long head = 0;
+  if constexpr (sizeof(T) == 4) {
+    // four elements per step with 16-byte accesses where the buffers allow
+    if ((((uintptr_t)b | (uintptr_t)r) & 15) == 0) {
+      head = n9 & ~3LL;
+      const double2* b2 = reinterpret_cast<const double2*>(b);
+      float4* r4 = reinterpret_cast<float4*>(r);
+      for (long long q = i0; q < head / 4; q += di) {
+        const double2 u = b2[2 * q], w = b2[2 * q + 1];
+        const float4 v = make_float4(rnd(u.x), rnd(u.y), rnd(w.x), rnd(w.y));
+        r4[q] = v;
+        put(v.x);
+        put(v.y);
+        put(v.z);
+        put(v.w);
+      }
+    }
+  }
+  for (long long i = head + i0; i < n9; i += di) {
     if constexpr (sizeof(T) == 4) {
-      const dw d = dw_split(b[i]);
-      const float v = __fadd_rn(d.hi, d.lo);
+      const float v = rnd(b[i]);
       r[i] = v;
-      const float pr = v * v;
-      const float e = fmaf(v, v, -pr);
-      float t = fs + pr;
-      fc += (fabsf(fs) >= fabsf(pr)) ? ((fs - t) + pr) : ((pr - t) + fs);
-      fs = t;
-      t = fs + e;
-      fc += (fabsf(fs) >= fabsf(e)) ? ((fs - t) + e) : ((e - t) + fs);
-      fs = t;
+      put(v);
     } else {
       const T v = (T)b[i];
       r[i] = v;
@@ -738,6 +826,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_update_h(double* __restrict
                                                               const HistState* hs, const Scalars* sc) {
   __shared__ double red[11][kThreads / 32];
   const bool defl = hs->defl.m > 0;
+  if (sizeof(T) == 4 && !defl) return;   // k_newton_update_f32_h
   double acc[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) acc[c] = 0.0;
@@ -809,6 +898,95 @@ __global__ void __launch_bounds__(kThreads) k_newton_update_h(double* __restrict
   }
 }
 
+// The common case of k_newton_update_h on its own: an FP32 correction
+// without deflation (the other kernel returns at once then, and this one
+// otherwise).  Few registers, so that enough voxels' loads are in flight for
+// a pass bound by HBM; same partials.
+// With p0 (the CG directions' buffers) the solve's last lagging update is
+// taken here instead of in x: dF = x + alpha p (the arithmetic of
+// k_axpy_last), or 0 when no CG iteration ran.
+__global__ void __launch_bounds__(kThreads, 3) k_newton_update_f32_h(double* __restrict__ F,
+                                                                     const float* __restrict__ x,
+                                                                     const float* __restrict__ p0,
+                                                                     const float* __restrict__ p1, long long N,
+                                                                     double* __restrict__ partials,
+                                                                     const HistState* hs, const Scalars* sc) {
+  if (hs->defl.m > 0) return;
+  const int its = p0 ? sc->its : -1;
+  const float* __restrict__ p = (its > 0) ? ((its & 1) ? p1 : p0) : nullptr;
+  const float a = p ? (float)sc->alpha : 0.f;
+  __shared__ double red[11][kThreads / 32];
+  float xs[9], xc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) { xs[c] = 0.f; xc[c] = 0.f; }
+  float mx = 0.f;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    float d[9];
+    double f[9];
+    if (its == 0) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) { d[c] = 0.f; f[c] = F[c * N + v]; }
+    } else if (p) {
+      float q[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) { d[c] = x[c * N + v]; q[c] = p[c * N + v]; f[c] = F[c * N + v]; }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) d[c] += a * q[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) { d[c] = x[c * N + v]; f[c] = F[c * N + v]; }
+    }
+    float n2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      F[c * N + v] = f[c] + f32_as_f64(d[c]);
+      const float tt = xs[c] + d[c];
+      xc[c] += (fabsf(xs[c]) >= fabsf(d[c])) ? ((xs[c] - tt) + d[c]) : ((d[c] - tt) + xs[c]);
+      xs[c] = tt;
+      n2 = fmaf(d[c], d[c], n2);
+    }
+    mx = fmaxf(mx, n2);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    double sv = (double)xs[c] + (double)xc[c];
+    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    if (lane == 0) red[c][warp] = sv;
+  }
+  double m = (double)mx;
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) red[9][warp] = m;
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double sv = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) sv += red[threadIdx.x][w];
+    partials[blockIdx.x * 10 + threadIdx.x] = sv;
+  } else if (threadIdx.x == 9) {
+    double mm = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) mm = fmax(mm, red[9][w]);
+    partials[blockIdx.x * 10 + 9] = mm;
+  }
+}
+
+// The solve's last lagging update x += alpha p (k_axpy_last) for an FP32
+// correction that is deflated before the update (k_newton_update_h reads
+// x); without deflation k_newton_update_f32_h takes it on the fly.
+__global__ void k_axpy_last_defl_h(float* __restrict__ x, const float* __restrict__ p0,
+                                   const float* __restrict__ p1, long long n, const HistState* hs,
+                                   const Scalars* sc) {
+  if (hs->defl.m == 0) return;
+  const int its = sc->its;
+  const float* p = (its & 1) ? p1 : p0;
+  const float a = (float)sc->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (its == 0) x[i] = 0.f;
+    else x[i] += a * p[i];
+  }
+}
+
 // Columns 0-8: the new averages; column 9: max abs(dF_v)^2 (grid 10).
 __global__ void __launch_bounds__(kThreads) k_fin_newton_h(const double* __restrict__ partials, int nblk,
                                                            long long N, Scalars* sc) {
@@ -845,7 +1023,7 @@ cudaError_t mf_launch_hist_init(HistState* hs, cudaGraphConditionalHandle h_step
 }
 
 cudaError_t mf_launch_step_begin(HistState* hs, HistTables t, cudaGraphConditionalHandle* h_first, cudaStream_t st) {
-  k_step_begin<<<1, 1, 0, st>>>(hs, t, h_first ? *h_first : cudaGraphConditionalHandle(), h_first ? 1 : 0);
+  k_step_begin<<<1, kCtlThreads, 0, st>>>(hs, t, h_first ? *h_first : cudaGraphConditionalHandle(), h_first ? 1 : 0);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
@@ -860,33 +1038,33 @@ cudaError_t mf_launch_predictor_hist(double* F, double* Fprev, double* Fprev2, l
 
 cudaError_t mf_launch_newton_pre(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_go,
                                  cudaGraphConditionalHandle h_newton, bool first, cudaStream_t st) {
-  k_newton_pre<<<1, 1, 0, st>>>(hs, sc, h_go, h_newton, first ? 1 : 0);
+  k_newton_pre<<<1, kCtlThreads, 0, st>>>(hs, sc, h_go, h_newton, first ? 1 : 0);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t mf_launch_proj_decide(HistState* hs, cudaGraphConditionalHandle h_proj, bool first, cudaStream_t st) {
-  k_proj_decide<<<1, 1, 0, st>>>(hs, h_proj, first ? 1 : 0);
+  k_proj_decide<<<1, kCtlThreads, 0, st>>>(hs, h_proj, first ? 1 : 0);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t mf_launch_newton_post(HistState* hs, Scalars* sc, cudaGraphConditionalHandle h_cons, cudaStream_t st) {
-  k_newton_post<<<1, 1, 0, st>>>(hs, sc, h_cons);
+  k_newton_post<<<1, kCtlThreads, 0, st>>>(hs, sc, h_cons);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t mf_launch_newton_cond(HistState* hs, const Scalars* sc, cudaGraphConditionalHandle h_newton,
                                   IterCounts cnt, cudaStream_t st) {
-  k_newton_cond<<<1, 1, 0, st>>>(hs, sc, h_newton, cnt);
+  k_newton_cond<<<1, kCtlThreads, 0, st>>>(hs, sc, h_newton, cnt);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t mf_launch_step_end(HistState* hs, const Scalars* sc, HistTables t, cudaGraphConditionalHandle h_step,
                                int kernels, int kernels_ex, cudaStream_t st) {
-  k_step_end<<<1, 1, 0, st>>>(hs, sc, t, h_step, kernels, kernels_ex);
+  k_step_end<<<1, kCtlThreads, 0, st>>>(hs, sc, t, h_step, kernels, kernels_ex);
   g_mf_launches += 1;
   return cudaGetLastError();
 }
@@ -916,11 +1094,27 @@ cudaError_t mf_launch_defl_project_hist(void* y, bool f32, bool apply, const dou
 }
 
 cudaError_t mf_launch_newton_update_hist(double* F, const void* x, bool f32, long long N, double* partials,
-                                         int nblk, const HistState* hs, Scalars* sc, cudaStream_t st) {
-  if (f32) k_newton_update_h<float><<<nblk, kThreads, 0, st>>>(F, (const float*)x, N, partials, hs, sc);
-  else k_newton_update_h<double><<<nblk, kThreads, 0, st>>>(F, (const double*)x, N, partials, hs, sc);
+                                         int nblk, const HistState* hs, Scalars* sc, cudaStream_t st,
+                                         const void* p0, const void* p1) {
+  // one wave of the update kernels (at most three blocks per SM resident)
+  nblk = nblk < 3 * 152 ? nblk : 3 * 152;
+  if (f32) {
+    k_newton_update_h<float><<<nblk, kThreads, 0, st>>>(F, (const float*)x, N, partials, hs, sc);
+    k_newton_update_f32_h<<<nblk, kThreads, 0, st>>>(F, (const float*)x, (const float*)p0, (const float*)p1, N,
+                                                    partials, hs, sc);
+    g_mf_launches += 1;
+  } else {
+    k_newton_update_h<double><<<nblk, kThreads, 0, st>>>(F, (const double*)x, N, partials, hs, sc);
+  }
   k_fin_newton_h<<<10, kThreads, 0, st>>>(partials, nblk, N, sc);
   g_mf_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t mf_launch_axpy_last_defl_hist(float* x, const float* p0, const float* p1, long long n,
+                                          const HistState* hs, const Scalars* sc, cudaStream_t st) {
+  k_axpy_last_defl_h<<<grid_for(n), kThreads, 0, st>>>(x, p0, p1, n, hs, sc);
+  g_mf_launches += 1;
   return cudaGetLastError();
 }
 

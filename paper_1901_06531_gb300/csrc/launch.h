@@ -321,9 +321,16 @@ cudaError_t mf_launch_cg_start_hist(Scalars* sc, int max_its, cudaGraphCondition
 cudaError_t mf_launch_defl_project_hist(void* y, bool f32, bool apply, const double* F, long long N,
                                         const HistState* hs, double* partials, int nblk, Scalars* sc,
                                         cudaStream_t st);
-// Newton update; the null-rotation correction is subtracted when hs->defl.m > 0
+// Newton update; the null-rotation correction is subtracted when hs->defl.m > 0.
+// p0, p1 (FP32, the CG directions' buffers): x still lacks the solve's last
+// lagging update alpha p, which the update adds on the fly when nothing is
+// deflated; mf_launch_axpy_last_defl_hist, launched before the deflation,
+// applies it to x otherwise.
 cudaError_t mf_launch_newton_update_hist(double* F, const void* x, bool f32, long long N, double* partials,
-                                         int nblk, const HistState* hs, Scalars* sc, cudaStream_t st);
+                                         int nblk, const HistState* hs, Scalars* sc, cudaStream_t st,
+                                         const void* p0 = nullptr, const void* p1 = nullptr);
+cudaError_t mf_launch_axpy_last_defl_hist(float* x, const float* p0, const float* p1, long long n,
+                                          const HistState* hs, const Scalars* sc, cudaStream_t st);
 
 // adjoint.cu: adjoint sensitivity at a converged state (neo-Hookean parameters)
 struct AdjWeights {

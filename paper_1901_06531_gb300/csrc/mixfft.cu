@@ -20,6 +20,29 @@
 
 namespace {
 
+// Phase timestamps of a load history (trace build, -DMF_TRACE): a one-thread
+// kernel between the graph's phases records the device's global timer and
+// the phase id (ids in include/mixfft.h, mf_trace_read); the release build
+// launches nothing.
+#ifdef MF_TRACE
+constexpr int kTraceCap = 65536;
+__device__ unsigned long long g_trace_t[kTraceCap];
+__device__ int g_trace_id[kTraceCap];
+__device__ int g_trace_n;
+__global__ void k_trace_mark(int id) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  const int i = atomicAdd(&g_trace_n, 1);
+  if (i < kTraceCap) {
+    g_trace_t[i] = t;
+    g_trace_id[i] = id;
+  }
+}
+void trace_mark(cudaStream_t s, int id) { k_trace_mark<<<1, 1, 0, s>>>(id); }
+#else
+void trace_mark(cudaStream_t, int) {}
+#endif
+
 constexpr int kMaxPhases = 65536;
 constexpr int kPointwiseBlocks = 152 * 8;
 
@@ -892,6 +915,7 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   memset(&cnt, 0, sizeof(cnt));
   cudaGraphConditionalHandle h_go;
   cudaError_t e = cap_handle(s, &h_go);
+  trace_mark(s, MF_TRACE_ITER_START);
   if (e == cudaSuccess) e = mf_launch_newton_pre(hs, sc, h_go, h_newton, first, s);
   cudaGraph_t go_body = nullptr;
   if (e == cudaSuccess) e = cap_conditional(s, h_go, cudaGraphCondTypeIf, 1, &go_body);
@@ -900,8 +924,10 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   if (e != cudaSuccess) return e;
   // FP32 inner solves: the null rotations out of the right-hand side
   if (f32) e = mf_launch_defl_project_hist(b, false, true, F, N, hs, part, c->pw_blocks, sc, s1);
+  trace_mark(s1, MF_TRACE_NEWTON_PRE);
   if (e == cudaSuccess)
     e = mf_launch_cg_init_hist(b, c->ws + c->or_, f32, 9 * N, part, c->pw_blocks, N, hs, sc, s1);
+  trace_mark(s1, MF_TRACE_CG_INIT);
   cudaGraphConditionalHandle h_cg;
   if (e == cudaSuccess) e = cap_handle(s1, &h_cg);
   if (e == cudaSuccess) e = mf_launch_cg_start_hist(sc, max_cg, h_cg, s1);
@@ -913,7 +939,10 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
     in_bodies += g_mf_launches - lb;
     cnt.cg_body = c->cg_body_kernels;
   }
-  if (e == cudaSuccess)
+  trace_mark(s1, MF_TRACE_CG_LOOP);
+  // the solve's last lagging update x += alpha p: FP64 here; FP32 in each
+  // branch below (the unprojected correction takes it inside the update)
+  if (e == cudaSuccess && !f32)
     e = mf_launch_axpy_last(c->ws + c->ox, c->ws + c->op, c->ws + c->op2, f32, 9 * N, sc, s1);
   if (e == cudaSuccess && f32) {
     // projection of the FP32 correction onto the range of G* (its rounding
@@ -929,7 +958,11 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
       if (e != cudaSuccess) break;
       void* corr = c->ws + c->ox;
       bool corr32 = true;
-      if (kind == 1) {
+      if (kind == 0) e = mf_launch_axpy_last_defl_hist(c->at<float>(c->ox), c->at<float>(c->op), c->at<float>(c->op2),
+                                                      9 * N, hs, sc, s2);
+      else e = mf_launch_axpy_last(c->ws + c->ox, c->ws + c->op, c->ws + c->op2, true, 9 * N, sc, s2);
+      if (e != cudaSuccess) {
+      } else if (kind == 1) {
         const ZArgs za = z_args(c, true, mask, 1.0 / (double)N);
         e = mf_launch_project(true, c->ws + c->ox, c->ws + c->ospec, c->ws + c->op2, 0, nullptr, xy_args(c, true), za,
                               nullptr, s2);
@@ -951,9 +984,14 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
         corr = b;
         corr32 = false;
       }
+      trace_mark(s2, MF_TRACE_PROJECTION);
       if (e == cudaSuccess)
         e = mf_launch_defl_project_hist(corr, corr32, false, F, N, hs, part, c->pw_blocks, sc, s2);
-      if (e == cudaSuccess) e = mf_launch_newton_update_hist(F, corr, corr32, N, part, c->pw_blocks, hs, sc, s2);
+      trace_mark(s2, MF_TRACE_DEFLATION);
+      if (e == cudaSuccess)
+        e = mf_launch_newton_update_hist(F, corr, corr32, N, part, c->pw_blocks, hs, sc, s2,
+                                         kind == 0 ? c->ws + c->op : nullptr, kind == 0 ? c->ws + c->op2 : nullptr);
+      trace_mark(s2, MF_TRACE_UPDATE);
       e = cap_end(s2, e);
       cnt.proj[kind] = (int)(g_mf_launches - lb);
       in_bodies += g_mf_launches - lb;
@@ -967,6 +1005,7 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   cudaGraphConditionalHandle h_cons;
   if (e == cudaSuccess) e = cap_handle(s1, &h_cons);
   if (e == cudaSuccess) e = mf_launch_newton_post(hs, sc, h_cons, s1);
+  trace_mark(s1, MF_TRACE_NEWTON_POST);
   // (FP32 inner) 2: the step ends, its averages from the linearisation,
   // which k_newton_post takes from the sums the solve's z-passes kept (no
   // body: the switch runs none for a value past its last body)
@@ -984,8 +1023,11 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
     // averages k_newton_post records)
     int st = 0;
     if (f32 && mf_launch_predictor_hist(F, nullptr, nullptr, N, hs, sc, true, s2) != cudaSuccess) st = MF_CUDA_ERROR;
+    trace_mark(s2, MF_TRACE_FBAR);
     if (!st) st = run_constitutive(c, more && !f32, more && f32, more && f32, false, s2);
+    trace_mark(s2, MF_TRACE_CONSTITUTIVE);
     if (!st && more && capture_residual(c, mask, false, s2) != cudaSuccess) st = MF_CUDA_ERROR;
+    trace_mark(s2, MF_TRACE_RESIDUAL);
     e = cap_end(s2, st ? cudaErrorUnknown : cudaSuccess);
     cnt.cons[kind] = (int)(g_mf_launches - lb);
     in_bodies += g_mf_launches - lb;
@@ -993,6 +1035,7 @@ cudaError_t capture_iteration(mf_ctx* c, cudaStream_t* caps, int lvl, bool first
   // the kernels outside the bodies, including the condition kernel below
   cnt.fixed = (int)(g_mf_launches - l0 - in_bodies) + 1;
   if (!f32) cnt.proj[1] = cnt.proj[2] = 0;
+  trace_mark(s1, MF_TRACE_CONS_SWITCH);
   if (e == cudaSuccess) e = mf_launch_newton_cond(hs, sc, h_newton, cnt, s1);
   return cap_end(s1, e);
 }
@@ -1035,7 +1078,9 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
       cudaGraphConditionalHandle h_first;
       const bool choose = extrap && dwr;
       if (choose) e = cap_handle(caps[1], &h_first);
+      trace_mark(caps[1], MF_TRACE_STEP_START);
       if (e == cudaSuccess) e = mf_launch_step_begin(hs, t, choose ? &h_first : nullptr, caps[1]);
+      trace_mark(caps[1], MF_TRACE_STEP_BEGIN);
       // the predictor: in the double-word constitutive pass that follows
       // (FP32 inner with a double-word outer level), else a pass of its own
       double* Fprev = extrap ? c->at<double>(c->oFprev) : nullptr;
@@ -1048,7 +1093,9 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
       int step_kernels = 0, step_kernels_ex = 0;
       auto first_pass = [&](bool res32, cudaStream_t st) {
         int r = run_constitutive(c, !f32, f32, f32, res32, st, fuse_pred ? &pred : nullptr);
+        trace_mark(st, MF_TRACE_FIRST_CONSTITUTIVE);
         if (!r && capture_residual(c, mask, res32, st) != cudaSuccess) r = MF_CUDA_ERROR;
+        trace_mark(st, MF_TRACE_FIRST_RESIDUAL);
         return r ? cudaErrorUnknown : cudaSuccess;
       };
       if (e == cudaSuccess && !choose) {
@@ -1074,7 +1121,9 @@ cudaError_t build_history(mf_ctx* c, cudaGraph_t G, const uint8_t* mask, int max
         e = cap_begin(caps[2], B2);
         if (e == cudaSuccess) e = cap_end(caps[2], capture_iteration(c, caps, 2, false, mask, max_cg, h_newton));
       }
+      trace_mark(caps[1], MF_TRACE_NEWTON_LOOP);
       if (e == cudaSuccess) e = mf_launch_step_end(hs, sc, t, h_step, step_kernels, step_kernels_ex, caps[1]);
+      trace_mark(caps[1], MF_TRACE_STEP_END);
       e = cap_end(caps[1], e);
     }
   }
@@ -1993,6 +2042,27 @@ int mf_set_outer_arith(mf_ctx* c, int arith) {
 }
 
 long long mf_kernel_launches(void) { return g_mf_launches; }
+
+int mf_trace_read(int cap, unsigned long long* t_ns, int* ids, int* n_out) {
+#ifdef MF_TRACE
+  if (cap < 0 || !n_out || (cap > 0 && (!t_ns || !ids))) return MF_INVALID_ARG;
+  int n = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MF_CUDA_ERROR;
+  if (cudaMemcpyFromSymbol(&n, g_trace_n, sizeof(int)) != cudaSuccess) return MF_CUDA_ERROR;
+  const int k = n < kTraceCap ? (n < cap ? n : cap) : (kTraceCap < cap ? kTraceCap : cap);
+  if (k > 0 && (cudaMemcpyFromSymbol(t_ns, g_trace_t, sizeof(unsigned long long) * k) != cudaSuccess ||
+                cudaMemcpyFromSymbol(ids, g_trace_id, sizeof(int) * k) != cudaSuccess))
+    return MF_CUDA_ERROR;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_trace_n, &zero, sizeof(int)) != cudaSuccess) return MF_CUDA_ERROR;
+  *n_out = n;
+  return MF_OK;
+#else
+  (void)cap; (void)t_ns; (void)ids;
+  if (n_out) *n_out = 0;
+  return MF_INVALID_ARG;
+#endif
+}
 
 int mf_debug_report(long long* count_out, int* line_out, long long* index_out, long long* extent_out) {
   if (!count_out) return MF_INVALID_ARG;

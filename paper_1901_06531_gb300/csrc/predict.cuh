@@ -51,19 +51,3 @@ __device__ __forceinline__ PredCoef pred_coef(const PredArgs& pa, const Scalars*
   }
   return k;
 }
-
-// Predict component c at voxel v from its current value f (also kept in its
-// slot); returns the new value, which the caller stores in F.  K: PredCoef,
-// or a volatile one in shared memory (read at each use, so that a
-// register-heavy caller does not keep the coefficients in registers).
-template <typename K>
-__device__ __forceinline__ double pred_apply(const PredArgs& pa, K& k, int c, long long N, long long v, double f) {
-  double fn = f;
-  const double v1 = k.v1, v2 = k.v2;
-  const int dst = k.dst;
-  if (v1 != 0.0) fn += v1 * (pa.A[c * N + v] - f);
-  if (v2 != 0.0) fn += v2 * (pa.B[c * N + v] - f);
-  if (dst == 0) pa.A[c * N + v] = f;
-  else if (dst == 1) pa.B[c * N + v] = f;
-  return fn + k.sh[c];
-}

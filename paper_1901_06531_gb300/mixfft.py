@@ -13,9 +13,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# MF_LIBRARY=debug selects the bounds-checking build (build.build(debug=True))
-LIB_PATH = os.path.join(_HERE, "libmixfft_debug.so" if os.environ.get("MF_LIBRARY") == "debug"
-                        else "libmixfft.so")
+# MF_LIBRARY=debug selects the bounds-checking build (build.build(debug=True)),
+# MF_LIBRARY=trace the phase-timestamp build (build.build(trace=True))
+LIB_PATH = os.path.join(_HERE, {"debug": "libmixfft_debug.so", "trace": "libmixfft_trace.so"}.get(
+    os.environ.get("MF_LIBRARY", ""), "libmixfft.so"))
 
 MF_OK, MF_INVALID_ARG, MF_NOT_CONVERGED, MF_CG_BREAKDOWN = 0, 1, 2, 3
 MF_NONPOSITIVE_J, MF_CUDA_ERROR, MF_DEVICE_TIMEOUT, MF_NO_WORKSPACE = 4, 5, 6, 7
@@ -25,6 +26,11 @@ MF_NEOHOOKE, MF_SVK_CUBIC = 0, 1
 MF_OUTER_DOUBLE_WORD, MF_OUTER_FP64 = 0, 1
 MF_PROJ_FP32, MF_PROJ_OUTER, MF_PROJ_AUTO = 0, 1, 2
 MF_PRED_UNIFORM, MF_PRED_EXTRAPOLATE, MF_PRED_QUADRATIC = 0, 1, 2
+MF_TRACE_STEP_START, MF_TRACE_STEP_BEGIN, MF_TRACE_FIRST_CONSTITUTIVE, MF_TRACE_FIRST_RESIDUAL = 1, 2, 3, 4
+MF_TRACE_ITER_START, MF_TRACE_NEWTON_PRE, MF_TRACE_CG_INIT, MF_TRACE_CG_LOOP = 10, 11, 12, 13
+MF_TRACE_PROJECTION, MF_TRACE_DEFLATION, MF_TRACE_UPDATE, MF_TRACE_NEWTON_POST = 14, 15, 16, 17
+MF_TRACE_FBAR, MF_TRACE_CONSTITUTIVE, MF_TRACE_RESIDUAL, MF_TRACE_CONS_SWITCH = 18, 19, 20, 21
+MF_TRACE_NEWTON_LOOP, MF_TRACE_STEP_END = 30, 31
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run paper_1901_06531_gb300.build.build() first")
@@ -68,6 +74,7 @@ _lib.mf_set_predictor.argtypes = [_vp, _i]
 _lib.mf_probe_fma.argtypes = [_i, _vp]
 _lib.mf_debug_report.argtypes = [_vp, _vp, _vp, _vp]
 _lib.mf_debug_selftest.argtypes = []
+_lib.mf_trace_read.argtypes = [_i, _vp, _vp, _vp]
 _lib.mf_set_xy_split.argtypes = [_vp, _i]
 _lib.mf_set_xy_persistent.argtypes = [_vp, _i]
 _lib.mf_set_xy_cluster.argtypes = [_vp, _i]
@@ -88,7 +95,7 @@ EXPORTED = ["mf_create", "mf_workspace_bytes", "mf_bind_workspace", "mf_set_mate
             "mf_time_kernels", "mf_cufft_workspace_bytes", "mf_cufft_bind", "mf_matvec_cufft",
             "mf_time_cufft", "mf_kernel_launches", "mf_sync", "mf_autotune", "mf_adjoint",
             "mf_set_outer_arith", "mf_set_xy_split", "mf_set_xy_persistent", "mf_set_xy_cluster", "mf_xy_schedule", "mf_set_projection_arith",
-            "mf_set_inexact_newton", "mf_set_predictor", "mf_probe_fma", "mf_debug_report", "mf_debug_selftest", "mf_selftest_wait_timeout", "mf_last_cuda_error",
+            "mf_set_inexact_newton", "mf_set_predictor", "mf_probe_fma", "mf_debug_report", "mf_debug_selftest", "mf_trace_read", "mf_selftest_wait_timeout", "mf_last_cuda_error",
             "mf_status_string", "mf_destroy"]
 
 
@@ -115,6 +122,21 @@ def debug_selftest():
     """mf_debug_selftest: status (MF_OK in a debug build, MF_INVALID_ARG in a
     release build)."""
     return int(_lib.mf_debug_selftest())
+
+
+# phase ids of mf_trace_read (include/mixfft.h, mf_trace_phase)
+TRACE_PHASES = {v: k[len("MF_TRACE_"):].lower() for k, v in dict(globals()).items() if k.startswith("MF_TRACE_")}
+
+
+def trace_read(cap=65536):
+    """mf_trace_read: (timestamps in ns, phase ids) recorded since the last
+    call by a trace build (MF_LIBRARY=trace); raises in a release build."""
+    t = np.zeros(cap, dtype=np.uint64)
+    ids = np.zeros(cap, dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check("mf_trace_read", _lib.mf_trace_read(cap, _ptr(t), _ptr(ids), ctypes.byref(n)))
+    k = min(n.value, cap)
+    return t[:k].copy(), ids[:k].copy()
 
 
 def kernel_launches():

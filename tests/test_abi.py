@@ -140,3 +140,11 @@ def test_wait_selftest_validates_its_bound_without_gpu(lib):
     lib.mf_selftest_wait_timeout.argtypes = [ctypes.c_int]
     assert lib.mf_selftest_wait_timeout(0) == 1
     assert lib.mf_selftest_wait_timeout((1 << 20) + 1) == 1
+
+
+def test_release_build_has_no_trace_without_gpu(lib):
+    lib.mf_trace_read.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    n = ctypes.c_int(5)
+    assert lib.mf_trace_read(0, None, None, ctypes.byref(n)) == 1 and n.value == 0
+    from paper_1901_06531_gb300 import mixfft
+    assert mixfft.TRACE_PHASES[mixfft.MF_TRACE_CG_LOOP] == "cg_loop" and len(mixfft.TRACE_PHASES) == 18
