@@ -388,27 +388,53 @@ __global__ void k_predictor_hist(double* __restrict__ F, PredArgs pa, long long 
     }
     return;
   }
-  const PredCoef k = pred_coef(pa, sc);
+  // a flat pass over the 9N values, two per step (16-byte accesses where N
+  // is even; a pair never spans two components then), the coefficients in
+  // shared memory; the form of predict.cuh
+  __shared__ double sh[9];
+  __shared__ double w12[2];
+  __shared__ int dsts;
+  if (threadIdx.x == 0) {
+    const PredCoef k = pred_coef(pa, sc);
+    for (int c = 0; c < 9; ++c) sh[c] = k.sh[c];
+    w12[0] = k.v1;
+    w12[1] = k.v2;
+    dsts = k.dst;
+  }
+  __syncthreads();
+  const double v1 = w12[0], v2 = w12[1];
+  const int dst = dsts;
   double* __restrict__ A = pa.A;
   double* __restrict__ B = pa.B;
-  for (long long v = v0; v < N; v += dv) {
-    // every load of the voxel issued before any store (F and the slots are
-    // distinct fields), then the form of predict.cuh
-    double f[9], fa[9], fb[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      f[c] = F[c * N + v];
-      fa[c] = k.v1 != 0.0 ? A[c * N + v] : 0.0;
-      fb[c] = k.v2 != 0.0 ? B[c * N + v] : 0.0;
+  auto one = [&](double f, double a, double b, int c) {
+    double fn = f;
+    if (v1 != 0.0) fn += v1 * (a - f);
+    if (v2 != 0.0) fn += v2 * (b - f);
+    return fn + sh[c];
+  };
+  const long long n9 = 9 * N;
+  if ((N & 1) == 0) {
+    double2* __restrict__ F2 = reinterpret_cast<double2*>(F);
+    double2* __restrict__ A2 = reinterpret_cast<double2*>(A);
+    double2* __restrict__ B2 = reinterpret_cast<double2*>(B);
+    for (long long q = v0; q < n9 / 2; q += dv) {
+      const int c = (int)((2 * q) / N);
+      const double2 f = F2[q];
+      const double2 a = v1 != 0.0 ? A2[q] : make_double2(0.0, 0.0);
+      const double2 b = v2 != 0.0 ? B2[q] : make_double2(0.0, 0.0);
+      if (dst == 0) A2[q] = f;
+      else if (dst == 1) B2[q] = f;
+      F2[q] = make_double2(one(f.x, a.x, b.x, c), one(f.y, a.y, b.y, c));
     }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      double fn = f[c];
-      if (k.v1 != 0.0) fn += k.v1 * (fa[c] - f[c]);
-      if (k.v2 != 0.0) fn += k.v2 * (fb[c] - f[c]);
-      if (k.dst == 0) A[c * N + v] = f[c];
-      else if (k.dst == 1) B[c * N + v] = f[c];
-      F[c * N + v] = fn + k.sh[c];
+  } else {
+    for (long long i = v0; i < n9; i += dv) {
+      const int c = (int)(i / N);
+      const double f = F[i];
+      const double a = v1 != 0.0 ? A[i] : 0.0;
+      const double b = v2 != 0.0 ? B[i] : 0.0;
+      if (dst == 0) A[i] = f;
+      else if (dst == 1) B[i] = f;
+      F[i] = one(f, a, b, c);
     }
   }
 }
