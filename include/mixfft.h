@@ -113,7 +113,12 @@ int mf_set_F(mf_ctx* ctx, const double* F_host);
  *           its first residual in the outer arithmetic and cg_rel; an
  *           iteration whose predecessor's correction was below
  *           sqrt(tol_newton) (expected to be the last) uses sqrt(cg_rel);
- *   Fbar_out, Pbar_out: host, nsteps*9 doubles or NULL: <F>, <P> per step;
+ *   Fbar_out, Pbar_out: host, nsteps*9 doubles or NULL: <F>, <P> per step
+ *           (FP32-inner contexts: a step other than the launch's last that
+ *           ends on a correction applied as computed reports <P> from the
+ *           linearisation <P(F)> + <K:dF>, a remainder of order
+ *           abs(K') abs(dF)^2, and <F> as updated; the last step of a
+ *           launch evaluates P at its final F);
  *   iters_out: host, nsteps*2 int32 or NULL: Newton iterations and total CG
  *              iterations per step.
  * The run continues from the current F (identity after mf_set_material).

@@ -28,6 +28,12 @@ int grid_for(long long n) {
   if (g > 4096) g = 4096;
   return (int)g;
 }
+// grid-stride passes that usually return at once (they act only when a
+// rigid rotation is null): four blocks per SM at most
+int rare_grid(long long n) {
+  const int g = grid_for(n);
+  return g < 4 * 152 ? g : 4 * 152;
+}
 
 // ------------------------------------------------------------ null rotations
 // Cyclic Jacobi eigen-decomposition of a symmetric m x m matrix (m <= 3): on
@@ -1112,8 +1118,10 @@ cudaError_t mf_launch_defl_project_hist(void* y, bool f32, bool apply, const dou
   k_defl_fin_h<<<1, kThreads, 0, st>>>(partials, nblk, hs, sc);
   g_mf_launches += 2;
   if (apply) {
-    if (f32) k_defl_apply_h<float><<<grid_for(N), kThreads, 0, st>>>((float*)y, F, N, hs, sc);
-    else k_defl_apply_h<double><<<grid_for(N), kThreads, 0, st>>>((double*)y, F, N, hs, sc);
+    // a grid of a few blocks per SM: the pass usually returns at once (no
+    // null rotation), and launching a full grid of empty blocks costs time
+    if (f32) k_defl_apply_h<float><<<rare_grid(N), kThreads, 0, st>>>((float*)y, F, N, hs, sc);
+    else k_defl_apply_h<double><<<rare_grid(N), kThreads, 0, st>>>((double*)y, F, N, hs, sc);
     g_mf_launches += 1;
   }
   return cudaGetLastError();
@@ -1139,7 +1147,7 @@ cudaError_t mf_launch_newton_update_hist(double* F, const void* x, bool f32, lon
 
 cudaError_t mf_launch_axpy_last_defl_hist(float* x, const float* p0, const float* p1, long long n,
                                           const HistState* hs, const Scalars* sc, cudaStream_t st) {
-  k_axpy_last_defl_h<<<grid_for(n), kThreads, 0, st>>>(x, p0, p1, n, hs, sc);
+  k_axpy_last_defl_h<<<rare_grid(n), kThreads, 0, st>>>(x, p0, p1, n, hs, sc);
   g_mf_launches += 1;
   return cudaGetLastError();
 }

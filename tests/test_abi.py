@@ -148,3 +148,21 @@ def test_release_build_has_no_trace_without_gpu(lib):
     assert lib.mf_trace_read(0, None, None, ctypes.byref(n)) == 1 and n.value == 0
     from paper_1901_06531_gb300 import mixfft
     assert mixfft.TRACE_PHASES[mixfft.MF_TRACE_CG_LOOP] == "cg_loop" and len(mixfft.TRACE_PHASES) == 18
+
+
+def test_phase_composition_of_synthetic_marks():
+    """bench.phase_composition: a phase lasts from the mark before it to its
+    own; steps split at the step-start marks; the first steps skipped."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    names = {1: "step_start", 2: "a", 3: "b"}
+    # two steps: marks at t (ns) = step 0: 0, 1000 (a), 4000 (b); step 1:
+    # 5000, 7000 (a), 13000 (b)
+    t = [0, 1000, 4000, 5000, 7000, 13000]
+    ids = [1, 2, 3, 1, 2, 3]
+    comp, totals = bench.phase_composition(t, ids, names, skip_steps=0)
+    assert totals == [5.0, 8.0]
+    assert comp == {"b": 4.5, "a": 1.5}
+    comp1, _ = bench.phase_composition(t, ids, names, skip_steps=1)
+    assert comp1 == {"b": 6.0, "a": 2.0}
